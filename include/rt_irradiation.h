@@ -1,0 +1,194 @@
+/*
+ * rt_irradiation.h -- C ABI of the GB300 (sm_103a) frequency-dependent
+ * first-order stellar irradiation ray tracer.
+ *
+ * The library computes, for a central star irradiating a spherical (r, theta, phi)
+ * grid along radial rays, the absorbed stellar power per unit volume q_abs and the
+ * radial radiative acceleration a_rad of every cell, following Kuiper et al. (2010):
+ *   Sect. 2.2, Eqs. 17-19   F(r) = F(R_s) (R_s/r)^2 exp(-tau(r)), tau = int kappa rho dr,
+ *                           tau = 0 at the inner grid radius;
+ *   Sect. 2.3, Eq. 20       a fixed set of frequency bins, each with its own opacity
+ *                           kappa(nu_i) and its own Planck-band stellar flux;
+ *   Sect. 3.3.4, Eqs. 27-36 cell-integrated absorption F_in (1 - exp(-dtau)) in the
+ *                           cancellation-free expm1 form; the geometric dilution does
+ *                           not contribute (Eq. 36);
+ *   Sect. 5                 a_rad = -div(F_s) / (rho c), radial.
+ * Dust above the sublimation temperature t_sub has no opacity (Sect. 2: evaporated
+ * dust leaves an optically thin region).
+ *
+ * Conventions
+ *  - Units are cgs: cm, g, s, K, Hz; q_abs in erg s^-1 cm^-3; a_rad in cm s^-2.
+ *  - Fields are float32 arrays of nphi * ntheta * nr elements in the layout
+ *    [nphi][ntheta][nr], r fastest (one radial ray is one contiguous run of nr).
+ *  - "device" pointers are CUDA global-memory addresses on the current device
+ *    (e.g. torch.Tensor.data_ptr()); "host" pointers are CPU addresses.
+ *  - Every call returns RT_OK (0) or a negative RT_ERR_* status; no C++ exception
+ *    crosses this interface. rt_last_error() gives the text of the last failure of
+ *    a context, rt_status_string() the name of a status.
+ *  - Work is enqueued asynchronously on the context's CUDA stream. A call that
+ *    returns results to the host (energy, host-buffer variants) synchronises that
+ *    stream before it returns.
+ *  - The caller owns every field buffer; the library owns the context, the
+ *    per-grid tables and every scratch buffer it allocates.
+ *  - A context must not be used from two host threads at once.
+ */
+#ifndef RT_IRRADIATION_H
+#define RT_IRRADIATION_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define RT_OK                   0
+#define RT_ERR_INVALID_ARG     (-1)  /* bad size, pointer, non-monotone grid, ...    */
+#define RT_ERR_NOT_CONFIGURED  (-2)  /* star or opacity table not set yet            */
+#define RT_ERR_CUDA            (-3)  /* a CUDA runtime call failed (see last_error)  */
+#define RT_ERR_TIMEOUT         (-4)  /* a bounded device wait gave up                */
+#define RT_ERR_NONFINITE_INPUT (-5)  /* NaN/Inf/negative density or NaN temperature  */
+#define RT_ERR_NO_MEMORY       (-6)  /* host or device allocation failed             */
+
+/* ---- precision of the optical-depth scan and of the per-bin arithmetic --- */
+#define RT_FP32_KAHAN 0  /* FP32 bins; column density scanned in compensated
+                            (double-float) FP32 and carried across tiles in the
+                            same form. The default. */
+#define RT_FP32_PLAIN 1  /* FP32 bins; plain FP32 running sum (precision study) */
+#define RT_FP64       2  /* FP64 scan and FP64 per-bin arithmetic (libm-grade exp
+                            and expm1); outputs still rounded to float32 */
+
+#define RT_MAX_NU 128    /* largest number of frequency bins per table */
+
+typedef struct rt_ctx rt_ctx;
+
+/* Grid description. All arrays are copied by rt_create; the caller may free them. */
+typedef struct rt_grid_desc {
+    int nr, ntheta, nphi;   /* cells per direction, each >= 1                      */
+    const double *r_if;     /* [nr+1] radial interfaces, strictly increasing, r_if[0] > 0 */
+    const double *theta_if; /* [ntheta+1] polar interfaces in [0, pi], strictly increasing */
+    const double *phi_if;   /* [nphi+1] azimuthal interfaces, strictly increasing;
+                               with nphi == 1 the span may be 2 pi (axisymmetric)   */
+    int precision;          /* RT_FP32_KAHAN, RT_FP32_PLAIN or RT_FP64              */
+} rt_grid_desc;
+
+/* Energy bookkeeping of one rt_irradiate call (Eqs. 33-35: the flux difference
+ * telescopes along a ray, so absorbed + escaped = emitted). */
+typedef struct rt_energy {
+    double e_abs;   /* sum over cells of q_abs * V (erg/s), from the kernel's own sums */
+    double e_esc;   /* power leaving the outer radial boundary (erg/s)                */
+    double l_star;  /* R_s^2 sigma T_s^4 sum_j dOmega_j: the stellar luminosity into the
+                       grid's solid angle (= 4 pi R_s^2 sigma T_s^4 on the full sphere)  */
+    double rel_err; /* (e_abs + e_esc) / l_star - 1                                  */
+} rt_energy;
+
+/* rt_create -- allocate a context for one grid (geometry of Sect. 2.2: radial rays
+ * along the r axis of a spherical grid; one ray per (theta, phi) column).
+ *   g            grid description (copied).
+ *   cuda_stream  cudaStream_t to enqueue work on; NULL = the legacy default stream.
+ *   out          receives the new context; *out is NULL on failure.
+ * Errors: RT_ERR_INVALID_ARG (sizes < 1, non-increasing or non-positive radii,
+ * theta outside [0, pi], unknown precision), RT_ERR_CUDA, RT_ERR_NO_MEMORY. */
+int rt_create(const rt_grid_desc *g, void *cuda_stream, rt_ctx **out);
+
+/* rt_set_stream -- change the CUDA stream later calls enqueue on. */
+int rt_set_stream(rt_ctx *ctx, void *cuda_stream);
+
+/* rt_set_opacity_table -- the frequency bins of Sect. 2.3.
+ *   n_nu        1..RT_MAX_NU bins.
+ *   nu_mid      [n_nu] host, bin mid-frequencies (Hz), strictly increasing, > 0. Bin
+ *               edges are the arithmetic midpoints (nu_{i-1}+nu_i)/2 of Eq. 20; the
+ *               first bin starts at 0 Hz and the last ends at infinity.
+ *   kappa       [n_nu] host, absorption opacity per bin (cm^2 g^-1), finite, >= 0.
+ *   t_sub       dust sublimation temperature (K): a cell with t_dust > t_sub has
+ *               zero opacity in every bin; t_dust == t_sub keeps its dust.
+ *   kappa_bf16  non-zero: round each kappa to bfloat16 before use (precision study).
+ * The Planck-band fluxes are (re)computed on the device once the star is also set.
+ * Errors: RT_ERR_INVALID_ARG, RT_ERR_CUDA. */
+int rt_set_opacity_table(rt_ctx *ctx, int n_nu, const double *nu_mid, const double *kappa,
+                         double t_sub, int kappa_bf16);
+
+/* rt_set_star -- the central black-body star (Eqs. 18 and 20).
+ *   t_star  effective temperature (K), > 0;  r_star  radius (cm), > 0.
+ * Bin fluxes F_i = pi * int B_nu(T_s) dnu over each bin (sum_i F_i = sigma T_s^4) are
+ * computed on the device in FP64. Errors: RT_ERR_INVALID_ARG, RT_ERR_CUDA. */
+int rt_set_star(rt_ctx *ctx, double t_star, double r_star);
+
+/* rt_irradiate -- trace every ray of the grid (Eqs. 17-20, 27-36).
+ *   rho       device [nphi][ntheta][nr] gas density (g cm^-3), >= 0 and finite.
+ *   t_dust    device, same layout, dust temperature (K).
+ *   q_abs     device, same layout, caller-allocated: absorbed stellar power per
+ *             volume (erg s^-1 cm^-3), i.e. -div(F_s), the source term of Eq. 15.
+ *   a_rad     device, same layout, caller-allocated: radial radiative acceleration
+ *             (cm s^-2) = q_abs / (rho c) for rho > 0, and its rho -> 0 limit
+ *             sum_i kappa_i F_i,in / c (cell-averaged) where rho == 0; 0 where the
+ *             dust is sublimated.
+ *   energy    NULL, or a host struct to receive the call's energy sums; when given
+ *             the call synchronises the stream.
+ * q_abs and a_rad are fully overwritten; inputs are only read. Input and output
+ * buffers must not overlap. Invalid input values (NaN/Inf/negative rho, NaN t_dust)
+ * are flagged on the device, never trapped: the call that requests energy (or
+ * rt_energy_last) returns RT_ERR_NONFINITE_INPUT if the traced fields held any.
+ * Errors: RT_ERR_NOT_CONFIGURED, RT_ERR_INVALID_ARG (NULL field), RT_ERR_CUDA,
+ * RT_ERR_NONFINITE_INPUT (only when energy != NULL). */
+int rt_irradiate(rt_ctx *ctx, const float *rho, const float *t_dust, float *q_abs,
+                 float *a_rad, rt_energy *energy);
+
+/* rt_irradiate_host -- as rt_irradiate, with HOST buffers of the same layout. The
+ * library copies rho and t_dust to device buffers it owns (allocated on first use,
+ * freed by rt_destroy), traces, and copies q_abs and a_rad back before it returns.
+ * Page-locked host memory makes the copies asynchronous DMA; pageable memory works
+ * but is slower. Errors: as rt_irradiate, plus RT_ERR_NO_MEMORY. */
+int rt_irradiate_host(rt_ctx *ctx, const float *rho, const float *t_dust, float *q_abs,
+                      float *a_rad, rt_energy *energy);
+
+/* rt_energy_last -- energy sums of the most recent trace on this context (runs the
+ * FP64 reduction of its per-tile partial sums, synchronises the stream).
+ * Errors: RT_ERR_NOT_CONFIGURED (nothing traced yet), RT_ERR_CUDA,
+ * RT_ERR_NONFINITE_INPUT (that trace saw invalid input; *out is still filled). */
+int rt_energy_last(rt_ctx *ctx, rt_energy *out);
+
+/* rt_get_bins -- copy the per-bin stellar surface fluxes F_i (erg s^-1 cm^-2, FP64,
+ * Eq. 20) that the device computed for the current star and table into host
+ * f_bin[n_nu]. Synchronises. Errors: RT_ERR_NOT_CONFIGURED, RT_ERR_CUDA. */
+int rt_get_bins(rt_ctx *ctx, double *f_bin);
+
+/* rt_set_tuning -- force the launch shape of the fused tracer: cells_per_lane
+ * (consecutive cells of the flattened ray array each thread owns) and
+ * warps_per_block. Both 0 restores automatic choice. Unsupported pairs return
+ * RT_ERR_INVALID_ARG; rt_get_tuning reports the pair in use. */
+int rt_set_tuning(rt_ctx *ctx, int cells_per_lane, int warps_per_block);
+int rt_get_tuning(const rt_ctx *ctx, int *cells_per_lane, int *warps_per_block);
+
+/* rt_autotune -- time every supported launch shape on the given device buffers
+ * (same meaning as rt_irradiate; q_abs and a_rad are overwritten), keep the fastest
+ * for this context and remember it for grids of the same shape class in this
+ * process. reps >= 1 timed calls per shape. Synchronises. Errors: as rt_irradiate. */
+int rt_autotune(rt_ctx *ctx, const float *rho, const float *t_dust, float *q_abs,
+                float *a_rad, int reps);
+
+/* rt_destroy -- free the context and everything it owns (NULL is ignored). Work
+ * still queued on the stream is waited for first. */
+void rt_destroy(rt_ctx *ctx);
+
+/* rt_last_error -- text of the last failure on ctx (never NULL; "" if none). With
+ * ctx == NULL: the last failure of rt_create in this thread. */
+const char *rt_last_error(const rt_ctx *ctx);
+
+/* rt_status_string -- constant name of a status code. */
+const char *rt_status_string(int status);
+
+/* ---- diagnostics (no counterpart in the paper) ---------------------------- */
+
+/* rt_probe_ex2 -- y[i] = 2^x[i] with the hardware approximation the FP32 tracer
+ * uses, for accuracy tests. x, y: device float32 arrays of n elements; runs on
+ * stream (NULL = default) and synchronises it. */
+int rt_probe_ex2(const float *x, float *y, long long n, void *cuda_stream);
+
+/* rt_probe_alu_rates -- micro-benchmark of the current device: sustained MUFU
+ * ex2.approx.f32 and FP32 FFMA throughput in operations per SM per clock, and the
+ * SM clock (MHz) measured during the ex2 run. Synchronises the device. */
+int rt_probe_alu_rates(double *ex2_per_sm_clk, double *ffma_per_sm_clk, double *sm_mhz);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RT_IRRADIATION_H */

@@ -1,0 +1,101 @@
+"""ctypes binding of ``librt_gb300.so`` (the C ABI in include/rt_irradiation.h).
+
+Argument marshalling only: every step of the ray tracer runs in the library's CUDA
+kernels. There is no fallback: if the library is missing or fails to load, the
+import of this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "librt_gb300.so")
+
+RT_OK = 0
+RT_ERR_INVALID_ARG = -1
+RT_ERR_NOT_CONFIGURED = -2
+RT_ERR_CUDA = -3
+RT_ERR_TIMEOUT = -4
+RT_ERR_NONFINITE_INPUT = -5
+RT_ERR_NO_MEMORY = -6
+
+RT_FP32_KAHAN = 0
+RT_FP32_PLAIN = 1
+RT_FP64 = 2
+RT_MAX_NU = 128
+
+PRECISIONS = {"fp32_kahan": RT_FP32_KAHAN, "fp32_plain": RT_FP32_PLAIN, "fp64": RT_FP64}
+
+
+class RtGridDesc(ctypes.Structure):
+    _fields_ = [("nr", ctypes.c_int), ("ntheta", ctypes.c_int), ("nphi", ctypes.c_int),
+                ("r_if", ctypes.POINTER(ctypes.c_double)),
+                ("theta_if", ctypes.POINTER(ctypes.c_double)),
+                ("phi_if", ctypes.POINTER(ctypes.c_double)),
+                ("precision", ctypes.c_int)]
+
+
+class RtEnergy(ctypes.Structure):
+    _fields_ = [("e_abs", ctypes.c_double), ("e_esc", ctypes.c_double),
+                ("l_star", ctypes.c_double), ("rel_err", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_DP = ctypes.POINTER(ctypes.c_double)
+
+# name -> (restype, argtypes); every symbol the header declares
+SIGNATURES = {
+    "rt_create": (_I, [ctypes.POINTER(RtGridDesc), _P, ctypes.POINTER(_P)]),
+    "rt_set_stream": (_I, [_P, _P]),
+    "rt_set_opacity_table": (_I, [_P, _I, _DP, _DP, _D, _I]),
+    "rt_set_star": (_I, [_P, _D, _D]),
+    "rt_irradiate": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(RtEnergy)]),
+    "rt_irradiate_host": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(RtEnergy)]),
+    "rt_energy_last": (_I, [_P, ctypes.POINTER(RtEnergy)]),
+    "rt_get_bins": (_I, [_P, _DP]),
+    "rt_set_tuning": (_I, [_P, _I, _I]),
+    "rt_get_tuning": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "rt_autotune": (_I, [_P, _P, _P, _P, _P, _I]),
+    "rt_destroy": (None, [_P]),
+    "rt_last_error": (ctypes.c_char_p, [_P]),
+    "rt_status_string": (ctypes.c_char_p, [_I]),
+    "rt_probe_ex2": (_I, [_P, _P, ctypes.c_longlong, _P]),
+    "rt_probe_alu_rates": (_I, [_DP, _DP, _DP]),
+}
+
+
+class RtError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_string(status)}: {msg}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = load()
+
+
+def status_string(status: int) -> str:
+    return lib.rt_status_string(int(status)).decode()
+
+
+def last_error(ctx) -> str:
+    return lib.rt_last_error(ctx).decode()
+
+
+def check(status: int, ctx=None):
+    if status != RT_OK:
+        raise RtError(status, last_error(ctx))
+    return status

@@ -1,0 +1,477 @@
+// C ABI of the irradiation ray tracer: contexts, configuration, launches.
+// Host code here validates arguments, owns device memory and enqueues kernels;
+// every step of the computation runs in the kernels of rt_setup.cu / rt_trace.cu.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+
+#include "rt_internal.cuh"
+
+using rt::DevScalars;
+using rt::NuEntry;
+using rt::Shape;
+
+struct rt_ctx {
+    int dev = 0;
+    int nr = 0, ntheta = 0, nphi = 0, precision = RT_FP32_KAHAN;
+    long long nrays = 0, ncells = 0, L = 0;
+    cudaStream_t stream = nullptr;
+
+    // geometry (device)
+    double *r_if = nullptr, *theta_if = nullptr, *phi_if = nullptr;
+    float4 *rtab = nullptr;
+    double4 *rtab64 = nullptr;
+    double *domega = nullptr;
+    // bins (device)
+    double *nu_mid = nullptr, *kappa = nullptr, *f_bin = nullptr;
+    NuEntry *nu_tab = nullptr;
+    float *kap = nullptr;
+    double2 *nu64 = nullptr;
+    DevScalars *sc = nullptr;
+    // per-call scratch (device)
+    double2 *partials = nullptr;
+    long long partials_cap = 0;
+    unsigned *bad = nullptr;
+    rt_energy *energy_d = nullptr;
+    // pinned host mirrors
+    rt_energy *energy_h = nullptr;
+    unsigned *bad_h = nullptr;
+    // device staging for the host-buffer entry point
+    float *h_rho = nullptr, *h_t = nullptr, *h_q = nullptr, *h_a = nullptr;
+
+    // configuration state
+    int n_nu = 0, kappa_bf16 = 0;
+    bool have_table = false, have_star = false, configured = false;
+    double t_sub = 0.0, t_star = 0.0, r_star = 0.0;
+    DevScalars sc_h{};
+    Shape shape{0, 0};
+    bool shape_forced = false;
+    unsigned seq = 0;
+    long long last_ntiles = 0;
+    bool traced = false;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int fail(rt_ctx *ctx, int status, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    else g_create_err = msg;
+    return status;
+}
+
+int cuda_fail(rt_ctx *ctx, const char *what, cudaError_t e)
+{
+    return fail(ctx, RT_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define RT_CK(ctx, call)                                      \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, #call, e_); \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t n)
+{
+    return cudaMalloc((void **)p, sizeof(T) * (n ? n : 1));
+}
+
+bool increasing(const double *a, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!isfinite(a[i]) || (i > 0 && !(a[i] > a[i - 1]))) return false;
+    return true;
+}
+
+// shape choice cache across contexts: (precision, nr, nrays, nnu_pad) -> shape
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, long long, int>, Shape> g_tune_cache;
+
+Shape default_shape(const rt_ctx *c)
+{
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(std::make_tuple(c->precision, c->nr, c->nrays, c->sc_h.nnu_pad));
+        if (it != g_tune_cache.end()) return it->second;
+    }
+    // Prefer the widest tile that still gives every SM several tiles.
+    Shape cand[16];
+    const int n = rt::trace_shapes(c->precision, cand, 16);
+    Shape best = cand[0];
+    long long best_t = 0;
+    for (int i = 0; i < n; ++i) {
+        const long long tiles = (c->L + rt::trace_tile_cells(cand[i]) - 1) / rt::trace_tile_cells(cand[i]);
+        const long long tc = rt::trace_tile_cells(cand[i]);
+        if (tiles >= 8LL * 152) {
+            if (tc > best_t) { best = cand[i]; best_t = tc; }
+        }
+    }
+    if (best_t == 0) {  // small grid: most tiles wins, then the smaller tile
+        long long most = -1;
+        for (int i = 0; i < n; ++i) {
+            const long long tiles = (c->L + rt::trace_tile_cells(cand[i]) - 1) / rt::trace_tile_cells(cand[i]);
+            if (tiles > most) { most = tiles; best = cand[i]; }
+        }
+    }
+    return best;
+}
+
+int finalize(rt_ctx *c)
+{
+    c->configured = false;
+    if (!(c->have_table && c->have_star)) return RT_OK;
+    cudaError_t e = rt::launch_setup_bins(c->n_nu, c->nu_mid, c->kappa, c->t_star, c->r_star,
+                                          c->kappa_bf16, c->f_bin, c->nu_tab, c->kap, c->nu64,
+                                          c->sc, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, "setup_bins", e);
+    e = rt::launch_setup_geometry(c->nr, c->ntheta, c->nphi, c->r_if, c->theta_if, c->phi_if,
+                                  c->t_star, c->rtab, c->rtab64, c->domega, c->sc, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, "setup_geometry", e);
+    RT_CK(c, cudaMemcpyAsync(&c->sc_h, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+    RT_CK(c, cudaStreamSynchronize(c->stream));
+    if (!c->shape_forced) c->shape = default_shape(c);
+    c->configured = true;
+    return RT_OK;
+}
+
+int ensure_partials(rt_ctx *c, long long ntiles)
+{
+    if (ntiles <= c->partials_cap) return RT_OK;
+    if (c->partials) cudaFree(c->partials);
+    c->partials = nullptr;
+    c->partials_cap = 0;
+    if (dalloc(&c->partials, (size_t)ntiles) != cudaSuccess)
+        return fail(c, RT_ERR_NO_MEMORY, "cannot allocate energy partials");
+    c->partials_cap = ntiles;
+    return RT_OK;
+}
+
+int trace(rt_ctx *c, const float *rho, const float *td, float *q, float *a, Shape s)
+{
+    const long long ntiles = (c->L + rt::trace_tile_cells(s) - 1) / rt::trace_tile_cells(s);
+    int st = ensure_partials(c, ntiles);
+    if (st != RT_OK) return st;
+    rt::TraceArgs args;
+    args.rho = rho;
+    args.tdust = td;
+    args.q = q;
+    args.a = a;
+    args.nu = c->nu_tab;
+    args.kap = c->kap;
+    args.nu64 = c->nu64;
+    args.rtab = c->rtab;
+    args.rtab64 = c->rtab64;
+    args.domega = c->domega;
+    args.partials = c->partials;
+    args.bad_input = c->bad;
+    args.seq = ++c->seq;
+    args.L = c->L;
+    args.nr = c->nr;
+    args.nnu_pad = c->sc_h.nnu_pad;
+    args.t_sub = (float)c->t_sub;
+    cudaError_t e = rt::launch_trace(c->precision, s, args, ntiles, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, "trace kernel launch", e);
+    c->last_ntiles = ntiles;
+    c->traced = true;
+    return RT_OK;
+}
+
+int read_energy(rt_ctx *c, rt_energy *out)
+{
+    cudaError_t e = rt::launch_energy_reduce(c->partials, c->last_ntiles, c->sc, c->energy_d, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, "energy reduce", e);
+    RT_CK(c, cudaMemcpyAsync(c->energy_h, c->energy_d, sizeof(rt_energy), cudaMemcpyDeviceToHost, c->stream));
+    RT_CK(c, cudaMemcpyAsync(c->bad_h, c->bad, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    RT_CK(c, cudaStreamSynchronize(c->stream));
+    *out = *c->energy_h;
+    if (*c->bad_h == c->seq) return fail(c, RT_ERR_NONFINITE_INPUT, "input field holds NaN/Inf/negative density or NaN temperature");
+    return RT_OK;
+}
+
+int check_call(rt_ctx *c, const void *rho, const void *td, const void *q, const void *a)
+{
+    if (!c) return RT_ERR_INVALID_ARG;
+    if (!rho || !td || !q || !a) return fail(c, RT_ERR_INVALID_ARG, "NULL field pointer");
+    if (!c->configured) return fail(c, RT_ERR_NOT_CONFIGURED, "call rt_set_star and rt_set_opacity_table first");
+    cudaError_t e = cudaSetDevice(c->dev);
+    if (e != cudaSuccess) return cuda_fail(c, "cudaSetDevice", e);
+    return RT_OK;
+}
+
+void free_all(rt_ctx *c)
+{
+    void *ptrs[] = {c->r_if, c->theta_if, c->phi_if, c->rtab, c->rtab64, c->domega, c->nu_mid,
+                    c->kappa, c->f_bin, c->nu_tab, c->kap, c->nu64, c->sc, c->partials, c->bad,
+                    c->energy_d, c->h_rho, c->h_t, c->h_q, c->h_a};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c->energy_h) cudaFreeHost(c->energy_h);
+    if (c->bad_h) cudaFreeHost(c->bad_h);
+}
+
+}  // namespace
+
+extern "C" {
+
+int rt_create(const rt_grid_desc *g, void *cuda_stream, rt_ctx **out)
+{
+    if (!out) return fail(nullptr, RT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!g || g->nr < 1 || g->ntheta < 1 || g->nphi < 1 || !g->r_if || !g->theta_if || !g->phi_if)
+        return fail(nullptr, RT_ERR_INVALID_ARG, "grid sizes must be >= 1 and interface arrays non-NULL");
+    if (g->precision != RT_FP32_KAHAN && g->precision != RT_FP32_PLAIN && g->precision != RT_FP64)
+        return fail(nullptr, RT_ERR_INVALID_ARG, "unknown precision");
+    if (!increasing(g->r_if, g->nr + 1) || !(g->r_if[0] > 0.0))
+        return fail(nullptr, RT_ERR_INVALID_ARG, "r_if must be finite, > 0 and strictly increasing");
+    if (!increasing(g->theta_if, g->ntheta + 1) || g->theta_if[0] < 0.0 ||
+        g->theta_if[g->ntheta] > 3.14159265358979323846 * (1 + 1e-15))
+        return fail(nullptr, RT_ERR_INVALID_ARG, "theta_if must be strictly increasing within [0, pi]");
+    if (!increasing(g->phi_if, g->nphi + 1))
+        return fail(nullptr, RT_ERR_INVALID_ARG, "phi_if must be strictly increasing");
+    const long long nrays = (long long)g->ntheta * g->nphi;
+    const long long ncells = nrays * g->nr;
+    if (ncells > (1LL << 40) || g->nr > (1 << 24))
+        return fail(nullptr, RT_ERR_INVALID_ARG, "grid too large");
+
+    rt_ctx *c = new (std::nothrow) rt_ctx();
+    if (!c) return fail(nullptr, RT_ERR_NO_MEMORY, "out of host memory");
+    c->nr = g->nr;
+    c->ntheta = g->ntheta;
+    c->nphi = g->nphi;
+    c->precision = g->precision;
+    c->nrays = nrays;
+    c->ncells = ncells;
+    c->L = nrays * (g->nr + 1);
+    c->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaGetDevice(&c->dev);
+    bool ok = e == cudaSuccess;
+    ok = ok && dalloc(&c->r_if, g->nr + 1) == cudaSuccess;
+    ok = ok && dalloc(&c->theta_if, g->ntheta + 1) == cudaSuccess;
+    ok = ok && dalloc(&c->phi_if, g->nphi + 1) == cudaSuccess;
+    ok = ok && dalloc(&c->rtab, g->nr) == cudaSuccess;
+    ok = ok && dalloc(&c->rtab64, g->nr) == cudaSuccess;
+    ok = ok && dalloc(&c->domega, (size_t)nrays) == cudaSuccess;
+    ok = ok && dalloc(&c->nu_mid, RT_MAX_NU) == cudaSuccess;
+    ok = ok && dalloc(&c->kappa, RT_MAX_NU) == cudaSuccess;
+    ok = ok && dalloc(&c->f_bin, RT_MAX_NU) == cudaSuccess;
+    ok = ok && dalloc(&c->nu_tab, RT_MAX_NU + rt::kNuPad) == cudaSuccess;
+    ok = ok && dalloc(&c->kap, RT_MAX_NU + rt::kNuPad) == cudaSuccess;
+    ok = ok && dalloc(&c->nu64, RT_MAX_NU + rt::kNuPad) == cudaSuccess;
+    ok = ok && dalloc(&c->sc, 1) == cudaSuccess;
+    ok = ok && dalloc(&c->bad, 1) == cudaSuccess;
+    ok = ok && dalloc(&c->energy_d, 1) == cudaSuccess;
+    ok = ok && cudaMallocHost((void **)&c->energy_h, sizeof(rt_energy)) == cudaSuccess;
+    ok = ok && cudaMallocHost((void **)&c->bad_h, sizeof(unsigned)) == cudaSuccess;
+    if (!ok) {
+        free_all(c);
+        delete c;
+        cudaGetLastError();
+        return fail(nullptr, RT_ERR_CUDA, "device allocation failed in rt_create");
+    }
+    ok = cudaMemcpyAsync(c->r_if, g->r_if, sizeof(double) * (g->nr + 1), cudaMemcpyHostToDevice, c->stream) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(c->theta_if, g->theta_if, sizeof(double) * (g->ntheta + 1), cudaMemcpyHostToDevice, c->stream) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(c->phi_if, g->phi_if, sizeof(double) * (g->nphi + 1), cudaMemcpyHostToDevice, c->stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(c->bad, 0, sizeof(unsigned), c->stream) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(c->stream) == cudaSuccess;
+    if (!ok) {
+        free_all(c);
+        delete c;
+        return fail(nullptr, RT_ERR_CUDA, std::string("copy in rt_create: ") + cudaGetErrorString(cudaGetLastError()));
+    }
+    *out = c;
+    return RT_OK;
+}
+
+int rt_set_stream(rt_ctx *ctx, void *cuda_stream)
+{
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return RT_OK;
+}
+
+int rt_set_opacity_table(rt_ctx *ctx, int n_nu, const double *nu_mid, const double *kappa,
+                         double t_sub, int kappa_bf16)
+{
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (n_nu < 1 || n_nu > RT_MAX_NU || !nu_mid || !kappa)
+        return fail(ctx, RT_ERR_INVALID_ARG, "n_nu must be in 1..128 with non-NULL arrays");
+    if (!increasing(nu_mid, n_nu) || !(nu_mid[0] > 0.0))
+        return fail(ctx, RT_ERR_INVALID_ARG, "nu_mid must be finite, > 0 and strictly increasing");
+    for (int i = 0; i < n_nu; ++i)
+        if (!(kappa[i] >= 0.0) || !isfinite(kappa[i]))
+            return fail(ctx, RT_ERR_INVALID_ARG, "kappa must be finite and >= 0");
+    if (isnan(t_sub)) return fail(ctx, RT_ERR_INVALID_ARG, "t_sub is NaN");
+    RT_CK(ctx, cudaSetDevice(ctx->dev));
+    RT_CK(ctx, cudaMemcpyAsync(ctx->nu_mid, nu_mid, sizeof(double) * n_nu, cudaMemcpyHostToDevice, ctx->stream));
+    RT_CK(ctx, cudaMemcpyAsync(ctx->kappa, kappa, sizeof(double) * n_nu, cudaMemcpyHostToDevice, ctx->stream));
+    ctx->n_nu = n_nu;
+    ctx->t_sub = t_sub;
+    ctx->kappa_bf16 = kappa_bf16 ? 1 : 0;
+    ctx->have_table = true;
+    return finalize(ctx);
+}
+
+int rt_set_star(rt_ctx *ctx, double t_star, double r_star)
+{
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (!(t_star > 0.0) || !(r_star > 0.0) || !isfinite(t_star) || !isfinite(r_star))
+        return fail(ctx, RT_ERR_INVALID_ARG, "t_star and r_star must be finite and > 0");
+    RT_CK(ctx, cudaSetDevice(ctx->dev));
+    ctx->t_star = t_star;
+    ctx->r_star = r_star;
+    ctx->have_star = true;
+    return finalize(ctx);
+}
+
+int rt_irradiate(rt_ctx *ctx, const float *rho, const float *t_dust, float *q_abs, float *a_rad,
+                 rt_energy *energy)
+{
+    int st = check_call(ctx, rho, t_dust, q_abs, a_rad);
+    if (st != RT_OK) return st;
+    st = trace(ctx, rho, t_dust, q_abs, a_rad, ctx->shape);
+    if (st != RT_OK || !energy) return st;
+    return read_energy(ctx, energy);
+}
+
+int rt_irradiate_host(rt_ctx *ctx, const float *rho, const float *t_dust, float *q_abs,
+                      float *a_rad, rt_energy *energy)
+{
+    int st = check_call(ctx, rho, t_dust, q_abs, a_rad);
+    if (st != RT_OK) return st;
+    const size_t bytes = sizeof(float) * (size_t)ctx->ncells;
+    if (!ctx->h_rho) {
+        bool ok = dalloc(&ctx->h_rho, ctx->ncells) == cudaSuccess &&
+                  dalloc(&ctx->h_t, ctx->ncells) == cudaSuccess &&
+                  dalloc(&ctx->h_q, ctx->ncells) == cudaSuccess &&
+                  dalloc(&ctx->h_a, ctx->ncells) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            return fail(ctx, RT_ERR_NO_MEMORY, "cannot allocate device staging buffers");
+        }
+    }
+    RT_CK(ctx, cudaMemcpyAsync(ctx->h_rho, rho, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    RT_CK(ctx, cudaMemcpyAsync(ctx->h_t, t_dust, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    st = trace(ctx, ctx->h_rho, ctx->h_t, ctx->h_q, ctx->h_a, ctx->shape);
+    if (st != RT_OK) return st;
+    RT_CK(ctx, cudaMemcpyAsync(q_abs, ctx->h_q, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    RT_CK(ctx, cudaMemcpyAsync(a_rad, ctx->h_a, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    if (energy) return read_energy(ctx, energy);
+    RT_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return RT_OK;
+}
+
+int rt_energy_last(rt_ctx *ctx, rt_energy *out)
+{
+    if (!ctx || !out) return RT_ERR_INVALID_ARG;
+    if (!ctx->traced) return fail(ctx, RT_ERR_NOT_CONFIGURED, "nothing traced yet");
+    RT_CK(ctx, cudaSetDevice(ctx->dev));
+    return read_energy(ctx, out);
+}
+
+int rt_get_bins(rt_ctx *ctx, double *f_bin)
+{
+    if (!ctx || !f_bin) return RT_ERR_INVALID_ARG;
+    if (!ctx->configured) return fail(ctx, RT_ERR_NOT_CONFIGURED, "star or table not set");
+    RT_CK(ctx, cudaSetDevice(ctx->dev));
+    RT_CK(ctx, cudaMemcpyAsync(f_bin, ctx->f_bin, sizeof(double) * ctx->n_nu, cudaMemcpyDeviceToHost, ctx->stream));
+    RT_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return RT_OK;
+}
+
+int rt_set_tuning(rt_ctx *ctx, int cells_per_lane, int warps_per_block)
+{
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (cells_per_lane == 0 && warps_per_block == 0) {
+        ctx->shape_forced = false;
+        if (ctx->configured) ctx->shape = default_shape(ctx);
+        return RT_OK;
+    }
+    if (!rt::trace_shape_supported(ctx->precision, cells_per_lane, warps_per_block))
+        return fail(ctx, RT_ERR_INVALID_ARG, "launch shape not compiled in for this precision");
+    ctx->shape = Shape{cells_per_lane, warps_per_block};
+    ctx->shape_forced = true;
+    return RT_OK;
+}
+
+int rt_get_tuning(const rt_ctx *ctx, int *cells_per_lane, int *warps_per_block)
+{
+    if (!ctx || !cells_per_lane || !warps_per_block) return RT_ERR_INVALID_ARG;
+    *cells_per_lane = ctx->shape.cells_per_lane;
+    *warps_per_block = ctx->shape.warps;
+    return RT_OK;
+}
+
+int rt_autotune(rt_ctx *ctx, const float *rho, const float *t_dust, float *q_abs, float *a_rad, int reps)
+{
+    int st = check_call(ctx, rho, t_dust, q_abs, a_rad);
+    if (st != RT_OK) return st;
+    if (reps < 1) return fail(ctx, RT_ERR_INVALID_ARG, "reps must be >= 1");
+    Shape cand[16];
+    const int n = rt::trace_shapes(ctx->precision, cand, 16);
+    cudaEvent_t e0, e1;
+    RT_CK(ctx, cudaEventCreate(&e0));
+    RT_CK(ctx, cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    Shape best = ctx->shape;
+    for (int i = 0; i < n; ++i) {
+        st = trace(ctx, rho, t_dust, q_abs, a_rad, cand[i]);  // warm-up
+        if (st != RT_OK) break;
+        cudaEventRecord(e0, ctx->stream);
+        for (int r = 0; r < reps && st == RT_OK; ++r) st = trace(ctx, rho, t_dust, q_abs, a_rad, cand[i]);
+        cudaEventRecord(e1, ctx->stream);
+        if (st != RT_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) { st = cuda_fail(ctx, "autotune sync", cudaGetLastError()); break; }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) { best_ms = ms; best = cand[i]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != RT_OK) return st;
+    ctx->shape = best;
+    ctx->shape_forced = true;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[std::make_tuple(ctx->precision, ctx->nr, ctx->nrays, ctx->sc_h.nnu_pad)] = best;
+    }
+    return RT_OK;
+}
+
+void rt_destroy(rt_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->dev);
+    cudaStreamSynchronize(ctx->stream);
+    free_all(ctx);
+    delete ctx;
+}
+
+const char *rt_last_error(const rt_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+const char *rt_status_string(int status)
+{
+    switch (status) {
+    case RT_OK: return "RT_OK";
+    case RT_ERR_INVALID_ARG: return "RT_ERR_INVALID_ARG";
+    case RT_ERR_NOT_CONFIGURED: return "RT_ERR_NOT_CONFIGURED";
+    case RT_ERR_CUDA: return "RT_ERR_CUDA";
+    case RT_ERR_TIMEOUT: return "RT_ERR_TIMEOUT";
+    case RT_ERR_NONFINITE_INPUT: return "RT_ERR_NONFINITE_INPUT";
+    case RT_ERR_NO_MEMORY: return "RT_ERR_NO_MEMORY";
+    default: return "RT_UNKNOWN_STATUS";
+    }
+}
+
+}  // extern "C"

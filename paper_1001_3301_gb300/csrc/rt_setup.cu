@@ -1,0 +1,212 @@
+// Set-up kernels: per-bin stellar fluxes (Eq. 20), geometry tables, and the FP64
+// energy reduction. All run once per configuration change (or once per energy
+// request) and are tiny next to the tracer.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "rt_internal.cuh"
+
+namespace rt {
+namespace {
+
+// t^3 / (e^t - 1), the Planck integrand in x = h nu / (k T)
+__device__ double planck_x(double t) { return t * t * t / expm1(t); }
+
+// 8-point Gauss-Legendre rule on [a, b] (nodes and weights of the Legendre
+// polynomial P_8, Abramowitz & Stegun Table 25.4).
+__device__ double gauss_legendre8(double a, double b)
+{
+    const double xs[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267,
+                          0.9602898564975363};
+    const double ws[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745,
+                          0.1012285362903763};
+    const double c = 0.5 * (a + b), h = 0.5 * (b - a);
+    double s = 0.0;
+    for (int i = 0; i < 4; ++i) s += ws[i] * (planck_x(c - h * xs[i]) + planck_x(c + h * xs[i]));
+    return s * h;
+}
+
+// int_a^b t^3/(e^t-1) dt by composite Gauss-Legendre on panels no wider than one
+// unit of x. The integrand is analytic with its nearest poles at +-2 pi i, so each
+// panel converges far below double rounding. An infinite upper edge is replaced by
+// a + 60: the neglected tail is below e^-60 of the integrand at a.
+__device__ double planck_band(double a, double b)
+{
+    if (isinf(b)) b = a + 60.0;
+    if (!(b > a)) return 0.0;
+    const int n = (int)ceil(b - a);
+    const double h = (b - a) / n;
+    double s = 0.0;
+    for (int p = 0; p < n; ++p) s += gauss_legendre8(a + p * h, a + (p + 1) * h);
+    return s;
+}
+
+__global__ void k_setup_bins(int n_nu, const double *nu_mid, const double *kappa, double t_star,
+                             double r_star, int kappa_bf16, double *f_bin, NuEntry *nu,
+                             float *kap, double2 *nu64, DevScalars *sc)
+{
+    __shared__ double s_f[RT_MAX_NU];
+    __shared__ double s_k[RT_MAX_NU];
+    const int i = threadIdx.x;
+    if (i < n_nu) {
+        // Eq. 20 with B_nu the specific intensity: F_i = pi int B_nu dnu over the bin
+        // = 2 pi (k T)^4 / (h^3 c^2) int_{x_lo}^{x_hi} t^3/(e^t-1) dt.
+        const double lo = (i == 0) ? 0.0 : 0.5 * (nu_mid[i - 1] + nu_mid[i]);
+        const double hi = (i == n_nu - 1) ? INFINITY : 0.5 * (nu_mid[i] + nu_mid[i + 1]);
+        const double kt_h = kKB * t_star / kH;
+        const double pref = 2.0 * kPi * pow(kKB * t_star, 4) / (kH * kH * kH * kC * kC);
+        const double f = pref * planck_band(lo / kt_h, hi / kt_h);
+        double k = kappa[i];
+        if (kappa_bf16) k = (double)__bfloat162float(__float2bfloat16_rn((float)k));
+        s_f[i] = f;
+        s_k[i] = k;
+        f_bin[i] = f;
+    }
+    __syncthreads();
+    if (i != 0) return;
+    double fmax = 0.0, ftr = 0.0;
+    for (int b = 0; b < n_nu; ++b) fmax = fmax > s_f[b] ? fmax : s_f[b];
+    int na = 0;
+    for (int b = 0; b < n_nu; ++b) {
+        if (s_k[b] > 0.0) {
+            nu[na].nk = (float)(-s_k[b] * kLog2e);
+            nu[na].lf = (float)log2(s_f[b] / fmax);
+            kap[na] = (float)s_k[b];
+            nu64[na] = make_double2(s_k[b], s_f[b] / fmax);
+            ++na;
+        } else {
+            ftr += s_f[b];
+        }
+    }
+    int pad = ((na + kNuPad - 1) / kNuPad) * kNuPad;
+    if (pad < kNuPad) pad = kNuPad;
+    for (int b = na; b < pad; ++b) {
+        nu[b].nk = -1.0f;
+        nu[b].lf = -INFINITY;
+        kap[b] = 0.0f;
+        nu64[b] = make_double2(1.0, 0.0);
+    }
+    sc->f_max = fmax;
+    sc->f_transparent = ftr;
+    sc->r2 = r_star * r_star;
+    sc->n_active = na;
+    sc->nnu_pad = pad;
+}
+
+// Per-radius and per-ray tables. Gq = 3 R*^2 F_max / (r+^3 - r-^3) turns the
+// per-ray sum of F_i/F_max e^-tau (1-e^-dtau) into power per volume; Ga0 = Gq dr / c
+// is the rho -> 0 force factor.
+__global__ void k_setup_geometry(int nr, int ntheta, int nphi, const double *r_if,
+                                 const double *theta_if, const double *phi_if, float4 *rtab,
+                                 double4 *rtab64, double *domega, const DevScalars *sc)
+{
+    const long long nrays = (long long)ntheta * nphi;
+    const long long n = nrays > nr ? nrays : nr;
+    const double gscale = 3.0 * sc->r2 * sc->f_max;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+        if (t < nr) {
+            const double r0 = r_if[t], r1 = r_if[t + 1];
+            const double dr = r1 - r0;
+            const double d3 = dr * (r1 * r1 + r1 * r0 + r0 * r0);  // r1^3 - r0^3
+            const double gq = gscale / d3;
+            const double ga0 = gq * dr / kC;
+            rtab[t] = make_float4((float)dr, (float)gq, (float)ga0, 0.0f);
+            rtab64[t] = make_double4(dr, gq, ga0, 0.0);
+        }
+        if (t < nrays) {
+            const int it = (int)(t % ntheta);
+            const int ip = (int)(t / ntheta);
+            domega[t] = (cos(theta_if[it]) - cos(theta_if[it + 1])) * (phi_if[ip + 1] - phi_if[ip]);
+        }
+    }
+}
+
+__device__ double block_sum(double v, double *s_red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) s_red[w] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    v = (threadIdx.x < nw) ? s_red[threadIdx.x] : 0.0;
+    if (w == 0)
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    return v;  // valid in thread 0
+}
+
+__global__ void k_sum_domega(long long nrays, const double *domega, double t_star,
+                             DevScalars *sc)
+{
+    __shared__ double s_red[32];
+    double v = 0.0;
+    for (long long j = threadIdx.x; j < nrays; j += blockDim.x) v += domega[j];
+    v = block_sum(v, s_red);
+    if (threadIdx.x == 0) {
+        const double sigma = 2.0 * pow(kPi, 5) * pow(kKB, 4) / (15.0 * kH * kH * kH * kC * kC);
+        sc->sum_domega = v;
+        sc->l_grid = sc->r2 * sigma * pow(t_star, 4) * v;
+    }
+}
+
+__global__ void k_energy_reduce(const double2 *partials, long long ntiles, const DevScalars *sc,
+                                rt_energy *out)
+{
+    __shared__ double s_red[32];
+    double sa = 0.0, se = 0.0;
+    for (long long t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        sa += partials[t].x;
+        se += partials[t].y;
+    }
+    sa = block_sum(sa, s_red);
+    se = block_sum(se, s_red);
+    if (threadIdx.x == 0) {
+        const double scale = sc->r2 * sc->f_max;
+        rt_energy e;
+        e.e_abs = scale * sa;
+        e.e_esc = scale * se + sc->r2 * sc->f_transparent * sc->sum_domega;
+        e.l_star = sc->l_grid;
+        e.rel_err = (e.e_abs + e.e_esc) / e.l_star - 1.0;
+        *out = e;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_setup_bins(int n_nu, const double *nu_mid_dev, const double *kappa_dev,
+                              double t_star, double r_star, int kappa_bf16, double *f_bin_dev,
+                              NuEntry *nu_dev, float *kap_dev, double2 *nu64_dev,
+                              DevScalars *sc_dev, cudaStream_t stream)
+{
+    k_setup_bins<<<1, RT_MAX_NU, 0, stream>>>(n_nu, nu_mid_dev, kappa_dev, t_star, r_star,
+                                              kappa_bf16, f_bin_dev, nu_dev, kap_dev, nu64_dev,
+                                              sc_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_setup_geometry(int nr, int ntheta, int nphi, const double *r_if_dev,
+                                  const double *theta_if_dev, const double *phi_if_dev,
+                                  double t_star, float4 *rtab, double4 *rtab64, double *domega,
+                                  DevScalars *sc_dev, cudaStream_t stream)
+{
+    const long long nrays = (long long)ntheta * nphi;
+    const long long n = nrays > nr ? nrays : nr;
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    k_setup_geometry<<<blocks, 256, 0, stream>>>(nr, ntheta, nphi, r_if_dev, theta_if_dev,
+                                                 phi_if_dev, rtab, rtab64, domega, sc_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_sum_domega<<<1, 1024, 0, stream>>>(nrays, domega, t_star, sc_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy_reduce(const double2 *partials, long long ntiles,
+                                 const DevScalars *sc_dev, rt_energy *out_dev, cudaStream_t stream)
+{
+    k_energy_reduce<<<1, 1024, 0, stream>>>(partials, ntiles, sc_dev, out_dev);
+    return cudaGetLastError();
+}
+
+}  // namespace rt

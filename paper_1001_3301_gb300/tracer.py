@@ -1,0 +1,182 @@
+"""Python front end of the GB300 irradiation ray tracer.
+
+A ``Tracer`` owns one library context (one grid). Device fields are torch CUDA
+tensors; the work is enqueued on torch's current CUDA stream. PyTorch provides
+device memory and streams only; the computation runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import RtEnergy, RtGridDesc, check, lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _stream_handle(stream=None) -> int:
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+class Energy:
+    """Energy sums of one trace (erg/s): absorbed, escaped, emitted, and the
+    relative mismatch (absorbed + escaped)/emitted - 1."""
+
+    def __init__(self, e: RtEnergy):
+        self.e_abs, self.e_esc, self.l_star, self.rel_err = e.e_abs, e.e_esc, e.l_star, e.rel_err
+
+    def __repr__(self):
+        return (f"Energy(e_abs={self.e_abs:.6e}, e_esc={self.e_esc:.6e}, "
+                f"l_star={self.l_star:.6e}, rel_err={self.rel_err:.3e})")
+
+
+class Tracer:
+    """One spherical grid; see include/rt_irradiation.h for the semantics."""
+
+    def __init__(self, r_if, theta_if, phi_if, precision: str | int = "fp32_kahan", stream=None):
+        self.r_if, self.theta_if, self.phi_if = _f64(r_if), _f64(theta_if), _f64(phi_if)
+        self.nr = len(self.r_if) - 1
+        self.ntheta = len(self.theta_if) - 1
+        self.nphi = len(self.phi_if) - 1
+        self.shape = (self.nphi, self.ntheta, self.nr)
+        self.precision = _lib.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        desc = RtGridDesc(self.nr, self.ntheta, self.nphi, _dptr(self.r_if), _dptr(self.theta_if),
+                          _dptr(self.phi_if), self.precision)
+        ctx = ctypes.c_void_p()
+        check(lib.rt_create(ctypes.byref(desc), ctypes.c_void_p(_stream_handle(stream)),
+                            ctypes.byref(ctx)), None)
+        self._ctx = ctx
+        self.n_nu = 0
+
+    @classmethod
+    def from_grid(cls, grid, precision="fp32_kahan", stream=None):
+        return cls(grid.r_if, grid.theta_if, grid.phi_if, precision, stream)
+
+    # -- configuration ---------------------------------------------------------
+    def set_opacity_table(self, nu_mid, kappa, t_sub: float, kappa_bf16: bool = False):
+        nu, kap = _f64(nu_mid), _f64(kappa)
+        check(lib.rt_set_opacity_table(self._ctx, len(nu), _dptr(nu), _dptr(kap), float(t_sub),
+                                       int(bool(kappa_bf16))), self._ctx)
+        self.n_nu = len(nu)
+
+    def set_star(self, t_star: float, r_star: float):
+        check(lib.rt_set_star(self._ctx, float(t_star), float(r_star)), self._ctx)
+
+    def set_stream(self, stream=None):
+        check(lib.rt_set_stream(self._ctx, ctypes.c_void_p(_stream_handle(stream))), self._ctx)
+
+    # -- tracing ---------------------------------------------------------------
+    def _check_field(self, t, name):
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+                and t.is_contiguous() and t.numel() == self.nr * self.ntheta * self.nphi):
+            raise ValueError(f"{name}: expected a contiguous float32 CUDA tensor of "
+                             f"{self.shape} elements")
+
+    def irradiate(self, rho, t_dust, q_abs=None, a_rad=None, energy: bool = False):
+        """Trace every ray. Returns (q_abs, a_rad, Energy or None); outputs are
+        allocated when not given."""
+        import torch
+        self._check_field(rho, "rho")
+        self._check_field(t_dust, "t_dust")
+        if q_abs is None:
+            q_abs = torch.empty(self.shape, dtype=torch.float32, device=rho.device)
+        if a_rad is None:
+            a_rad = torch.empty(self.shape, dtype=torch.float32, device=rho.device)
+        self._check_field(q_abs, "q_abs")
+        self._check_field(a_rad, "a_rad")
+        e = RtEnergy()
+        check(lib.rt_irradiate(self._ctx, rho.data_ptr(), t_dust.data_ptr(), q_abs.data_ptr(),
+                               a_rad.data_ptr(), ctypes.byref(e) if energy else None), self._ctx)
+        return q_abs, a_rad, (Energy(e) if energy else None)
+
+    def irradiate_host(self, rho, t_dust, q_abs, a_rad, energy: bool = False):
+        """Host-buffer variant: rho, t_dust, q_abs, a_rad are C-contiguous float32
+        numpy arrays or CPU torch tensors (page-locked for asynchronous copies)."""
+        ptrs = []
+        for x, name in ((rho, "rho"), (t_dust, "t_dust"), (q_abs, "q_abs"), (a_rad, "a_rad")):
+            ptrs.append(_host_ptr(x, self.nr * self.ntheta * self.nphi, name))
+        e = RtEnergy()
+        check(lib.rt_irradiate_host(self._ctx, *ptrs, ctypes.byref(e) if energy else None), self._ctx)
+        return Energy(e) if energy else None
+
+    def energy_last(self) -> Energy:
+        e = RtEnergy()
+        check(lib.rt_energy_last(self._ctx, ctypes.byref(e)), self._ctx)
+        return Energy(e)
+
+    def bins(self) -> np.ndarray:
+        out = np.empty(self.n_nu, dtype=np.float64)
+        check(lib.rt_get_bins(self._ctx, _dptr(out)), self._ctx)
+        return out
+
+    # -- launch shape ----------------------------------------------------------
+    def set_tuning(self, cells_per_lane: int = 0, warps: int = 0):
+        check(lib.rt_set_tuning(self._ctx, int(cells_per_lane), int(warps)), self._ctx)
+
+    def tuning(self):
+        c, w = ctypes.c_int(), ctypes.c_int()
+        check(lib.rt_get_tuning(self._ctx, ctypes.byref(c), ctypes.byref(w)), self._ctx)
+        return c.value, w.value
+
+    def autotune(self, rho, t_dust, q_abs, a_rad, reps: int = 3):
+        check(lib.rt_autotune(self._ctx, rho.data_ptr(), t_dust.data_ptr(), q_abs.data_ptr(),
+                              a_rad.data_ptr(), int(reps)), self._ctx)
+        return self.tuning()
+
+    # -- lifetime --------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_ctx", None):
+            lib.rt_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _host_ptr(x, n, name):
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float32 or not x.flags["C_CONTIGUOUS"] or x.size != n:
+            raise ValueError(f"{name}: expected a C-contiguous float32 array of {n} elements")
+        return x.ctypes.data
+    import torch
+    if isinstance(x, torch.Tensor):
+        if x.is_cuda or x.dtype != torch.float32 or not x.is_contiguous() or x.numel() != n:
+            raise ValueError(f"{name}: expected a contiguous float32 CPU tensor of {n} elements")
+        return x.data_ptr()
+    raise TypeError(f"{name}: numpy array or CPU tensor expected")
+
+
+def probe_ex2(x):
+    """2^x on the device with the FP32 tracer's hardware exp2 (torch CUDA tensor in/out)."""
+    import torch
+    y = torch.empty_like(x)
+    check(lib.rt_probe_ex2(x.data_ptr(), y.data_ptr(), x.numel(),
+                           ctypes.c_void_p(_stream_handle())))
+    return y
+
+
+def probe_alu_rates():
+    """(ex2 per SM per clock, FFMA per SM per clock, SM MHz) measured on the device."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    check(lib.rt_probe_alu_rates(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value

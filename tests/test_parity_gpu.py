@@ -1,0 +1,338 @@
+"""GPU parity: the CUDA tracer through the C ABI against the FP64 oracle,
+element by element, on seeded synthetic inputs (tolerances in tests/_parity.py)."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import _parity, _pins
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1001_3301_gb300  # noqa: F401  (raises if the library is missing)
+
+
+def _w3(nr, nth, nph, nnu, tau, seed=1):
+    return synth.disk3d(nr, nth, nph, n_nu=nnu, tau550=tau, seed=seed)
+
+
+# --------------------------------------------------------------------------
+# the 2-D benchmark disk (64 x 32 x 1, 32 bins, tau550 = 1, 50 K dust)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("precision,rtol", [("fp32_kahan", 1e-5), ("fp64", 3e-7)])
+def test_disk2d(precision, rtol):
+    w = synth.disk2d()
+    orc = _parity.oracle_for(w)
+    q, a, e = _parity.run_gpu(w, precision)
+    _parity.assert_parity(w, q, a, e, orc, rtol_q=rtol, rtol_a=rtol,
+                          rtol_energy=1e-6 if precision != "fp64" else 1e-9, label=precision)
+
+
+# --------------------------------------------------------------------------
+# ragged sizes, every compiled launch shape (several tiles, rays straddling
+# lanes, warps and tiles, a partial last tile)
+# --------------------------------------------------------------------------
+RAGGED = [(1, 1, 1, 1), (2, 3, 1, 2), (3, 5, 2, 5), (33, 7, 3, 9), (65, 9, 2, 17),
+          (129, 3, 5, 79), (257, 2, 3, 32), (512, 3, 2, 128)]
+SHAPES = {"fp32_kahan": [(2, 4), (4, 4), (8, 4), (16, 4), (4, 8), (8, 8), (16, 8)],
+          "fp32_plain": [(2, 4), (8, 8), (16, 8)],
+          "fp64": [(2, 4), (4, 4), (8, 4)]}
+
+
+@pytest.mark.parametrize("dims", RAGGED, ids=lambda d: "x".join(map(str, d)))
+def test_ragged_all_shapes(dims):
+    nr, nth, nph, nnu = dims
+    w = _w3(nr, nth, nph, nnu, tau=10.0, seed=nr + nth)
+    orc = _parity.oracle_for(w)
+    for shape in SHAPES["fp32_kahan"]:
+        q, a, e = _parity.run_gpu(w, "fp32_kahan", shape=shape)
+        _parity.assert_parity(w, q, a, e, orc, label=f"{dims} {shape}")
+
+
+@pytest.mark.parametrize("precision", ["fp32_plain", "fp64"])
+def test_ragged_other_precisions(precision):
+    w = _w3(65, 9, 2, 17, tau=10.0, seed=3)
+    orc = _parity.oracle_for(w)
+    rtol = 3e-7 if precision == "fp64" else 1e-4
+    for shape in SHAPES[precision]:
+        q, a, e = _parity.run_gpu(w, precision, shape=shape)
+        _parity.assert_parity(w, q, a, e, orc, rtol_q=rtol, rtol_a=rtol,
+                              rtol_energy=1e-6, label=f"{precision} {shape}")
+
+
+# --------------------------------------------------------------------------
+# the 3-D disk-plus-envelope workload at a size the oracle runs in seconds
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("tau", [0.1, 1.0, 10.0, 100.0])
+def test_disk3d_reduced(tau):
+    w = _w3(256, 32, 8, 79, tau=tau, seed=1)
+    orc = _parity.oracle_for(w)
+    q, a, e = _parity.run_gpu(w, "fp32_kahan")
+    stats = _parity.assert_parity(w, q, a, e, orc, label=f"tau={tau}")
+    assert stats["n_mask"] > 1000
+
+
+# --------------------------------------------------------------------------
+# full 256 x 128 x 256, 79-bin size in the bench's launch configuration:
+# sampled rays against the oracle, energy of the whole grid
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("tau", [1.0, 100.0])
+def test_disk3d_full_sampled(tau):
+    w = _w3(256, 128, 256, 79, tau=tau, seed=1)
+    q, a, e = _parity.run_gpu(w, "fp32_kahan")
+    assert abs(e.rel_err) < 1e-6
+    g = w.grid
+    rng = np.random.default_rng(7)
+    rays = rng.choice(g.ntheta * g.nphi, size=384, replace=False)
+    rho = w.rho32().reshape(-1, g.nr)[rays]
+    td = w.tdust32().reshape(-1, g.nr)[rays]
+    # q and a of a ray depend on its own cells and the radial grid only
+    th = np.linspace(0.0, math.pi, len(rays) + 1)
+    orc = oracle.irradiate(g.r_if, th, np.array([0.0, 2 * math.pi]), w.t_star, w.r_star, w.nu,
+                           w.kappa, w.t_sub, rho.astype(np.float64), td.astype(np.float64))
+    qs, as_ = q.reshape(-1, g.nr)[rays], a.reshape(-1, g.nr)[rays]
+    dom = _pins.solid_angles(g.theta_if, g.phi_if).reshape(-1)[rays]
+    p_cell = orc.q_abs.reshape(len(rays), g.nr) * dom[:, None] * _pins.shell_volumes(g.r_if)[None, :]
+    lstar = 4 * math.pi * w.r_star ** 2 * oracle.sigma_sb() * w.t_star ** 4
+    m = p_cell > 1e-12 * lstar
+    assert m.sum() > 1000
+    oq = orc.q_abs.reshape(len(rays), g.nr)
+    oa = orc.a_rad.reshape(len(rays), g.nr)
+    assert np.max(np.abs(qs[m] - oq[m]) / oq[m]) <= 1e-5
+    assert np.max(np.abs(as_[m] - oa[m]) / oa[m]) <= 1e-5
+    assert np.all(np.isfinite(q)) and np.all(np.isfinite(a))
+
+
+def test_disk3d_full_energy_against_oracle():
+    """Whole-grid absorbed and escaped power at the full size, against the oracle
+    run on every ray (OpenMP over rays)."""
+    w = _w3(256, 128, 256, 79, tau=1.0, seed=1)
+    q, a, e = _parity.run_gpu(w, "fp32_kahan")
+    orc = oracle.irradiate_workload(w, nthreads=oracle.max_threads())
+    assert abs(e.rel_err) < 1e-6
+    assert abs(e.e_abs - orc.e_abs) < 1e-6 * orc.l_star
+    assert abs(e.e_esc - orc.e_esc) < 1e-6 * orc.l_star
+    mq, _ = _parity.masks(w, orc)
+    rq = np.abs(q[mq] - orc.q_abs[mq]) / orc.q_abs[mq]
+    assert rq.max() <= 1e-5
+
+
+# --------------------------------------------------------------------------
+# degenerate and edge cases
+# --------------------------------------------------------------------------
+def test_thin_limit_gpu():
+    """rho = 0: nothing absorbed, everything escapes, force = kappa-weighted flux / c."""
+    w = _w3(40, 6, 3, 24, tau=1.0)
+    rho = np.zeros(w.grid.shape)
+    td = np.full(w.grid.shape, 50.0)
+    orc = _parity.oracle_for(w, rho=rho, tdust=td)
+    q, a, e = _parity.run_gpu(w, rho=rho, tdust=td)
+    assert np.all(q == 0.0)
+    assert e.e_abs == 0.0 and abs(e.e_esc / e.l_star - 1) < 1e-6
+    np.testing.assert_allclose(a, orc.a_rad, rtol=1e-5)
+
+
+def test_all_sublimated_gpu():
+    w = _w3(40, 6, 3, 24, tau=100.0)
+    td = np.full(w.grid.shape, 2000.0)
+    q, a, e = _parity.run_gpu(w, tdust=td)
+    assert np.all(q == 0.0) and np.all(a == 0.0)
+    assert abs(e.e_esc / e.l_star - 1) < 1e-6
+
+
+def test_transparent_bins():
+    """Bins with kappa = 0 never absorb; their flux is added to the escape."""
+    w = _w3(48, 8, 4, 16, tau=30.0)
+    kap = w.kappa.copy()
+    kap[::3] = 0.0
+    orc = _parity.oracle_for(w, kappa=kap)
+    q, a, e = _parity.run_gpu(w, kappa=kap)
+    _parity.assert_parity(w, q, a, e, orc)
+    kap0 = np.zeros_like(kap)
+    q0, a0, e0 = _parity.run_gpu(w, kappa=kap0)
+    assert np.all(q0 == 0.0) and np.all(a0 == 0.0) and abs(e0.e_esc / e0.l_star - 1) < 1e-9
+
+
+def test_gray_single_bin():
+    w = _w3(64, 8, 2, 1, tau=20.0)
+    orc = _parity.oracle_for(w)
+    q, a, e = _parity.run_gpu(w)
+    _parity.assert_parity(w, q, a, e, orc)
+
+
+def test_density_floor_zeros():
+    """The 2-D disk without envelope has polar cells at the 1e-100 floor, which
+    flush to rho = 0 in float32: the force there is the rho -> 0 limit."""
+    w = synth.disk2d(64, 32, 16, tau550=100.0)
+    assert (w.rho32() == 0).any()
+    orc = _parity.oracle_for(w)
+    q, a, e = _parity.run_gpu(w)
+    _parity.assert_parity(w, q, a, e, orc)
+
+
+def test_bf16_table():
+    """kappa rounded to bfloat16 on the device equals the oracle run on the
+    bfloat16-rounded table."""
+    w = _w3(128, 16, 4, 79, tau=10.0)
+    k32 = w.kappa.astype(np.float32)
+    bits = k32.view(np.uint32).astype(np.uint64)
+    rounded = ((bits + 0x7FFF + ((bits >> 16) & 1)) >> 16) << 16  # round to nearest even
+    kb = rounded.astype(np.uint32).view(np.float32).astype(np.float64)
+    orc = _parity.oracle_for(w, kappa=kb)
+    q, a, e = _parity.run_gpu(w, kappa_bf16=True)
+    _parity.assert_parity(w, q, a, e, orc, label="bf16")
+
+
+def test_absorbed_fraction_sweep():
+    """One cell per ray, optical depths 1e-8..80 across the poly/ex2 split: the
+    FP32 absorbed fraction 1 - e^-dtau against the oracle's expm1."""
+    n = 4096
+    g = synth.log_grid(1, n, 1)
+    dtau = np.geomspace(1e-8, 80.0, n)
+    nu = np.array([synth.NU_550NM_HZ])
+    kap = np.array([100.0])
+    rho = (dtau / (kap[0] * (g.r_if[1] - g.r_if[0]))).reshape(g.shape)
+    w = synth.Workload("sweep", g, nu, kap, rho, np.full(g.shape, 50.0))
+    orc = _parity.oracle_for(w)
+    q, a, e = _parity.run_gpu(w)
+    rel = np.abs(q - orc.q_abs) / orc.q_abs
+    assert rel.max() < 3e-6, rel.max()
+
+
+def test_nonfinite_input_is_flagged():
+    import torch
+    from paper_1001_3301_gb300 import Tracer
+    from paper_1001_3301_gb300._lib import RT_ERR_NONFINITE_INPUT, RtError
+    w = _w3(32, 4, 2, 8, tau=1.0)
+    tr = Tracer.from_grid(w.grid)
+    tr.set_opacity_table(w.nu, w.kappa, w.t_sub)
+    tr.set_star(w.t_star, w.r_star)
+    rho = torch.from_numpy(w.rho32()).cuda()
+    td = torch.from_numpy(w.tdust32()).cuda()
+    tr.irradiate(rho, td, energy=True)  # clean
+    for bad in (float("nan"), -1.0, float("inf")):
+        r2 = rho.clone()
+        r2.view(-1)[77] = bad
+        with pytest.raises(RtError) as ei:
+            tr.irradiate(r2, td, energy=True)
+        assert ei.value.status == RT_ERR_NONFINITE_INPUT
+    t2 = td.clone()
+    t2.view(-1)[5] = float("nan")
+    with pytest.raises(RtError):
+        tr.irradiate(rho, t2, energy=True)
+    tr.irradiate(rho, td, energy=True)  # clean again: the flag is per call
+    tr.close()
+
+
+def test_not_configured_and_bad_args():
+    import torch
+    from paper_1001_3301_gb300 import Tracer
+    from paper_1001_3301_gb300._lib import RT_ERR_INVALID_ARG, RT_ERR_NOT_CONFIGURED, RtError
+    g = synth.log_grid(8, 2, 1)
+    tr = Tracer.from_grid(g)
+    x = torch.zeros(g.shape, device="cuda")
+    with pytest.raises(RtError) as ei:
+        tr.irradiate(x, x)
+    assert ei.value.status == RT_ERR_NOT_CONFIGURED
+    tr.set_star(5800.0, 7e10)
+    with pytest.raises(RtError) as ei:
+        tr.irradiate(x, x)
+    assert ei.value.status == RT_ERR_NOT_CONFIGURED
+    with pytest.raises(RtError) as ei:
+        tr.set_opacity_table([2e14, 1e14], [1.0, 2.0], 1500.0)
+    assert ei.value.status == RT_ERR_INVALID_ARG
+    with pytest.raises(RtError) as ei:
+        tr.set_tuning(3, 4)
+    assert ei.value.status == RT_ERR_INVALID_ARG
+    tr.close()
+
+
+# --------------------------------------------------------------------------
+# set-up, determinism, host-buffer path, autotuner
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n_nu,t", [(1, 5800.0), (32, 5800.0), (79, 5800.0), (128, 5800.0),
+                                    (16, 40000.0), (16, 300.0)])
+def test_device_bins_match_oracle(n_nu, t):
+    """Eq. 20 on the device (Gauss-Legendre) against the oracle (series)."""
+    from paper_1001_3301_gb300 import Tracer
+    nu = synth.nu_bins(n_nu)
+    g = synth.log_grid(4, 2, 1)
+    tr = Tracer.from_grid(g)
+    tr.set_opacity_table(nu, synth.kappa_synth(nu), 1500.0)
+    tr.set_star(t, 7e10)
+    f_dev = tr.bins()
+    tr.close()
+    f_orc = oracle.planck_bins(t, nu)
+    big = f_orc > 1e-25 * f_orc.sum()
+    np.testing.assert_allclose(f_dev[big], f_orc[big], rtol=1e-12)
+
+
+def test_repeat_calls_bitwise_and_host_path():
+    import torch
+    from paper_1001_3301_gb300 import Tracer
+    w = _w3(100, 12, 6, 40, tau=10.0)
+    tr = Tracer.from_grid(w.grid)
+    tr.set_opacity_table(w.nu, w.kappa, w.t_sub)
+    tr.set_star(w.t_star, w.r_star)
+    rho = torch.from_numpy(w.rho32()).cuda()
+    td = torch.from_numpy(w.tdust32()).cuda()
+    q1, a1, e1 = tr.irradiate(rho, td, energy=True)
+    q2, a2, e2 = tr.irradiate(rho, td, energy=True)
+    assert torch.equal(q1, q2) and torch.equal(a1, a2) and e1.e_abs == e2.e_abs
+    hq = np.empty(w.grid.shape, np.float32)
+    ha = np.empty(w.grid.shape, np.float32)
+    e3 = tr.irradiate_host(w.rho32(), w.tdust32(), hq, ha, energy=True)
+    assert np.array_equal(hq, q1.cpu().numpy()) and np.array_equal(ha, a1.cpu().numpy())
+    assert e3.e_abs == e1.e_abs
+    # pinned torch buffers
+    pr = torch.from_numpy(w.rho32()).pin_memory()
+    pt = torch.from_numpy(w.tdust32()).pin_memory()
+    pq = torch.empty(w.grid.shape, dtype=torch.float32).pin_memory()
+    pa = torch.empty(w.grid.shape, dtype=torch.float32).pin_memory()
+    tr.irradiate_host(pr, pt, pq, pa)
+    assert torch.equal(pq, q1.cpu())
+    tr.close()
+
+
+def test_autotune_and_streams():
+    import torch
+    from paper_1001_3301_gb300 import Tracer
+    w = _w3(128, 32, 16, 32, tau=10.0)
+    orc = _parity.oracle_for(w)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        tr = Tracer.from_grid(w.grid)
+        tr.set_opacity_table(w.nu, w.kappa, w.t_sub)
+        tr.set_star(w.t_star, w.r_star)
+        rho = torch.from_numpy(w.rho32()).cuda()
+        td = torch.from_numpy(w.tdust32()).cuda()
+        q = torch.empty_like(rho)
+        a = torch.empty_like(rho)
+        shape = tr.autotune(rho, td, q, a, reps=2)
+        assert shape in [tuple(x) for x in SHAPES["fp32_kahan"]]
+        q, a, e = tr.irradiate(rho, td, q, a, energy=True)
+    s.synchronize()
+    _parity.assert_parity(w, q.double().cpu().numpy(), a.double().cpu().numpy(), e, orc)
+    tr.close()
+
+
+def test_ex2_accuracy():
+    """The hardware exp2 the FP32 tracer uses stays within 2^-21 relative over the
+    range the tracer feeds it; the split point of the absorbed fraction relies on it."""
+    import torch
+    from paper_1001_3301_gb300 import probe_ex2
+    x = torch.linspace(-100.0, 0.0, 2_000_001, dtype=torch.float32, device="cuda")
+    y = probe_ex2(x).double().cpu().numpy()
+    ref = np.exp2(x.double().cpu().numpy())
+    rel = np.abs(y - ref) / ref
+    assert rel.max() < 2.0 ** -21, rel.max()
