@@ -36,7 +36,9 @@ METRIC = "ray-traced cell·freq updates/s (plain vs MLP surrogate @≤1e-3 err);
 UNIT = "cell·nu updates/s"
 TAUS = (0.1, 1.0, 10.0, 100.0)
 NR, NTH, NPH, NNU = 256, 128, 256, 79
-WORKLOAD = "disk3d 256x128x256 (r,theta,phi), 79 nu bins, tau550 in {0.1,1,10,100}, env+20% lognormal, T_dust U(20,1600)"
+def workload_name(taus):
+    return (f"disk3d {NR}x{NTH}x{NPH} (r,theta,phi), {NNU} nu bins, tau550 in "
+            f"{{{','.join(f'{t:g}' for t in taus)}}}, env+20% lognormal, T_dust U(20,1600)")
 EXP_PER_CELL_NU = 2  # e^{-tau_in} and e^{-dtau} per (cell, bin): the direct form
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_trace_disk3d_256x128x256_nu79.md")
 
@@ -50,6 +52,10 @@ def parse():
     p.add_argument("--precision", default="fp32_kahan")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--grids", default=",".join(str(t) for t in TAUS),
+                   help="comma-separated tau550 values of the grids in one step")
+    p.add_argument("--shape", default=None,
+                   help="force the tracer shape 'kind,cells_per_lane,warps,min_blocks' (skips the autotuner)")
     return p.parse_args()
 
 
@@ -60,8 +66,8 @@ def dist_env():
     return rank, world, local
 
 
-def workloads(seed_offset=0):
-    return [synth.disk3d(NR, NTH, NPH, n_nu=NNU, tau550=t, seed=1 + seed_offset) for t in TAUS]
+def workloads(seed_offset=0, taus=TAUS):
+    return [synth.disk3d(NR, NTH, NPH, n_nu=NNU, tau550=t, seed=1 + seed_offset) for t in taus]
 
 
 # --------------------------------------------------------------------------
@@ -164,21 +170,21 @@ def cpu_baseline(ws, target_s=12.0):
     import oracle
     oracle.build()
     cores = oracle.max_threads()
-    w = ws[1]
+    w = ws[min(1, len(ws) - 1)]
     probe_rays = 64
     dt = oracle_sample(w, probe_rays, cores)
     n_rays = int(min(w.grid.ntheta * w.grid.nphi, max(probe_rays, probe_rays * target_s / max(dt, 1e-3))))
     dt = oracle_sample(w, n_rays, cores)
     units = n_rays * w.grid.nr * len(w.nu)
     return {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n_rays} evenly spaced rays x {w.grid.nr} cells x {len(w.nu)} bins of the tau550=1 grid "
+            "sample": f"{n_rays} evenly spaced rays x {w.grid.nr} cells x {len(w.nu)} bins of the tau550={w.tau550:g} grid "
                       f"({units:.3e} cell-nu updates, {dt:.1f} s, OpenMP over rays)"}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    ws = workloads()
+    ws = workloads(taus=tuple(float(x) for x in args.grids.split(",")))
     import oracle
     oracle.build()
     cores = oracle.max_threads()
@@ -196,7 +202,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_per_step":
+            "data": "synthetic", "config": {"workload": workload_name([w.tau550 for w in ws]), "sample_per_step":
                                             f"{n_rays} rays of each of the 4 grids"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"per step {n_rays} rays x {NR} cells x {NNU} bins of each tau grid"},
@@ -216,7 +222,8 @@ def run_ours(args, rank, world, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1001_3301_gb300 import Tracer, probe_alu_rates
 
-    ws = workloads(seed_offset=rank)
+    taus = tuple(float(x) for x in args.grids.split(","))
+    ws = workloads(seed_offset=rank, taus=taus)
     stream = torch.cuda.current_stream()
     tracers, rho, td, q, a = [], [], [], [], []
     for w in ws:
@@ -229,8 +236,11 @@ def run_ours(args, rank, world, local):
         q.append(torch.empty(w.grid.shape, dtype=torch.float32, device="cuda"))
         a.append(torch.empty(w.grid.shape, dtype=torch.float32, device="cuda"))
     # launch shape from the autotuner (untimed; cached for same-shape grids)
-    shape = tracers[0].autotune(rho[0], td[0], q[0], a[0], reps=3)
-    for tr in tracers[1:]:
+    if args.shape:
+        shape = tuple(int(x) for x in args.shape.split(","))
+    else:
+        shape = tracers[0].autotune(rho[0], td[0], q[0], a[0], reps=3)
+    for tr in tracers:
         tr.set_tuning(*shape)
 
     units_per_step = sum(w.grid.ncells * len(w.nu) for w in ws)
@@ -324,10 +334,11 @@ def run_ours(args, rank, world, local):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded disk+envelope density, uniform dust temperatures, synthetic kappa_nu)",
-            "config": {"workload": WORKLOAD, "precision": args.precision, "grids_per_step": len(ws),
+            "config": {"workload": workload_name(taus), "precision": args.precision, "grids_per_step": len(ws),
                        "cells_per_step": sum(w.grid.ncells for w in ws), "nu_bins": NNU,
-                       "launch_shape": {"cells_per_lane": shape[0], "warps": shape[1]},
-                       "l2": "no flush: inputs+outputs 537 MB per step exceed the 129 MB L2",
+                       "launch_shape": {"kernel": ["tile", "ray"][shape[0]], "cells_per_lane": shape[1],
+                                        "warps": shape[2], "min_blocks_per_sm": shape[3]},
+                       "l2": f"no flush: inputs+outputs {16 * sum(w.grid.ncells for w in ws) / 1e6:.0f} MB per step exceed the 129 MB L2",
                        "replicas_per_rank": 1},
             "roofline": {"bound": "alu", "unit": "Gop/s (MUFU ex2)", "achieved": achieved,
                          "peak": peak, "frac": achieved / peak, "traffic": traffic,

@@ -151,14 +151,30 @@ int rt_energy_last(rt_ctx *ctx, rt_energy *out);
  * f_bin[n_nu]. Synchronises. Errors: RT_ERR_NOT_CONFIGURED, RT_ERR_CUDA. */
 int rt_get_bins(rt_ctx *ctx, double *f_bin);
 
-/* rt_set_tuning -- force the launch shape of the fused tracer: cells_per_lane
- * (consecutive cells of the flattened ray array each thread owns) and
- * warps_per_block. Both 0 restores automatic choice. Unsupported pairs return
- * RT_ERR_INVALID_ARG; rt_get_tuning reports the pair in use. */
-int rt_set_tuning(rt_ctx *ctx, int cells_per_lane, int warps_per_block);
-int rt_get_tuning(const rt_ctx *ctx, int *cells_per_lane, int *warps_per_block);
+/* Tracer kernels. RT_KERNEL_TILE: the flattened ray array in tiles of
+ * 32 * warps * cells_per_lane cells, any nr (rays straddle threads and tiles).
+ * RT_KERNEL_RAY: one warp per ray, each lane cells_per_lane consecutive cells of
+ * it; only for nr <= 32 * cells_per_lane. Neither applies to the FP64 mode's
+ * ray kernel, which does not exist (FP64 always uses tiles). */
+#define RT_KERNEL_TILE 0
+#define RT_KERNEL_RAY  1
 
-/* rt_autotune -- time every supported launch shape on the given device buffers
+/* rt_set_tuning -- force the tracer kernel and its launch shape: kind
+ * (RT_KERNEL_TILE or RT_KERNEL_RAY), cells_per_lane, warps_per_block and
+ * min_blocks_per_sm (the resident CTAs per SM the registers are capped for; 0 =
+ * the first compiled variant). cells_per_lane = warps_per_block = 0 restores
+ * automatic choice. Shapes that are not compiled in or do not fit the grid return
+ * RT_ERR_INVALID_ARG. rt_get_tuning reports the shape in use; rt_list_tunings
+ * writes the shapes that apply to this context's grid and precision (up to max of
+ * them) into the four arrays and returns their number (negative status on error). */
+int rt_set_tuning(rt_ctx *ctx, int kind, int cells_per_lane, int warps_per_block,
+                  int min_blocks_per_sm);
+int rt_get_tuning(const rt_ctx *ctx, int *kind, int *cells_per_lane, int *warps_per_block,
+                  int *min_blocks_per_sm);
+int rt_list_tunings(const rt_ctx *ctx, int *kinds, int *cells_per_lane, int *warps_per_block,
+                    int *min_blocks_per_sm, int max);
+
+/* rt_autotune -- time every applicable kernel and launch shape on the given device buffers
  * (same meaning as rt_irradiate; q_abs and a_rad are overwritten), keep the fastest
  * for this context and remember it for grids of the same shape class in this
  * process. reps >= 1 timed calls per shape. Synchronises. Errors: as rt_irradiate. */

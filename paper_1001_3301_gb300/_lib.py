@@ -20,6 +20,9 @@ RT_ERR_TIMEOUT = -4
 RT_ERR_NONFINITE_INPUT = -5
 RT_ERR_NO_MEMORY = -6
 
+RT_KERNEL_TILE = 0
+RT_KERNEL_RAY = 1
+
 RT_FP32_KAHAN = 0
 RT_FP32_PLAIN = 1
 RT_FP64 = 2
@@ -56,8 +59,9 @@ SIGNATURES = {
     "rt_irradiate_host": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(RtEnergy)]),
     "rt_energy_last": (_I, [_P, ctypes.POINTER(RtEnergy)]),
     "rt_get_bins": (_I, [_P, _DP]),
-    "rt_set_tuning": (_I, [_P, _I, _I]),
-    "rt_get_tuning": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "rt_set_tuning": (_I, [_P, _I, _I, _I, _I]),
+    "rt_get_tuning": (_I, [_P] + [ctypes.POINTER(_I)] * 4),
+    "rt_list_tunings": (_I, [_P] + [ctypes.POINTER(_I)] * 4 + [_I]),
     "rt_autotune": (_I, [_P, _P, _P, _P, _P, _I]),
     "rt_destroy": (None, [_P]),
     "rt_last_error": (ctypes.c_char_p, [_P]),

@@ -27,6 +27,7 @@ struct rt_ctx {
     float4 *rtab = nullptr;
     double4 *rtab64 = nullptr;
     double *domega = nullptr;
+    float *domega32 = nullptr;
     // bins (device)
     double *nu_mid = nullptr, *kappa = nullptr, *f_bin = nullptr;
     NuEntry *nu_tab = nullptr;
@@ -49,7 +50,7 @@ struct rt_ctx {
     bool have_table = false, have_star = false, configured = false;
     double t_sub = 0.0, t_star = 0.0, r_star = 0.0;
     DevScalars sc_h{};
-    Shape shape{0, 0};
+    Shape shape{0, 0, 0, 0};
     bool shape_forced = false;
     unsigned seq = 0;
     long long last_ntiles = 0;
@@ -96,6 +97,16 @@ bool increasing(const double *a, int n)
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, long long, int>, Shape> g_tune_cache;
 
+long long total_tiles(const rt_ctx *c, Shape s);
+
+// every compiled shape that applies to this context: tile shapes, then ray shapes
+int all_shapes(const rt_ctx *c, Shape *out, int max_out)
+{
+    int n = rt::trace_shapes(c->precision, out, max_out);
+    if (c->precision != RT_FP64) n += rt::ray_shapes(c->precision, c->nr, out + n, max_out - n);
+    return n;
+}
+
 Shape default_shape(const rt_ctx *c)
 {
     {
@@ -103,13 +114,24 @@ Shape default_shape(const rt_ctx *c)
         auto it = g_tune_cache.find(std::make_tuple(c->precision, c->nr, c->nrays, c->sc_h.nnu_pad));
         if (it != g_tune_cache.end()) return it->second;
     }
-    // Prefer the widest tile that still gives every SM several tiles.
-    Shape cand[16];
-    const int n = rt::trace_shapes(c->precision, cand, 16);
+    // Prefer the warp-per-ray kernel with the fewest cells per lane when the rays
+    // fill at least 3/4 of its 32 C cells; else the widest tile that still gives
+    // every SM several tiles.
+    if (c->precision != RT_FP64) {
+        Shape rs[32];
+        const int nrs = rt::ray_shapes(c->precision, c->nr, rs, 32);
+        int bi = -1;
+        for (int i = 0; i < nrs; ++i)
+            if (4 * c->nr >= 3 * 32 * rs[i].cells_per_lane && (bi < 0 || rs[i].cells_per_lane < rs[bi].cells_per_lane))
+                bi = i;
+        if (bi >= 0) return rs[bi];
+    }
+    Shape cand[32];
+    const int n = rt::trace_shapes(c->precision, cand, 32);
     Shape best = cand[0];
     long long best_t = 0;
     for (int i = 0; i < n; ++i) {
-        const long long tiles = (c->L + rt::trace_tile_cells(cand[i]) - 1) / rt::trace_tile_cells(cand[i]);
+        const long long tiles = total_tiles(c, cand[i]);
         const long long tc = rt::trace_tile_cells(cand[i]);
         if (tiles >= 8LL * 152) {
             if (tc > best_t) { best = cand[i]; best_t = tc; }
@@ -118,7 +140,7 @@ Shape default_shape(const rt_ctx *c)
     if (best_t == 0) {  // small grid: most tiles wins, then the smaller tile
         long long most = -1;
         for (int i = 0; i < n; ++i) {
-            const long long tiles = (c->L + rt::trace_tile_cells(cand[i]) - 1) / rt::trace_tile_cells(cand[i]);
+            const long long tiles = total_tiles(c, cand[i]);
             if (tiles > most) { most = tiles; best = cand[i]; }
         }
     }
@@ -134,7 +156,8 @@ int finalize(rt_ctx *c)
                                           c->sc, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, "setup_bins", e);
     e = rt::launch_setup_geometry(c->nr, c->ntheta, c->nphi, c->r_if, c->theta_if, c->phi_if,
-                                  c->t_star, c->rtab, c->rtab64, c->domega, c->sc, c->stream);
+                                  c->t_star, c->rtab, c->rtab64, c->domega, c->domega32, c->sc,
+                                  c->stream);
     if (e != cudaSuccess) return cuda_fail(c, "setup_geometry", e);
     RT_CK(c, cudaMemcpyAsync(&c->sc_h, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
     RT_CK(c, cudaStreamSynchronize(c->stream));
@@ -155,32 +178,61 @@ int ensure_partials(rt_ctx *c, long long ntiles)
     return RT_OK;
 }
 
+// Number of tiles of one grid; rays are launched in chunks of at most
+// kMaxLaunchCells flattened cells (32-bit indexing inside the kernel).
+long long chunk_rays(const rt_ctx *c) { return rt::kMaxLaunchCells / (c->nr + 1); }
+
+long long total_tiles(const rt_ctx *c, Shape s)
+{
+    const long long T = rt::trace_tile_cells(s), cr = chunk_rays(c);
+    long long tiles = 0;
+    for (long long r0 = 0; r0 < c->nrays; r0 += cr) {
+        const long long nr_c = (c->nrays - r0 < cr) ? c->nrays - r0 : cr;
+        tiles += (s.kind == rt::kKindRay) ? (nr_c + s.warps - 1) / s.warps
+                                          : (nr_c * (c->nr + 1) + T - 1) / T;
+    }
+    return tiles;
+}
+
 int trace(rt_ctx *c, const float *rho, const float *td, float *q, float *a, Shape s)
 {
-    const long long ntiles = (c->L + rt::trace_tile_cells(s) - 1) / rt::trace_tile_cells(s);
-    int st = ensure_partials(c, ntiles);
+    // at most one persistent CTA per tile per chunk
+    int st = ensure_partials(c, total_tiles(c, s));
     if (st != RT_OK) return st;
     rt::TraceArgs args;
-    args.rho = rho;
-    args.tdust = td;
-    args.q = q;
-    args.a = a;
     args.nu = c->nu_tab;
     args.kap = c->kap;
     args.nu64 = c->nu64;
     args.rtab = c->rtab;
     args.rtab64 = c->rtab64;
-    args.domega = c->domega;
-    args.partials = c->partials;
     args.bad_input = c->bad;
     args.seq = ++c->seq;
-    args.L = c->L;
+    args.r1div = rt::FastDiv::make((unsigned)c->nr + 1u);
     args.nr = c->nr;
     args.nnu_pad = c->sc_h.nnu_pad;
+    args.n_active = c->sc_h.n_active;
     args.t_sub = (float)c->t_sub;
-    cudaError_t e = rt::launch_trace(c->precision, s, args, ntiles, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, "trace kernel launch", e);
-    c->last_ntiles = ntiles;
+    const long long T = rt::trace_tile_cells(s), cr = chunk_rays(c);
+    long long npart = 0;
+    for (long long r0 = 0; r0 < c->nrays; r0 += cr) {
+        const long long nr_c = (c->nrays - r0 < cr) ? c->nrays - r0 : cr;
+        const size_t off = (size_t)r0 * c->nr;
+        args.rho = rho + off;
+        args.tdust = td + off;
+        args.q = q + off;
+        args.a = a + off;
+        args.domega = c->domega + r0;
+        args.domega32 = c->domega32 + r0;
+        args.partials = c->partials + npart;
+        args.L = (unsigned)(nr_c * (c->nr + 1));
+        args.nrays = (unsigned)nr_c;
+        const long long nt = (nr_c * (c->nr + 1) + T - 1) / T;
+        unsigned grid = 0;
+        cudaError_t e = rt::launch_trace(c->precision, s, args, (unsigned)nt, c->stream, &grid);
+        if (e != cudaSuccess) return cuda_fail(c, "trace kernel launch", e);
+        npart += grid;
+    }
+    c->last_ntiles = npart;
     c->traced = true;
     return RT_OK;
 }
@@ -209,7 +261,7 @@ int check_call(rt_ctx *c, const void *rho, const void *td, const void *q, const 
 
 void free_all(rt_ctx *c)
 {
-    void *ptrs[] = {c->r_if, c->theta_if, c->phi_if, c->rtab, c->rtab64, c->domega, c->nu_mid,
+    void *ptrs[] = {c->r_if, c->theta_if, c->phi_if, c->rtab, c->rtab64, c->domega, c->domega32, c->nu_mid,
                     c->kappa, c->f_bin, c->nu_tab, c->kap, c->nu64, c->sc, c->partials, c->bad,
                     c->energy_d, c->h_rho, c->h_t, c->h_q, c->h_a};
     for (void *p : ptrs)
@@ -260,6 +312,7 @@ int rt_create(const rt_grid_desc *g, void *cuda_stream, rt_ctx **out)
     ok = ok && dalloc(&c->rtab, g->nr) == cudaSuccess;
     ok = ok && dalloc(&c->rtab64, g->nr) == cudaSuccess;
     ok = ok && dalloc(&c->domega, (size_t)nrays) == cudaSuccess;
+    ok = ok && dalloc(&c->domega32, (size_t)nrays) == cudaSuccess;
     ok = ok && dalloc(&c->nu_mid, RT_MAX_NU) == cudaSuccess;
     ok = ok && dalloc(&c->kappa, RT_MAX_NU) == cudaSuccess;
     ok = ok && dalloc(&c->f_bin, RT_MAX_NU) == cudaSuccess;
@@ -387,7 +440,7 @@ int rt_get_bins(rt_ctx *ctx, double *f_bin)
     return RT_OK;
 }
 
-int rt_set_tuning(rt_ctx *ctx, int cells_per_lane, int warps_per_block)
+int rt_set_tuning(rt_ctx *ctx, int kind, int cells_per_lane, int warps_per_block, int min_blocks_per_sm)
 {
     if (!ctx) return RT_ERR_INVALID_ARG;
     if (cells_per_lane == 0 && warps_per_block == 0) {
@@ -395,19 +448,43 @@ int rt_set_tuning(rt_ctx *ctx, int cells_per_lane, int warps_per_block)
         if (ctx->configured) ctx->shape = default_shape(ctx);
         return RT_OK;
     }
-    if (!rt::trace_shape_supported(ctx->precision, cells_per_lane, warps_per_block))
-        return fail(ctx, RT_ERR_INVALID_ARG, "launch shape not compiled in for this precision");
-    ctx->shape = Shape{cells_per_lane, warps_per_block};
-    ctx->shape_forced = true;
+    Shape all[64];
+    const int n = all_shapes(ctx, all, 64);
+    for (int i = 0; i < n; ++i) {
+        if (all[i].kind == kind && all[i].cells_per_lane == cells_per_lane && all[i].warps == warps_per_block &&
+            (min_blocks_per_sm == 0 || all[i].min_blocks == min_blocks_per_sm)) {
+            ctx->shape = all[i];
+            ctx->shape_forced = true;
+            return RT_OK;
+        }
+    }
+    return fail(ctx, RT_ERR_INVALID_ARG, "launch shape not compiled in, or not applicable to this grid");
+}
+
+int rt_get_tuning(const rt_ctx *ctx, int *kind, int *cells_per_lane, int *warps_per_block, int *min_blocks_per_sm)
+{
+    if (!ctx || !kind || !cells_per_lane || !warps_per_block || !min_blocks_per_sm) return RT_ERR_INVALID_ARG;
+    *kind = ctx->shape.kind;
+    *cells_per_lane = ctx->shape.cells_per_lane;
+    *warps_per_block = ctx->shape.warps;
+    *min_blocks_per_sm = ctx->shape.min_blocks;
     return RT_OK;
 }
 
-int rt_get_tuning(const rt_ctx *ctx, int *cells_per_lane, int *warps_per_block)
+int rt_list_tunings(const rt_ctx *ctx, int *kinds, int *cells_per_lane, int *warps_per_block,
+                    int *min_blocks_per_sm, int max)
 {
-    if (!ctx || !cells_per_lane || !warps_per_block) return RT_ERR_INVALID_ARG;
-    *cells_per_lane = ctx->shape.cells_per_lane;
-    *warps_per_block = ctx->shape.warps;
-    return RT_OK;
+    if (!ctx || max < 0 || (max > 0 && (!kinds || !cells_per_lane || !warps_per_block || !min_blocks_per_sm)))
+        return RT_ERR_INVALID_ARG;
+    Shape all[64];
+    const int n = all_shapes(ctx, all, 64);
+    for (int i = 0; i < n && i < max; ++i) {
+        kinds[i] = all[i].kind;
+        cells_per_lane[i] = all[i].cells_per_lane;
+        warps_per_block[i] = all[i].warps;
+        min_blocks_per_sm[i] = all[i].min_blocks;
+    }
+    return n;
 }
 
 int rt_autotune(rt_ctx *ctx, const float *rho, const float *t_dust, float *q_abs, float *a_rad, int reps)
@@ -415,8 +492,8 @@ int rt_autotune(rt_ctx *ctx, const float *rho, const float *t_dust, float *q_abs
     int st = check_call(ctx, rho, t_dust, q_abs, a_rad);
     if (st != RT_OK) return st;
     if (reps < 1) return fail(ctx, RT_ERR_INVALID_ARG, "reps must be >= 1");
-    Shape cand[16];
-    const int n = rt::trace_shapes(ctx->precision, cand, 16);
+    Shape cand[64];
+    const int n = all_shapes(ctx, cand, 64);
     cudaEvent_t e0, e1;
     RT_CK(ctx, cudaEventCreate(&e0));
     RT_CK(ctx, cudaEventCreate(&e1));

@@ -1,0 +1,266 @@
+// Device helpers shared by the two tracer kernels (rt_trace.cu: flattened tiles;
+// rt_ray.cu: one warp per ray): the hardware exp2, compensated FP32 sums, packed
+// per-lane cell storage, and the per-bin absorbed-fraction classes.
+//
+// FP32 arithmetic per (cell, bin). The exponential g = F_i/F_max e^{-kappa_i N_in}
+// runs on the MUFU unit (ex2.approx). The absorbed fraction 1 - 2^y,
+// y = -kappa dN log2(e) (Eqs. 31-32), is taken from whichever form is exact to well
+// below the accuracy target:
+//   - the Taylor series of 1 - e^{-x} truncated after n terms (n = 1, 2, 3, 5),
+//     where the largest x in the warp keeps the first omitted term x^n/(n+1)! below
+//     5e-7 of the value (FMA pipe only, no cancellation);
+//   - 1 - ex2(y) (MUFU), where every x in the warp is at least 1/8, so the hardware
+//     exp2 error (measured below 1.5e-7) is amplified by at most 7.5;
+//   - both and a per-cell select, for the bins whose x straddles 1/8 in the warp.
+// The bins are sorted by opacity at set-up, so each class is one contiguous range of
+// bins per warp, found with a few ballots; the loops carry no per-bin branch. Two
+// cells share every FMA-pipe instruction (packed f32x2).
+#pragma once
+
+#include <float.h>
+#include <math.h>
+
+#include <type_traits>
+
+#include "rt_internal.cuh"
+
+namespace rt {
+namespace {
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float2 ex2_approx2(float2 x)
+{
+    return make_float2(ex2_approx(x.x), ex2_approx(x.y));
+}
+
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+// Knuth's TwoSum: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Running sums of one ray's column density. KahanSum is a compensated FP32 pair:
+// value = hi + lo; two pairs combine exactly with TwoSum.
+struct KahanSum {
+    float hi, lo;
+    __device__ void zero() { hi = lo = 0.0f; }
+    // one term: Kahan's compensated summation (lo carries the lost low-order part;
+    // error below 2 eps of the sum of the terms, in any order)
+    __device__ void add(float v)
+    {
+        const float y = v + lo;
+        const float t = hi + y;
+        lo = y - (t - hi);
+        hi = t;
+    }
+    __device__ void add(const KahanSum &o)
+    {
+        float s, e;
+        two_sum(o.hi, hi, s, e);
+        hi = s;
+        lo = lo + o.lo + e;
+    }
+    __device__ float value() const { return hi + lo; }
+    __device__ KahanSum shfl_up(int d) const
+    {
+        KahanSum r;
+        r.hi = __shfl_up_sync(0xffffffffu, hi, d);
+        r.lo = __shfl_up_sync(0xffffffffu, lo, d);
+        return r;
+    }
+    __device__ KahanSum shfl_xor(int d) const
+    {
+        KahanSum r;
+        r.hi = __shfl_xor_sync(0xffffffffu, hi, d);
+        r.lo = __shfl_xor_sync(0xffffffffu, lo, d);
+        return r;
+    }
+};
+
+template <typename Real>
+struct PlainSum {  // one accumulator, no compensation
+    Real hi;
+    __device__ void zero() { hi = Real(0); }
+    __device__ void add(Real v) { hi += v; }
+    __device__ void add(const PlainSum &o) { hi += o.hi; }
+    __device__ Real value() const { return hi; }
+    __device__ PlainSum shfl_up(int d) const
+    {
+        PlainSum r;
+        r.hi = __shfl_up_sync(0xffffffffu, hi, d);
+        return r;
+    }
+    __device__ PlainSum shfl_xor(int d) const
+    {
+        PlainSum r;
+        r.hi = __shfl_xor_sync(0xffffffffu, hi, d);
+        return r;
+    }
+};
+
+// the column-density sum of each precision mode
+template <int MODE>
+using ColSum = typename std::conditional<
+    MODE == RT_FP32_KAHAN, KahanSum,
+    typename std::conditional<MODE == RT_FP64, PlainSum<double>, PlainSum<float>>::type>::type;
+
+// Per-lane cell values. In FP32 they are stored as packed pairs (the layout the
+// f32x2 bin loop works on), so no second scalar copy stays alive in registers;
+// get/set with a compile-time j resolve to one register.
+template <typename Real, int C>
+struct Cells {
+    Real v[C];
+    __device__ __forceinline__ Real get(int j) const { return v[j]; }
+    __device__ __forceinline__ void set(int j, Real x) { v[j] = x; }
+};
+template <int C>
+struct Cells<float, C> {
+    float2 v[C / 2];
+    __device__ __forceinline__ float get(int j) const { return (j & 1) ? v[j >> 1].y : v[j >> 1].x; }
+    __device__ __forceinline__ void set(int j, float x)
+    {
+        if (j & 1) v[j >> 1].y = x;
+        else v[j >> 1].x = x;
+    }
+};
+
+// 1 - 2^y = -sum_{k>=1} (y ln2)^k / k!  =  y * sum_{k>=0} p_k y^k,
+// p_k = -ln2^{k+1} / (k+1)!  (Taylor series of 1 - e^{-x} at x = -y ln2 >= 0).
+__host__ __device__ constexpr double taylor_coeff(int k)
+{
+    double c = -kLn2;
+    for (int i = 1; i <= k; ++i) c *= kLn2 / (i + 1);
+    return c;
+}
+
+// Largest x = kappa dN for which n terms keep the first omitted term x^n/(n+1)!
+// below 5e-7 of the value; the last class ends where the MUFU form takes over.
+constexpr double kTrunc = 5e-7;
+constexpr double kXSplit = 0.125;
+__host__ __device__ constexpr double taylor_xmax(int n)
+{
+    // solve x^n / (n+1)! = kTrunc by bisection at compile time
+    double fact = 1.0;
+    for (int i = 2; i <= n + 1; ++i) fact *= i;
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        double p = 1.0;
+        for (int i = 0; i < n; ++i) p *= mid;
+        if (p / fact < kTrunc) lo = mid;
+        else hi = mid;
+    }
+    return lo < kXSplit ? lo : kXSplit;
+}
+
+// |y| thresholds (log2 units) of the classes n = 1..3, and the MUFU split
+constexpr float kYT1 = (float)(taylor_xmax(1) * kLog2e);
+constexpr float kYT2 = (float)(taylor_xmax(2) * kLog2e);
+constexpr float kYT3 = (float)(taylor_xmax(3) * kLog2e);
+constexpr float kYSplit = (float)(kXSplit * kLog2e);
+
+// y * sum_{k<n} p_k y^k for a pair of cells (Horner, packed)
+template <int N>
+__device__ __forceinline__ float2 taylor_fraction(float2 y)
+{
+    float2 p = f2((float)taylor_coeff(N - 1));
+#pragma unroll
+    for (int k = N - 2; k >= 0; --k) p = __ffma2_rn(p, y, f2((float)taylor_coeff(k)));
+    return __fmul2_rn(y, p);
+}
+
+// Bin classes per warp: 1, 2, 3, 5 = Taylor with that many terms, 6 = mixed,
+// 7 = MUFU. The common classes 1 and 2 are unrolled over two bins.
+template <int CLASS, int C>
+__device__ __forceinline__ void bin_range(int i0, int i1, const float4 *s_nu, const float2 (&n2)[C / 2],
+                                          const float2 (&d2)[C / 2], float2 (&a2)[C / 2])
+{
+#pragma unroll(CLASS <= 2 ? 2 : 1)
+    for (int i = i0; i < i1; ++i) {
+        const float4 e = s_nu[i];
+        const float2 nk = make_float2(e.x, e.y), lf = make_float2(e.z, e.w);
+        const float2 nk1 = __fmul2_rn(nk, f2((float)taylor_coeff(0)));  // class 1
+#pragma unroll
+        for (int m = 0; m < C / 2; ++m) {
+            const float2 g = ex2_approx2(__ffma2_rn(nk, n2[m], lf));
+            float2 om;
+            if constexpr (CLASS == 1) {
+                om = __fmul2_rn(nk1, d2[m]);
+            } else {
+                const float2 y = __fmul2_rn(nk, d2[m]);
+                if constexpr (CLASS <= 5) {
+                    om = taylor_fraction<CLASS>(y);
+                } else if constexpr (CLASS == 7) {
+                    om = __ffma2_rn(ex2_approx2(y), f2(-1.0f), f2(1.0f));
+                } else {
+                    const float2 big = __ffma2_rn(ex2_approx2(y), f2(-1.0f), f2(1.0f));
+                    const float2 small = taylor_fraction<5>(y);
+                    om = make_float2(y.x > -kYSplit ? small.x : big.x, y.y > -kYSplit ? small.y : big.y);
+                }
+            }
+            a2[m] = __ffma2_rn(g, om, a2[m]);
+        }
+    }
+}
+
+// Class boundaries of one warp: with the bins sorted by |nk| ascending, b1, b2,
+// b3 and b5 count the bins whose largest |y| = |nk| dmax in the warp stays below
+// the thresholds of 1, 2, 3 and 5 Taylor terms, and bb those whose smallest non-zero
+// |y| = |nk| dmin stays below the MUFU split (bins from bb on are MUFU-only).
+// Warp-uniform results; one pass over the bins, 32 at a time.
+struct BinClasses {
+    int b1, b2, b3, b5, bb;
+};
+__device__ __forceinline__ BinClasses classify_bins(const float4 *s_nu, int n_active, int lane,
+                                                     float dmax, float dmin)
+{
+    BinClasses c{0, 0, 0, 0, 0};
+    for (int c0 = 0; c0 < n_active; c0 += 32) {
+        const int i = c0 + lane;
+        const float ak = (i < n_active) ? -s_nu[i].x : INFINITY;
+        const float ym = ak * dmax, yn = ak * dmin;
+        c.b1 += __popc(__ballot_sync(0xffffffffu, ym < kYT1));
+        c.b2 += __popc(__ballot_sync(0xffffffffu, ym < kYT2));
+        c.b3 += __popc(__ballot_sync(0xffffffffu, ym < kYT3));
+        c.b5 += __popc(__ballot_sync(0xffffffffu, ym < kYSplit));
+        c.bb += __popc(__ballot_sync(0xffffffffu, yn < kYSplit));
+    }
+    c.bb = c.bb > c.b5 ? c.bb : c.b5;
+    return c;
+}
+
+// solid angle of ray r of this launch, in the mode's precision
+template <int MODE>
+__device__ __forceinline__ auto solid_angle(const TraceArgs &p, unsigned r)
+{
+    if constexpr (MODE == RT_FP64) return __ldg(p.domega + r);
+    else return __ldg(p.domega32 + r);
+}
+
+__device__ __forceinline__ double to_double(const KahanSum &s) { return (double)s.hi + (double)s.lo; }
+__device__ __forceinline__ double to_double(const PlainSum<double> &s) { return s.hi; }
+
+// acc += part * w for a compensated (hi, lo) part, or a plain FP64 one
+__device__ __forceinline__ void add_weighted(KahanSum &acc, const KahanSum &part, float w)
+{
+    acc.add(part.hi * w);
+    acc.add(part.lo * w);
+}
+__device__ __forceinline__ void add_weighted(PlainSum<double> &acc, const PlainSum<double> &part, double w)
+{
+    acc.add(part.hi * w);
+}
+
+
+}  // namespace
+}  // namespace rt

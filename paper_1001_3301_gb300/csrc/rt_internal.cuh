@@ -24,7 +24,8 @@ constexpr int kNuPad = 4;
 
 // Per-bin table consumed by the FP32 tracer: nk = -kappa_i log2(e) and
 // lf = log2(F_i / F_max), so F_i/F_max * exp(-kappa_i N) = 2^(nk N + lf).
-// Padding bins have nk = -1, lf = -inf and contribute exactly zero.
+// Only bins with kappa_i > 0 are listed, sorted by kappa ascending; padding bins
+// after them have nk = -1, lf = -inf and contribute exactly zero.
 struct alignas(8) NuEntry {
     float nk;
     float lf;
@@ -41,7 +42,32 @@ struct DevScalars {
     int nnu_pad;           // n_active rounded up to kNuPad (>= kNuPad)
 };
 
-// Arguments of the fused tracer kernel (passed by value).
+// Division by an invariant 32-bit divisor d >= 1 with one multiply-high, two
+// shifts and an add (Granlund & Montgomery 1994, unsigned case), exact for all
+// 32-bit numerators.
+struct FastDiv {
+    unsigned m;
+    int s1, s2;
+    __host__ static FastDiv make(unsigned d)
+    {
+        int l = 0;
+        while ((1ull << l) < d) ++l;  // ceil(log2 d)
+        const unsigned long long m = (((1ull << l) - d) << 32) / d + 1;
+        return FastDiv{(unsigned)m, l > 0 ? 1 : 0, l > 0 ? l - 1 : 0};
+    }
+    __device__ __forceinline__ unsigned div(unsigned n) const
+    {
+        const unsigned t = __umulhi(n, m);
+        return (t + ((n - t) >> s1)) >> s2;
+    }
+};
+
+// Largest flattened length one launch of the tracer covers; longer grids are
+// split into ray chunks by the host.
+constexpr long long kMaxLaunchCells = (1LL << 31) - (1LL << 16);
+
+// Arguments of the fused tracer kernel (passed by value). Field, solid-angle and
+// partials pointers are offset by the host to the launch's first ray / tile.
 struct TraceArgs {
     const float *rho;
     const float *tdust;
@@ -53,27 +79,39 @@ struct TraceArgs {
     const float4 *rtab;       // [nr] (dr, Gq, Ga0, 0)
     const double4 *rtab64;    // [nr] same in FP64
     const double *domega;     // [nrays]
-    double2 *partials;        // [ntiles] (sum of absorbed, sum of escaped) / (R*^2 F_max)
+    const float *domega32;    // [nrays] the same in FP32
+    double2 *partials;        // [CTAs] (sum of absorbed, sum of escaped) / (R*^2 F_max)
     unsigned *bad_input;      // set to `seq` when an input value is invalid
     unsigned seq;
-    long long L;              // flattened length nrays * (nr + 1)
+    unsigned L;               // flattened length of this launch, nrays * (nr + 1)
+    unsigned nrays;           // rays of this launch
+    FastDiv r1div;            // division by nr + 1
     int nr;
     int nnu_pad;
+    int n_active;             // bins with kappa > 0, sorted by kappa ascending
     float t_sub;
 };
 
 // Launch shapes of the fused tracer that are compiled in.
+constexpr int kKindTile = RT_KERNEL_TILE;  // flattened tiles, any nr (rt_trace.cu)
+constexpr int kKindRay = RT_KERNEL_RAY;    // one warp per ray, nr <= 32 C (rt_ray.cu)
 struct Shape {
+    int kind;
     int cells_per_lane;
     int warps;
+    int min_blocks;  // minimum resident CTAs per SM the registers are capped for
 };
 
-// Host-side launchers (rt_trace.cu)
-bool trace_shape_supported(int precision, int cells_per_lane, int warps);
-int trace_shapes(int precision, Shape *out, int max_out);
+// Host-side launchers (rt_trace.cu, rt_ray.cu)
+int trace_shapes(int precision, Shape *out, int max_out);      // tile kernel
+int ray_shapes(int precision, int nr, Shape *out, int max_out);  // ray kernel, 32 C >= nr
 long long trace_tile_cells(Shape s);
-cudaError_t launch_trace(int precision, Shape s, const TraceArgs &args, long long ntiles,
-                         cudaStream_t stream);
+cudaError_t launch_ray_shape(int precision, Shape s, const TraceArgs &args, cudaStream_t stream,
+                             unsigned *grid_out);
+// Launches the persistent tracer over `ntiles` tiles; *grid_out receives the
+// number of CTAs (= energy partials written).
+cudaError_t launch_trace(int precision, Shape s, const TraceArgs &args, unsigned ntiles,
+                         cudaStream_t stream, unsigned *grid_out);
 
 // Set-up kernels (rt_setup.cu)
 cudaError_t launch_setup_bins(int n_nu, const double *nu_mid_dev, const double *kappa_dev,
@@ -83,7 +121,8 @@ cudaError_t launch_setup_bins(int n_nu, const double *nu_mid_dev, const double *
 cudaError_t launch_setup_geometry(int nr, int ntheta, int nphi, const double *r_if_dev,
                                   const double *theta_if_dev, const double *phi_if_dev,
                                   double t_star, float4 *rtab, double4 *rtab64,
-                                  double *domega, DevScalars *sc_dev, cudaStream_t stream);
+                                  double *domega, float *domega32, DevScalars *sc_dev,
+                                  cudaStream_t stream);
 cudaError_t launch_energy_reduce(const double2 *partials, long long ntiles,
                                  const DevScalars *sc_dev, rt_energy *out_dev,
                                  cudaStream_t stream);

@@ -1,0 +1,285 @@
+// Warp-per-ray form of the frequency-dependent tracer (Kuiper et al. 2010,
+// Sect. 2.2-2.3, 3.3.4), for grids whose rays fill most of 32 * C cells.
+//
+// One warp traces one radial ray at a time; lane l owns the cells [l C, (l+1) C)
+// of the ray, so the radial constants of a lane never change and the ray's fields
+// are read straight from HBM in 16-byte vectors (no staging, no block barrier in
+// the ray loop). Per ray:
+//   - dN = [T <= t_sub] rho dr per cell, and its exclusive prefix N_in along the
+//     ray (Eq. 19, tau = 0 at the inner radius): compensated lane sums, then a
+//     compensated warp scan;
+//   - the per-bin loop of rt_device.cuh (Eqs. 17, 20, 31-32) into one accumulator
+//     per cell, with the warp's bin classes chosen from its largest and smallest
+//     column;
+//   - escaping power sum_i F_i/F_max e^{-kappa_i N_total} (Eqs. 33-35), the lanes
+//     sharing the bins;
+//   - q_abs = Gq acc and a_rad = q/(rho c) = Ga0 acc / dN (Sect. 5; the rho -> 0
+//     limit where dN = 0 with dust), stored as 16-byte vectors;
+//   - energy sums per lane, reduced once per CTA at the end.
+// Persistent: the grid holds (SMs x resident CTAs) CTAs that stride over the rays.
+#include "rt_device.cuh"
+
+namespace rt {
+namespace {
+
+template <int C, int W, int MODE, int MINB>
+__global__ void __launch_bounds__(W * 32, MINB) k_ray(const TraceArgs p)
+{
+    static_assert(MODE != RT_FP64, "the FP64 mode uses the tile kernel");
+    static_assert(C % 2 == 0, "cells per lane must be even");
+    using Sum = ColSum<MODE>;
+    using ESum = KahanSum;
+    constexpr int V = (C % 4 == 0) ? 4 : 2;  // vector width of the field loads
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nr = p.nr;
+    const int c0 = lane * C;
+    const int nv = nr - c0 < 0 ? 0 : (nr - c0 > C ? C : nr - c0);  // valid cells of this lane
+
+    // Radial constants of every lane's cells, stored [j][lane] so that the lanes of
+    // a warp read consecutive words (lane l's cell j is radial index l C + j; a
+    // [k] layout would put all 32 lanes on one shared-memory bank).
+    __shared__ float s_dr[C][32], s_gq[C][32], s_ga[C][32];
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *s_kap = reinterpret_cast<float *>(smem);
+    float4 *s_nu = reinterpret_cast<float4 *>(s_kap + p.nnu_pad);
+    __shared__ ESum s_red[W][2];
+
+    for (int i = tid; i < p.nnu_pad; i += W * 32) {
+        s_kap[i] = p.kap[i];
+        const NuEntry e = p.nu[i];
+        s_nu[i] = make_float4(e.nk, e.nk, e.lf, e.lf);
+    }
+    for (int i = tid; i < 32 * C; i += W * 32) {
+        const int l = i / C, j = i % C, k = l * C + j;
+        const float4 g = (k < nr) ? __ldg(&p.rtab[k]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        s_dr[j][l] = g.x;
+        s_gq[j][l] = g.y;
+        s_ga[j][l] = g.z;
+    }
+    __syncthreads();
+
+    // vector access needs every lane start and the field bases 4V-byte aligned
+    const bool vec = (nr % V == 0) &&
+                     ((reinterpret_cast<size_t>(p.rho) | reinterpret_cast<size_t>(p.tdust) |
+                       reinterpret_cast<size_t>(p.q) | reinterpret_cast<size_t>(p.a)) % (4 * V) == 0);
+
+    ESum eabs, eesc;
+    eabs.zero();
+    eesc.zero();
+
+    for (unsigned ray = blockIdx.x * W + warp; ray < p.nrays; ray += gridDim.x * W) {
+        const size_t base = (size_t)ray * nr + c0;
+        float rho[C], td[C];
+        if (vec && nv == C) {
+#pragma unroll
+            for (int j = 0; j < C; j += V) {
+                if constexpr (V == 4) {
+                    const float4 r4 = __ldg(reinterpret_cast<const float4 *>(p.rho + base + j));
+                    const float4 t4 = __ldg(reinterpret_cast<const float4 *>(p.tdust + base + j));
+                    rho[j] = r4.x; rho[j + 1] = r4.y; rho[j + 2] = r4.z; rho[j + 3] = r4.w;
+                    td[j] = t4.x; td[j + 1] = t4.y; td[j + 2] = t4.z; td[j + 3] = t4.w;
+                } else {
+                    const float2 r2 = __ldg(reinterpret_cast<const float2 *>(p.rho + base + j));
+                    const float2 t2 = __ldg(reinterpret_cast<const float2 *>(p.tdust + base + j));
+                    rho[j] = r2.x; rho[j + 1] = r2.y;
+                    td[j] = t2.x; td[j + 1] = t2.y;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                rho[j] = 0.0f;
+                td[j] = 0.0f;
+                if (j < nv) {
+                    rho[j] = __ldg(p.rho + base + j);
+                    td[j] = __ldg(p.tdust + base + j);
+                }
+            }
+        }
+
+        // column density of the dust in each cell, and invalid-input flags
+        Cells<float, C> D, N, acc;
+        unsigned zero_m = 0;
+        bool bad = false;
+        Sum lsum;
+        lsum.zero();
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            const bool dust = td[j] <= p.t_sub;
+            const float d = (j < nv && dust) ? rho[j] * s_dr[j][lane] : 0.0f;
+            D.set(j, d);
+            if (j < nv) {
+                bad |= !(rho[j] >= 0.0f && rho[j] <= FLT_MAX) || (td[j] != td[j]);
+                if (dust && d == 0.0f) zero_m |= 1u << j;
+            }
+            lsum.add(d);
+        }
+        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicMax(p.bad_input, p.seq);
+
+        // exclusive prefix along the ray: warp scan of the lane sums
+        Sum inc = lsum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const Sum o = inc.shfl_up(d);
+            if (lane >= d) inc.add(o);
+        }
+        Sum pre = inc.shfl_up(1);
+        if (lane == 0) pre.zero();
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            N.set(j, pre.value());
+            pre.add(D.get(j));
+            acc.set(j, 0.0f);
+        }
+        const float ntot = __shfl_sync(0xffffffffu, pre.value(), 31);
+
+        // the warp's largest and smallest non-zero column decide each bin's class
+        float dmax = 0.0f, dmin = INFINITY;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            dmax = fmaxf(dmax, D.get(j));
+            if (D.get(j) > 0.0f) dmin = fminf(dmin, D.get(j));
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+            dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+        }
+        const int na = p.n_active;
+        const BinClasses bc = classify_bins(s_nu, na, lane, dmax, dmin);
+        bin_range<1, C>(0, bc.b1, s_nu, N.v, D.v, acc.v);
+        bin_range<2, C>(bc.b1, bc.b2, s_nu, N.v, D.v, acc.v);
+        bin_range<3, C>(bc.b2, bc.b3, s_nu, N.v, D.v, acc.v);
+        bin_range<5, C>(bc.b3, bc.b5, s_nu, N.v, D.v, acc.v);
+        bin_range<6, C>(bc.b5, bc.bb, s_nu, N.v, D.v, acc.v);
+        bin_range<7, C>(bc.bb, na, s_nu, N.v, D.v, acc.v);
+
+        // cells with dust but no column: the rho -> 0 force limit sum_i kappa_i g_i
+        if (__any_sync(0xffffffffu, zero_m != 0u)) {
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                if (__any_sync(0xffffffffu, (zero_m >> j) & 1u)) {
+                    float s = 0.0f;
+                    for (int i = 0; i < p.nnu_pad; ++i)
+                        s = fmaf(s_kap[i], ex2_approx(fmaf(s_nu[i].x, N.get(j), s_nu[i].z)), s);
+                    if ((zero_m >> j) & 1u) D.set(j, s);
+                }
+            }
+        }
+
+        // escaping power of the ray, the lanes sharing the bins
+        const float w = __ldg(p.domega32 + ray);
+        {
+            float s = 0.0f;
+            for (int i = lane; i < p.nnu_pad; i += 32) s += ex2_approx(fmaf(s_nu[i].x, ntot, s_nu[i].z));
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) eesc.add(s * w);
+        }
+
+        // outputs and the lane's absorbed power
+        float qv[C], av[C];
+        float lane_abs = 0.0f;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            const float aj = acc.get(j), dj = D.get(j);
+            const bool zc = (zero_m >> j) & 1u;
+            qv[j] = zc ? 0.0f : s_gq[j][lane] * aj;
+            av[j] = s_ga[j][lane] * (zc ? dj : (dj > 0.0f ? __fdividef(aj, dj) : 0.0f));
+            lane_abs += (j < nv && !zc) ? aj : 0.0f;
+        }
+        eabs.add(lane_abs * w);
+        if (vec && nv == C) {
+#pragma unroll
+            for (int j = 0; j < C; j += V) {
+                if constexpr (V == 4) {
+                    *reinterpret_cast<float4 *>(p.q + base + j) = make_float4(qv[j], qv[j + 1], qv[j + 2], qv[j + 3]);
+                    *reinterpret_cast<float4 *>(p.a + base + j) = make_float4(av[j], av[j + 1], av[j + 2], av[j + 3]);
+                } else {
+                    *reinterpret_cast<float2 *>(p.q + base + j) = make_float2(qv[j], qv[j + 1]);
+                    *reinterpret_cast<float2 *>(p.a + base + j) = make_float2(av[j], av[j + 1]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                if (j < nv) {
+                    p.q[base + j] = qv[j];
+                    p.a[base + j] = av[j];
+                }
+            }
+        }
+    }
+
+    for (int o = 16; o > 0; o >>= 1) {
+        eabs.add(eabs.shfl_xor(o));
+        eesc.add(eesc.shfl_xor(o));
+    }
+    if (lane == 0) { s_red[warp][0] = eabs; s_red[warp][1] = eesc; }
+    __syncthreads();
+    if (tid == 0) {
+        ESum sa = s_red[0][0], se = s_red[0][1];
+        for (int w2 = 1; w2 < W; ++w2) { sa.add(s_red[w2][0]); se.add(s_red[w2][1]); }
+        p.partials[blockIdx.x] = make_double2(to_double(sa), to_double(se));
+    }
+}
+
+template <int C, int W, int MODE, int MINB>
+cudaError_t launch_ray(const TraceArgs &a, unsigned, cudaStream_t stream, unsigned *grid_out)
+{
+    const size_t smem = (size_t)a.nnu_pad * (sizeof(float) + 16) + 16;
+    auto kern = k_ray<C, W, MODE, MINB>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    unsigned grid = (unsigned)nsm * (unsigned)per_sm;
+    const unsigned need = (a.nrays + W - 1) / W;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    kern<<<grid, W * 32, smem, stream>>>(a);
+    *grid_out = grid;
+    return cudaGetLastError();
+}
+
+struct RayEntry {
+    int precision, c, w, minb;
+    cudaError_t (*fn)(const TraceArgs &, unsigned, cudaStream_t, unsigned *);
+};
+
+#define RT_RAY(P, C, W, MB) {P, C, W, MB, &launch_ray<C, W, P, MB>}
+const RayEntry kRayShapes[] = {
+    RT_RAY(RT_FP32_KAHAN, 2, 4, 8),  RT_RAY(RT_FP32_KAHAN, 4, 4, 8),  RT_RAY(RT_FP32_KAHAN, 6, 4, 8),
+    RT_RAY(RT_FP32_KAHAN, 8, 4, 6),  RT_RAY(RT_FP32_KAHAN, 8, 4, 8),  RT_RAY(RT_FP32_KAHAN, 12, 4, 5),
+    RT_RAY(RT_FP32_KAHAN, 16, 4, 3), RT_RAY(RT_FP32_KAHAN, 16, 4, 4), RT_RAY(RT_FP32_PLAIN, 4, 4, 8),
+    RT_RAY(RT_FP32_PLAIN, 8, 4, 6),  RT_RAY(RT_FP32_PLAIN, 16, 4, 4),
+};
+#undef RT_RAY
+
+}  // namespace
+
+int ray_shapes(int precision, int nr, Shape *out, int max_out)
+{
+    int n = 0;
+    for (const RayEntry &s : kRayShapes)
+        if (s.precision == precision && 32 * s.c >= nr && n < max_out)
+            out[n++] = Shape{kKindRay, s.c, s.w, s.minb};
+    return n;
+}
+
+cudaError_t launch_ray_shape(int precision, Shape s, const TraceArgs &args, cudaStream_t stream,
+                             unsigned *grid_out)
+{
+    for (const RayEntry &e : kRayShapes)
+        if (e.precision == precision && e.c == s.cells_per_lane && e.w == s.warps &&
+            (s.min_blocks == 0 || e.minb == s.min_blocks) && 32 * e.c >= args.nr)
+            return e.fn(args, 0, stream, grid_out);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace rt

@@ -27,56 +27,74 @@ __device__ double gauss_legendre8(double a, double b)
 }
 
 // int_a^b t^3/(e^t-1) dt by composite Gauss-Legendre on panels no wider than one
-// unit of x. The integrand is analytic with its nearest poles at +-2 pi i, so each
-// panel converges far below double rounding. An infinite upper edge is replaced by
-// a + 60: the neglected tail is below e^-60 of the integrand at a.
-__device__ double planck_band(double a, double b)
+// unit of x, the panels spread over the 32 lanes of a warp. The integrand is
+// analytic with its nearest poles at +-2 pi i, so each panel converges far below
+// double rounding. An infinite upper edge is replaced by a + 60: the neglected
+// tail is below e^-60 of the integrand at a. Result valid in every lane.
+__device__ double planck_band_warp(double a, double b, int lane)
 {
     if (isinf(b)) b = a + 60.0;
-    if (!(b > a)) return 0.0;
-    const int n = (int)ceil(b - a);
-    const double h = (b - a) / n;
     double s = 0.0;
-    for (int p = 0; p < n; ++p) s += gauss_legendre8(a + p * h, a + (p + 1) * h);
+    if (b > a) {
+        const int n = (int)ceil(b - a);
+        const double h = (b - a) / n;
+        for (int p = lane; p < n; p += 32) s += gauss_legendre8(a + p * h, a + (p + 1) * h);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return s;
 }
 
+// One warp per bin (the block has RT_MAX_NU / 4 warps, each doing four bins),
+// then thread 0 compacts the bins with kappa > 0 into the tracer's table.
 __global__ void k_setup_bins(int n_nu, const double *nu_mid, const double *kappa, double t_star,
                              double r_star, int kappa_bf16, double *f_bin, NuEntry *nu,
                              float *kap, double2 *nu64, DevScalars *sc)
 {
     __shared__ double s_f[RT_MAX_NU];
     __shared__ double s_k[RT_MAX_NU];
-    const int i = threadIdx.x;
-    if (i < n_nu) {
+    const int lane = threadIdx.x & 31;
+    for (int i = threadIdx.x >> 5; i < n_nu; i += blockDim.x >> 5) {
         // Eq. 20 with B_nu the specific intensity: F_i = pi int B_nu dnu over the bin
         // = 2 pi (k T)^4 / (h^3 c^2) int_{x_lo}^{x_hi} t^3/(e^t-1) dt.
         const double lo = (i == 0) ? 0.0 : 0.5 * (nu_mid[i - 1] + nu_mid[i]);
         const double hi = (i == n_nu - 1) ? INFINITY : 0.5 * (nu_mid[i] + nu_mid[i + 1]);
         const double kt_h = kKB * t_star / kH;
         const double pref = 2.0 * kPi * pow(kKB * t_star, 4) / (kH * kH * kH * kC * kC);
-        const double f = pref * planck_band(lo / kt_h, hi / kt_h);
+        const double f = pref * planck_band_warp(lo / kt_h, hi / kt_h, lane);
         double k = kappa[i];
         if (kappa_bf16) k = (double)__bfloat162float(__float2bfloat16_rn((float)k));
-        s_f[i] = f;
-        s_k[i] = k;
-        f_bin[i] = f;
+        if (lane == 0) {
+            s_f[i] = f;
+            s_k[i] = k;
+            f_bin[i] = f;
+        }
     }
     __syncthreads();
-    if (i != 0) return;
+    if (threadIdx.x != 0) return;
     double fmax = 0.0, ftr = 0.0;
     for (int b = 0; b < n_nu; ++b) fmax = fmax > s_f[b] ? fmax : s_f[b];
+    // bins with kappa > 0, sorted by kappa ascending (insertion sort, <= 128 bins);
+    // the tracer classifies contiguous ranges of this order per warp
+    int order[RT_MAX_NU];
     int na = 0;
     for (int b = 0; b < n_nu; ++b) {
         if (s_k[b] > 0.0) {
-            nu[na].nk = (float)(-s_k[b] * kLog2e);
-            nu[na].lf = (float)log2(s_f[b] / fmax);
-            kap[na] = (float)s_k[b];
-            nu64[na] = make_double2(s_k[b], s_f[b] / fmax);
-            ++na;
+            int pos = na++;
+            while (pos > 0 && s_k[order[pos - 1]] > s_k[b]) {
+                order[pos] = order[pos - 1];
+                --pos;
+            }
+            order[pos] = b;
         } else {
             ftr += s_f[b];
         }
+    }
+    for (int a = 0; a < na; ++a) {
+        const int b = order[a];
+        nu[a].nk = (float)(-s_k[b] * kLog2e);
+        nu[a].lf = (float)log2(s_f[b] / fmax);
+        kap[a] = (float)s_k[b];
+        nu64[a] = make_double2(s_k[b], s_f[b] / fmax);
     }
     int pad = ((na + kNuPad - 1) / kNuPad) * kNuPad;
     if (pad < kNuPad) pad = kNuPad;
@@ -98,7 +116,8 @@ __global__ void k_setup_bins(int n_nu, const double *nu_mid, const double *kappa
 // is the rho -> 0 force factor.
 __global__ void k_setup_geometry(int nr, int ntheta, int nphi, const double *r_if,
                                  const double *theta_if, const double *phi_if, float4 *rtab,
-                                 double4 *rtab64, double *domega, const DevScalars *sc)
+                                 double4 *rtab64, double *domega, float *domega32,
+                                 const DevScalars *sc)
 {
     const long long nrays = (long long)ntheta * nphi;
     const long long n = nrays > nr ? nrays : nr;
@@ -117,7 +136,9 @@ __global__ void k_setup_geometry(int nr, int ntheta, int nphi, const double *r_i
         if (t < nrays) {
             const int it = (int)(t % ntheta);
             const int ip = (int)(t / ntheta);
-            domega[t] = (cos(theta_if[it]) - cos(theta_if[it + 1])) * (phi_if[ip + 1] - phi_if[ip]);
+            const double dom = (cos(theta_if[it]) - cos(theta_if[it + 1])) * (phi_if[ip + 1] - phi_if[ip]);
+            domega[t] = dom;
+            domega32[t] = (float)dom;
         }
     }
 }
@@ -179,7 +200,7 @@ cudaError_t launch_setup_bins(int n_nu, const double *nu_mid_dev, const double *
                               NuEntry *nu_dev, float *kap_dev, double2 *nu64_dev,
                               DevScalars *sc_dev, cudaStream_t stream)
 {
-    k_setup_bins<<<1, RT_MAX_NU, 0, stream>>>(n_nu, nu_mid_dev, kappa_dev, t_star, r_star,
+    k_setup_bins<<<1, 32 * (RT_MAX_NU / 4), 0, stream>>>(n_nu, nu_mid_dev, kappa_dev, t_star, r_star,
                                               kappa_bf16, f_bin_dev, nu_dev, kap_dev, nu64_dev,
                                               sc_dev);
     return cudaGetLastError();
@@ -188,14 +209,14 @@ cudaError_t launch_setup_bins(int n_nu, const double *nu_mid_dev, const double *
 cudaError_t launch_setup_geometry(int nr, int ntheta, int nphi, const double *r_if_dev,
                                   const double *theta_if_dev, const double *phi_if_dev,
                                   double t_star, float4 *rtab, double4 *rtab64, double *domega,
-                                  DevScalars *sc_dev, cudaStream_t stream)
+                                  float *domega32, DevScalars *sc_dev, cudaStream_t stream)
 {
     const long long nrays = (long long)ntheta * nphi;
     const long long n = nrays > nr ? nrays : nr;
     int blocks = (int)((n + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     k_setup_geometry<<<blocks, 256, 0, stream>>>(nr, ntheta, nphi, r_if_dev, theta_if_dev,
-                                                 phi_if_dev, rtab, rtab64, domega, sc_dev);
+                                                 phi_if_dev, rtab, rtab64, domega, domega32, sc_dev);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_sum_domega<<<1, 1024, 0, stream>>>(nrays, domega, t_star, sc_dev);

@@ -18,446 +18,464 @@
 //      earlier tiles is re-summed from global memory (at most nr cells), so no tile
 //      waits for another;
 //   3. for every bin: g = F_i/F_max e^{-kappa_i N_in} (Eq. 17 without the dilution,
-//      which Eq. 36 removes) and the absorbed fraction 1 - e^{-kappa_i dN} (Eqs.
-//      31-32) accumulated into one register per cell; the escape cell takes
-//      fraction 1 and so collects the escaping power (Eqs. 33-35);
-//   4. q_abs = Gq(r) * sum, a_rad = q_abs / (rho c) (Sect. 5; its rho -> 0 limit
-//      where rho == 0), and per-tile FP64 energy partials.
+//      which Eq. 36 removes) times the absorbed fraction 1 - e^{-kappa_i dN} (Eqs.
+//      31-32), accumulated into one register per cell;
+//   4. escaping power per ray (Eqs. 33-35) from the column at the ray's escape cell,
+//      q_abs = Gq(r) * sum, a_rad = q_abs / (rho c) (Sect. 5; its rho -> 0 limit
+//      where the column is 0), and per-tile FP64 energy partials.
 //
-// FP32 arithmetic per (cell, bin): exponentials on the MUFU unit (ex2.approx);
-// 1 - 2^y for small |y| from its Taylor series on the FMA pipe, where 1 - ex2(y)
-// would cancel.
-#include <float.h>
-#include <math.h>
-
-#include <type_traits>
-
-#include "rt_internal.cuh"
+//
+// The per-(cell, bin) arithmetic is described in rt_device.cuh.
+#include "rt_device.cuh"
 
 namespace rt {
 namespace {
 
-__device__ __forceinline__ float ex2_approx(float x)
+// radial table staged in shared memory up to this many cells per ray
+constexpr int kRtabSmemMax = 1024;
+
+// Shared-memory index with one padding word per 32: lanes that own C consecutive
+// cells read at stride C, which this skew spreads over distinct banks.
+__device__ __forceinline__ int skew(int i) { return i + (i >> 5); }
+// (rounded up to 4 floats so the float4 tables after the buffers stay 16-byte aligned)
+template <int T>
+constexpr int skewed_len() { return (T + T / 32 + 1 + 3) & ~3; }
+
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src)
 {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(gmem_src) : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Knuth's TwoSum: s + e == a + b exactly.
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
-{
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-
-// Running sums of one ray's column density. KahanSum is double-float: value = hi + lo.
-struct KahanSum {
-    float hi, lo;
-    __device__ void zero() { hi = lo = 0.0f; }
-    __device__ void add(float v)
-    {
-        float s, e;
-        two_sum(hi, v, s, e);
-        hi = s;
-        lo += e;
-    }
-    __device__ void add(const KahanSum &o)
-    {
-        float s, e;
-        two_sum(o.hi, hi, s, e);
-        hi = s;
-        lo = lo + o.lo + e;
-    }
-    __device__ float value() const { return hi + lo; }
-    __device__ KahanSum shfl_up(int d) const
-    {
-        KahanSum r;
-        r.hi = __shfl_up_sync(0xffffffffu, hi, d);
-        r.lo = __shfl_up_sync(0xffffffffu, lo, d);
-        return r;
-    }
-    __device__ KahanSum shfl_xor(int d) const
-    {
-        KahanSum r;
-        r.hi = __shfl_xor_sync(0xffffffffu, hi, d);
-        r.lo = __shfl_xor_sync(0xffffffffu, lo, d);
-        return r;
-    }
-};
-
-template <typename Real>
-struct PlainSum {  // one accumulator, no compensation
-    Real hi;
-    __device__ void zero() { hi = Real(0); }
-    __device__ void add(Real v) { hi += v; }
-    __device__ void add(const PlainSum &o) { hi += o.hi; }
-    __device__ Real value() const { return hi; }
-    __device__ PlainSum shfl_up(int d) const
-    {
-        PlainSum r;
-        r.hi = __shfl_up_sync(0xffffffffu, hi, d);
-        return r;
-    }
-    __device__ PlainSum shfl_xor(int d) const
-    {
-        PlainSum r;
-        r.hi = __shfl_xor_sync(0xffffffffu, hi, d);
-        return r;
-    }
-};
-
-// the column-density sum of each precision mode
-template <int MODE>
-using ColSum = typename std::conditional<
-    MODE == RT_FP32_KAHAN, KahanSum,
-    typename std::conditional<MODE == RT_FP64, PlainSum<double>, PlainSum<float>>::type>::type;
-
-// 1 - 2^y = -sum_{n>=1} (y ln2)^n / n!  =  y * P(y),  P(y) = sum_{n=0}^{4} p_n y^n,
-// p_n = -ln2^{n+1} / (n+1)!. Used for -Y0 < y <= 0 (dtau < 1/8): the first omitted
-// term is below 4.2e-8 of the value there.
-constexpr double kDtauSplit = 0.125;
-constexpr float kY0 = (float)(kDtauSplit * kLog2e);
-constexpr float kP0 = (float)(-kLn2);
-constexpr float kP1 = (float)(-kLn2 * kLn2 / 2.0);
-constexpr float kP2 = (float)(-kLn2 * kLn2 * kLn2 / 6.0);
-constexpr float kP3 = (float)(-kLn2 * kLn2 * kLn2 * kLn2 / 24.0);
-constexpr float kP4 = (float)(-kLn2 * kLn2 * kLn2 * kLn2 * kLn2 / 120.0);
-
-// absorbed fraction 1 - 2^y of one cell in one bin, y = -kappa dN log2(e) <= 0
-__device__ __forceinline__ float absorbed_fraction(float y)
-{
-    const float big = 1.0f - ex2_approx(y);
-    const float p = fmaf(fmaf(fmaf(fmaf(kP4, y, kP3), y, kP2), y, kP1), y, kP0);
-    return (y > -kY0) ? y * p : big;
-}
-
-template <int MODE>
-__device__ __forceinline__ auto cell_column(float rho, float td, int k, const TraceArgs &p)
-{
-    if constexpr (MODE == RT_FP64) {
-        const double dr = __ldg(&p.rtab64[k].x);
-        return (td <= p.t_sub) ? (double)rho * dr : 0.0;
-    } else {
-        const float dr = __ldg(&p.rtab[k].x);
-        return (td <= p.t_sub) ? rho * dr : 0.0f;
-    }
-}
-
-template <int C, int W, int MODE>
-__global__ void __launch_bounds__(W * 32) k_trace(const TraceArgs p)
+// Persistent tracer: CTA b walks the contiguous tiles [b*n/G, (b+1)*n/G) of the
+// flattened ray array, prefetching tile t+1 (cp.async, double buffer) while it
+// computes tile t, and handing the column of the ray that runs into the next
+// tile over in shared memory, so only its first tile re-reads an earlier tile.
+template <int C, int W, int MODE, int MINB>
+__global__ void __launch_bounds__(W * 32, MINB) k_trace(const TraceArgs p)
 {
     using Real = typename std::conditional<MODE == RT_FP64, double, float>::type;
     using Sum = ColSum<MODE>;
+    // energy sums: compensated FP32 (the FP64 pipe of this part is far narrower
+    // than its FP32 pipes), plain FP64 in the FP64 mode
+    using ESum = typename std::conditional<MODE == RT_FP64, PlainSum<double>, KahanSum>::type;
     constexpr int T = 32 * W * C;
+    static_assert(C % 2 == 0, "cells per lane must be even");
 
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nr = p.nr;
+    const unsigned R1 = (unsigned)nr + 1u;
+    const bool rt_staged = (MODE != RT_FP64) && nr <= kRtabSmemMax;
+
+    // dynamic shared memory: input double buffer, output staging, radial table,
+    // bin tables
+    constexpr int TS = skewed_len<T>();
+    const int nrs = rt_staged ? ((nr + nr / 32 + 1 + 3) & ~3) : 0;  // skewed radial length
     extern __shared__ __align__(16) unsigned char smem[];
-    float *s_rho = reinterpret_cast<float *>(smem);
-    float *s_t = s_rho + T;
-    float *s_kap = s_t + T;  // [nnu_pad]
-    NuEntry *s_nu = reinterpret_cast<NuEntry *>(s_kap + p.nnu_pad);
+    float *s_in = reinterpret_cast<float *>(smem);  // [2][rho | tdust][TS]
+    float *s_out = s_in + 4 * TS;                    // [q | a][TS]
+    float *s_rdr = s_out + 2 * TS;                   // radial dr, Gq, Ga0 [nrs] each
+    float *s_rgq = s_rdr + nrs;
+    float *s_rga = s_rgq + nrs;
+    float *s_kap = s_rga + nrs;
+    // (nk, nk, lf, lf): each bin's constants duplicated for packed f32x2 math
+    float4 *s_nu = reinterpret_cast<float4 *>(s_kap + p.nnu_pad);
     double2 *s_nu64 = reinterpret_cast<double2 *>(s_kap + p.nnu_pad);
 
     __shared__ Sum s_wsum[W];
     __shared__ int s_whead[W];
-    __shared__ Sum s_carry;
-    __shared__ double s_red[W][2];
+    __shared__ Sum s_cpart[W];  // first tile: per-warp shares of the re-summed column
+    __shared__ Sum s_carry[2];  // column handed from tile to tile (double buffered)
+    __shared__ ESum s_red[W][2];
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nr = p.nr, R1 = nr + 1;
-    const long long f0 = (long long)blockIdx.x * T;
-    const long long f1 = (f0 + T < p.L) ? f0 + T : p.L;
-    const long long ray0 = f0 / R1;
-    const int k0 = (int)(f0 - ray0 * R1);
-    const long long m0 = ray0 * nr + (k0 < nr ? k0 : nr);
-    const long long rayE = f1 / R1;
-    const int kE = (int)(f1 - rayE * R1);
-    const long long m1 = rayE * nr + (kE < nr ? kE : nr);
-    const int nreal = (int)(m1 - m0);
+    const unsigned ntiles = (p.L + (unsigned)T - 1u) / (unsigned)T;
+    const unsigned t_begin = (unsigned)((unsigned long long)blockIdx.x * ntiles / gridDim.x);
+    const unsigned t_end = (unsigned)((unsigned long long)(blockIdx.x + 1) * ntiles / gridDim.x);
 
-    // 1. bin table and the tile's fields -> shared memory
+    // tile t covers flattened cells [t T, min((t+1) T, L)); its real cells are the
+    // contiguous field elements [m0, m0 + nreal)
+    auto tile_bounds = [&](unsigned t, unsigned &f0, unsigned &f1, unsigned &m0, int &nreal, int &k0) {
+        f0 = t * (unsigned)T;
+        f1 = (f0 + (unsigned)T < p.L) ? f0 + (unsigned)T : p.L;
+        const unsigned ray0 = p.r1div.div(f0);
+        k0 = (int)(f0 - ray0 * R1);
+        m0 = ray0 * (unsigned)nr + (unsigned)(k0 < nr ? k0 : nr);
+        const unsigned rayE = p.r1div.div(f1);
+        const int kE = (int)(f1 - rayE * R1);
+        nreal = (int)(rayE * (unsigned)nr + (unsigned)(kE < nr ? kE : nr) - m0);
+    };
+    auto prefetch = [&](unsigned t, int buf) {
+        unsigned f0, f1, m0;
+        int nreal, k0;
+        tile_bounds(t, f0, f1, m0, nreal, k0);
+        float *dr = s_in + buf * 2 * TS;
+        for (int i = tid; i < nreal; i += W * 32) {
+            cp_async4(dr + skew(i), p.rho + m0 + i);
+            cp_async4(dr + TS + skew(i), p.tdust + m0 + i);
+        }
+        cp_async_commit();
+    };
+    auto rad_dr = [&](int k) -> float { return rt_staged ? s_rdr[skew(k)] : __ldg(&p.rtab[k].x); };
+    auto rad_gq = [&](int k) -> float { return rt_staged ? s_rgq[skew(k)] : __ldg(&p.rtab[k].y); };
+    auto rad_ga = [&](int k) -> float { return rt_staged ? s_rga[skew(k)] : __ldg(&p.rtab[k].z); };
+    auto column = [&](float rho, float td, int k) -> Real {
+        if constexpr (MODE == RT_FP64) return (td <= p.t_sub) ? (double)rho * __ldg(&p.rtab64[k].x) : 0.0;
+        else return (td <= p.t_sub) ? rho * rad_dr(k) : 0.0f;
+    };
+
+    // prologue: tables, first prefetch, the first tile's incoming column
+    if (t_begin < t_end) prefetch(t_begin, 0);
     for (int i = tid; i < p.nnu_pad; i += W * 32) {
         s_kap[i] = p.kap[i];
-        if constexpr (MODE == RT_FP64) s_nu64[i] = p.nu64[i];
-        else s_nu[i] = p.nu[i];
+        if constexpr (MODE == RT_FP64) {
+            s_nu64[i] = p.nu64[i];
+        } else {
+            const NuEntry e = p.nu[i];
+            s_nu[i] = make_float4(e.nk, e.nk, e.lf, e.lf);
+        }
     }
-    for (int i = tid; i < nreal; i += W * 32) {
-        s_rho[i] = __ldg(p.rho + m0 + i);
-        s_t[i] = __ldg(p.tdust + m0 + i);
-    }
-
-    // 2a. column density of the part of ray0 that precedes this tile
-    if (warp == 0) {
+    if (rt_staged)
+        for (int k = tid; k < nr; k += W * 32) {
+            const float4 g = __ldg(&p.rtab[k]);
+            s_rdr[skew(k)] = g.x;
+            s_rgq[skew(k)] = g.y;
+            s_rga[skew(k)] = g.z;
+        }
+    __syncthreads();  // radial table visible before the column re-sum uses it
+    if (t_begin < t_end) {
+        unsigned f0, f1, m0;
+        int nreal, k0;
+        tile_bounds(t_begin, f0, f1, m0, nreal, k0);
+        const unsigned ray0 = p.r1div.div(f0);
         Sum c;
         c.zero();
         const int kc = k0 < nr ? k0 : nr;
-        const float *rr = p.rho + ray0 * nr;
-        const float *tt = p.tdust + ray0 * nr;
-        for (int k = lane; k < kc; k += 32) c.add(cell_column<MODE>(__ldg(rr + k), __ldg(tt + k), k, p));
+        const float *rr = p.rho + (size_t)ray0 * nr;
+        const float *tt = p.tdust + (size_t)ray0 * nr;
+        for (int k = tid; k < kc; k += W * 32) c.add(column(__ldg(rr + k), __ldg(tt + k), k));
         for (int o = 16; o > 0; o >>= 1) c.add(c.shfl_xor(o));
-        if (lane == 0) s_carry = c;
-    }
-    __syncthreads();
-
-    // 2b. this lane's cells
-    const long long fl = f0 + (long long)(warp * 32 + lane) * C;
-    const long long rayl = fl / R1;
-    const int kl = (int)(fl - rayl * R1);
-    Real D[C], N[C];
-    unsigned real_m = 0, virt_m = 0, head_m = 0, zero_m = 0;
-    bool bad = false;
-    {
-        long long ray = rayl;
-        int k = kl;
-#pragma unroll
-        for (int j = 0; j < C; ++j) {
-            D[j] = Real(0);
-            if (fl + j < f1) {
-                if (k == 0) head_m |= 1u << j;
-                if (k < nr) {
-                    real_m |= 1u << j;
-                    const int idx = (int)(ray * nr + k - m0);
-                    const float rho = s_rho[idx], td = s_t[idx];
-                    bad |= !(rho >= 0.0f && rho <= FLT_MAX) || (td != td);
-                    D[j] = cell_column<MODE>(rho, td, k, p);
-                    if (td <= p.t_sub && D[j] == Real(0)) zero_m |= 1u << j;
-                } else {
-                    virt_m |= 1u << j;
-                }
-            }
-            if (++k > nr) { k = 0; ++ray; }
-        }
-    }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicMax(p.bad_input, p.seq);
-
-    // 2c. segmented exclusive scan of D along each ray
-    Sum agg;
-    agg.zero();
-    bool hh = false;
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-        if ((head_m >> j) & 1u) { agg.zero(); hh = true; }
-        agg.add(D[j]);
-    }
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const Sum o = agg.shfl_up(d);
-        const bool oh = __shfl_up_sync(0xffffffffu, hh, d);
-        if (lane >= d) {
-            if (!hh) agg.add(o);
-            hh = hh || oh;
-        }
-    }
-    Sum excl = agg.shfl_up(1);
-    bool exh = __shfl_up_sync(0xffffffffu, hh, 1);
-    if (lane == 0) { excl.zero(); exh = false; }
-    if (lane == 31) { s_wsum[warp] = agg; s_whead[warp] = hh; }
-    __syncthreads();
-    Sum pre = s_carry;
-    for (int w = 0; w < warp; ++w) {
-        if (s_whead[w]) pre = s_wsum[w];
-        else pre.add(s_wsum[w]);
-    }
-    if (exh) pre = excl;
-    else pre.add(excl);
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-        if ((head_m >> j) & 1u) pre.zero();
-        N[j] = pre.value();
-        pre.add(D[j]);
-        if ((virt_m >> j) & 1u) D[j] = Real(INFINITY);  // escape cell absorbs all
+        if (lane == 0) s_cpart[warp] = c;
     }
 
-    // 3. frequency loop
-    Real acc[C];
-#pragma unroll
-    for (int j = 0; j < C; ++j) acc[j] = Real(0);
-    if constexpr (MODE == RT_FP64) {
-#pragma unroll 1
-        for (int i = 0; i < p.nnu_pad; ++i) {
-            const double2 e = s_nu64[i];  // (kappa_i, F_i / F_max)
+    ESum eabs, eesc;
+    eabs.zero();
+    eesc.zero();
+
+    for (unsigned t = t_begin; t < t_end; ++t) {
+        const int buf = (int)((t - t_begin) & 1u);
+        if (t + 1 < t_end) prefetch(t + 1, buf ^ 1);
+        else cp_async_commit();  // keep one group per iteration
+        cp_async_wait_prev();    // this thread's copies of tile t have landed
+        __syncthreads();         // ... and everyone else's
+
+        unsigned f0, f1, m0;
+        int nreal, k0;
+        tile_bounds(t, f0, f1, m0, nreal, k0);
+        const float *s_rho = s_in + buf * 2 * TS;
+        const float *s_t = s_rho + TS;
+
+        // this lane's cells: slot j is flattened cell fl + j with radial index k
+        // (k == nr is the escape cell); real cells sit at consecutive tile
+        // indices from idx0
+        const unsigned fl = f0 + (unsigned)(warp * 32 + lane) * C;
+        const unsigned rayl = p.r1div.div(fl);
+        const int kl = (int)(fl - rayl * R1);
+        const int idx0 = (int)(rayl * (unsigned)nr + (unsigned)(kl < nr ? kl : nr) - m0);
+        Cells<Real, C> D, N;
+        unsigned real_m = 0, virt_m = 0, head_m = 0, zero_m = 0;
+        bool bad = false;
+        {
+            int k = kl, idx = idx0;
 #pragma unroll
             for (int j = 0; j < C; ++j) {
-                const double g = e.y * exp(-e.x * N[j]);
-                acc[j] = fma(g, -expm1(-e.x * D[j]), acc[j]);
+                D.set(j, Real(0));
+                if (fl + j < f1) {
+                    if (k == 0) head_m |= 1u << j;
+                    if (k < nr) {
+                        real_m |= 1u << j;
+                        const float rho = s_rho[skew(idx)], td = s_t[skew(idx)];
+                        bad |= !(rho >= 0.0f && rho <= FLT_MAX) || (td != td);
+                        D.set(j, column(rho, td, k));
+                        if (td <= p.t_sub && D.get(j) == Real(0)) zero_m |= 1u << j;
+                        ++idx;
+                    } else {
+                        virt_m |= 1u << j;
+                    }
+                }
+                if (++k > nr) k = 0;
             }
         }
-    } else {
-#pragma unroll 1
-        for (int i = 0; i < p.nnu_pad; i += kNuPad) {
+        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicMax(p.bad_input, p.seq);
+
+        // segmented exclusive scan of D along each ray
+        Sum agg;
+        agg.zero();
+        bool hh = false;
 #pragma unroll
-            for (int u = 0; u < kNuPad; ++u) {
-                const NuEntry e = s_nu[i + u];
+        for (int j = 0; j < C; ++j) {
+            if ((head_m >> j) & 1u) { agg.zero(); hh = true; }
+            agg.add(D.get(j));
+        }
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const Sum o = agg.shfl_up(d);
+            const bool oh = __shfl_up_sync(0xffffffffu, hh, d);
+            if (lane >= d) {
+                if (!hh) agg.add(o);
+                hh = hh || oh;
+            }
+        }
+        Sum excl = agg.shfl_up(1);
+        bool exh = __shfl_up_sync(0xffffffffu, hh, 1);
+        if (lane == 0) { excl.zero(); exh = false; }
+        if (lane == 31) { s_wsum[warp] = agg; s_whead[warp] = hh; }
+        __syncthreads();
+        Sum pre;
+        if (t == t_begin) {
+            pre.zero();
+            for (int w = 0; w < W; ++w) pre.add(s_cpart[w]);
+        } else {
+            pre = s_carry[buf];
+        }
+        for (int w = 0; w < warp; ++w) {
+            if (s_whead[w]) pre = s_wsum[w];
+            else pre.add(s_wsum[w]);
+        }
+        if (exh) pre = excl;
+        else pre.add(excl);
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            if ((head_m >> j) & 1u) pre.zero();
+            N.set(j, pre.value());
+            pre.add(D.get(j));
+        }
+        // the column at the end of this tile continues into the next one
+        if (tid == W * 32 - 1) s_carry[buf ^ 1] = pre;
+
+        // frequency loop (escape cells carry D = 0 and absorb nothing here)
+        Cells<Real, C> acc;
+#pragma unroll
+        for (int j = 0; j < C; ++j) acc.set(j, Real(0));
+        if constexpr (MODE == RT_FP64) {
+#pragma unroll 1
+            for (int i = 0; i < p.nnu_pad; ++i) {
+                const double2 e = s_nu64[i];  // (kappa_i, F_i / F_max)
 #pragma unroll
                 for (int j = 0; j < C; ++j) {
-                    const float g = ex2_approx(fmaf(e.nk, N[j], e.lf));
-                    acc[j] = fmaf(g, absorbed_fraction(e.nk * D[j]), acc[j]);
+                    const double g = e.y * exp(-e.x * N.get(j));
+                    acc.set(j, fma(g, -expm1(-e.x * D.get(j)), acc.get(j)));
                 }
             }
-        }
-    }
-
-    // rho == 0 cells with dust: the force limit sum_i kappa_i g_i (rare; per slot,
-    // only in warps that hold such a cell). Reuses D (0 there).
+        } else {
+            // the warp's largest and smallest non-zero column decide each bin's class
+            float dmax = 0.0f, dmin = INFINITY;
 #pragma unroll
-    for (int j = 0; j < C; ++j) {
-        if (__any_sync(0xffffffffu, (zero_m >> j) & 1u)) {
-            Real s = Real(0);
-            for (int i = 0; i < p.nnu_pad; ++i) {
-                if constexpr (MODE == RT_FP64) s = fma((double)s_kap[i] * s_nu64[i].y, exp(-s_nu64[i].x * N[j]), s);
-                else s = fmaf(s_kap[i], ex2_approx(fmaf(s_nu[i].nk, N[j], s_nu[i].lf)), s);
+            for (int j = 0; j < C; ++j) {
+                dmax = fmaxf(dmax, D.get(j));
+                if (D.get(j) > 0.0f) dmin = fminf(dmin, D.get(j));
             }
-            if ((zero_m >> j) & 1u) D[j] = s;
+            for (int o = 16; o > 0; o >>= 1) {
+                dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+                dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+            }
+            const int na = p.n_active;
+            const BinClasses bc = classify_bins(s_nu, na, lane, dmax, dmin);
+            bin_range<1, C>(0, bc.b1, s_nu, N.v, D.v, acc.v);
+            bin_range<2, C>(bc.b1, bc.b2, s_nu, N.v, D.v, acc.v);
+            bin_range<3, C>(bc.b2, bc.b3, s_nu, N.v, D.v, acc.v);
+            bin_range<5, C>(bc.b3, bc.b5, s_nu, N.v, D.v, acc.v);
+            bin_range<6, C>(bc.b5, bc.bb, s_nu, N.v, D.v, acc.v);
+            bin_range<7, C>(bc.bb, na, s_nu, N.v, D.v, acc.v);
         }
-    }
 
-    // 4a. energy partials: per ray, compensated FP32 (or FP64) sum of the lane's
-    // absorbed cells, weighted by the ray's solid angle in FP64
-    double e_abs = 0.0, e_esc = 0.0;
-    {
-        long long ray = rayl;
-        int k = kl;
-        Sum part;
-        part.zero();
-        long long pray = -1;  // ray of the cells summed in `part`, -1 if none
+        // rho == 0 cells with dust: the force limit sum_i kappa_i g_i (rare; per
+        // slot, only in warps that hold such a cell). Reuses D (0 there).
+        if (__any_sync(0xffffffffu, zero_m != 0u)) {
 #pragma unroll
         for (int j = 0; j < C; ++j) {
-            if ((real_m >> j) & 1u) { part.add(acc[j]); pray = ray; }
-            if ((virt_m >> j) & 1u) {
-                const double w = __ldg(p.domega + ray);
-                if (pray >= 0) e_abs += (double)part.value() * w;
-                e_esc += (double)acc[j] * w;
-                part.zero();
-                pray = -1;
-            }
-            if (++k > nr) { k = 0; ++ray; }
-        }
-        if (pray >= 0) e_abs += (double)part.value() * __ldg(p.domega + pray);
-    }
-
-    // 4b. q_abs and a_rad into registers (reusing acc and N)
-    {
-        long long ray = rayl;
-        int k = kl;
-#pragma unroll
-        for (int j = 0; j < C; ++j) {
-            if ((real_m >> j) & 1u) {
-                const int idx = (int)(ray * nr + k - m0);
-                const float rho = s_rho[idx];
-                Real q, a;
-                if constexpr (MODE == RT_FP64) {
-                    const double4 g = p.rtab64[k];
-                    q = g.y * acc[j];
-                    a = ((zero_m >> j) & 1u) ? g.z * D[j]
-                        : (D[j] > 0.0 ? q / ((double)rho * kC) : 0.0);
-                } else {
-                    const float4 g = __ldg(&p.rtab[k]);
-                    q = g.y * acc[j];
-                    a = ((zero_m >> j) & 1u) ? g.z * D[j]
-                        : (D[j] > 0.0f ? q / (rho * (float)kC) : 0.0f);
+            if (__any_sync(0xffffffffu, (zero_m >> j) & 1u)) {
+                Real s = Real(0);
+                for (int i = 0; i < p.nnu_pad; ++i) {
+                    if constexpr (MODE == RT_FP64) s = fma((double)s_kap[i] * s_nu64[i].y, exp(-s_nu64[i].x * N.get(j)), s);
+                    else s = fmaf(s_kap[i], ex2_approx(fmaf(s_nu[i].x, N.get(j), s_nu[i].z)), s);
                 }
-                acc[j] = q;
-                N[j] = a;
+                if ((zero_m >> j) & 1u) D.set(j, s);
             }
-            if (++k > nr) { k = 0; ++ray; }
         }
-    }
-    __syncthreads();  // every lane has read s_rho
+        }
 
-    // 4c. outputs through shared memory, then coalesced stores
-    {
-        long long ray = rayl;
-        int k = kl;
+        // escaping power of every ray whose escape cell is in this warp: the
+        // warp's lanes share the bins of sum_i F_i/F_max e^{-kappa_i N_total}
 #pragma unroll
         for (int j = 0; j < C; ++j) {
-            if ((real_m >> j) & 1u) {
-                const int idx = (int)(ray * nr + k - m0);
-                s_rho[idx] = (float)acc[j];
-                s_t[idx] = (float)N[j];
+            unsigned vb = __ballot_sync(0xffffffffu, (virt_m >> j) & 1u);
+            while (vb) {
+                const int src = __ffs(vb) - 1;
+                vb &= vb - 1;
+                const Real ntot = __shfl_sync(0xffffffffu, N.get(j), src);
+                const unsigned fsrc = __shfl_sync(0xffffffffu, fl, src) + (unsigned)j;
+                Real s = Real(0);
+                for (int i = lane; i < p.nnu_pad; i += 32) {
+                    if constexpr (MODE == RT_FP64) s += s_nu64[i].y * exp(-s_nu64[i].x * ntot);
+                    else s += ex2_approx(fmaf(s_nu[i].x, ntot, s_nu[i].z));
+                }
+                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) eesc.add(s * solid_angle<MODE>(p, p.r1div.div(fsrc)));
             }
-            if (++k > nr) { k = 0; ++ray; }
+        }
+
+        // q_abs, a_rad (= q/(rho c) = Ga0 acc / dN) into the warp's slice of the
+        // output staging; the lane's absorbed power, summed per ray and weighted by
+        // the ray's solid angle, into the CTA's energy; then the warp stores its
+        // contiguous run of cells
+        {
+            int k = kl, idx = idx0;
+            unsigned ray = rayl;
+            ESum part;
+            part.zero();
+            bool pend = false;
+            unsigned pray = 0;
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                if ((real_m >> j) & 1u) {
+                    if (pend && pray != ray) {
+                        add_weighted(eabs, part, solid_angle<MODE>(p, pray));
+                        part.zero();
+                    }
+                    part.add(acc.get(j));
+                    pray = ray;
+                    pend = true;
+                    const bool zc = (zero_m >> j) & 1u;
+                    const Real dj = D.get(j);
+                    Real q, a;
+                    if constexpr (MODE == RT_FP64) {
+                        const double4 g = p.rtab64[k];
+                        q = zc ? 0.0 : g.y * acc.get(j);
+                        a = g.z * (zc ? dj : (dj > 0.0 ? acc.get(j) / dj : 0.0));
+                    } else {
+                        q = (dj > 0.0f && !zc) ? rad_gq(k) * acc.get(j) : 0.0f;
+                        a = rad_ga(k) * (zc ? dj : (dj > 0.0f ? __fdividef(acc.get(j), dj) : 0.0f));
+                    }
+                    s_out[skew(idx)] = (float)q;
+                    s_out[TS + skew(idx)] = (float)a;
+                    ++idx;
+                }
+                if (++k > nr) { k = 0; ++ray; }
+            }
+            if (pend) add_weighted(eabs, part, solid_angle<MODE>(p, pray));
+            // the warp's real cells are the tile indices [lane 0's idx0, lane 31's
+            // end); lanes past the end of a partial tile point beyond nreal
+            const int wend_lane = idx;
+            const int wbeg = min(__shfl_sync(0xffffffffu, idx0, 0), nreal);
+            const int wend = min(__shfl_sync(0xffffffffu, wend_lane, 31), nreal);
+            __syncwarp();
+            for (int i = wbeg + lane; i < wend; i += 32) {
+                p.q[m0 + i] = s_out[skew(i)];
+                p.a[m0 + i] = s_out[TS + skew(i)];
+            }
         }
     }
+    cp_async_commit();  // no copies remain in flight at exit
+    asm volatile("cp.async.wait_all;" ::: "memory");
+
     for (int o = 16; o > 0; o >>= 1) {
-        e_abs += __shfl_xor_sync(0xffffffffu, e_abs, o);
-        e_esc += __shfl_xor_sync(0xffffffffu, e_esc, o);
+        eabs.add(eabs.shfl_xor(o));
+        eesc.add(eesc.shfl_xor(o));
     }
-    if (lane == 0) { s_red[warp][0] = e_abs; s_red[warp][1] = e_esc; }
+    if (lane == 0) { s_red[warp][0] = eabs; s_red[warp][1] = eesc; }
     __syncthreads();
-    for (int i = tid; i < nreal; i += W * 32) {
-        p.q[m0 + i] = s_rho[i];
-        p.a[m0 + i] = s_t[i];
-    }
     if (tid == 0) {
-        double sa = 0.0, se = 0.0;
-        for (int w = 0; w < W; ++w) { sa += s_red[w][0]; se += s_red[w][1]; }
-        p.partials[blockIdx.x] = make_double2(sa, se);
+        ESum sa = s_red[0][0], se = s_red[0][1];
+        for (int w = 1; w < W; ++w) { sa.add(s_red[w][0]); se.add(s_red[w][1]); }
+        p.partials[blockIdx.x] = make_double2(to_double(sa), to_double(se));
     }
 }
 
 template <int C, int W, int MODE>
-cudaError_t launch_shape(const TraceArgs &a, long long ntiles, cudaStream_t stream)
+size_t trace_smem_bytes(const TraceArgs &a)
 {
-    constexpr int T = 32 * W * C;
-    const size_t smem = (size_t)T * 2 * sizeof(float) + (size_t)a.nnu_pad * sizeof(float) +
-                        (size_t)a.nnu_pad * (MODE == RT_FP64 ? sizeof(double2) : sizeof(NuEntry)) + 16;
+    constexpr int TS = skewed_len<32 * W * C>();
+    const bool staged = (MODE != RT_FP64) && a.nr <= kRtabSmemMax;
+    const size_t nrs = staged ? (size_t)((a.nr + a.nr / 32 + 1 + 3) & ~3) : 0;
+    return (size_t)TS * 6 * sizeof(float) + 3 * nrs * sizeof(float) +
+           (size_t)a.nnu_pad * sizeof(float) + (size_t)a.nnu_pad * 16 + 16;
+}
+
+// Launch one chunk with a persistent grid of (SMs x resident CTAs) CTAs, or fewer
+// when there are fewer tiles. Returns the grid size (energy partials written).
+template <int C, int W, int MODE, int MINB>
+cudaError_t launch_shape(const TraceArgs &a, unsigned ntiles, cudaStream_t stream, unsigned *grid_out)
+{
+    const size_t smem = trace_smem_bytes<C, W, MODE>(a);
+    auto kern = k_trace<C, W, MODE, MINB>;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_trace<C, W, MODE>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_trace<C, W, MODE><<<(unsigned)ntiles, W * 32, smem, stream>>>(a);
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    unsigned grid = (unsigned)nsm * (unsigned)per_sm;
+    if (grid > ntiles) grid = ntiles;
+    if (grid < 1) grid = 1;
+    kern<<<grid, W * 32, smem, stream>>>(a);
+    *grid_out = grid;
     return cudaGetLastError();
 }
 
-using LaunchFn = cudaError_t (*)(const TraceArgs &, long long, cudaStream_t);
+using LaunchFn = cudaError_t (*)(const TraceArgs &, unsigned, cudaStream_t, unsigned *);
 struct ShapeEntry {
-    int precision, c, w;
+    int precision, c, w, minb;
     LaunchFn fn;
 };
 
-#define RT_SHAPE(P, C, W) {P, C, W, &launch_shape<C, W, P>}
+// (cells per lane, warps per CTA, minimum resident CTAs per SM): the last one caps
+// the registers per thread at 64K / (32 W MINB) and so trades ILP for occupancy.
+#define RT_SHAPE(P, C, W, MB) {P, C, W, MB, &launch_shape<C, W, P, MB>}
 const ShapeEntry kShapes[] = {
-    RT_SHAPE(RT_FP32_KAHAN, 2, 4),  RT_SHAPE(RT_FP32_KAHAN, 4, 4),  RT_SHAPE(RT_FP32_KAHAN, 8, 4),
-    RT_SHAPE(RT_FP32_KAHAN, 16, 4), RT_SHAPE(RT_FP32_KAHAN, 4, 8),  RT_SHAPE(RT_FP32_KAHAN, 8, 8),
-    RT_SHAPE(RT_FP32_KAHAN, 16, 8), RT_SHAPE(RT_FP32_PLAIN, 2, 4),  RT_SHAPE(RT_FP32_PLAIN, 4, 4),
-    RT_SHAPE(RT_FP32_PLAIN, 8, 4),  RT_SHAPE(RT_FP32_PLAIN, 16, 4), RT_SHAPE(RT_FP32_PLAIN, 8, 8),
-    RT_SHAPE(RT_FP32_PLAIN, 16, 8), RT_SHAPE(RT_FP64, 2, 4),        RT_SHAPE(RT_FP64, 4, 4),
-    RT_SHAPE(RT_FP64, 8, 4),
+    RT_SHAPE(RT_FP32_KAHAN, 2, 4, 8),  RT_SHAPE(RT_FP32_KAHAN, 4, 4, 6),
+    RT_SHAPE(RT_FP32_KAHAN, 4, 4, 8),  RT_SHAPE(RT_FP32_KAHAN, 8, 4, 4),
+    RT_SHAPE(RT_FP32_KAHAN, 8, 4, 5),  RT_SHAPE(RT_FP32_KAHAN, 8, 4, 6),
+    RT_SHAPE(RT_FP32_KAHAN, 16, 4, 2), RT_SHAPE(RT_FP32_KAHAN, 16, 4, 3),
+    RT_SHAPE(RT_FP32_KAHAN, 4, 8, 4),  RT_SHAPE(RT_FP32_KAHAN, 8, 8, 2),
+    RT_SHAPE(RT_FP32_KAHAN, 8, 8, 3),  RT_SHAPE(RT_FP32_PLAIN, 2, 4, 8),
+    RT_SHAPE(RT_FP32_PLAIN, 4, 4, 6),  RT_SHAPE(RT_FP32_PLAIN, 8, 4, 4),
+    RT_SHAPE(RT_FP32_PLAIN, 8, 8, 2),  RT_SHAPE(RT_FP64, 2, 4, 8),
+    RT_SHAPE(RT_FP64, 4, 4, 4),        RT_SHAPE(RT_FP64, 8, 4, 2),
 };
 #undef RT_SHAPE
 
-const ShapeEntry *find_shape(int precision, int c, int w)
+const ShapeEntry *find_shape(int precision, int c, int w, int mb)
 {
     for (const ShapeEntry &s : kShapes)
-        if (s.precision == precision && s.c == c && s.w == w) return &s;
+        if (s.precision == precision && s.c == c && s.w == w && (mb == 0 || s.minb == mb)) return &s;
     return nullptr;
 }
 
 }  // namespace
 
-bool trace_shape_supported(int precision, int cells_per_lane, int warps)
-{
-    return find_shape(precision, cells_per_lane, warps) != nullptr;
-}
-
 int trace_shapes(int precision, Shape *out, int max_out)
 {
     int n = 0;
     for (const ShapeEntry &s : kShapes)
-        if (s.precision == precision && n < max_out) out[n++] = Shape{s.c, s.w};
+        if (s.precision == precision && n < max_out) out[n++] = Shape{kKindTile, s.c, s.w, s.minb};
     return n;
 }
 
 long long trace_tile_cells(Shape s) { return 32LL * s.warps * s.cells_per_lane; }
 
-cudaError_t launch_trace(int precision, Shape s, const TraceArgs &args, long long ntiles,
-                         cudaStream_t stream)
+cudaError_t launch_trace(int precision, Shape s, const TraceArgs &args, unsigned ntiles,
+                         cudaStream_t stream, unsigned *grid_out)
 {
-    const ShapeEntry *e = find_shape(precision, s.cells_per_lane, s.warps);
+    if (s.kind == kKindRay) return launch_ray_shape(precision, s, args, stream, grid_out);
+    const ShapeEntry *e = find_shape(precision, s.cells_per_lane, s.warps, s.min_blocks);
     if (!e) return cudaErrorInvalidValue;
-    return e->fn(args, ntiles, stream);
+    return e->fn(args, ntiles, stream, grid_out);
 }
 
 }  // namespace rt

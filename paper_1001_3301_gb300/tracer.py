@@ -121,13 +121,26 @@ class Tracer:
         return out
 
     # -- launch shape ----------------------------------------------------------
-    def set_tuning(self, cells_per_lane: int = 0, warps: int = 0):
-        check(lib.rt_set_tuning(self._ctx, int(cells_per_lane), int(warps)), self._ctx)
+    def set_tuning(self, kind: int = 0, cells_per_lane: int = 0, warps: int = 0, min_blocks: int = 0):
+        """Force (kernel kind, cells per lane, warps per CTA, min resident CTAs per SM);
+        all zero restores the automatic choice."""
+        check(lib.rt_set_tuning(self._ctx, int(kind), int(cells_per_lane), int(warps), int(min_blocks)),
+              self._ctx)
 
     def tuning(self):
-        c, w = ctypes.c_int(), ctypes.c_int()
-        check(lib.rt_get_tuning(self._ctx, ctypes.byref(c), ctypes.byref(w)), self._ctx)
-        return c.value, w.value
+        """(kernel kind, cells per lane, warps per CTA, min resident CTAs per SM) in use."""
+        v = [ctypes.c_int() for _ in range(4)]
+        check(lib.rt_get_tuning(self._ctx, *[ctypes.byref(x) for x in v]), self._ctx)
+        return tuple(x.value for x in v)
+
+    def tunings(self):
+        """Every compiled launch shape that applies to this grid and precision."""
+        n = 64
+        arrs = [(ctypes.c_int * n)() for _ in range(4)]
+        m = lib.rt_list_tunings(self._ctx, *arrs, n)
+        if m < 0:
+            check(m, self._ctx)
+        return [tuple(a[i] for a in arrs) for i in range(min(m, n))]
 
     def autotune(self, rho, t_dust, q_abs, a_rad, reps: int = 3):
         check(lib.rt_autotune(self._ctx, rho.data_ptr(), t_dust.data_ptr(), q_abs.data_ptr(),

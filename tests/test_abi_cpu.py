@@ -85,7 +85,7 @@ def test_null_context_calls(rtlib):
     L = rtlib.lib
     assert L.rt_set_star(None, 5800.0, 7e10) == rtlib.RT_ERR_INVALID_ARG
     assert L.rt_irradiate(None, None, None, None, None, None) == rtlib.RT_ERR_INVALID_ARG
-    assert L.rt_set_tuning(None, 8, 8) == rtlib.RT_ERR_INVALID_ARG
+    assert L.rt_set_tuning(None, 0, 8, 8, 0) == rtlib.RT_ERR_INVALID_ARG
     L.rt_destroy(None)
 
 

@@ -44,17 +44,22 @@ def test_disk2d(precision, rtol):
 # --------------------------------------------------------------------------
 RAGGED = [(1, 1, 1, 1), (2, 3, 1, 2), (3, 5, 2, 5), (33, 7, 3, 9), (65, 9, 2, 17),
           (129, 3, 5, 79), (257, 2, 3, 32), (512, 3, 2, 128)]
-SHAPES = {"fp32_kahan": [(2, 4), (4, 4), (8, 4), (16, 4), (4, 8), (8, 8), (16, 8)],
-          "fp32_plain": [(2, 4), (8, 8), (16, 8)],
-          "fp64": [(2, 4), (4, 4), (8, 4)]}
+def shapes_of(tr):
+    """Every compiled launch shape that applies to the tracer's grid."""
+    return tr.tunings()
 
 
 @pytest.mark.parametrize("dims", RAGGED, ids=lambda d: "x".join(map(str, d)))
 def test_ragged_all_shapes(dims):
+    from paper_1001_3301_gb300 import Tracer
     nr, nth, nph, nnu = dims
     w = _w3(nr, nth, nph, nnu, tau=10.0, seed=nr + nth)
     orc = _parity.oracle_for(w)
-    for shape in SHAPES["fp32_kahan"]:
+    shapes = shapes_of(Tracer.from_grid(w.grid))
+    assert any(s[0] == 0 for s in shapes)
+    if nr <= 512:
+        assert any(s[0] == 1 for s in shapes)  # the warp-per-ray kernel applies
+    for shape in shapes:
         q, a, e = _parity.run_gpu(w, "fp32_kahan", shape=shape)
         _parity.assert_parity(w, q, a, e, orc, label=f"{dims} {shape}")
 
@@ -63,8 +68,9 @@ def test_ragged_all_shapes(dims):
 def test_ragged_other_precisions(precision):
     w = _w3(65, 9, 2, 17, tau=10.0, seed=3)
     orc = _parity.oracle_for(w)
+    from paper_1001_3301_gb300 import Tracer
     rtol = 3e-7 if precision == "fp64" else 1e-4
-    for shape in SHAPES[precision]:
+    for shape in shapes_of(Tracer.from_grid(w.grid, precision)):
         q, a, e = _parity.run_gpu(w, precision, shape=shape)
         _parity.assert_parity(w, q, a, e, orc, rtol_q=rtol, rtol_a=rtol,
                               rtol_energy=1e-6, label=f"{precision} {shape}")
@@ -209,6 +215,28 @@ def test_absorbed_fraction_sweep():
     assert rel.max() < 3e-6, rel.max()
 
 
+@pytest.mark.parametrize("n_nu", [5, 40])
+def test_absorbed_fraction_classes(n_nu):
+    """Many bins spanning 7 decades of opacity over one-cell rays whose optical
+    depths rise slowly from ray to ray: every warp meets every Taylor class, the
+    mixed class and the MUFU class, including bins right at their boundaries."""
+    n = 6000
+    g = synth.log_grid(1, n, 1)
+    dn = np.geomspace(1e-12, 2.0, n)                 # column density per ray (g/cm^2)
+    nu = synth.nu_bins(n_nu)
+    kap = np.geomspace(1e-3, 3e4, n_nu)
+    rho = (dn / (g.r_if[1] - g.r_if[0])).reshape(g.shape)
+    w = synth.Workload("classes", g, nu, kap, rho, np.full(g.shape, 50.0))
+    orc = _parity.oracle_for(w)
+    from paper_1001_3301_gb300 import Tracer
+    for shape in shapes_of(Tracer.from_grid(w.grid)):
+        q, a, e = _parity.run_gpu(w, shape=shape)
+        m = orc.q_abs > 0
+        rel = np.abs(q[m] - orc.q_abs[m]) / orc.q_abs[m]
+        assert rel.max() < 3e-6, (shape, rel.max())
+        assert abs(e.rel_err) < 1e-6
+
+
 def test_nonfinite_input_is_flagged():
     import torch
     from paper_1001_3301_gb300 import Tracer
@@ -252,7 +280,7 @@ def test_not_configured_and_bad_args():
         tr.set_opacity_table([2e14, 1e14], [1.0, 2.0], 1500.0)
     assert ei.value.status == RT_ERR_INVALID_ARG
     with pytest.raises(RtError) as ei:
-        tr.set_tuning(3, 4)
+        tr.set_tuning(0, 3, 4, 0)
     assert ei.value.status == RT_ERR_INVALID_ARG
     tr.close()
 
@@ -319,7 +347,7 @@ def test_autotune_and_streams():
         q = torch.empty_like(rho)
         a = torch.empty_like(rho)
         shape = tr.autotune(rho, td, q, a, reps=2)
-        assert shape in [tuple(x) for x in SHAPES["fp32_kahan"]]
+        assert shape in tr.tunings()
         q, a, e = tr.irradiate(rho, td, q, a, energy=True)
     s.synchronize()
     _parity.assert_parity(w, q.double().cpu().numpy(), a.double().cpu().numpy(), e, orc)
@@ -336,3 +364,6 @@ def test_ex2_accuracy():
     ref = np.exp2(x.double().cpu().numpy())
     rel = np.abs(y - ref) / ref
     assert rel.max() < 2.0 ** -21, rel.max()
+    # 2^0 is exactly 1, so 1 - ex2(y) of a cell without dust is exactly 0
+    z = probe_ex2(torch.zeros(4, dtype=torch.float32, device="cuda"))
+    assert torch.all(z == 1.0)
