@@ -192,6 +192,45 @@ const char *rt_last_error(const rt_ctx *ctx);
 /* rt_status_string -- constant name of a status code. */
 const char *rt_status_string(int status);
 
+/* ---- allocation-free form (no counterpart in the paper) -------------------- */
+
+/* Limits of rt_irradiate_static: its scratch is one fixed device array of about
+ * 1.9 MB that every GPU loading this library holds until the process exits. */
+#define RT_STATIC_MAX_NR     1024
+#define RT_STATIC_MAX_NTHETA 8192
+#define RT_STATIC_MAX_NPHI   8192
+#define RT_STATIC_MAX_RAYS   131072   /* ntheta * nphi */
+
+/* rt_irradiate_static -- the whole trace in one call that allocates no memory.
+ *
+ * For callers that cannot allocate device memory when they need the irradiation:
+ * host codes whose own pool allocator has already reserved the GPU, or time loops
+ * in which cudaMalloc/cudaFree (both synchronise the device) would stall other
+ * work. Instead of a context (rt_create allocates), everything is passed in and
+ * every intermediate lives in one file-scope device array of fixed size.
+ *   g, t_star, r_star, n_nu, nu_mid, kappa, t_sub, kappa_bf16
+ *       as for rt_create, rt_set_star and rt_set_opacity_table (host memory);
+ *       additionally nr <= RT_STATIC_MAX_NR, ntheta <= RT_STATIC_MAX_NTHETA,
+ *       nphi <= RT_STATIC_MAX_NPHI and ntheta * nphi <= RT_STATIC_MAX_RAYS;
+ *       larger grids are rejected with RT_ERR_INVALID_ARG (use rt_irradiate).
+ *   rho, t_dust, q_abs, a_rad, energy
+ *       as for rt_irradiate (device fields owned by the caller; energy may be NULL).
+ *   cuda_stream
+ *       the stream to work on (NULL = legacy default stream).
+ * No cudaMalloc, cudaFree or allocating library call is made. The call copies the
+ * grid and bin arrays into the array, runs the set-up kernels, reads back a few
+ * scalars (so it synchronises the stream), then launches the tracer; with energy
+ * it synchronises again. The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any stream
+ * capture. Every call uses the same array and leaves its contents behind: calls
+ * whose work overlaps on the GPU (other streams, other host threads) race with
+ * each other; calls on one stream are ordered. Errors as rt_create and
+ * rt_irradiate; the failure text is rt_last_error(NULL). */
+int rt_irradiate_static(const rt_grid_desc *g, double t_star, double r_star, int n_nu,
+                        const double *nu_mid, const double *kappa, double t_sub, int kappa_bf16,
+                        const float *rho, const float *t_dust, float *q_abs, float *a_rad,
+                        rt_energy *energy, void *cuda_stream);
+
 /* ---- diagnostics (no counterpart in the paper) ---------------------------- */
 
 /* rt_probe_ex2 -- y[i] = 2^x[i] with the hardware approximation the FP32 tracer

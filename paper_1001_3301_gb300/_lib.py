@@ -66,6 +66,8 @@ SIGNATURES = {
     "rt_destroy": (None, [_P]),
     "rt_last_error": (ctypes.c_char_p, [_P]),
     "rt_status_string": (ctypes.c_char_p, [_I]),
+    "rt_irradiate_static": (_I, [ctypes.POINTER(RtGridDesc), _D, _D, _I, _DP, _DP, _D, _I,
+                                 _P, _P, _P, _P, ctypes.POINTER(RtEnergy), _P]),
     "rt_probe_ex2": (_I, [_P, _P, ctypes.c_longlong, _P]),
     "rt_probe_alu_rates": (_I, [_DP, _DP, _DP]),
 }

@@ -272,6 +272,11 @@ void free_all(rt_ctx *c)
 
 }  // namespace
 
+namespace rt {
+// failure text of context-less calls, reported by rt_last_error(NULL)
+void set_thread_error(const std::string &msg) { g_create_err = msg; }
+}  // namespace rt
+
 extern "C" {
 
 int rt_create(const rt_grid_desc *g, void *cuda_stream, rt_ctx **out)
