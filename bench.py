@@ -39,8 +39,11 @@ NR, NTH, NPH, NNU = 256, 128, 256, 79
 def workload_name(taus):
     return (f"disk3d {NR}x{NTH}x{NPH} (r,theta,phi), {NNU} nu bins, tau550 in "
             f"{{{','.join(f'{t:g}' for t in taus)}}}, env+20% lognormal, T_dust U(20,1600)")
-EXP_PER_CELL_NU = 2  # e^{-tau_in} and e^{-dtau} per (cell, bin): the direct form
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_trace_disk3d_256x128x256_nu79.md")
+# exp-class operations per (cell, bin) the method cannot avoid: e^{-tau_in}. The
+# absorbed fraction 1 - e^{-dtau} needs a second one only where dtau is not small.
+EXP_PER_CELL_NU = 1
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_ray_disk3d_256x128x256_nu79.md")
+KERNEL_SOURCES = ("rt_ray.cu", "rt_device.cuh")
 
 
 def parse():
@@ -145,8 +148,10 @@ def traffic_from_profile(src_hash: str):
 
 
 def kernel_source_hash():
-    p = os.path.join(ROOT, "paper_1001_3301_gb300", "csrc", "rt_trace.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1001_3301_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 # --------------------------------------------------------------------------
@@ -342,7 +347,8 @@ def run_ours(args, rank, world, local):
                        "replicas_per_rank": 1},
             "roofline": {"bound": "alu", "unit": "Gop/s (MUFU ex2)", "achieved": achieved,
                          "peak": peak, "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_trace", "ops_per_cell_nu": EXP_PER_CELL_NU,
+                         "kernel": "k_ray" if shape[0] == 1 else "k_trace",
+                         "ops_per_cell_nu": EXP_PER_CELL_NU,
                          "avg_launch_ms": avg_launch_s * 1e3,
                          "peak_basis": f"measured {ex2_clk:.2f} ex2/SM/clk x {nsm} SMs x {mhz:.0f} MHz",
                          "ffma_per_sm_clk": ffma_clk, "kernel_source_sha256": src_hash},
