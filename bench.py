@@ -59,6 +59,13 @@ def parse():
                    help="comma-separated tau550 values of the grids in one step")
     p.add_argument("--shape", default=None,
                    help="force the tracer shape 'kind,cells_per_lane,warps,min_blocks' (skips the autotuner)")
+    p.add_argument("--precision-sweep", action="store_true",
+                   help="instead of the throughput line: error of every precision mode against the "
+                        "FP64 oracle on the 512x256x512, 79-bin disk at tau550 = 1 and 100")
+    p.add_argument("--sweep-grid", default="512x256x512")
+    p.add_argument("--batch", action="store_true",
+                   help="instead of the throughput line of the 4-grid step: the 96-grid uneven "
+                        "batch (one persistent launch per step, CUDA-graph replay)")
     return p.parse_args()
 
 
@@ -366,9 +373,137 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def bf16_round(x):
+    """Round float64 values to bfloat16 (through float32, nearest-even)."""
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def run_precision_sweep(args, local):
+    """Errors of q_abs, a_rad and the energy sums of every precision mode (scan in
+    FP64, compensated FP32, plain FP32; opacity table in FP32 or BF16) against the
+    FP64 oracle, in the cells that absorb more than 1e-12 L*."""
+    import torch
+    import oracle
+    from paper_1001_3301_gb300 import Tracer
+    torch.cuda.set_device(local)
+    oracle.build()
+    nr, nth, nph = (int(x) for x in args.sweep_grid.split("x"))
+    rows = []
+    for tau in (1.0, 100.0):
+        w = synth.disk3d(nr, nth, nph, n_nu=NNU, tau550=tau, seed=2)
+        rho = torch.from_numpy(w.rho32()).cuda()
+        td = torch.from_numpy(w.tdust32()).cuda()
+        t0 = time.perf_counter()
+        orc = oracle.irradiate_workload(w, nthreads=oracle.max_threads())
+        t_orc = time.perf_counter() - t0
+        orc_b = oracle.irradiate_workload(w, kappa=bf16_round(w.kappa), nthreads=oracle.max_threads())
+        mask = orc.p_abs > 1e-12 * orc.l_star
+        for prec in ("fp64", "fp32_kahan", "fp32_plain"):
+            for bf16 in (False, True):
+                tr = Tracer.from_grid(w.grid, prec)
+                tr.set_opacity_table(w.nu, w.kappa, w.t_sub, kappa_bf16=bf16)
+                tr.set_star(w.t_star, w.r_star)
+                q, a, e = tr.irradiate(rho, td, energy=True)
+                torch.cuda.synchronize()
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                reps = 3
+                ev[0].record()
+                for _ in range(reps):
+                    tr.irradiate(rho, td, q, a)
+                ev[1].record()
+                torch.cuda.synchronize()
+                ms = ev[0].elapsed_time(ev[1]) / reps
+                qh, ah = q.double().cpu().numpy(), a.double().cpu().numpy()
+                row = {"tau550": tau, "scan": prec, "kappa_table": "bf16" if bf16 else "fp32",
+                       "ms": ms, "cell_nu_per_s": w.grid.ncells * NNU / (ms * 1e-3),
+                       "tuning": tr.tuning(), "cells_in_mask": int(mask.sum())}
+                for ref_name, ref in (("vs_fp64_oracle", orc), ("vs_oracle_same_table", orc_b if bf16 else orc)):
+                    rq = np.abs(qh[mask] - ref.q_abs[mask]) / ref.q_abs[mask]
+                    ra = np.abs(ah[mask] - ref.a_rad[mask]) / np.abs(ref.a_rad[mask])
+                    row[ref_name] = {"q_max": float(rq.max()), "q_p999": float(np.quantile(rq, 0.999)),
+                                     "a_max": float(ra.max()), "a_p999": float(np.quantile(ra, 0.999)),
+                                     "e_abs_rel": abs(e.e_abs - ref.e_abs) / ref.l_star,
+                                     "energy_closure": e.rel_err}
+                rows.append(row)
+                tr.close()
+                del q, a
+        rows.append({"tau550": tau, "oracle_seconds": t_orc, "oracle_cores": oracle.max_threads()})
+        del rho, td, orc, orc_b
+        torch.cuda.empty_cache()
+    print(json.dumps({"mode": "precision_sweep", "grid": args.sweep_grid, "nu_bins": NNU,
+                      "mask": "cells absorbing > 1e-12 L*", "rows": rows}), flush=True)
+
+
+def run_batch(args, local):
+    """cell-nu updates/s of the 96-grid batch (Nr 64-512, Ntheta 32-256, Nphi 1/64/128,
+    32/79/128 bins, tau550 log-uniform 0.1-100), one graph replay per step."""
+    import torch
+    from paper_1001_3301_gb300 import Batch, Tracer
+    torch.cuda.set_device(local)
+    specs = synth.batch_specs(96, seed=3)
+    trs, rho, td, q, a = [], [], [], [], []
+    units = 0
+    for sp in specs:
+        w = synth.disk3d(sp["nr"], sp["ntheta"], sp["nphi"], n_nu=sp["n_nu"], tau550=sp["tau550"],
+                         seed=sp["seed"])
+        tr = Tracer.from_grid(w.grid, args.precision)
+        tr.set_opacity_table(w.nu, w.kappa, w.t_sub)
+        tr.set_star(w.t_star, w.r_star)
+        trs.append(tr)
+        rho.append(torch.from_numpy(w.rho32()).cuda())
+        td.append(torch.from_numpy(w.tdust32()).cuda())
+        q.append(torch.empty_like(rho[-1]))
+        a.append(torch.empty_like(rho[-1]))
+        units += w.grid.ncells * len(w.nu)
+    b = Batch(trs)
+    shape = b.autotune(rho, td, q, a, reps=2)
+    for _ in range(args.warmup):
+        b.run(rho, td, q, a)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            b.run(rho, td, q, a)
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    es = b.energy()
+    # the same grids one launch each (rt_irradiate, autotuned per shape class)
+    for tr, r, t, qq, aa in zip(trs, rho, td, q, a):
+        tr.autotune(r, t, qq, aa, reps=1)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        for tr, r, t, qq, aa in zip(trs, rho, td, q, a):
+            tr.irradiate(r, t, qq, aa)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_single = e0.elapsed_time(e1) / args.steps
+    b.close()
+    for tr in trs:
+        tr.close()
+    print(json.dumps({"mode": "batch", "grids": len(specs), "cells": sum(x.numel() for x in rho),
+                      "cell_nu_per_step": units, "ms_per_step": ms, "value": units / (ms * 1e-3),
+                      "unit": UNIT, "tuning": shape, "steps": args.steps,
+                      "per_grid_launches_ms": ms_single, "per_grid_launches_value": units / (ms_single * 1e-3),
+                      "energy_max_rel_err": max(abs(e.rel_err) for e in es),
+                      "clocks": clk.summary()}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.batch:
+        if rank == 0:
+            run_batch(args, local)
+        return
+    if args.precision_sweep:
+        if rank == 0:
+            run_precision_sweep(args, local)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

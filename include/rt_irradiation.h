@@ -192,6 +192,51 @@ const char *rt_last_error(const rt_ctx *ctx);
 /* rt_status_string -- constant name of a status code. */
 const char *rt_status_string(int status);
 
+/* ---- many grids in one launch --------------------------------------------- */
+
+#define RT_BATCH_MAX 256  /* contexts per batch */
+
+typedef struct rt_batch rt_batch;
+
+/* rt_batch_create -- plan one persistent launch over several grids of any size
+ * (each a configured context; all of one precision and one device; each below
+ * 2^31 - 2^16 flattened cells). The grids' tiles are concatenated and split over
+ * the CTAs by cost (tiles weighted by the grid's bin count); the launch, a reset of
+ * the energy partials and a per-grid FP64 energy reduction are built into a CUDA
+ * graph once. The contexts must outlive the batch and must not be reconfigured
+ * while it exists (re-create the batch after rt_set_star/rt_set_opacity_table).
+ *   ctxs  [n] contexts, n in 1..RT_BATCH_MAX;  cuda_stream  the stream runs use.
+ * Errors: RT_ERR_INVALID_ARG, RT_ERR_NOT_CONFIGURED, RT_ERR_CUDA, RT_ERR_NO_MEMORY;
+ * failure text via rt_last_error(NULL). */
+int rt_batch_create(rt_ctx *const *ctxs, int n, void *cuda_stream, rt_batch **out);
+
+/* rt_batch_run -- trace every grid of the batch (the semantics of rt_irradiate
+ * per grid). rho[g], t_dust[g], q_abs[g], a_rad[g]: device fields of grid g, layout
+ * as in rt_irradiate. One graph replay on the batch's stream; does not
+ * synchronise. Errors: RT_ERR_INVALID_ARG (NULL pointer), RT_ERR_CUDA. */
+int rt_batch_run(rt_batch *b, const float *const *rho, const float *const *t_dust,
+                 float *const *q_abs, float *const *a_rad);
+
+/* rt_batch_energy -- the energy sums of every grid of the last run into host
+ * energies[n]; synchronises. RT_ERR_NONFINITE_INPUT if any field held invalid
+ * values (energies are still filled). */
+int rt_batch_energy(rt_batch *b, rt_energy *energies);
+
+/* rt_batch_autotune -- time every compiled tile shape of the batch's precision on
+ * the given fields (overwriting q_abs and a_rad), keep the fastest and rebuild the
+ * graph. reps >= 1. Synchronises. rt_batch_get_tuning reports the shape in use
+ * (kind is always RT_KERNEL_TILE). */
+int rt_batch_autotune(rt_batch *b, const float *const *rho, const float *const *t_dust,
+                      float *const *q_abs, float *const *a_rad, int reps);
+int rt_batch_get_tuning(const rt_batch *b, int *kind, int *cells_per_lane, int *warps_per_block,
+                        int *min_blocks_per_sm);
+
+/* rt_batch_last_error -- text of the batch's last failure ("" if none). */
+const char *rt_batch_last_error(const rt_batch *b);
+
+/* rt_batch_destroy -- wait for the batch's stream, free the batch (NULL ignored). */
+void rt_batch_destroy(rt_batch *b);
+
 /* ---- allocation-free form (no counterpart in the paper) -------------------- */
 
 /* Limits of rt_irradiate_static: its scratch is one fixed device array of about

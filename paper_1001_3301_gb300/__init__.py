@@ -9,11 +9,11 @@ from __future__ import annotations
 
 from .build import build  # noqa: F401
 
-__all__ = ["build", "Tracer", "Energy", "probe_ex2", "probe_alu_rates"]
+__all__ = ["build", "Tracer", "Batch", "Energy", "probe_ex2", "probe_alu_rates"]
 
 
 def __getattr__(name):
-    if name in ("Tracer", "Energy", "probe_ex2", "probe_alu_rates"):
+    if name in ("Tracer", "Batch", "Energy", "probe_ex2", "probe_alu_rates"):
         from . import tracer
         return getattr(tracer, name)
     raise AttributeError(name)

@@ -27,6 +27,7 @@ RT_FP32_KAHAN = 0
 RT_FP32_PLAIN = 1
 RT_FP64 = 2
 RT_MAX_NU = 128
+RT_BATCH_MAX = 256
 
 PRECISIONS = {"fp32_kahan": RT_FP32_KAHAN, "fp32_plain": RT_FP32_PLAIN, "fp64": RT_FP64}
 
@@ -66,6 +67,15 @@ SIGNATURES = {
     "rt_destroy": (None, [_P]),
     "rt_last_error": (ctypes.c_char_p, [_P]),
     "rt_status_string": (ctypes.c_char_p, [_I]),
+    "rt_batch_create": (_I, [ctypes.POINTER(_P), _I, _P, ctypes.POINTER(_P)]),
+    "rt_batch_run": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                          ctypes.POINTER(_P)]),
+    "rt_batch_energy": (_I, [_P, ctypes.POINTER(RtEnergy)]),
+    "rt_batch_autotune": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                               ctypes.POINTER(_P), _I]),
+    "rt_batch_get_tuning": (_I, [_P] + [ctypes.POINTER(_I)] * 4),
+    "rt_batch_last_error": (ctypes.c_char_p, [_P]),
+    "rt_batch_destroy": (None, [_P]),
     "rt_irradiate_static": (_I, [ctypes.POINTER(RtGridDesc), _D, _D, _I, _DP, _DP, _D, _I,
                                  _P, _P, _P, _P, ctypes.POINTER(RtEnergy), _P]),
     "rt_probe_ex2": (_I, [_P, _P, ctypes.c_longlong, _P]),

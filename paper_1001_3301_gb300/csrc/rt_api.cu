@@ -275,6 +275,36 @@ void free_all(rt_ctx *c)
 namespace rt {
 // failure text of context-less calls, reported by rt_last_error(NULL)
 void set_thread_error(const std::string &msg) { g_create_err = msg; }
+
+// The device tables of a configured context, for the batch launcher (rt_batch.cu):
+// a TraceArgs with every table pointer and size set (field pointers, partials and
+// validity word left for the caller), its scalars, and identity.
+bool ctx_view(const rt_ctx *c, CtxView *v)
+{
+    if (!c || !c->configured) return false;
+    TraceArgs a{};
+    a.nu = c->nu_tab;
+    a.kap = c->kap;
+    a.nu64 = c->nu64;
+    a.rtab = c->rtab;
+    a.rtab64 = c->rtab64;
+    a.domega = c->domega;
+    a.domega32 = c->domega32;
+    a.L = (unsigned)((c->L < kMaxLaunchCells) ? c->L : 0);
+    a.nrays = (unsigned)c->nrays;
+    a.r1div = FastDiv::make((unsigned)c->nr + 1u);
+    a.nr = c->nr;
+    a.nnu_pad = c->sc_h.nnu_pad;
+    a.n_active = c->sc_h.n_active;
+    a.t_sub = (float)c->t_sub;
+    v->args = a;
+    v->sc = c->sc;
+    v->precision = c->precision;
+    v->dev = c->dev;
+    v->flat_cells = c->L;
+    v->ncells = c->ncells;
+    return true;
+}
 }  // namespace rt
 
 extern "C" {

@@ -113,6 +113,21 @@ cudaError_t launch_ray_shape(int precision, Shape s, const TraceArgs &args, cuda
 cudaError_t launch_trace(int precision, Shape s, const TraceArgs &args, unsigned ntiles,
                          cudaStream_t stream, unsigned *grid_out);
 
+// A configured context's device tables, for the batch launcher (rt_api.cu).
+struct CtxView {
+    TraceArgs args;        // tables and sizes; field pointers, partials, validity word unset
+    DevScalars *sc;        // device scalars of the grid
+    int precision;
+    int dev;
+    long long flat_cells;  // nrays * (nr + 1)
+    long long ncells;
+};
+}  // namespace rt
+struct rt_ctx;
+namespace rt {
+bool ctx_view(const rt_ctx *c, CtxView *v);
+void set_thread_error(const std::string &msg);  // text for rt_last_error(NULL)
+
 // Set-up kernels (rt_setup.cu)
 cudaError_t launch_setup_bins(int n_nu, const double *nu_mid_dev, const double *kappa_dev,
                               double t_star, double r_star, int kappa_bf16,

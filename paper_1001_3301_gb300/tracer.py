@@ -193,3 +193,66 @@ def probe_alu_rates():
     a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     check(lib.rt_probe_alu_rates(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return a.value, b.value, c.value
+
+
+class Batch:
+    """Several configured tracers traced by one persistent launch replayed from a
+    CUDA graph (include/rt_irradiation.h, rt_batch_*). The tracers must outlive
+    the batch and keep their configuration."""
+
+    def __init__(self, tracers, stream=None):
+        n = len(tracers)
+        arr = (ctypes.c_void_p * n)(*[t._ctx.value for t in tracers])
+        b = ctypes.c_void_p()
+        check(lib.rt_batch_create(arr, n, ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(b)), None)
+        self._b = b
+        self.tracers = list(tracers)
+        self.n = n
+
+    def _ptrs(self, tensors, name):
+        if len(tensors) != self.n:
+            raise ValueError(f"{name}: expected {self.n} tensors")
+        for t, tr in zip(tensors, self.tracers):
+            tr._check_field(t, name)
+        return (ctypes.c_void_p * self.n)(*[t.data_ptr() for t in tensors])
+
+    def _check(self, status):
+        if status != _lib.RT_OK:
+            raise _lib.RtError(status, lib.rt_batch_last_error(self._b).decode())
+
+    def run(self, rho, t_dust, q_abs, a_rad):
+        """Trace every grid: lists of device tensors, one per tracer."""
+        self._check(lib.rt_batch_run(self._b, self._ptrs(rho, "rho"), self._ptrs(t_dust, "t_dust"),
+                                     self._ptrs(q_abs, "q_abs"), self._ptrs(a_rad, "a_rad")))
+
+    def energy(self):
+        out = (RtEnergy * self.n)()
+        self._check(lib.rt_batch_energy(self._b, out))
+        return [Energy(e) for e in out]
+
+    def autotune(self, rho, t_dust, q_abs, a_rad, reps: int = 3):
+        self._check(lib.rt_batch_autotune(self._b, self._ptrs(rho, "rho"), self._ptrs(t_dust, "t_dust"),
+                                          self._ptrs(q_abs, "q_abs"), self._ptrs(a_rad, "a_rad"), int(reps)))
+        return self.tuning()
+
+    def tuning(self):
+        v = [ctypes.c_int() for _ in range(4)]
+        self._check(lib.rt_batch_get_tuning(self._b, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib.rt_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
