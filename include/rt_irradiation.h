@@ -288,6 +288,27 @@ int rt_probe_ex2(const float *x, float *y, long long n, void *cuda_stream);
  * SM clock (MHz) measured during the ex2 run. Synchronises the device. */
 int rt_probe_alu_rates(double *ex2_per_sm_clk, double *ffma_per_sm_clk, double *sm_mhz);
 
+/* rt_probe_tanh -- y[i] = tanh(x[i]) with the hardware approximation (tanh.approx)
+ * the surrogate network's activations use: FP32 when packed_bf16 == 0, else the
+ * packed BF16 form applied to x[i] rounded to BF16. x, y: device, n floats.
+ * Synchronises `cuda_stream`. */
+int rt_probe_tanh(const float *x, float *y, long long n, int packed_bf16, void *cuda_stream);
+
+/* rt_probe_umma -- one fifth-generation tensor-core product D = A B^T with
+ * M = N = 128 and K = k (a multiple of 16, at most 128), through the shared-memory
+ * operand layout, matrix descriptors and TMEM read-back the surrogate's inference
+ * kernel uses. a, b: device, [128][k] BF16 bit patterns, row-major (both K-major);
+ * d: device, [128][128] FP32. Synchronises `cuda_stream`; RT_ERR_TIMEOUT if the
+ * product did not complete within the kernel's bounded wait. */
+int rt_probe_umma(const unsigned short *a, const unsigned short *b, int k, float *d, void *cuda_stream);
+
+/* rt_probe_tensor_rates -- sustained rates per SM per clock on the current device:
+ * multiply-adds of the warp-level BF16 MMA (mma.sync m16n8k16, 32 warps per SM)
+ * and of tcgen05 BF16 products with M = 128, K = 16 and N = 128 or 256 (one CTA
+ * per SM, one issuing thread); tanh.approx instructions in FP32 and packed BF16. */
+int rt_probe_tensor_rates(double *mma_sync_mac, double *umma_n128_mac, double *umma_n256_mac,
+                          double *tanh_f32, double *tanh_bf16x2);
+
 #ifdef __cplusplus
 }
 #endif

@@ -9,11 +9,13 @@ from __future__ import annotations
 
 from .build import build  # noqa: F401
 
-__all__ = ["build", "Tracer", "Batch", "Energy", "probe_ex2", "probe_alu_rates"]
+_LAZY = ("Tracer", "Batch", "Energy", "probe_ex2", "probe_alu_rates", "probe_tanh", "probe_umma",
+         "probe_tensor_rates")
+__all__ = ["build", *_LAZY]
 
 
 def __getattr__(name):
-    if name in ("Tracer", "Batch", "Energy", "probe_ex2", "probe_alu_rates"):
+    if name in _LAZY:
         from . import tracer
         return getattr(tracer, name)
     raise AttributeError(name)

@@ -80,6 +80,9 @@ SIGNATURES = {
                                  _P, _P, _P, _P, ctypes.POINTER(RtEnergy), _P]),
     "rt_probe_ex2": (_I, [_P, _P, ctypes.c_longlong, _P]),
     "rt_probe_alu_rates": (_I, [_DP, _DP, _DP]),
+    "rt_probe_tanh": (_I, [_P, _P, ctypes.c_longlong, _I, _P]),
+    "rt_probe_umma": (_I, [_P, _P, _I, _P, _P]),
+    "rt_probe_tensor_rates": (_I, [_DP, _DP, _DP, _DP, _DP]),
 }
 
 

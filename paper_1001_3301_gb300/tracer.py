@@ -195,6 +195,35 @@ def probe_alu_rates():
     return a.value, b.value, c.value
 
 
+def probe_tanh(x, packed_bf16=False):
+    """tanh(x) with the hardware approximation of the surrogate's activations."""
+    import torch
+    y = torch.empty_like(x)
+    check(lib.rt_probe_tanh(x.data_ptr(), y.data_ptr(), x.numel(), int(bool(packed_bf16)),
+                            ctypes.c_void_p(_stream_handle())))
+    return y
+
+
+def probe_umma(a_bits, b_bits):
+    """D = A B^T (128 x 128) on the tcgen05 tensor core; a_bits, b_bits: int16 CUDA
+    tensors [128][k] holding BF16 bit patterns."""
+    import torch
+    k = a_bits.shape[1]
+    d = torch.empty((128, 128), dtype=torch.float32, device=a_bits.device)
+    check(lib.rt_probe_umma(a_bits.data_ptr(), b_bits.data_ptr(), k, d.data_ptr(),
+                            ctypes.c_void_p(_stream_handle())))
+    return d
+
+
+def probe_tensor_rates():
+    """Per SM per clock: mma.sync MACs, tcgen05 MACs at N = 128 and 256, tanh.approx
+    f32 and packed-bf16 instructions."""
+    v = [ctypes.c_double() for _ in range(5)]
+    check(lib.rt_probe_tensor_rates(*[ctypes.byref(x) for x in v]))
+    return dict(zip(("mma_sync_mac", "umma_n128_mac", "umma_n256_mac", "tanh_f32", "tanh_bf16x2"),
+                    (x.value for x in v)))
+
+
 class Batch:
     """Several configured tracers traced by one persistent launch replayed from a
     CUDA graph (include/rt_irradiation.h, rt_batch_*). The tracers must outlive
