@@ -66,6 +66,14 @@ def parse():
     p.add_argument("--batch", action="store_true",
                    help="instead of the throughput line of the 4-grid step: the 96-grid uneven "
                         "batch (one persistent launch per step, CUDA-graph replay)")
+    p.add_argument("--no-surrogate", action="store_true",
+                   help="skip the learned-surrogate leg of the default line")
+    p.add_argument("--surrogate", action="store_true",
+                   help="print only the learned-surrogate leg (train, then time against the exact tracer)")
+    p.add_argument("--sur-grid", default="512x256x512", help="grid the surrogate is timed on")
+    p.add_argument("--sur-train-grid", default="256x128x128", help="geometry of the training fields")
+    p.add_argument("--sur-steps", type=int, default=60000, help="Adam steps of the surrogate training")
+    p.add_argument("--sur-reps", type=int, default=10, help="timed calls per mode")
     return p.parse_args()
 
 
@@ -339,6 +347,14 @@ def run_ours(args, rank, world, local):
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(ws)
+    sur = None
+    if rank == 0 and world == 1 and not args.no_surrogate:
+        for tr in tracers:  # free the step's grids first
+            tr.close()
+        tracers = []
+        del rho, td, q, a
+        torch.cuda.empty_cache()
+        sur = run_surrogate(args, local)
 
     if rank == 0:
         line = {
@@ -365,12 +381,127 @@ def run_ours(args, rank, world, local):
             "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                        "reasons": clocks["reasons"]},
             "energy_max_rel_err": max_energy_err,
+            "surrogate": sur,
         }
         print(json.dumps(line), flush=True)
     for tr in tracers:
         tr.close()
     if dist:
         dist.destroy_process_group()
+
+
+SUR_TAUS = (0.1, 0.3, 1.0, 3.0, 10.0, 30.0, 100.0)
+SUR_TOL = 1e-3
+
+
+def _dims(spec):
+    return tuple(int(x) for x in spec.split("x"))
+
+
+def run_surrogate(args, local):
+    """The learned surrogate (8 -> 128 -> 128 -> 1 SiLU network on the tensor cores):
+    trained on cells the exact tracer traced on seven optical depths (0.1-100) of the
+    disk, then timed against the exact tracer on the surrogate grid (tau550 = 1,
+    seed 2): gated by its trust map (validate = 0), the network alone (validate = 2),
+    and judged by the exact tracer (validate = 1) for its error."""
+    import torch
+    from paper_1001_3301_gb300 import Tracer, probe_alu_rates, probe_tensor_rates
+    torch.cuda.set_device(local)
+    nr, nth, nph = _dims(args.sur_train_grid)
+    trs = []
+    t0 = time.perf_counter()
+    train_w = [synth.disk3d(nr, nth, nph, n_nu=NNU, tau550=t, seed=10 + i) for i, t in enumerate(SUR_TAUS)]
+    t_gen = time.perf_counter() - t0
+    tr_train = Tracer.from_grid(train_w[0].grid)
+    tr_train.set_opacity_table(train_w[0].nu, train_w[0].kappa, train_w[0].t_sub)
+    tr_train.set_star(train_w[0].t_star, train_w[0].r_star)
+    rho_t = [torch.from_numpy(w.rho32()).cuda() for w in train_w]
+    td_t = [torch.from_numpy(w.tdust32()).cuda() for w in train_w]
+    st = tr_train.surrogate_train(rho_t, td_t, n_samples=20_000_000, batch=8192, steps=args.sur_steps,
+                                  lr=1e-3, seed=1)
+    del rho_t, td_t
+    path = os.path.join(os.environ.get("TMPDIR", "/tmp"), f"rt_surrogate_{os.getpid()}.bin")
+    tr_train.surrogate_save(path)
+    tr_train.close()
+
+    nr, nth, nph = _dims(args.sur_grid)
+    w = synth.disk3d(nr, nth, nph, n_nu=NNU, tau550=1.0, seed=2)
+    tr = Tracer.from_grid(w.grid)
+    tr.set_opacity_table(w.nu, w.kappa, w.t_sub)
+    tr.set_star(w.t_star, w.r_star)
+    tr.surrogate_load(path)
+    os.remove(path)
+    rho = torch.from_numpy(w.rho32()).cuda()
+    td = torch.from_numpy(w.tdust32()).cuda()
+    q_ex = torch.empty_like(rho)
+    a_ex = torch.empty_like(rho)
+    q_s = torch.empty_like(rho)
+    a_s = torch.empty_like(rho)
+    shape = tr.autotune(rho, td, q_ex, a_ex, reps=2)
+    _, _, e = tr.irradiate(rho, td, q_ex, a_ex, energy=True)
+    _, _, vst = tr.irradiate_surrogate(rho, td, q_s, a_s, err_tol=SUR_TOL, validate=1)
+    _, _, gst = tr.irradiate_surrogate(rho, td, q_s, a_s, err_tol=SUR_TOL, validate=0)
+    # error of the gated result against the exact tracer where a cell absorbs > 1e-12 L*
+    g = w.grid
+    dom = torch.from_numpy(np.outer(np.diff(g.phi_if), np.cos(g.theta_if[:-1]) - np.cos(g.theta_if[1:]))).cuda()
+    d3 = torch.from_numpy((g.r_if[1:] ** 3 - g.r_if[:-1] ** 3) / 3.0).cuda()
+    mask = (q_ex.double() * dom[:, :, None] * d3[None, None, :]) > 1e-12 * e.l_star
+    rel = ((q_s.double() - q_ex.double()).abs() / q_ex.double().clamp_min(1e-300))[mask]
+    gate_max = float(rel.max()) if rel.numel() else 0.0
+    gate_over = int((rel > SUR_TOL).sum()) if rel.numel() else 0
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.sur_reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.sur_reps
+
+    with ClockSampler(local) as clk:
+        time.sleep(0.2)
+        t_ex = timed(lambda: tr.irradiate(rho, td, q_ex, a_ex))
+        t_gate = timed(lambda: tr.irradiate_surrogate(rho, td, q_s, a_s, err_tol=SUR_TOL, validate=0, stats=False))
+        t_net = timed(lambda: tr.irradiate_surrogate(rho, td, q_s, a_s, err_tol=SUR_TOL, validate=2, stats=False))
+    clocks = clk.summary()
+    rates = probe_tensor_rates()
+    ex2_clk, _, probe_mhz = probe_alu_rates()
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = clocks["sm_mhz"] or probe_mhz
+    n = g.ncells
+    # MUFU work of the network per cell: 256 SiLU = 256 ex2 + 256 rcp; the clock
+    # cycles one SM needs for it at the measured rates bound the network alone
+    clk_per_cell = 256.0 / ex2_clk + 256.0 / rates["rcp_f32"]
+    peak_cells = nsm * mhz * 1e6 / clk_per_cell
+    tr.close()
+    return {
+        "workload": f"disk3d {nr}x{nth}x{nph}, {NNU} nu bins, tau550 = 1, seed 2; trained on "
+                    f"{args.sur_train_grid} x {len(SUR_TAUS)} optical depths 0.1-100",
+        "err_tol": SUR_TOL,
+        "exact": {"ms": t_ex, "cells_per_s": n / (t_ex * 1e-3), "cell_nu_per_s": n * NNU / (t_ex * 1e-3),
+                  "launch_shape": list(shape)},
+        "gated": {"ms": t_gate, "cells_per_s": n / (t_gate * 1e-3),
+                  "equiv_cell_nu_per_s": n * NNU / (t_gate * 1e-3), "speedup_vs_exact": t_ex / t_gate,
+                  "fallback_frac": gst["n_fallback"] / max(gst["n_dust"], 1),
+                  "max_rel_err_vs_exact": gate_max, "cells_over_tol": gate_over,
+                  "judged_cells": int(mask.sum()), "energy_rel_err": gst["rel_err"]},
+        "network_only": {"ms": t_net, "cells_per_s": n / (t_net * 1e-3),
+                         "equiv_cell_nu_per_s": n * NNU / (t_net * 1e-3), "speedup_vs_exact": t_ex / t_net},
+        "validate": {"answered_frac": 1 - vst["n_fallback"] / max(vst["n_dust"], 1),
+                     "max_rel_err": vst["max_rel_err"], "mean_rel_err": vst["mean_rel_err"]},
+        "train": {"n_train": st["n_train"], "n_val": st["n_val"], "steps": args.sur_steps, "batch": 8192,
+                  "val_rms_ln_g": st["val_rms"], "val_max_ln_g": st["val_max"], "train_ms": st["train_ms"],
+                  "field_generation_s": t_gen},
+        "roofline": {"bound": "alu", "unit": "cells/s (MUFU: 256 ex2 + 256 rcp per cell)",
+                     "achieved": n / (t_net * 1e-3), "peak": peak_cells, "frac": n / (t_net * 1e-3) / peak_cells,
+                     "peak_basis": f"measured {ex2_clk:.1f} ex2 and {rates['rcp_f32']:.1f} rcp /SM/clk x {nsm} SMs x {mhz:.0f} MHz",
+                     "tensor_mac_per_cell": 36864, "umma_mac_per_sm_clk": rates["umma_n128_mac"]},
+        "clocks": clocks,
+    }
 
 
 def bf16_round(x):
@@ -503,6 +634,10 @@ def main():
     if args.precision_sweep:
         if rank == 0:
             run_precision_sweep(args, local)
+        return
+    if args.surrogate:
+        if rank == 0:
+            print(json.dumps({"mode": "surrogate", **run_surrogate(args, local)}), flush=True)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)

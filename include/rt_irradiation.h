@@ -278,6 +278,117 @@ int rt_irradiate_static(const rt_grid_desc *g, double t_star, double r_star, int
 
 /* ---- diagnostics (no counterpart in the paper) ---------------------------- */
 
+/* ------------------------------------------------------------------------
+ * Learned surrogate of the per-bin sum of one cell.
+ *
+ * Along a ray the tracer gives a cell with dust column N_in in front of it and
+ * dust column dN of its own the absorbed share
+ *     acc = sum_i (F_i / F_max) exp(-kappa_i N_in) (1 - exp(-kappa_i dN))
+ * of the power R*^2 F_max dOmega entering the ray (Sect. 2.3, Eqs. 17, 28-32, 36).
+ * The surrogate is an 8 -> 128 -> 128 -> 1 SiLU network whose inputs are
+ *     x_m = log2(kappa_m N_in + 2^-20) / 16   (m = 0..5: the bins nearest 1e11,
+ *                                              1e12, ..., 1e16 Hz in |ln nu|),
+ *     x_6 = T_dust / 1000 - 0.8,
+ *     x_7 = log2(kappa_550 dN + 2^-30) / 16   (the bin nearest 550 nm),
+ * and whose output y gives g = acc / (kappa_550 dN) by ln g = mu + sigma y. Then
+ * q_abs = Gq g kappa_550 dN and a_rad = q_abs / (rho c) = Gq (dr / c) g kappa_550.
+ * BF16 weights with FP32 accumulation on the tensor cores: W1, b1 and W2 in BF16,
+ * b2, w3 and b3 in FP32; inputs and first-layer activations reach the tensor core
+ * as sums of BF16 parts, so they keep FP32-like precision.
+ *
+ * A surrogate belongs to one context and is valid for the opacity table,
+ * sublimation temperature and stellar temperature it was made with (other grids
+ * and stellar radii are fine: the inputs and output do not depend on them).
+ * ------------------------------------------------------------------------ */
+#define RT_SUR_NPARAMS 17793   /* W1 [8][128], b1 [128], W2 [128][128], b2 [128], w3 [128], b3 */
+
+typedef struct {
+    long long n_samples;  /* training cells drawn from the grids; <= 0: 20,000,000 */
+    int batch;            /* minibatch rows, a multiple of 256; <= 0: 8192 */
+    int steps;            /* Adam steps (warm-up, then cosine decay); <= 0: 30000 */
+    float lr;             /* peak learning rate; <= 0: 2e-3 */
+    unsigned long long seed;
+} rt_train_cfg;
+
+typedef struct {
+    long long n_train, n_val;  /* cells collected for training / held out */
+    double mu, sigma;          /* standardisation of ln g */
+    double final_loss;         /* mean minibatch loss of the last 1 % of steps (standardised units) */
+    double val_rms, val_max;   /* error of ln g on the held-out cells (to first order the
+                                  relative error of q_abs), inference arithmetic */
+    double train_ms;           /* device time of the optimisation loop */
+} rt_train_stats;
+
+typedef struct {
+    long long n_dust;      /* cells with dust (T_dust <= t_sub) */
+    long long n_fallback;  /* of those, answered by the exact per-bin sum */
+    long long n_judged;    /* validate == 1: cells absorbing more than 1e-12 of L* */
+    double max_rel_err;    /* validate == 1: largest |q_net / q_exact - 1| over judged cells (before fallback) */
+    double mean_rel_err;   /* validate == 1: its mean */
+    double e_abs, e_esc, rel_err;  /* energy of the returned fields, as in rt_energy */
+} rt_surrogate_stats;
+
+/* rt_surrogate_train -- train the context's surrogate on cells of `ngrids` density
+ * and temperature fields of this context's grid (device pointers, the layout of
+ * rt_irradiate). The exact tracer (rt_irradiate) traces every field; cells with
+ * dust that absorb more than 1e-12 of L* are sampled (a counter hash of cfg->seed
+ * and the cell; 2-5 % held out), and the network is trained on the GPU by the
+ * library's forward, backward and Adam kernels. Deterministic for a given input.
+ * Replaces any previous surrogate of the context. Synchronises the stream.
+ * Errors: RT_ERR_INVALID_ARG (no opacity at 550 nm, fewer than 1024 usable cells,
+ * bad cfg), RT_ERR_NOT_CONFIGURED, RT_ERR_NO_MEMORY, RT_ERR_CUDA. */
+int rt_surrogate_train(rt_ctx *ctx, const rt_train_cfg *cfg, const float *const *rho,
+                       const float *const *t_dust, int ngrids, rt_train_stats *stats_or_null);
+
+/* rt_irradiate_surrogate -- rt_irradiate with the surrogate in place of the per-bin
+ * loop. rho, t_dust, q_abs, a_rad as in rt_irradiate (fully overwritten).
+ *   validate == 0  a trust map over (log2 tau_550 in front of the cell,
+ *                  log2 dtau_550 of the cell), built on first use for `err_tol`
+ *                  by judging 32 points per bin against the exact per-bin sum,
+ *                  decides per cell; cells outside it take the exact sum.
+ *   validate == 1  the exact tracer runs first and judges every cell; cells whose
+ *                  q_abs differs by more than err_tol (relative) take the exact values.
+ *   validate == 2  the network everywhere (no gate; for tests).
+ * Cells without dust get q_abs = a_rad = 0 exactly. Asynchronous on the
+ * context's stream unless stats is non-NULL (then filled after a synchronisation;
+ * without stats an invalid input or a timeout is not reported). The first call
+ * with validate == 0 for a new err_tol builds the trust map (synchronous). Errors as rt_irradiate, and
+ * RT_ERR_NOT_CONFIGURED without a surrogate for this table, RT_ERR_TIMEOUT if a
+ * tensor-core product did not complete within the kernel's bounded wait. */
+int rt_irradiate_surrogate(rt_ctx *ctx, const float *rho, const float *t_dust, float *q_abs,
+                           float *a_rad, float err_tol, int validate, rt_surrogate_stats *stats_or_null);
+
+/* Parameters of the network, host buffers of RT_SUR_NPARAMS floats in the order of
+ * RT_SUR_NPARAMS; set creates the surrogate for the context's current table. */
+int rt_surrogate_set_params(rt_ctx *ctx, const float *params, double mu, double sigma);
+int rt_surrogate_get_params(rt_ctx *ctx, float *params, double *mu_or_null, double *sigma_or_null);
+
+/* rt_surrogate_grad -- one forward and backward pass of the training kernels on
+ * n given rows (host buffers): x [n][8] features, t [n] standardised targets;
+ * grad [RT_SUR_NPARAMS] receives d/dparams of mean((y - t)^2), loss that mean.
+ * For checking the training kernels; the parameters are not changed. */
+int rt_surrogate_grad(rt_ctx *ctx, const float *x, const float *t, int n, float *grad, double *loss);
+
+/* rt_surrogate_eval -- network output y [n] (standardised) for feature rows
+ * x [n][8] (host buffers), with the inference kernel's arithmetic. */
+int rt_surrogate_eval(rt_ctx *ctx, const float *x, int n, float *y);
+
+/* rt_surrogate_loss_history -- minibatch losses of the last training, one per step;
+ * copies min(steps, max) values and returns the number of steps. */
+int rt_surrogate_loss_history(rt_ctx *ctx, float *loss, int max);
+
+/* rt_surrogate_trust_map -- build the trust map for err_tol and copy its 64 x 64
+ * bits (bin iu * 64 + iv, 128 words) to `bits`; ranges (if non-NULL) receives
+ * (u0, du, v0, dv): bin iu covers u0 + iu du .. u0 + (iu + 1) du, bin 0 also all
+ * smaller values; likewise for v. */
+int rt_surrogate_trust_map(rt_ctx *ctx, float err_tol, unsigned *bits, float *ranges_or_null);
+
+/* Save / load the surrogate (parameters, standardisation, feature constants and
+ * the fingerprint of the table it belongs to). Loading into a context whose table
+ * differs fails with RT_ERR_NOT_CONFIGURED. */
+int rt_surrogate_save(rt_ctx *ctx, const char *path);
+int rt_surrogate_load(rt_ctx *ctx, const char *path);
+
 /* rt_probe_ex2 -- y[i] = 2^x[i] with the hardware approximation the FP32 tracer
  * uses, for accuracy tests. x, y: device float32 arrays of n elements; runs on
  * stream (NULL = default) and synchronises it. */
@@ -305,9 +416,10 @@ int rt_probe_umma(const unsigned short *a, const unsigned short *b, int k, float
 /* rt_probe_tensor_rates -- sustained rates per SM per clock on the current device:
  * multiply-adds of the warp-level BF16 MMA (mma.sync m16n8k16, 32 warps per SM)
  * and of tcgen05 BF16 products with M = 128, K = 16 and N = 128 or 256 (one CTA
- * per SM, one issuing thread); tanh.approx instructions in FP32 and packed BF16. */
+ * per SM, one issuing thread); tanh.approx instructions in FP32 and packed BF16;
+ * rcp.approx.f32 instructions (the reciprocal of the surrogate's SiLU). */
 int rt_probe_tensor_rates(double *mma_sync_mac, double *umma_n128_mac, double *umma_n256_mac,
-                          double *tanh_f32, double *tanh_bf16x2);
+                          double *tanh_f32, double *tanh_bf16x2, double *rcp_f32);
 
 #ifdef __cplusplus
 }

@@ -11,10 +11,13 @@ from .build import build  # noqa: F401
 
 _LAZY = ("Tracer", "Batch", "Energy", "probe_ex2", "probe_alu_rates", "probe_tanh", "probe_umma",
          "probe_tensor_rates")
-__all__ = ["build", *_LAZY]
+__all__ = ["build", "RtError", *_LAZY]
 
 
 def __getattr__(name):
+    if name == "RtError":
+        from ._lib import RtError
+        return RtError
     if name in _LAZY:
         from . import tracer
         return getattr(tracer, name)

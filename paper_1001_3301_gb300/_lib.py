@@ -45,6 +45,27 @@ class RtEnergy(ctypes.Structure):
                 ("l_star", ctypes.c_double), ("rel_err", ctypes.c_double)]
 
 
+RT_SUR_NPARAMS = 17793
+
+
+class RtTrainCfg(ctypes.Structure):
+    _fields_ = [("n_samples", ctypes.c_longlong), ("batch", ctypes.c_int), ("steps", ctypes.c_int),
+                ("lr", ctypes.c_float), ("seed", ctypes.c_ulonglong)]
+
+
+class RtTrainStats(ctypes.Structure):
+    _fields_ = [("n_train", ctypes.c_longlong), ("n_val", ctypes.c_longlong),
+                ("mu", ctypes.c_double), ("sigma", ctypes.c_double), ("final_loss", ctypes.c_double),
+                ("val_rms", ctypes.c_double), ("val_max", ctypes.c_double), ("train_ms", ctypes.c_double)]
+
+
+class RtSurrogateStats(ctypes.Structure):
+    _fields_ = [("n_dust", ctypes.c_longlong), ("n_fallback", ctypes.c_longlong),
+                ("n_judged", ctypes.c_longlong), ("max_rel_err", ctypes.c_double),
+                ("mean_rel_err", ctypes.c_double), ("e_abs", ctypes.c_double),
+                ("e_esc", ctypes.c_double), ("rel_err", ctypes.c_double)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.c_double
@@ -80,9 +101,21 @@ SIGNATURES = {
                                  _P, _P, _P, _P, ctypes.POINTER(RtEnergy), _P]),
     "rt_probe_ex2": (_I, [_P, _P, ctypes.c_longlong, _P]),
     "rt_probe_alu_rates": (_I, [_DP, _DP, _DP]),
+    "rt_surrogate_train": (_I, [_P, ctypes.POINTER(RtTrainCfg), ctypes.POINTER(_P), ctypes.POINTER(_P), _I,
+                                ctypes.POINTER(RtTrainStats)]),
+    "rt_irradiate_surrogate": (_I, [_P, _P, _P, _P, _P, ctypes.c_float, _I, ctypes.POINTER(RtSurrogateStats)]),
+    "rt_surrogate_set_params": (_I, [_P, ctypes.POINTER(ctypes.c_float), _D, _D]),
+    "rt_surrogate_get_params": (_I, [_P, ctypes.POINTER(ctypes.c_float), _DP, _DP]),
+    "rt_surrogate_grad": (_I, [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _I,
+                               ctypes.POINTER(ctypes.c_float), _DP]),
+    "rt_surrogate_eval": (_I, [_P, ctypes.POINTER(ctypes.c_float), _I, ctypes.POINTER(ctypes.c_float)]),
+    "rt_surrogate_loss_history": (_I, [_P, ctypes.POINTER(ctypes.c_float), _I]),
+    "rt_surrogate_trust_map": (_I, [_P, ctypes.c_float, ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(ctypes.c_float)]),
+    "rt_surrogate_save": (_I, [_P, ctypes.c_char_p]),
+    "rt_surrogate_load": (_I, [_P, ctypes.c_char_p]),
     "rt_probe_tanh": (_I, [_P, _P, ctypes.c_longlong, _I, _P]),
     "rt_probe_umma": (_I, [_P, _P, _I, _P, _P]),
-    "rt_probe_tensor_rates": (_I, [_DP, _DP, _DP, _DP, _DP]),
+    "rt_probe_tensor_rates": (_I, [_DP, _DP, _DP, _DP, _DP, _DP]),
 }
 
 

@@ -9,6 +9,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <vector>
 
 #include "rt_internal.cuh"
 
@@ -44,6 +45,12 @@ struct rt_ctx {
     unsigned *bad_h = nullptr;
     // device staging for the host-buffer entry point
     float *h_rho = nullptr, *h_t = nullptr, *h_q = nullptr, *h_a = nullptr;
+
+    // host copies of the table as the tracer uses it, and its fingerprint
+    std::vector<double> nu_h, kappa_h;
+    unsigned long long fingerprint = 0;
+    // learned surrogate (rt_surrogate.cu), created by rt_surrogate_train / _load
+    rt::SurState *sur = nullptr;
 
     // configuration state
     int n_nu = 0, kappa_bf16 = 0;
@@ -162,6 +169,18 @@ int finalize(rt_ctx *c)
     RT_CK(c, cudaMemcpyAsync(&c->sc_h, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
     RT_CK(c, cudaStreamSynchronize(c->stream));
     if (!c->shape_forced) c->shape = default_shape(c);
+    // FNV-1a over what fixes the per-cell absorption function of (N_in, dN)
+    unsigned long long h = 1469598103934665603ULL;
+    auto mix = [&h](const void *p, size_t n) {
+        const unsigned char *b = static_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ULL;
+    };
+    mix(&c->n_nu, sizeof(int));
+    mix(c->nu_h.data(), sizeof(double) * c->nu_h.size());
+    mix(c->kappa_h.data(), sizeof(double) * c->kappa_h.size());
+    mix(&c->t_sub, sizeof(double));
+    mix(&c->t_star, sizeof(double));
+    c->fingerprint = h;
     c->configured = true;
     return RT_OK;
 }
@@ -305,6 +324,34 @@ bool ctx_view(const rt_ctx *c, CtxView *v)
     v->ncells = c->ncells;
     return true;
 }
+
+bool ctx_info(const rt_ctx *c, CtxInfo *o)
+{
+    if (!c) return false;
+    o->dev = c->dev;
+    o->stream = c->stream;
+    o->configured = c->configured;
+    o->nr = c->nr;
+    o->nrays = c->nrays;
+    o->ncells = c->ncells;
+    o->t_sub = c->t_sub;
+    o->t_star = c->t_star;
+    o->r_star = c->r_star;
+    o->n_nu = c->n_nu;
+    o->nu_h = c->nu_h.data();
+    o->kappa_h = c->kappa_h.data();
+    o->table_fingerprint = c->fingerprint;
+    o->rtab = c->rtab;
+    o->domega32 = c->domega32;
+    o->nu_tab = c->nu_tab;
+    o->kap = c->kap;
+    o->sc = c->sc_h;
+    return true;
+}
+
+SurState *&ctx_surrogate(rt_ctx *c) { return c->sur; }
+
+int ctx_fail(rt_ctx *c, int status, const std::string &msg) { return fail(c, status, msg); }
 }  // namespace rt
 
 extern "C" {
@@ -404,6 +451,17 @@ int rt_set_opacity_table(rt_ctx *ctx, int n_nu, const double *nu_mid, const doub
     ctx->n_nu = n_nu;
     ctx->t_sub = t_sub;
     ctx->kappa_bf16 = kappa_bf16 ? 1 : 0;
+    ctx->nu_h.assign(nu_mid, nu_mid + n_nu);
+    ctx->kappa_h.assign(kappa, kappa + n_nu);
+    if (ctx->kappa_bf16)  // the tracer's table: kappa rounded to BF16 (nearest, ties to even)
+        for (double &k : ctx->kappa_h) {
+            float f = (float)k;
+            unsigned u;
+            memcpy(&u, &f, 4);
+            u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+            memcpy(&f, &u, 4);
+            k = f;
+        }
     ctx->have_table = true;
     return finalize(ctx);
 }
@@ -563,6 +621,7 @@ void rt_destroy(rt_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->dev);
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->sur) rt::sur_free(ctx->sur);
     free_all(ctx);
     delete ctx;
 }

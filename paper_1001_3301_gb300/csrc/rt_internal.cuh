@@ -128,6 +128,30 @@ namespace rt {
 bool ctx_view(const rt_ctx *c, CtxView *v);
 void set_thread_error(const std::string &msg);  // text for rt_last_error(NULL)
 
+// What the learned surrogate (rt_surrogate.cu) reads of a context (rt_api.cu).
+struct CtxInfo {
+    int dev;
+    cudaStream_t stream;
+    bool configured;
+    int nr;
+    long long nrays, ncells;
+    double t_sub, t_star, r_star;
+    int n_nu;
+    const double *nu_h;        // host copies of the table the tracer uses (kappa
+    const double *kappa_h;     // after the optional BF16 rounding)
+    unsigned long long table_fingerprint;  // of (n_nu, nu, kappa, t_sub, t_star)
+    const float4 *rtab;        // [nr] (dr, Gq, Ga0, 0)
+    const float *domega32;     // [nrays]
+    const NuEntry *nu_tab;     // [nnu_pad], kappa-sorted active bins
+    const float *kap;          // [nnu_pad]
+    DevScalars sc;             // host copy of the grid's scalars
+};
+struct SurState;
+bool ctx_info(const rt_ctx *c, CtxInfo *out);
+SurState *&ctx_surrogate(rt_ctx *c);   // owned by the context, freed by rt_destroy
+void sur_free(SurState *s);
+int ctx_fail(rt_ctx *c, int status, const std::string &msg);
+
 // Set-up kernels (rt_setup.cu)
 cudaError_t launch_setup_bins(int n_nu, const double *nu_mid_dev, const double *kappa_dev,
                               double t_star, double r_star, int kappa_bf16,

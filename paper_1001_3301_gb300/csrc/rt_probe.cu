@@ -95,7 +95,15 @@ __global__ void k_probe_tanh(const float *x, float *y, long long n, int packed)
     }
 }
 
-// Chains v <- tanh(v) (contracting towards 0, so bounded), eight per thread.
+__device__ __forceinline__ float rcp_f32(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Chains v <- tanh(v) (contracting towards 0, so bounded), eight per thread;
+// packed == 2: v <- 1 / (1 + v) instead (reciprocal; bounded in (0.5, 1)).
 __global__ void k_bench_tanh(int iters, int packed, float seed, float *sink, long long *cycles)
 {
     float v[kChains];
@@ -108,7 +116,12 @@ __global__ void k_bench_tanh(int iters, int packed, float seed, float *sink, lon
     }
     __syncthreads();
     const long long t0 = clock64();
-    if (packed) {
+    if (packed == 2) {
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) v[c] = rcp_f32(1.0f + v[c]);
+        }
+    } else if (packed) {
         for (int i = 0; i < iters; ++i) {
 #pragma unroll
             for (int c = 0; c < kChains; ++c) w[c] = tanh_bf16x2(w[c]);
@@ -350,9 +363,10 @@ int rt_probe_umma(const unsigned short *a, const unsigned short *b, int k, float
 }
 
 int rt_probe_tensor_rates(double *mma_sync_mac, double *umma_n128_mac, double *umma_n256_mac,
-                          double *tanh_f32, double *tanh_bf16x2)
+                          double *tanh_f32, double *tanh_bf16x2, double *rcp_f32_rate)
 {
-    if (!mma_sync_mac || !umma_n128_mac || !umma_n256_mac || !tanh_f32 || !tanh_bf16x2) return RT_ERR_INVALID_ARG;
+    if (!mma_sync_mac || !umma_n128_mac || !umma_n256_mac || !tanh_f32 || !tanh_bf16x2 || !rcp_f32_rate)
+        return RT_ERR_INVALID_ARG;
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RT_ERR_CUDA;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return RT_ERR_CUDA;
@@ -376,11 +390,12 @@ int rt_probe_tensor_rates(double *mma_sync_mac, double *umma_n128_mac, double *u
     // unused dynamic shared memory keeps the tcgen05 benchmark at one CTA per SM
     if (cudaFuncSetAttribute(k_bench_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, kUmmaBenchPad) != cudaSuccess)
         status = RT_ERR_CUDA;
-    // which: 0 mma.sync, 1 tanh f32, 2 tanh bf16x2, 3 umma N=128, 4 umma N=256
-    for (int which = 0; which < 5 && status == RT_OK; ++which) {
+    // which: 0 mma.sync, 1 tanh f32, 2 tanh bf16x2, 3 umma N=128, 4 umma N=256, 5 rcp f32
+    for (int which = 0; which < 6 && status == RT_OK; ++which) {
         for (int rep = 0; rep < 2; ++rep) {
             if (which == 0) k_bench_mma_sync<<<blocks, threads>>>(1024, sink, cyc);
             else if (which <= 2) k_bench_tanh<<<blocks, threads>>>(4096, which == 2, 0.5f, sink, cyc);
+            else if (which == 5) k_bench_tanh<<<blocks, threads>>>(4096, 2, 0.5f, sink, cyc);
             else k_bench_umma<<<nsm, 128, kUmmaBenchPad>>>(which == 3 ? 8192 : 4096, which == 3 ? 128 : 256, cyc, st);
         }
         if (cudaDeviceSynchronize() != cudaSuccess) { status = RT_ERR_CUDA; break; }
@@ -388,7 +403,8 @@ int rt_probe_tensor_rates(double *mma_sync_mac, double *umma_n128_mac, double *u
         else if (which == 1) *tanh_f32 = 4096.0 * kChains * threads * per_sm / max_cycles(blocks);
         else if (which == 2) *tanh_bf16x2 = 4096.0 * kChains * threads * per_sm / max_cycles(blocks);
         else if (which == 3) *umma_n128_mac = 8192.0 * 128 * 128 * 16 / max_cycles(nsm);
-        else *umma_n256_mac = 4096.0 * 128 * 256 * 16 / max_cycles(nsm);
+        else if (which == 4) *umma_n256_mac = 4096.0 * 128 * 256 * 16 / max_cycles(nsm);
+        else *rcp_f32_rate = 4096.0 * kChains * threads * per_sm / max_cycles(blocks);
     }
     unsigned st_h = 0;
     cudaMemcpy(&st_h, st, sizeof(unsigned), cudaMemcpyDeviceToHost);

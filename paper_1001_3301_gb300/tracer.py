@@ -7,11 +7,13 @@ device memory and streams only; the computation runs in the library's kernels.
 from __future__ import annotations
 
 import ctypes
+import os
 
 import numpy as np
 
 from . import _lib
-from ._lib import RtEnergy, RtGridDesc, check, lib
+from ._lib import (RT_SUR_NPARAMS, RtEnergy, RtGridDesc, RtSurrogateStats, RtTrainCfg, RtTrainStats, check,
+                   lib)
 
 
 def _f64(a) -> np.ndarray:
@@ -147,6 +149,101 @@ class Tracer:
                               a_rad.data_ptr(), int(reps)), self._ctx)
         return self.tuning()
 
+    # -- learned surrogate (rt_surrogate_*) -------------------------------------
+    def surrogate_train(self, rho_list, t_list, n_samples=0, batch=0, steps=0, lr=0.0, seed=1):
+        """Train the context's surrogate on the given fields (CUDA tensors of this
+        grid); returns the training statistics as a dict."""
+        for t in list(rho_list) + list(t_list):
+            self._check_field(t, "training field")
+        n = len(rho_list)
+        if n != len(t_list) or n < 1:
+            raise ValueError("rho_list and t_list must have the same non-zero length")
+        rp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in rho_list])
+        tp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in t_list])
+        cfg = RtTrainCfg(int(n_samples), int(batch), int(steps), float(lr), int(seed))
+        st = RtTrainStats()
+        check(lib.rt_surrogate_train(self._ctx, ctypes.byref(cfg), rp, tp, n, ctypes.byref(st)), self._ctx)
+        return {k: getattr(st, k) for k, _ in RtTrainStats._fields_}
+
+    def irradiate_surrogate(self, rho, t_dust, q_abs=None, a_rad=None, err_tol=1e-3, validate=0, stats=True):
+        """(q_abs, a_rad, stats dict or None) with the surrogate in place of the per-bin
+        sum; validate: 0 trust-map gate, 1 judged by the exact tracer, 2 network only.
+        stats=False leaves the call asynchronous."""
+        import torch
+        self._check_field(rho, "rho")
+        self._check_field(t_dust, "t_dust")
+        if q_abs is None:
+            q_abs = torch.empty(self.shape, dtype=torch.float32, device=rho.device)
+        if a_rad is None:
+            a_rad = torch.empty(self.shape, dtype=torch.float32, device=rho.device)
+        self._check_field(q_abs, "q_abs")
+        self._check_field(a_rad, "a_rad")
+        st = RtSurrogateStats()
+        check(lib.rt_irradiate_surrogate(self._ctx, rho.data_ptr(), t_dust.data_ptr(), q_abs.data_ptr(),
+                                         a_rad.data_ptr(), float(err_tol), int(validate),
+                                         ctypes.byref(st) if stats else None), self._ctx)
+        return q_abs, a_rad, ({k: getattr(st, k) for k, _ in RtSurrogateStats._fields_} if stats else None)
+
+    def surrogate_set_params(self, params, mu, sigma):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != RT_SUR_NPARAMS:
+            raise ValueError(f"expected {RT_SUR_NPARAMS} parameters")
+        check(lib.rt_surrogate_set_params(self._ctx, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                          float(mu), float(sigma)), self._ctx)
+
+    def surrogate_params(self):
+        """(params [RT_SUR_NPARAMS] float32, mu, sigma)"""
+        p = np.empty(RT_SUR_NPARAMS, dtype=np.float32)
+        mu, sg = ctypes.c_double(), ctypes.c_double()
+        check(lib.rt_surrogate_get_params(self._ctx, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                          ctypes.byref(mu), ctypes.byref(sg)), self._ctx)
+        return p, mu.value, sg.value
+
+    def surrogate_grad(self, x, t):
+        """(loss, grad [RT_SUR_NPARAMS]) of mean((y - t)^2) by the training kernels."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        n = t.size
+        if x.shape != (n, 8):
+            raise ValueError("x must be [n][8]")
+        g = np.empty(RT_SUR_NPARAMS, dtype=np.float32)
+        loss = ctypes.c_double()
+        fp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        check(lib.rt_surrogate_grad(self._ctx, fp(x), fp(t), n, fp(g), ctypes.byref(loss)), self._ctx)
+        return loss.value, g
+
+    def surrogate_eval(self, x):
+        """Standardised network outputs for feature rows x [n][8] (inference kernel)."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        n = x.shape[0]
+        y = np.empty(n, dtype=np.float32)
+        fp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        check(lib.rt_surrogate_eval(self._ctx, fp(x), n, fp(y)), self._ctx)
+        return y
+
+    def surrogate_loss_history(self):
+        n = lib.rt_surrogate_loss_history(self._ctx, None, 0)
+        if n < 0:
+            check(n, self._ctx)
+        out = np.empty(n, dtype=np.float32)
+        lib.rt_surrogate_loss_history(self._ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), n)
+        return out
+
+    def surrogate_trust_map(self, err_tol=1e-3):
+        """(bits as a [64][64] bool array indexed [iu][iv], (u0, du, v0, dv))"""
+        bits = (ctypes.c_uint * 128)()
+        rng = (ctypes.c_float * 4)()
+        check(lib.rt_surrogate_trust_map(self._ctx, float(err_tol), bits, rng), self._ctx)
+        w = np.array(bits[:], dtype=np.uint32)
+        b = np.array([(w[i >> 5] >> (i & 31)) & 1 for i in range(64 * 64)], dtype=bool).reshape(64, 64)
+        return b, tuple(rng[:])
+
+    def surrogate_save(self, path):
+        check(lib.rt_surrogate_save(self._ctx, os.fsencode(path)), self._ctx)
+
+    def surrogate_load(self, path):
+        check(lib.rt_surrogate_load(self._ctx, os.fsencode(path)), self._ctx)
+
     # -- lifetime --------------------------------------------------------------
     def close(self):
         if getattr(self, "_ctx", None):
@@ -217,10 +314,10 @@ def probe_umma(a_bits, b_bits):
 
 def probe_tensor_rates():
     """Per SM per clock: mma.sync MACs, tcgen05 MACs at N = 128 and 256, tanh.approx
-    f32 and packed-bf16 instructions."""
-    v = [ctypes.c_double() for _ in range(5)]
+    f32 and packed-bf16 instructions, rcp.approx f32 instructions."""
+    v = [ctypes.c_double() for _ in range(6)]
     check(lib.rt_probe_tensor_rates(*[ctypes.byref(x) for x in v]))
-    return dict(zip(("mma_sync_mac", "umma_n128_mac", "umma_n256_mac", "tanh_f32", "tanh_bf16x2"),
+    return dict(zip(("mma_sync_mac", "umma_n128_mac", "umma_n256_mac", "tanh_f32", "tanh_bf16x2", "rcp_f32"),
                     (x.value for x in v)))
 
 
