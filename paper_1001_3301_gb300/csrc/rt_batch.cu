@@ -182,7 +182,7 @@ size_t tile_smem(const rt::TraceArgs &a, const BatchShape &s)
     const long long TS = (T + T / 32 + 1 + 3) & ~3LL;
     const bool staged = (s.precision != RT_FP64) && a.nr <= 1024;
     const long long nrs = staged ? ((a.nr + a.nr / 32 + 1 + 3) & ~3) : 0;
-    return (size_t)(TS * 6 * 4 + 3 * nrs * 4 + (long long)a.nnu_pad * 4 + (long long)a.nnu_pad * 16 + 16);
+    return (size_t)(TS * 6 * 4 + 3 * nrs * 4 + (long long)a.nnu_pad * 4 + (long long)a.nnu_pad * (16 + 32) + 16);
 }
 
 // Shape-dependent plan: tile ranges per CTA balanced by cost, partials, graph.

@@ -179,8 +179,64 @@ __device__ __forceinline__ float2 taylor_fraction(float2 y)
     return __fmul2_rn(y, p);
 }
 
+// Moment form of the truncated series for the classes with 1-3 terms. With
+// c_k = p_k nk^{k+1} per bin,
+//   sum_i g_i (1 - 2^{nk_i dN}) = sum_k dN^{k+1} M_k,   M_k = sum_i g_i c_{k,i},
+// so each (cell, bin) costs one FMA per term (every term of one M_k has the sign of
+// p_k: no cancellation), and dN enters once per cell and range (Horner).
+// s_mom[2 i] = (c0, c0, c1, c1), s_mom[2 i + 1] = (c2, c2, c3, c3).
+__device__ __forceinline__ void fill_moments(float4 *s_mom, int i, float nk)
+{
+    const float c0 = (float)taylor_coeff(0) * nk;
+    const float c1 = (float)taylor_coeff(1) * nk * nk;
+    const float c2 = (float)taylor_coeff(2) * nk * nk * nk;
+    const float c3 = (float)taylor_coeff(3) * nk * nk * nk * nk;
+    s_mom[2 * i] = make_float4(c0, c0, c1, c1);
+    s_mom[2 * i + 1] = make_float4(c2, c2, c3, c3);
+}
+
+template <int NT, int C>
+__device__ __forceinline__ void moment_range(int i0, int i1, const float4 *s_nu, const float4 *s_mom,
+                                             const float2 (&n2)[C / 2], const float2 (&d2)[C / 2],
+                                             float2 (&a2)[C / 2])
+{
+    static_assert(NT >= 1 && NT <= 3, "moment form for 1-3 terms");
+    if (i0 >= i1) return;  // warp-uniform
+    float2 M[NT][C / 2];
+#pragma unroll
+    for (int k = 0; k < NT; ++k)
+#pragma unroll
+        for (int m = 0; m < C / 2; ++m) M[k][m] = f2(0.0f);
+#pragma unroll(NT <= 2 ? 2 : 1)
+    for (int i = i0; i < i1; ++i) {
+        const float4 e = s_nu[i];
+        const float2 nk = make_float2(e.x, e.y), lf = make_float2(e.z, e.w);
+        const float4 m01 = s_mom[2 * i];
+        const float2 c0 = make_float2(m01.x, m01.y), c1 = make_float2(m01.z, m01.w);
+        float2 c2 = f2(0.0f);
+        if constexpr (NT >= 3) {
+            const float4 m23 = s_mom[2 * i + 1];
+            c2 = make_float2(m23.x, m23.y);
+        }
+#pragma unroll
+        for (int m = 0; m < C / 2; ++m) {
+            const float2 g = ex2_approx2(__ffma2_rn(nk, n2[m], lf));
+            M[0][m] = __ffma2_rn(g, c0, M[0][m]);
+            if constexpr (NT >= 2) M[1][m] = __ffma2_rn(g, c1, M[1][m]);
+            if constexpr (NT >= 3) M[2][m] = __ffma2_rn(g, c2, M[2][m]);
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < C / 2; ++m) {
+        float2 t = M[NT - 1][m];
+#pragma unroll
+        for (int k = NT - 2; k >= 0; --k) t = __ffma2_rn(t, d2[m], M[k][m]);
+        a2[m] = __ffma2_rn(t, d2[m], a2[m]);
+    }
+}
+
 // Bin classes per warp: 1, 2, 3, 5 = Taylor with that many terms, 6 = mixed,
-// 7 = MUFU. The common classes 1 and 2 are unrolled over two bins.
+// 7 = MUFU. Classes 1-3 run in the moment form above; bin_range serves 5-7.
 template <int CLASS, int C>
 __device__ __forceinline__ void bin_range(int i0, int i1, const float4 *s_nu, const float2 (&n2)[C / 2],
                                           const float2 (&d2)[C / 2], float2 (&a2)[C / 2])

@@ -43,12 +43,14 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray(const TraceArgs p)
     extern __shared__ __align__(16) unsigned char smem[];
     float *s_kap = reinterpret_cast<float *>(smem);
     float4 *s_nu = reinterpret_cast<float4 *>(s_kap + p.nnu_pad);
+    float4 *s_mom = s_nu + p.nnu_pad;  // series moments' constants, two per bin
     __shared__ ESum s_red[W][2];
 
     for (int i = tid; i < p.nnu_pad; i += W * 32) {
         s_kap[i] = p.kap[i];
         const NuEntry e = p.nu[i];
         s_nu[i] = make_float4(e.nk, e.nk, e.lf, e.lf);
+        fill_moments(s_mom, i, e.nk);
     }
     for (int i = tid; i < 32 * C; i += W * 32) {
         const int l = i / C, j = i % C, k = l * C + j;
@@ -147,8 +149,8 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray(const TraceArgs p)
         }
         const int na = p.n_active;
         const BinClasses bc = classify_bins(s_nu, na, lane, dmax, dmin);
-        bin_range<1, C>(0, bc.b1, s_nu, N.v, D.v, acc.v);
-        bin_range<2, C>(bc.b1, bc.b2, s_nu, N.v, D.v, acc.v);
+        moment_range<1, C>(0, bc.b1, s_nu, s_mom, N.v, D.v, acc.v);
+        moment_range<2, C>(bc.b1, bc.b2, s_nu, s_mom, N.v, D.v, acc.v);
         bin_range<3, C>(bc.b2, bc.b3, s_nu, N.v, D.v, acc.v);
         bin_range<5, C>(bc.b3, bc.b5, s_nu, N.v, D.v, acc.v);
         bin_range<6, C>(bc.b5, bc.bb, s_nu, N.v, D.v, acc.v);
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray(const TraceArgs p)
 template <int C, int W, int MODE, int MINB>
 cudaError_t launch_ray(const TraceArgs &a, unsigned, cudaStream_t stream, unsigned *grid_out)
 {
-    const size_t smem = (size_t)a.nnu_pad * (sizeof(float) + 16) + 16;
+    const size_t smem = (size_t)a.nnu_pad * (sizeof(float) + 16 + 32) + 16;
     auto kern = k_ray<C, W, MODE, MINB>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

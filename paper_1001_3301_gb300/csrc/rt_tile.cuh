@@ -67,6 +67,7 @@ __device__ __forceinline__ void trace_tile_range(const TraceArgs &p, unsigned t_
     // (nk, nk, lf, lf): each bin's constants duplicated for packed f32x2 math
     float4 *s_nu = reinterpret_cast<float4 *>(s_kap + p.nnu_pad);
     double2 *s_nu64 = reinterpret_cast<double2 *>(s_kap + p.nnu_pad);
+    float4 *s_mom = s_nu + p.nnu_pad;  // series moments' constants (FP32 modes), two per bin
 
     __shared__ Sum s_wsum[W];
     __shared__ int s_whead[W];
@@ -115,6 +116,7 @@ __device__ __forceinline__ void trace_tile_range(const TraceArgs &p, unsigned t_
         } else {
             const NuEntry e = p.nu[i];
             s_nu[i] = make_float4(e.nk, e.nk, e.lf, e.lf);
+            fill_moments(s_mom, i, e.nk);
         }
     }
     if (rt_staged)
@@ -261,8 +263,8 @@ __device__ __forceinline__ void trace_tile_range(const TraceArgs &p, unsigned t_
             }
             const int na = p.n_active;
             const BinClasses bc = classify_bins(s_nu, na, lane, dmax, dmin);
-            bin_range<1, C>(0, bc.b1, s_nu, N.v, D.v, acc.v);
-            bin_range<2, C>(bc.b1, bc.b2, s_nu, N.v, D.v, acc.v);
+            moment_range<1, C>(0, bc.b1, s_nu, s_mom, N.v, D.v, acc.v);
+            moment_range<2, C>(bc.b1, bc.b2, s_nu, s_mom, N.v, D.v, acc.v);
             bin_range<3, C>(bc.b2, bc.b3, s_nu, N.v, D.v, acc.v);
             bin_range<5, C>(bc.b3, bc.b5, s_nu, N.v, D.v, acc.v);
             bin_range<6, C>(bc.b5, bc.bb, s_nu, N.v, D.v, acc.v);
@@ -386,7 +388,7 @@ size_t trace_smem_bytes(const TraceArgs &a)
     const bool staged = (MODE != RT_FP64) && a.nr <= kRtabSmemMax;
     const size_t nrs = staged ? (size_t)((a.nr + a.nr / 32 + 1 + 3) & ~3) : 0;
     return (size_t)TS * 6 * sizeof(float) + 3 * nrs * sizeof(float) +
-           (size_t)a.nnu_pad * sizeof(float) + (size_t)a.nnu_pad * 16 + 16;
+           (size_t)a.nnu_pad * sizeof(float) + (size_t)a.nnu_pad * (16 + 32) + 16;
 }
 
 }  // namespace
