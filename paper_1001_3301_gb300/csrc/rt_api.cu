@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
@@ -14,6 +15,7 @@
 #include "rt_internal.cuh"
 
 using rt::DevScalars;
+using rt::RadRow64;
 using rt::NuEntry;
 using rt::Shape;
 
@@ -26,7 +28,7 @@ struct rt_ctx {
     // geometry (device)
     double *r_if = nullptr, *theta_if = nullptr, *phi_if = nullptr;
     float4 *rtab = nullptr;
-    double4 *rtab64 = nullptr;
+    RadRow64 *rtab64 = nullptr;
     double *domega = nullptr;
     float *domega32 = nullptr;
     // bins (device)
@@ -43,8 +45,10 @@ struct rt_ctx {
     // pinned host mirrors
     rt_energy *energy_h = nullptr;
     unsigned *bad_h = nullptr;
-    // device staging for the host-buffer entry point
+    // device staging for the host-buffer entry point, and its copy pipeline
     float *h_rho = nullptr, *h_t = nullptr, *h_q = nullptr, *h_a = nullptr;
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev_in[8] = {}, ev_done[8] = {}, ev_start = nullptr;
 
     // host copies of the table as the tracer uses it, and its fingerprint
     std::vector<double> nu_h, kappa_h;
@@ -68,6 +72,8 @@ struct rt_ctx {
 namespace {
 
 thread_local std::string g_create_err;
+
+constexpr int kHostChunks = 8;  // most ray chunks of the host-buffer pipeline
 
 int fail(rt_ctx *ctx, int status, const std::string &msg)
 {
@@ -122,14 +128,15 @@ Shape default_shape(const rt_ctx *c)
         if (it != g_tune_cache.end()) return it->second;
     }
     // Prefer the warp-per-ray kernel with the fewest cells per lane when the rays
-    // fill at least 3/4 of its 32 C cells; else the widest tile that still gives
-    // every SM several tiles.
+    // fill at least 3/4 of the G C cells of their lane segment; else the widest tile
+    // that still gives every SM several tiles.
     if (c->precision != RT_FP64) {
         Shape rs[32];
         const int nrs = rt::ray_shapes(c->precision, c->nr, rs, 32);
         int bi = -1;
         for (int i = 0; i < nrs; ++i)
-            if (4 * c->nr >= 3 * 32 * rs[i].cells_per_lane && (bi < 0 || rs[i].cells_per_lane < rs[bi].cells_per_lane))
+            if (4 * c->nr >= 3 * rt::ray_lanes(rs[i].cells_per_lane, c->nr) * rs[i].cells_per_lane &&
+                (bi < 0 || rs[i].cells_per_lane < rs[bi].cells_per_lane))
                 bi = i;
         if (bi >= 0) return rs[bi];
     }
@@ -213,11 +220,12 @@ long long total_tiles(const rt_ctx *c, Shape s)
     return tiles;
 }
 
-int trace(rt_ctx *c, const float *rho, const float *td, float *q, float *a, Shape s)
+// Launches the tracer on rays [r_begin, r_end) of the context's fields (pointers to
+// the whole grid) on `stream`; the CTAs' energy partials go to c->partials from
+// *npart on, which advances. The caller has sized c->partials and set c->seq.
+int trace_range(rt_ctx *c, const float *rho, const float *td, float *q, float *a, Shape s, long long r_begin,
+                long long r_end, cudaStream_t stream, long long *npart)
 {
-    // at most one persistent CTA per tile per chunk
-    int st = ensure_partials(c, total_tiles(c, s));
-    if (st != RT_OK) return st;
     rt::TraceArgs args;
     args.nu = c->nu_tab;
     args.kap = c->kap;
@@ -225,16 +233,15 @@ int trace(rt_ctx *c, const float *rho, const float *td, float *q, float *a, Shap
     args.rtab = c->rtab;
     args.rtab64 = c->rtab64;
     args.bad_input = c->bad;
-    args.seq = ++c->seq;
+    args.seq = c->seq;
     args.r1div = rt::FastDiv::make((unsigned)c->nr + 1u);
     args.nr = c->nr;
     args.nnu_pad = c->sc_h.nnu_pad;
     args.n_active = c->sc_h.n_active;
     args.t_sub = (float)c->t_sub;
     const long long T = rt::trace_tile_cells(s), cr = chunk_rays(c);
-    long long npart = 0;
-    for (long long r0 = 0; r0 < c->nrays; r0 += cr) {
-        const long long nr_c = (c->nrays - r0 < cr) ? c->nrays - r0 : cr;
+    for (long long r0 = r_begin; r0 < r_end; r0 += cr) {
+        const long long nr_c = (r_end - r0 < cr) ? r_end - r0 : cr;
         const size_t off = (size_t)r0 * c->nr;
         args.rho = rho + off;
         args.tdust = td + off;
@@ -242,15 +249,39 @@ int trace(rt_ctx *c, const float *rho, const float *td, float *q, float *a, Shap
         args.a = a + off;
         args.domega = c->domega + r0;
         args.domega32 = c->domega32 + r0;
-        args.partials = c->partials + npart;
+        args.partials = c->partials + *npart;
         args.L = (unsigned)(nr_c * (c->nr + 1));
         args.nrays = (unsigned)nr_c;
         const long long nt = (nr_c * (c->nr + 1) + T - 1) / T;
         unsigned grid = 0;
-        cudaError_t e = rt::launch_trace(c->precision, s, args, (unsigned)nt, c->stream, &grid);
+        cudaError_t e = rt::launch_trace(c->precision, s, args, (unsigned)nt, stream, &grid);
         if (e != cudaSuccess) return cuda_fail(c, "trace kernel launch", e);
-        npart += grid;
+        *npart += grid;
     }
+    return RT_OK;
+}
+
+// tiles (an upper bound of the CTAs) of the launches over rays [r_begin, r_end)
+long long range_tiles(const rt_ctx *c, Shape s, long long r_begin, long long r_end)
+{
+    const long long T = rt::trace_tile_cells(s), cr = chunk_rays(c);
+    long long tiles = 0;
+    for (long long r0 = r_begin; r0 < r_end; r0 += cr) {
+        const long long nr_c = (r_end - r0 < cr) ? r_end - r0 : cr;
+        tiles += (s.kind == rt::kKindRay) ? (nr_c + s.warps - 1) / s.warps : (nr_c * (c->nr + 1) + T - 1) / T;
+    }
+    return tiles;
+}
+
+int trace(rt_ctx *c, const float *rho, const float *td, float *q, float *a, Shape s)
+{
+    // at most one persistent CTA per tile per chunk
+    int st = ensure_partials(c, total_tiles(c, s));
+    if (st != RT_OK) return st;
+    ++c->seq;
+    long long npart = 0;
+    st = trace_range(c, rho, td, q, a, s, 0, c->nrays, c->stream, &npart);
+    if (st != RT_OK) return st;
     c->last_ntiles = npart;
     c->traced = true;
     return RT_OK;
@@ -504,14 +535,60 @@ int rt_irradiate_host(rt_ctx *ctx, const float *rho, const float *t_dust, float 
             return fail(ctx, RT_ERR_NO_MEMORY, "cannot allocate device staging buffers");
         }
     }
-    RT_CK(ctx, cudaMemcpyAsync(ctx->h_rho, rho, bytes, cudaMemcpyHostToDevice, ctx->stream));
-    RT_CK(ctx, cudaMemcpyAsync(ctx->h_t, t_dust, bytes, cudaMemcpyHostToDevice, ctx->stream));
-    st = trace(ctx, ctx->h_rho, ctx->h_t, ctx->h_q, ctx->h_a, ctx->shape);
+    (void)bytes;
+    // Pipeline over ray chunks: the copies in of chunk k+1 (stream s_in) and out of
+    // chunk k-1 (stream s_out, the other direction of the link) overlap the trace of
+    // chunk k on the context's stream.
+    if (!ctx->s_in) {
+        bool ok = cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking) == cudaSuccess;
+        for (int k = 0; ok && k < kHostChunks; ++k)
+            ok = cudaEventCreateWithFlags(&ctx->ev_in[k], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&ctx->ev_done[k], cudaEventDisableTiming) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) return cuda_fail(ctx, "host pipeline streams", cudaGetLastError());
+    }
+    const long long cells_min = 1LL << 20;  // at least ~1 M cells per chunk
+    int nch = (int)std::min<long long>(kHostChunks, std::max<long long>(1, ctx->ncells / cells_min));
+    if (nch > ctx->nrays) nch = (int)ctx->nrays;
+    long long bound = 0;
+    for (int k = 0; k < nch; ++k)
+        bound += range_tiles(ctx, ctx->shape, ctx->nrays * k / nch, ctx->nrays * (k + 1) / nch);
+    st = ensure_partials(ctx, bound);
     if (st != RT_OK) return st;
-    RT_CK(ctx, cudaMemcpyAsync(q_abs, ctx->h_q, bytes, cudaMemcpyDeviceToHost, ctx->stream));
-    RT_CK(ctx, cudaMemcpyAsync(a_rad, ctx->h_a, bytes, cudaMemcpyDeviceToHost, ctx->stream));
-    if (energy) return read_energy(ctx, energy);
+    ++ctx->seq;
+    // the staging buffers are free once earlier work on the context's stream is done
+    RT_CK(ctx, cudaEventRecord(ctx->ev_start, ctx->stream));
+    RT_CK(ctx, cudaStreamWaitEvent(ctx->s_in, ctx->ev_start, 0));
+    long long npart = 0;
+    for (int k = 0; k < nch; ++k) {
+        const long long r0 = ctx->nrays * k / nch, r1 = ctx->nrays * (k + 1) / nch;
+        const size_t off = (size_t)r0 * ctx->nr, n = (size_t)(r1 - r0) * ctx->nr * sizeof(float);
+        RT_CK(ctx, cudaMemcpyAsync(ctx->h_rho + off, rho + off, n, cudaMemcpyHostToDevice, ctx->s_in));
+        RT_CK(ctx, cudaMemcpyAsync(ctx->h_t + off, t_dust + off, n, cudaMemcpyHostToDevice, ctx->s_in));
+        RT_CK(ctx, cudaEventRecord(ctx->ev_in[k], ctx->s_in));
+        RT_CK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_in[k], 0));
+        st = trace_range(ctx, ctx->h_rho, ctx->h_t, ctx->h_q, ctx->h_a, ctx->shape, r0, r1, ctx->stream, &npart);
+        if (st != RT_OK) return st;
+        RT_CK(ctx, cudaEventRecord(ctx->ev_done[k], ctx->stream));
+        RT_CK(ctx, cudaStreamWaitEvent(ctx->s_out, ctx->ev_done[k], 0));
+        RT_CK(ctx, cudaMemcpyAsync(q_abs + off, ctx->h_q + off, n, cudaMemcpyDeviceToHost, ctx->s_out));
+        RT_CK(ctx, cudaMemcpyAsync(a_rad + off, ctx->h_a + off, n, cudaMemcpyDeviceToHost, ctx->s_out));
+    }
+    ctx->last_ntiles = npart;
+    ctx->traced = true;
+    if (energy) {
+        st = read_energy(ctx, energy);
+        if (st != RT_OK && st != RT_ERR_NONFINITE_INPUT) return st;
+        RT_CK(ctx, cudaStreamSynchronize(ctx->s_out));
+        return st;
+    }
+    RT_CK(ctx, cudaStreamSynchronize(ctx->s_out));
     RT_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    RT_CK(ctx, cudaMemcpyAsync(ctx->bad_h, ctx->bad, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+    RT_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (*ctx->bad_h == ctx->seq)
+        return fail(ctx, RT_ERR_NONFINITE_INPUT, "input field holds NaN/Inf/negative density or NaN temperature");
     return RT_OK;
 }
 
@@ -622,6 +699,17 @@ void rt_destroy(rt_ctx *ctx)
     cudaSetDevice(ctx->dev);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->sur) rt::sur_free(ctx->sur);
+    if (ctx->s_in) {
+        cudaStreamSynchronize(ctx->s_in);
+        cudaStreamSynchronize(ctx->s_out);
+        cudaStreamDestroy(ctx->s_in);
+        cudaStreamDestroy(ctx->s_out);
+        for (int k = 0; k < kHostChunks; ++k) {
+            if (ctx->ev_in[k]) cudaEventDestroy(ctx->ev_in[k]);
+            if (ctx->ev_done[k]) cudaEventDestroy(ctx->ev_done[k]);
+        }
+        if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
+    }
     free_all(ctx);
     delete ctx;
 }

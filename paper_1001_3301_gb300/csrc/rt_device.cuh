@@ -71,11 +71,11 @@ struct KahanSum {
         lo = lo + o.lo + e;
     }
     __device__ float value() const { return hi + lo; }
-    __device__ KahanSum shfl_up(int d) const
+    __device__ KahanSum shfl_up(int d, int width = 32) const
     {
         KahanSum r;
-        r.hi = __shfl_up_sync(0xffffffffu, hi, d);
-        r.lo = __shfl_up_sync(0xffffffffu, lo, d);
+        r.hi = __shfl_up_sync(0xffffffffu, hi, d, width);
+        r.lo = __shfl_up_sync(0xffffffffu, lo, d, width);
         return r;
     }
     __device__ KahanSum shfl_xor(int d) const
@@ -94,10 +94,10 @@ struct PlainSum {  // one accumulator, no compensation
     __device__ void add(Real v) { hi += v; }
     __device__ void add(const PlainSum &o) { hi += o.hi; }
     __device__ Real value() const { return hi; }
-    __device__ PlainSum shfl_up(int d) const
+    __device__ PlainSum shfl_up(int d, int width = 32) const
     {
         PlainSum r;
-        r.hi = __shfl_up_sync(0xffffffffu, hi, d);
+        r.hi = __shfl_up_sync(0xffffffffu, hi, d, width);
         return r;
     }
     __device__ PlainSum shfl_xor(int d) const

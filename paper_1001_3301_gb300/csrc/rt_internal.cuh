@@ -62,6 +62,11 @@ struct FastDiv {
     }
 };
 
+// Radial constants of one cell in FP64: dr, Gq, Ga0 (and padding), 32-byte aligned.
+struct alignas(32) RadRow64 {
+    double x, y, z, w;
+};
+
 // Largest flattened length one launch of the tracer covers; longer grids are
 // split into ray chunks by the host.
 constexpr long long kMaxLaunchCells = (1LL << 31) - (1LL << 16);
@@ -77,7 +82,7 @@ struct TraceArgs {
     const float *kap;         // [nnu_pad] kappa_i (rho -> 0 force limit)
     const double2 *nu64;      // [nnu_pad] (kappa_i, F_i/F_max), FP64 mode
     const float4 *rtab;       // [nr] (dr, Gq, Ga0, 0)
-    const double4 *rtab64;    // [nr] same in FP64
+    const RadRow64 *rtab64;    // [nr] same in FP64
     const double *domega;     // [nrays]
     const float *domega32;    // [nrays] the same in FP32
     double2 *partials;        // [CTAs] (sum of absorbed, sum of escaped) / (R*^2 F_max)
@@ -101,6 +106,10 @@ struct Shape {
     int warps;
     int min_blocks;  // minimum resident CTAs per SM the registers are capped for
 };
+
+// Lanes per ray of the warp-per-ray kernel with C cells per lane: the fewest of 8,
+// 16 and 32 that hold the ray (a warp then traces 32 / G rays at a time).
+inline int ray_lanes(int c, int nr) { return 8 * c >= nr ? 8 : (16 * c >= nr ? 16 : 32); }
 
 // Host-side launchers (rt_trace.cu, rt_ray.cu)
 int trace_shapes(int precision, Shape *out, int max_out);      // tile kernel
@@ -159,7 +168,7 @@ cudaError_t launch_setup_bins(int n_nu, const double *nu_mid_dev, const double *
                               double2 *nu64_dev, DevScalars *sc_dev, cudaStream_t stream);
 cudaError_t launch_setup_geometry(int nr, int ntheta, int nphi, const double *r_if_dev,
                                   const double *theta_if_dev, const double *phi_if_dev,
-                                  double t_star, float4 *rtab, double4 *rtab64,
+                                  double t_star, float4 *rtab, RadRow64 *rtab64,
                                   double *domega, float *domega32, DevScalars *sc_dev,
                                   cudaStream_t stream);
 cudaError_t launch_energy_reduce(const double2 *partials, long long ntiles,

@@ -1,10 +1,11 @@
 // Warp-per-ray form of the frequency-dependent tracer (Kuiper et al. 2010,
 // Sect. 2.2-2.3, 3.3.4), for grids whose rays fill most of 32 * C cells.
 //
-// One warp traces one radial ray at a time; lane l owns the cells [l C, (l+1) C)
-// of the ray, so the radial constants of a lane never change and the ray's fields
-// are read straight from HBM in 16-byte vectors (no staging, no block barrier in
-// the ray loop). Per ray:
+// A segment of G lanes traces one radial ray (a warp holds 32 / G rays at a time,
+// so rays shorter than 32 C cells keep every lane busy); lane l of a segment owns
+// the cells [l C, (l+1) C) of its ray, so the radial constants of a lane never
+// change and the ray's fields are read straight from HBM in 16-byte vectors (no
+// staging, no block barrier in the ray loop). Per ray:
 //   - dN = [T <= t_sub] rho dr per cell, and its exclusive prefix N_in along the
 //     ray (Eq. 19, tau = 0 at the inner radius): compensated lane sums, then a
 //     compensated warp scan;
@@ -22,22 +23,25 @@
 namespace rt {
 namespace {
 
-template <int C, int W, int MODE, int MINB>
+template <int C, int W, int MODE, int MINB, int G>
 __global__ void __launch_bounds__(W * 32, MINB) k_ray(const TraceArgs p)
 {
     static_assert(MODE != RT_FP64, "the FP64 mode uses the tile kernel");
     static_assert(C % 2 == 0, "cells per lane must be even");
+    static_assert(G == 8 || G == 16 || G == 32, "lanes per ray");
     using Sum = ColSum<MODE>;
     using ESum = KahanSum;
     constexpr int V = (C % 4 == 0) ? 4 : 2;  // vector width of the field loads
+    constexpr int R = 32 / G;                // rays per warp
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int seg = lane / G, ll = lane % G;  // ray slot of the lane, lane within the ray
     const int nr = p.nr;
-    const int c0 = lane * C;
-    const int nv = nr - c0 < 0 ? 0 : (nr - c0 > C ? C : nr - c0);  // valid cells of this lane
+    const int c0 = ll * C;
+    const int nv_ray = nr - c0 < 0 ? 0 : (nr - c0 > C ? C : nr - c0);  // valid cells of this lane
 
     // Radial constants of every lane's cells, stored [j][lane] so that the lanes of
-    // a warp read consecutive words (lane l's cell j is radial index l C + j; a
+    // a warp read consecutive words (lane l's cell j is radial index (l mod G) C + j; a
     // [k] layout would put all 32 lanes on one shared-memory bank).
     __shared__ float s_dr[C][32], s_gq[C][32], s_ga[C][32];
     extern __shared__ __align__(16) unsigned char smem[];
@@ -53,7 +57,7 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray(const TraceArgs p)
         fill_moments(s_mom, i, e.nk);
     }
     for (int i = tid; i < 32 * C; i += W * 32) {
-        const int l = i / C, j = i % C, k = l * C + j;
+        const int l = i / C, j = i % C, k = (l % G) * C + j;
         const float4 g = (k < nr) ? __ldg(&p.rtab[k]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         s_dr[j][l] = g.x;
         s_gq[j][l] = g.y;
@@ -70,8 +74,11 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray(const TraceArgs p)
     eabs.zero();
     eesc.zero();
 
-    for (unsigned ray = blockIdx.x * W + warp; ray < p.nrays; ray += gridDim.x * W) {
-        const size_t base = (size_t)ray * nr + c0;
+    for (unsigned wr = blockIdx.x * W + warp; wr * R < p.nrays; wr += gridDim.x * W) {
+        const unsigned ray = wr * R + seg;
+        const bool live = ray < p.nrays;  // the last warp may hold fewer than R rays
+        const int nv = live ? nv_ray : 0;
+        const size_t base = (size_t)(live ? ray : 0u) * nr + c0;
         float rho[C], td[C];
         if (vec && nv == C) {
 #pragma unroll
@@ -119,22 +126,22 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray(const TraceArgs p)
         }
         if (__any_sync(0xffffffffu, bad) && lane == 0) atomicMax(p.bad_input, p.seq);
 
-        // exclusive prefix along the ray: warp scan of the lane sums
+        // exclusive prefix along the ray: scan of the lane sums within the segment
         Sum inc = lsum;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const Sum o = inc.shfl_up(d);
-            if (lane >= d) inc.add(o);
+        for (int d = 1; d < G; d <<= 1) {
+            const Sum o = inc.shfl_up(d, G);
+            if (ll >= d) inc.add(o);
         }
-        Sum pre = inc.shfl_up(1);
-        if (lane == 0) pre.zero();
+        Sum pre = inc.shfl_up(1, G);
+        if (ll == 0) pre.zero();
 #pragma unroll
         for (int j = 0; j < C; ++j) {
             N.set(j, pre.value());
             pre.add(D.get(j));
             acc.set(j, 0.0f);
         }
-        const float ntot = __shfl_sync(0xffffffffu, pre.value(), 31);
+        const float ntot = __shfl_sync(0xffffffffu, pre.value(), G - 1, G);
 
         // the warp's largest and smallest non-zero column decide each bin's class
         float dmax = 0.0f, dmin = INFINITY;
@@ -169,13 +176,13 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray(const TraceArgs p)
             }
         }
 
-        // escaping power of the ray, the lanes sharing the bins
-        const float w = __ldg(p.domega32 + ray);
+        // escaping power of the ray, the lanes of its segment sharing the bins
+        const float w = live ? __ldg(p.domega32 + ray) : 0.0f;
         {
             float s = 0.0f;
-            for (int i = lane; i < p.nnu_pad; i += 32) s += ex2_approx(fmaf(s_nu[i].x, ntot, s_nu[i].z));
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) eesc.add(s * w);
+            for (int i = ll; i < p.nnu_pad; i += G) s += ex2_approx(fmaf(s_nu[i].x, ntot, s_nu[i].z));
+            for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (ll == 0) eesc.add(s * w);
         }
 
         // outputs and the lane's absorbed power
@@ -225,11 +232,12 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray(const TraceArgs p)
     }
 }
 
-template <int C, int W, int MODE, int MINB>
-cudaError_t launch_ray(const TraceArgs &a, unsigned, cudaStream_t stream, unsigned *grid_out)
+template <int C, int W, int MODE, int MINB, int G>
+cudaError_t launch_ray_g(const TraceArgs &a, cudaStream_t stream, unsigned *grid_out)
 {
+    constexpr int R = 32 / G;
     const size_t smem = (size_t)a.nnu_pad * (sizeof(float) + 16 + 32) + 16;
-    auto kern = k_ray<C, W, MODE, MINB>;
+    auto kern = k_ray<C, W, MODE, MINB, G>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -241,12 +249,21 @@ cudaError_t launch_ray(const TraceArgs &a, unsigned, cudaStream_t stream, unsign
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     unsigned grid = (unsigned)nsm * (unsigned)per_sm;
-    const unsigned need = (a.nrays + W - 1) / W;
+    const unsigned need = (a.nrays + W * R - 1) / (W * R);
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     kern<<<grid, W * 32, smem, stream>>>(a);
     *grid_out = grid;
     return cudaGetLastError();
+}
+
+// The fewest lanes per ray that still hold the ray: 8, 16 or 32 (G C >= nr).
+template <int C, int W, int MODE, int MINB>
+cudaError_t launch_ray(const TraceArgs &a, unsigned, cudaStream_t stream, unsigned *grid_out)
+{
+    if (8 * C >= a.nr) return launch_ray_g<C, W, MODE, MINB, 8>(a, stream, grid_out);
+    if (16 * C >= a.nr) return launch_ray_g<C, W, MODE, MINB, 16>(a, stream, grid_out);
+    return launch_ray_g<C, W, MODE, MINB, 32>(a, stream, grid_out);
 }
 
 struct RayEntry {

@@ -116,7 +116,7 @@ __global__ void k_setup_bins(int n_nu, const double *nu_mid, const double *kappa
 // is the rho -> 0 force factor.
 __global__ void k_setup_geometry(int nr, int ntheta, int nphi, const double *r_if,
                                  const double *theta_if, const double *phi_if, float4 *rtab,
-                                 double4 *rtab64, double *domega, float *domega32,
+                                 RadRow64 *rtab64, double *domega, float *domega32,
                                  const DevScalars *sc)
 {
     const long long nrays = (long long)ntheta * nphi;
@@ -131,7 +131,7 @@ __global__ void k_setup_geometry(int nr, int ntheta, int nphi, const double *r_i
             const double gq = gscale / d3;
             const double ga0 = gq * dr / kC;
             rtab[t] = make_float4((float)dr, (float)gq, (float)ga0, 0.0f);
-            rtab64[t] = make_double4(dr, gq, ga0, 0.0);
+            rtab64[t] = RadRow64{dr, gq, ga0, 0.0};
         }
         if (t < nrays) {
             const int it = (int)(t % ntheta);
@@ -208,7 +208,7 @@ cudaError_t launch_setup_bins(int n_nu, const double *nu_mid_dev, const double *
 
 cudaError_t launch_setup_geometry(int nr, int ntheta, int nphi, const double *r_if_dev,
                                   const double *theta_if_dev, const double *phi_if_dev,
-                                  double t_star, float4 *rtab, double4 *rtab64, double *domega,
+                                  double t_star, float4 *rtab, RadRow64 *rtab64, double *domega,
                                   float *domega32, DevScalars *sc_dev, cudaStream_t stream)
 {
     const long long nrays = (long long)ntheta * nphi;

@@ -41,7 +41,7 @@ struct StaticScratch {
     float kap[RT_MAX_NU + rt::kNuPad];
     double2 nu64[RT_MAX_NU + rt::kNuPad];
     float4 rtab[kStaticMaxNr];
-    double4 rtab64[kStaticMaxNr];
+    rt::RadRow64 rtab64[kStaticMaxNr];
     double domega[kStaticMaxRays];
     float domega32[kStaticMaxRays];
     double2 partials[kStaticMaxCtas];
@@ -106,7 +106,8 @@ rt::Shape pick_shape(int precision, int nr)
         const int n = rt::ray_shapes(precision, nr, s, 32);
         int bi = -1;
         for (int i = 0; i < n; ++i)
-            if (4 * nr >= 3 * 32 * s[i].cells_per_lane && (bi < 0 || s[i].cells_per_lane < s[bi].cells_per_lane))
+            if (4 * nr >= 3 * rt::ray_lanes(s[i].cells_per_lane, nr) * s[i].cells_per_lane &&
+                (bi < 0 || s[i].cells_per_lane < s[bi].cells_per_lane))
                 bi = i;
         if (bi >= 0) return s[bi];
     }

@@ -332,7 +332,7 @@ __device__ __forceinline__ void trace_tile_range(const TraceArgs &p, unsigned t_
                     const Real dj = D.get(j);
                     Real q, a;
                     if constexpr (MODE == RT_FP64) {
-                        const double4 g = p.rtab64[k];
+                        const RadRow64 g = p.rtab64[k];
                         q = zc ? 0.0 : g.y * acc.get(j);
                         a = g.z * (zc ? dj : (dj > 0.0 ? acc.get(j) / dj : 0.0));
                     } else {
