@@ -344,6 +344,31 @@ def run_ours(args, rank, world, local):
         e2e = {"value": world * units_per_step * args.steps / dt, "unit": UNIT,
                "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": 2 * nbytes}
 
+    # the dust-temperature update (Eq. 16) on the step's grids, fed by their a_rad
+    # (untimed above; timed here on its own, 8 bytes per cell against HBM)
+    temp = None
+    if rank == 0:
+        t_out = [torch.empty(w.grid.shape, dtype=torch.float32, device="cuda") for w in ws]
+        for i, tr in enumerate(tracers):
+            tr.dust_temperature(a[i], None, t_out[i])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            for i, tr in enumerate(tracers):
+                tr.dust_temperature(a[i], None, t_out[i])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_ms = e0.elapsed_time(e1) / (args.steps * len(ws))
+        ncell = ws[0].grid.ncells
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm = float(peaks.get("hbm_gbs") or 6678.0)
+        temp = {"ms_per_grid": t_ms, "cells_per_s": ncell / (t_ms * 1e-3),
+                "achieved_gbs": 8.0 * ncell / (t_ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm,
+                "frac_of_hbm": 8.0 * ncell / (t_ms * 1e-3) / 1e9 / hbm,
+                "median_t_k": float(t_out[1].median())}
+        del t_out
+
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(ws)
@@ -381,6 +406,7 @@ def run_ours(args, rank, world, local):
             "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                        "reasons": clocks["reasons"]},
             "energy_max_rel_err": max_energy_err,
+            "dust_temperature": temp,
             "surrogate": sur,
         }
         print(json.dumps(line), flush=True)

@@ -279,6 +279,31 @@ int rt_irradiate_static(const rt_grid_desc *g, double t_star, double r_star, int
 /* ---- diagnostics (no counterpart in the paper) ---------------------------- */
 
 /* ------------------------------------------------------------------------
+ * Planck-mean opacity and the dust temperature (Sect. 2.2, Eq. 16).
+ * ------------------------------------------------------------------------ */
+
+/* rt_planck_mean_opacity -- kappa_P(T) = sum_i kappa_i B_i(T) / sum_i B_i(T) of the
+ * context's table, B_i(T) the Planck integral over bin i (the bin edges of Eq. 20)
+ * at temperature t (K, > 0), in FP64 on the device. kappa_P(T_star) is the gray
+ * opacity of Eq. 19: a one-bin table with that kappa gives the gray irradiation.
+ * Synchronises the context's stream. */
+int rt_planck_mean_opacity(rt_ctx *ctx, double t, double *kappa_p);
+
+/* rt_dust_temperature -- Eq. 16 with the frequency-dependent fluxes: per cell the
+ * dust temperature T with
+ *     a T^4 = E_R + sum_i kappa_i F_i / (c kappa_P(T))  =  E_R + a_rad / kappa_P(T),
+ * since over a cell sum_i kappa_i F_i = q_abs / rho = c a_rad.
+ *   a_rad   device, [nphi][ntheta][nr] FP32, the rt_irradiate output (cm s^-2);
+ *   e_rad   device, same layout, the radiation energy density E_R of the diffuse
+ *           field (erg cm^-3), or NULL for E_R = 0;
+ *   t_dust  device, same layout, receives T (K); 0 where a_rad = E_R = 0.
+ * kappa_P(T) is tabulated for the context's table on 1 K .. 1e5 K (1024 points of
+ * ln T, cubic interpolation) and held constant outside; the root is found by
+ * Newton's method on ln T in FP32. Asynchronous on the context's stream (the first
+ * call per table builds the table and synchronises). */
+int rt_dust_temperature(rt_ctx *ctx, const float *a_rad, const float *e_rad, float *t_dust);
+
+/* ------------------------------------------------------------------------
  * Learned surrogate of the per-bin sum of one cell.
  *
  * Along a ray the tracer gives a cell with dust column N_in in front of it and

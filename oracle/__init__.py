@@ -45,6 +45,11 @@ def _configure(lib):
     lib.rto_planck_G_large.argtypes = [ctypes.c_double]
     lib.rto_planck_band.restype = ctypes.c_double
     lib.rto_planck_band.argtypes = [ctypes.c_double, ctypes.c_double]
+    lib.rto_planck_mean.restype = ctypes.c_double
+    lib.rto_planck_mean.argtypes = [ctypes.c_double, ctypes.c_int, _D, _D]
+    lib.rto_dust_temperature.restype = ctypes.c_int
+    lib.rto_dust_temperature.argtypes = [ctypes.c_longlong, _D, _D, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_int, _D, _D, _D, ctypes.c_int]
     lib.rto_planck_bins.restype = ctypes.c_int
     lib.rto_planck_bins.argtypes = [ctypes.c_double, ctypes.c_int, _D, _D]
     lib.rto_irradiate.restype = ctypes.c_int
@@ -107,6 +112,28 @@ def planck_bins(t_star: float, nu_mid) -> np.ndarray:
     if _load().rto_planck_bins(float(t_star), len(nu), _ptr(nu), _ptr(out)) != 0:
         raise ValueError("rto_planck_bins: bad argument")
     return out
+
+
+def planck_mean(t: float, nu_mid, kappa) -> float:
+    """kappa_P(T) of a bin table: sum kappa_i B_i(T) / sum B_i(T) (Eq. 16's mean)."""
+    nu, k = _f64(nu_mid), _f64(kappa)
+    v = _load().rto_planck_mean(float(t), len(nu), _ptr(nu), _ptr(k))
+    if v < 0:
+        raise ValueError("rto_planck_mean: bad argument")
+    return v
+
+
+def dust_temperature(a_rad, e_rad, nu_mid, kappa, t_lo=1.0, t_hi=1e5, nthreads=0) -> np.ndarray:
+    """T per cell from a T^4 = E_R + a_rad / kappa_P(T) (Eq. 16, frequency-dependent
+    fluxes), kappa_P held constant outside [t_lo, t_hi]; bisection in FP64."""
+    ar = _f64(a_rad).ravel()
+    er = None if e_rad is None else _f64(e_rad).ravel()
+    nu, k = _f64(nu_mid), _f64(kappa)
+    out = np.empty_like(ar)
+    if _load().rto_dust_temperature(ar.size, _ptr(ar), _ptr(er), float(t_lo), float(t_hi), len(nu), _ptr(nu),
+                                    _ptr(k), _ptr(out), int(nthreads or max_threads())) != 0:
+        raise ValueError("rto_dust_temperature: bad argument")
+    return out.reshape(np.shape(a_rad))
 
 
 def max_threads() -> int:

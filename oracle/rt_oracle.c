@@ -125,6 +125,64 @@ int rto_planck_bins(double t_star, int n_nu, const double *nu_mid, double *f_bin
     return 0;
 }
 
+/* Planck mean opacity of a bin table at temperature t (kappa_P(T) of Eq. 16):
+ * sum_i kappa_i B_i(t) / sum_i B_i(t), B_i the Planck integral over bin i with the
+ * bin edges of Eq. 20. Returns a negative value on a bad argument. */
+double rto_planck_mean(double t, int n_nu, const double *nu_mid, const double *kappa)
+{
+    double *f = (double *)malloc(sizeof(double) * (size_t)(n_nu > 0 ? n_nu : 1));
+    if (!f) return -1.0;
+    if (rto_planck_bins(t, n_nu, nu_mid, f) != 0) {
+        free(f);
+        return -1.0;
+    }
+    double num = 0.0, den = 0.0;
+    for (int i = 0; i < n_nu; ++i) {
+        num += kappa[i] * f[i];
+        den += f[i];
+    }
+    free(f);
+    return den > 0.0 ? num / den : 0.0;
+}
+
+/* Eq. 16 with frequency-dependent fluxes, per cell: the dust temperature T with
+ *     a T^4 = E_R + a_rad / kappa_P(T),   a = 4 sigma / c,
+ * (sum_i kappa_i F_i over the cell is q_abs / rho = c a_rad). kappa_P is evaluated
+ * at T clamped to [t_lo, t_hi]. Bisection on ln T over [ln 1e-3, ln 1e9] until the
+ * bracket is 1e-14 wide in ln T; T = 0 where a_rad = E_R = 0. e_rad may be NULL
+ * (E_R = 0). Returns 0, or -1 on a bad argument. */
+int rto_dust_temperature(long long n, const double *a_rad, const double *e_rad, double t_lo, double t_hi,
+                         int n_nu, const double *nu_mid, const double *kappa, double *t_out, int nthreads)
+{
+    if (n < 0 || !a_rad || !t_out || n_nu < 1 || !(t_lo > 0.0) || !(t_hi > t_lo)) return -1;
+    const double a_rad_const = 4.0 * rto_sigma_sb() / RTO_C;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (long long c = 0; c < n; ++c) {
+        const double ar = a_rad[c] > 0.0 ? a_rad[c] : 0.0;
+        const double er = (e_rad && e_rad[c] > 0.0) ? e_rad[c] : 0.0;
+        if (ar == 0.0 && er == 0.0) {
+            t_out[c] = 0.0;
+            continue;
+        }
+        double ylo = log(1e-3), yhi = log(1e9);
+        while (yhi - ylo > 1e-14) {
+            const double y = 0.5 * (ylo + yhi);
+            double tt = exp(y);
+            const double tk = tt < t_lo ? t_lo : (tt > t_hi ? t_hi : tt);
+            const double kp = rto_planck_mean(tk, n_nu, nu_mid, kappa);
+            const double f = a_rad_const * tt * tt * tt * tt - er - ar / kp;
+            if (f > 0.0) yhi = y;
+            else ylo = y;
+        }
+        t_out[c] = exp(0.5 * (ylo + yhi));
+    }
+    (void)nthreads;
+    return 0;
+}
+
 /* Neumaier-compensated running sum */
 typedef struct { double s, c; } rto_sum;
 static void rto_add(rto_sum *acc, double x)

@@ -101,6 +101,8 @@ SIGNATURES = {
                                  _P, _P, _P, _P, ctypes.POINTER(RtEnergy), _P]),
     "rt_probe_ex2": (_I, [_P, _P, ctypes.c_longlong, _P]),
     "rt_probe_alu_rates": (_I, [_DP, _DP, _DP]),
+    "rt_planck_mean_opacity": (_I, [_P, _D, _DP]),
+    "rt_dust_temperature": (_I, [_P, _P, _P, _P]),
     "rt_surrogate_train": (_I, [_P, ctypes.POINTER(RtTrainCfg), ctypes.POINTER(_P), ctypes.POINTER(_P), _I,
                                 ctypes.POINTER(RtTrainStats)]),
     "rt_irradiate_surrogate": (_I, [_P, _P, _P, _P, _P, ctypes.c_float, _I, ctypes.POINTER(RtSurrogateStats)]),

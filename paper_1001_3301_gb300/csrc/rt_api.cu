@@ -55,6 +55,9 @@ struct rt_ctx {
     unsigned long long fingerprint = 0;
     // learned surrogate (rt_surrogate.cu), created by rt_surrogate_train / _load
     rt::SurState *sur = nullptr;
+    // Planck-mean table of the dust-temperature update (rt_temperature.cu)
+    float *temp_lkp = nullptr;
+    unsigned long long temp_fp = 0;
 
     // configuration state
     int n_nu = 0, kappa_bf16 = 0;
@@ -313,7 +316,7 @@ void free_all(rt_ctx *c)
 {
     void *ptrs[] = {c->r_if, c->theta_if, c->phi_if, c->rtab, c->rtab64, c->domega, c->domega32, c->nu_mid,
                     c->kappa, c->f_bin, c->nu_tab, c->kap, c->nu64, c->sc, c->partials, c->bad,
-                    c->energy_d, c->h_rho, c->h_t, c->h_q, c->h_a};
+                    c->energy_d, c->h_rho, c->h_t, c->h_q, c->h_a, c->temp_lkp};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->energy_h) cudaFreeHost(c->energy_h);
@@ -381,6 +384,8 @@ bool ctx_info(const rt_ctx *c, CtxInfo *o)
 }
 
 SurState *&ctx_surrogate(rt_ctx *c) { return c->sur; }
+float *&ctx_temp_table(rt_ctx *c) { return c->temp_lkp; }
+unsigned long long &ctx_temp_fingerprint(rt_ctx *c) { return c->temp_fp; }
 
 int ctx_fail(rt_ctx *c, int status, const std::string &msg) { return fail(c, status, msg); }
 }  // namespace rt

@@ -158,6 +158,10 @@ struct CtxInfo {
 struct SurState;
 bool ctx_info(const rt_ctx *c, CtxInfo *out);
 SurState *&ctx_surrogate(rt_ctx *c);   // owned by the context, freed by rt_destroy
+// the context's Planck-mean table of the temperature update (device, freed by
+// rt_destroy) and the table fingerprint it was built for
+float *&ctx_temp_table(rt_ctx *c);
+unsigned long long &ctx_temp_fingerprint(rt_ctx *c);
 void sur_free(SurState *s);
 int ctx_fail(rt_ctx *c, int status, const std::string &msg);
 

@@ -5,44 +5,10 @@
 #include <math.h>
 
 #include "rt_internal.cuh"
+#include "rt_planck.cuh"
 
 namespace rt {
 namespace {
-
-// t^3 / (e^t - 1), the Planck integrand in x = h nu / (k T)
-__device__ double planck_x(double t) { return t * t * t / expm1(t); }
-
-// 8-point Gauss-Legendre rule on [a, b] (nodes and weights of the Legendre
-// polynomial P_8, Abramowitz & Stegun Table 25.4).
-__device__ double gauss_legendre8(double a, double b)
-{
-    const double xs[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267,
-                          0.9602898564975363};
-    const double ws[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745,
-                          0.1012285362903763};
-    const double c = 0.5 * (a + b), h = 0.5 * (b - a);
-    double s = 0.0;
-    for (int i = 0; i < 4; ++i) s += ws[i] * (planck_x(c - h * xs[i]) + planck_x(c + h * xs[i]));
-    return s * h;
-}
-
-// int_a^b t^3/(e^t-1) dt by composite Gauss-Legendre on panels no wider than one
-// unit of x, the panels spread over the 32 lanes of a warp. The integrand is
-// analytic with its nearest poles at +-2 pi i, so each panel converges far below
-// double rounding. An infinite upper edge is replaced by a + 60: the neglected
-// tail is below e^-60 of the integrand at a. Result valid in every lane.
-__device__ double planck_band_warp(double a, double b, int lane)
-{
-    if (isinf(b)) b = a + 60.0;
-    double s = 0.0;
-    if (b > a) {
-        const int n = (int)ceil(b - a);
-        const double h = (b - a) / n;
-        for (int p = lane; p < n; p += 32) s += gauss_legendre8(a + p * h, a + (p + 1) * h);
-    }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    return s;
-}
 
 // One warp per bin (the block has RT_MAX_NU / 4 warps, each doing four bins),
 // then thread 0 compacts the bins with kappa > 0 into the tracer's table.

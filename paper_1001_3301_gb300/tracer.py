@@ -149,6 +149,26 @@ class Tracer:
                               a_rad.data_ptr(), int(reps)), self._ctx)
         return self.tuning()
 
+    # -- Planck mean and dust temperature (Eq. 16) -------------------------------
+    def planck_mean_opacity(self, t: float) -> float:
+        """kappa_P(T) of the configured table (cm^2/g)."""
+        k = ctypes.c_double()
+        check(lib.rt_planck_mean_opacity(self._ctx, float(t), ctypes.byref(k)), self._ctx)
+        return k.value
+
+    def dust_temperature(self, a_rad, e_rad=None, t_dust=None):
+        """Dust temperature from a T^4 = E_R + a_rad / kappa_P(T) (CUDA tensors)."""
+        import torch
+        self._check_field(a_rad, "a_rad")
+        if e_rad is not None:
+            self._check_field(e_rad, "e_rad")
+        if t_dust is None:
+            t_dust = torch.empty(self.shape, dtype=torch.float32, device=a_rad.device)
+        self._check_field(t_dust, "t_dust")
+        check(lib.rt_dust_temperature(self._ctx, a_rad.data_ptr(), None if e_rad is None else e_rad.data_ptr(),
+                                      t_dust.data_ptr()), self._ctx)
+        return t_dust
+
     # -- learned surrogate (rt_surrogate_*) -------------------------------------
     def surrogate_train(self, rho_list, t_list, n_samples=0, batch=0, steps=0, lr=0.0, seed=1):
         """Train the context's surrogate on the given fields (CUDA tensors of this
