@@ -106,6 +106,20 @@ int rt_set_stream(rt_ctx *ctx, void *cuda_stream);
 int rt_set_opacity_table(rt_ctx *ctx, int n_nu, const double *nu_mid, const double *kappa,
                          double t_sub, int kappa_bf16);
 
+/* rt_set_opacity_table_t -- temperature-dependent opacities (an extension the
+ * paper's tabulated dust opacities allow): kappa_t [n_nu][n_t] (cm^2 g^-1, >= 0,
+ * row-major, bin-major) on the strictly increasing temperature grid t_grid [n_t]
+ * (K, 2 <= n_t <= 32); a cell's kappa of bin i is row i linear in T between the
+ * bracketing grid points (the end values beyond the grid), zero where
+ * T_dust > t_sub. The optical depth of every bin is then its own scan along the
+ * ray (Eq. 19), traced by a separate warp-per-ray kernel (nr <= 1024). The
+ * temperature-independent entry rt_set_opacity_table switches back. Not
+ * available to the multi-grid batch or the learned surrogate (their calls fail
+ * with RT_ERR_INVALID_ARG); rt_planck_mean_opacity / rt_dust_temperature use
+ * kappa_i(T). Host arrays, copied. */
+int rt_set_opacity_table_t(rt_ctx *ctx, int n_nu, const double *nu_mid, int n_t, const double *t_grid,
+                           const double *kappa_t, double t_sub);
+
 /* rt_set_star -- the central black-body star (Eqs. 18 and 20).
  *   t_star  effective temperature (K), > 0;  r_star  radius (cm), > 0.
  * Bin fluxes F_i = pi * int B_nu(T_s) dnu over each bin (sum_i F_i = sigma T_s^4) are

@@ -45,6 +45,10 @@ def _configure(lib):
     lib.rto_planck_G_large.argtypes = [ctypes.c_double]
     lib.rto_planck_band.restype = ctypes.c_double
     lib.rto_planck_band.argtypes = [ctypes.c_double, ctypes.c_double]
+    lib.rto_irradiate_tdep.restype = ctypes.c_int
+    lib.rto_irradiate_tdep.argtypes = ([ctypes.c_int] * 3 + [_D] * 3 + [ctypes.c_double] * 2 +
+                                       [ctypes.c_int, _D, ctypes.c_int, _D, _D, ctypes.c_double] + [_D] * 8 +
+                                       [ctypes.c_int])
     lib.rto_planck_mean.restype = ctypes.c_double
     lib.rto_planck_mean.argtypes = [ctypes.c_double, ctypes.c_int, _D, _D]
     lib.rto_dust_temperature.restype = ctypes.c_int
@@ -173,6 +177,30 @@ def irradiate(r_if, theta_if, phi_if, t_star, r_star, nu_mid, kappa, t_sub, rho,
     if rc != 0:
         raise ValueError("rto_irradiate: bad argument")
     return Result(q, a, p, fl, pe, en)
+
+
+def irradiate_tdep(r_if, theta_if, phi_if, t_star, r_star, nu_mid, t_grid, kappa_t, t_sub, rho, tdust,
+                   nthreads: int = 1) -> Result:
+    """The oracle with temperature-dependent opacities kappa_t [n_nu][n_t] on t_grid."""
+    r_if, theta_if, phi_if = _f64(r_if), _f64(theta_if), _f64(phi_if)
+    nu, tg = _f64(nu_mid), _f64(t_grid)
+    kt = np.ascontiguousarray(kappa_t, dtype=np.float64)
+    assert kt.shape == (len(nu), len(tg))
+    nr, nth, nph = len(r_if) - 1, len(theta_if) - 1, len(phi_if) - 1
+    rho = _f64(rho).reshape(nph, nth, nr)
+    tdust = _f64(tdust).reshape(nph, nth, nr)
+    q = np.empty_like(rho)
+    a = np.empty_like(rho)
+    p = np.empty_like(rho)
+    pe = np.empty((nph, nth))
+    en = np.empty(4)
+    rc = _load().rto_irradiate_tdep(nr, nth, nph, _ptr(r_if), _ptr(theta_if), _ptr(phi_if), float(t_star),
+                                    float(r_star), len(nu), _ptr(nu), len(tg), _ptr(tg), _ptr(kt), float(t_sub),
+                                    _ptr(rho), _ptr(tdust), _ptr(q), _ptr(a), _ptr(p), None, _ptr(pe), _ptr(en),
+                                    int(nthreads))
+    if rc != 0:
+        raise ValueError("rto_irradiate_tdep: bad argument")
+    return Result(q, a, p, None, pe, en)
 
 
 def irradiate_workload(w, rho=None, tdust=None, kappa=None, want_flux=False, nthreads=1) -> Result:

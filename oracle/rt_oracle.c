@@ -24,6 +24,8 @@
  *    source evaluated at the interface radius (Eq. 17).
  *  - kappa_nu is zero in a cell whose dust temperature exceeds t_sub (evaporated
  *    dust, Sect. 2); a cell at exactly t_sub keeps its dust.
+ *  - Temperature-dependent tables (rto_irradiate_tdep, an extension the paper's
+ *    "tabulated dust opacities" allow): kappa_i linear in T between grid points.
  *  - Absorbed power of cell k in bin i (Eqs. 28-32 carried to spherical shells,
  *    Eq. 36): P = F_i R_s^2 dOmega exp(-tau_in) (-expm1(-dtau)), dtau = kappa rho dr.
  *  - a_rad = -div(F_s)/(rho c) (Sect. 5) written without the division by rho:
@@ -217,19 +219,34 @@ static double rto_phi(double x) { return x > 0.0 ? -expm1(-x) / x : 1.0; }
  * sums are Neumaier-compensated, ray partials added in ray order.
  * Returns 0, or -1 on a bad argument.
  */
-int rto_irradiate(int nr, int ntheta, int nphi,
-                  const double *r_if, const double *theta_if, const double *phi_if,
-                  double t_star, double r_star,
-                  int n_nu, const double *nu_mid, const double *kappa, double t_sub,
-                  const double *rho, const double *tdust,
-                  double *q_abs, double *a_rad,
-                  double *p_abs, double *flux_if, double *p_esc,
-                  double *energy, int nthreads)
+/* kappa of bin row `row` (n_t values on t_grid) at dust temperature t: linear in T
+ * between the two bracketing grid points, the end values beyond the grid. With
+ * n_t == 1 the opacity does not depend on T. */
+static double rto_kappa_at(const double *row, int n_t, const double *t_grid, double t)
 {
-    if (nr < 1 || ntheta < 1 || nphi < 1 || n_nu < 1 || !(r_star > 0.0)) return -1;
+    if (n_t == 1 || t <= t_grid[0]) return row[0];
+    if (t >= t_grid[n_t - 1]) return row[n_t - 1];
+    int j = 0;
+    while (!(t < t_grid[j + 1])) ++j;
+    const double w = (t - t_grid[j]) / (t_grid[j + 1] - t_grid[j]);
+    return row[j] + (row[j + 1] - row[j]) * w;
+}
+
+static int rto_irradiate_impl(int nr, int ntheta, int nphi,
+                              const double *r_if, const double *theta_if, const double *phi_if,
+                              double t_star, double r_star,
+                              int n_nu, const double *nu_mid, int n_t, const double *t_grid,
+                              const double *kappa, double t_sub,
+                              const double *rho, const double *tdust,
+                              double *q_abs, double *a_rad,
+                              double *p_abs, double *flux_if, double *p_esc,
+                              double *energy, int nthreads)
+{
+    if (nr < 1 || ntheta < 1 || nphi < 1 || n_nu < 1 || n_t < 1 || !(r_star > 0.0)) return -1;
     if (!(r_if[0] > 0.0)) return -1;
     for (int k = 0; k < nr; ++k) if (!(r_if[k + 1] > r_if[k])) return -1;
-    for (int i = 0; i < n_nu; ++i) if (!(kappa[i] >= 0.0)) return -1;
+    for (int i = 0; i < n_nu * n_t; ++i) if (!(kappa[i] >= 0.0)) return -1;
+    for (int j = 1; j < n_t; ++j) if (!(t_grid[j] > t_grid[j - 1])) return -1;
 
     double *f_bin = (double *)malloc(sizeof(double) * (size_t)n_nu);
     if (!f_bin) return -1;
@@ -265,7 +282,7 @@ int rto_irradiate(int nr, int ntheta, int nphi,
             double tau = 0.0;
             for (int k = 0; k < nr; ++k) {
                 const double dr = r_if[k + 1] - r_if[k];
-                const double kap = (t_ray[k] <= t_sub) ? kappa[i] : 0.0;
+                const double kap = (t_ray[k] <= t_sub) ? rto_kappa_at(kappa + (size_t)i * n_t, n_t, t_grid, t_ray[k]) : 0.0;
                 const double dtau = kap * rho_ray[k] * dr;
                 const double att = exp(-tau);
                 Fif[k] += f_bin[i] * (r2 / (r_if[k] * r_if[k])) * att;
@@ -309,6 +326,37 @@ int rto_irradiate(int nr, int ntheta, int nphi,
     }
     free(f_bin); free(ray_abs); free(ray_esc); free(ray_dom);
     return 0;
+}
+
+int rto_irradiate(int nr, int ntheta, int nphi,
+                  const double *r_if, const double *theta_if, const double *phi_if,
+                  double t_star, double r_star,
+                  int n_nu, const double *nu_mid, const double *kappa, double t_sub,
+                  const double *rho, const double *tdust,
+                  double *q_abs, double *a_rad,
+                  double *p_abs, double *flux_if, double *p_esc,
+                  double *energy, int nthreads)
+{
+    return rto_irradiate_impl(nr, ntheta, nphi, r_if, theta_if, phi_if, t_star, r_star, n_nu, nu_mid, 1, NULL,
+                              kappa, t_sub, rho, tdust, q_abs, a_rad, p_abs, flux_if, p_esc, energy, nthreads);
+}
+
+/* rto_irradiate with temperature-dependent opacities: kappa_t [n_nu][n_t] on the
+ * increasing temperature grid t_grid [n_t]; each cell's kappa of bin i is that row
+ * at the cell's dust temperature (rto_kappa_at), zero above t_sub. */
+int rto_irradiate_tdep(int nr, int ntheta, int nphi,
+                       const double *r_if, const double *theta_if, const double *phi_if,
+                       double t_star, double r_star,
+                       int n_nu, const double *nu_mid, int n_t, const double *t_grid,
+                       const double *kappa_t, double t_sub,
+                       const double *rho, const double *tdust,
+                       double *q_abs, double *a_rad,
+                       double *p_abs, double *flux_if, double *p_esc,
+                       double *energy, int nthreads)
+{
+    if (n_t < 2 || !t_grid) return -1;
+    return rto_irradiate_impl(nr, ntheta, nphi, r_if, theta_if, phi_if, t_star, r_star, n_nu, nu_mid, n_t, t_grid,
+                              kappa_t, t_sub, rho, tdust, q_abs, a_rad, p_abs, flux_if, p_esc, energy, nthreads);
 }
 
 int rto_max_threads(void)

@@ -77,6 +77,7 @@ SIGNATURES = {
     "rt_set_stream": (_I, [_P, _P]),
     "rt_set_opacity_table": (_I, [_P, _I, _DP, _DP, _D, _I]),
     "rt_set_star": (_I, [_P, _D, _D]),
+    "rt_set_opacity_table_t": (_I, [_P, _I, _DP, _I, _DP, _DP, _D]),
     "rt_irradiate": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(RtEnergy)]),
     "rt_irradiate_host": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(RtEnergy)]),
     "rt_energy_last": (_I, [_P, ctypes.POINTER(RtEnergy)]),

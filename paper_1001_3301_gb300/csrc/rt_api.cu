@@ -52,6 +52,13 @@ struct rt_ctx {
 
     // host copies of the table as the tracer uses it, and its fingerprint
     std::vector<double> nu_h, kappa_h;
+    // temperature-dependent table (rt_set_opacity_table_t): grid, rows, sorted pairs
+    int n_t = 0;
+    std::vector<double> tgrid_h, kappa_t_h;
+    double *kappa_t_d = nullptr;
+    float *tg32 = nullptr;
+    float2 *kt2 = nullptr;
+    int *order_d = nullptr;
     unsigned long long fingerprint = 0;
     // learned surrogate (rt_surrogate.cu), created by rt_surrogate_train / _load
     rt::SurState *sur = nullptr;
@@ -118,6 +125,7 @@ long long total_tiles(const rt_ctx *c, Shape s);
 // every compiled shape that applies to this context: tile shapes, then ray shapes
 int all_shapes(const rt_ctx *c, Shape *out, int max_out)
 {
+    if (c->n_t > 0) return rt::tdep_shapes(c->nr, out, max_out);
     int n = rt::trace_shapes(c->precision, out, max_out);
     if (c->precision != RT_FP64) n += rt::ray_shapes(c->precision, c->nr, out + n, max_out - n);
     return n;
@@ -125,6 +133,16 @@ int all_shapes(const rt_ctx *c, Shape *out, int max_out)
 
 Shape default_shape(const rt_ctx *c)
 {
+    if (c->n_t > 0) {  // temperature-dependent table: the fewest cells per lane that hold a ray
+        Shape ts[16];
+        const int n = rt::tdep_shapes(c->nr, ts, 16);
+        int bi = -1;
+        for (int i = 0; i < n; ++i)
+            if (bi < 0 || ts[i].cells_per_lane < ts[bi].cells_per_lane ||
+                (ts[i].cells_per_lane == ts[bi].cells_per_lane && ts[i].min_blocks > ts[bi].min_blocks))
+                bi = i;
+        return bi >= 0 ? ts[bi] : Shape{rt::kKindRay, 0, 0, 0};
+    }
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(std::make_tuple(c->precision, c->nr, c->nrays, c->sc_h.nnu_pad));
@@ -170,7 +188,7 @@ int finalize(rt_ctx *c)
     if (!(c->have_table && c->have_star)) return RT_OK;
     cudaError_t e = rt::launch_setup_bins(c->n_nu, c->nu_mid, c->kappa, c->t_star, c->r_star,
                                           c->kappa_bf16, c->f_bin, c->nu_tab, c->kap, c->nu64,
-                                          c->sc, c->stream);
+                                          c->sc, c->stream, c->order_d);
     if (e != cudaSuccess) return cuda_fail(c, "setup_bins", e);
     e = rt::launch_setup_geometry(c->nr, c->ntheta, c->nphi, c->r_if, c->theta_if, c->phi_if,
                                   c->t_star, c->rtab, c->rtab64, c->domega, c->domega32, c->sc,
@@ -178,6 +196,12 @@ int finalize(rt_ctx *c)
     if (e != cudaSuccess) return cuda_fail(c, "setup_geometry", e);
     RT_CK(c, cudaMemcpyAsync(&c->sc_h, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
     RT_CK(c, cudaStreamSynchronize(c->stream));
+    if (c->n_t > 0) {
+        e = rt::launch_build_tdep(c->sc_h.n_active, c->sc_h.nnu_pad, c->n_t, c->kappa_t_d, c->order_d, c->kt2,
+                                  c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, "build temperature table", e);
+        RT_CK(c, cudaStreamSynchronize(c->stream));
+    }
     if (!c->shape_forced) c->shape = default_shape(c);
     // FNV-1a over what fixes the per-cell absorption function of (N_in, dN)
     unsigned long long h = 1469598103934665603ULL;
@@ -190,6 +214,9 @@ int finalize(rt_ctx *c)
     mix(c->kappa_h.data(), sizeof(double) * c->kappa_h.size());
     mix(&c->t_sub, sizeof(double));
     mix(&c->t_star, sizeof(double));
+    mix(&c->n_t, sizeof(int));
+    mix(c->tgrid_h.data(), sizeof(double) * c->tgrid_h.size());
+    mix(c->kappa_t_h.data(), sizeof(double) * c->kappa_t_h.size());
     c->fingerprint = h;
     c->configured = true;
     return RT_OK;
@@ -257,7 +284,8 @@ int trace_range(rt_ctx *c, const float *rho, const float *td, float *q, float *a
         args.nrays = (unsigned)nr_c;
         const long long nt = (nr_c * (c->nr + 1) + T - 1) / T;
         unsigned grid = 0;
-        cudaError_t e = rt::launch_trace(c->precision, s, args, (unsigned)nt, stream, &grid);
+        cudaError_t e = c->n_t > 0 ? rt::launch_tdep(s, args, c->kt2, c->tg32, c->n_t, stream, &grid)
+                                   : rt::launch_trace(c->precision, s, args, (unsigned)nt, stream, &grid);
         if (e != cudaSuccess) return cuda_fail(c, "trace kernel launch", e);
         *npart += grid;
     }
@@ -307,6 +335,8 @@ int check_call(rt_ctx *c, const void *rho, const void *td, const void *q, const 
     if (!c) return RT_ERR_INVALID_ARG;
     if (!rho || !td || !q || !a) return fail(c, RT_ERR_INVALID_ARG, "NULL field pointer");
     if (!c->configured) return fail(c, RT_ERR_NOT_CONFIGURED, "call rt_set_star and rt_set_opacity_table first");
+    if (c->n_t > 0 && c->shape.cells_per_lane == 0)
+        return fail(c, RT_ERR_INVALID_ARG, "temperature-dependent opacity tables need nr <= 1024");
     cudaError_t e = cudaSetDevice(c->dev);
     if (e != cudaSuccess) return cuda_fail(c, "cudaSetDevice", e);
     return RT_OK;
@@ -316,7 +346,8 @@ void free_all(rt_ctx *c)
 {
     void *ptrs[] = {c->r_if, c->theta_if, c->phi_if, c->rtab, c->rtab64, c->domega, c->domega32, c->nu_mid,
                     c->kappa, c->f_bin, c->nu_tab, c->kap, c->nu64, c->sc, c->partials, c->bad,
-                    c->energy_d, c->h_rho, c->h_t, c->h_q, c->h_a, c->temp_lkp};
+                    c->energy_d, c->h_rho, c->h_t, c->h_q, c->h_a, c->temp_lkp, c->kappa_t_d,
+                    c->tg32, c->kt2, c->order_d};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->energy_h) cudaFreeHost(c->energy_h);
@@ -356,6 +387,7 @@ bool ctx_view(const rt_ctx *c, CtxView *v)
     v->dev = c->dev;
     v->flat_cells = c->L;
     v->ncells = c->ncells;
+    v->tdep = c->n_t > 0;
     return true;
 }
 
@@ -375,6 +407,9 @@ bool ctx_info(const rt_ctx *c, CtxInfo *o)
     o->nu_h = c->nu_h.data();
     o->kappa_h = c->kappa_h.data();
     o->table_fingerprint = c->fingerprint;
+    o->n_t = c->n_t;
+    o->t_grid_h = c->tgrid_h.data();
+    o->kappa_t_h = c->kappa_t_h.data();
     o->rtab = c->rtab;
     o->domega32 = c->domega32;
     o->nu_tab = c->nu_tab;
@@ -438,6 +473,7 @@ int rt_create(const rt_grid_desc *g, void *cuda_stream, rt_ctx **out)
     ok = ok && dalloc(&c->kap, RT_MAX_NU + rt::kNuPad) == cudaSuccess;
     ok = ok && dalloc(&c->nu64, RT_MAX_NU + rt::kNuPad) == cudaSuccess;
     ok = ok && dalloc(&c->sc, 1) == cudaSuccess;
+    ok = ok && dalloc(&c->order_d, RT_MAX_NU) == cudaSuccess;
     ok = ok && dalloc(&c->bad, 1) == cudaSuccess;
     ok = ok && dalloc(&c->energy_d, 1) == cudaSuccess;
     ok = ok && cudaMallocHost((void **)&c->energy_h, sizeof(rt_energy)) == cudaSuccess;
@@ -487,6 +523,9 @@ int rt_set_opacity_table(rt_ctx *ctx, int n_nu, const double *nu_mid, const doub
     ctx->n_nu = n_nu;
     ctx->t_sub = t_sub;
     ctx->kappa_bf16 = kappa_bf16 ? 1 : 0;
+    ctx->n_t = 0;
+    ctx->tgrid_h.clear();
+    ctx->kappa_t_h.clear();
     ctx->nu_h.assign(nu_mid, nu_mid + n_nu);
     ctx->kappa_h.assign(kappa, kappa + n_nu);
     if (ctx->kappa_bf16)  // the tracer's table: kappa rounded to BF16 (nearest, ties to even)
@@ -498,6 +537,54 @@ int rt_set_opacity_table(rt_ctx *ctx, int n_nu, const double *nu_mid, const doub
             memcpy(&f, &u, 4);
             k = f;
         }
+    ctx->have_table = true;
+    return finalize(ctx);
+}
+
+int rt_set_opacity_table_t(rt_ctx *ctx, int n_nu, const double *nu_mid, int n_t, const double *t_grid,
+                           const double *kappa_t, double t_sub)
+{
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (n_nu < 1 || n_nu > RT_MAX_NU || !nu_mid || !kappa_t || !t_grid)
+        return fail(ctx, RT_ERR_INVALID_ARG, "n_nu must be in 1..128 with non-NULL arrays");
+    if (n_t < 2 || n_t > rt::kMaxTdepPoints) return fail(ctx, RT_ERR_INVALID_ARG, "n_t must be in 2..32");
+    if (!increasing(nu_mid, n_nu) || !(nu_mid[0] > 0.0))
+        return fail(ctx, RT_ERR_INVALID_ARG, "nu_mid must be finite, > 0 and strictly increasing");
+    if (!increasing(t_grid, n_t) || !(t_grid[0] > 0.0))
+        return fail(ctx, RT_ERR_INVALID_ARG, "t_grid must be finite, > 0 and strictly increasing");
+    for (int i = 0; i < n_nu * n_t; ++i)
+        if (!(kappa_t[i] >= 0.0) || !isfinite(kappa_t[i]))
+            return fail(ctx, RT_ERR_INVALID_ARG, "kappa_t must be finite and >= 0");
+    if (isnan(t_sub)) return fail(ctx, RT_ERR_INVALID_ARG, "t_sub is NaN");
+    RT_CK(ctx, cudaSetDevice(ctx->dev));
+    if (!ctx->kappa_t_d) {
+        bool ok = dalloc(&ctx->kappa_t_d, (size_t)RT_MAX_NU * rt::kMaxTdepPoints) == cudaSuccess &&
+                  dalloc(&ctx->tg32, rt::kMaxTdepPoints) == cudaSuccess &&
+                  dalloc(&ctx->kt2, (size_t)(RT_MAX_NU + rt::kNuPad) * rt::kMaxTdepPoints) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            return fail(ctx, RT_ERR_NO_MEMORY, "cannot allocate the temperature-dependent table");
+        }
+    }
+    // each bin's largest value orders the bins and bounds the absorbed-fraction classes
+    std::vector<double> kmax(n_nu, 0.0);
+    for (int i = 0; i < n_nu; ++i)
+        for (int j = 0; j < n_t; ++j) kmax[i] = std::max(kmax[i], kappa_t[(size_t)i * n_t + j]);
+    std::vector<float> tg(t_grid, t_grid + n_t);
+    RT_CK(ctx, cudaMemcpyAsync(ctx->nu_mid, nu_mid, sizeof(double) * n_nu, cudaMemcpyHostToDevice, ctx->stream));
+    RT_CK(ctx, cudaMemcpyAsync(ctx->kappa, kmax.data(), sizeof(double) * n_nu, cudaMemcpyHostToDevice, ctx->stream));
+    RT_CK(ctx, cudaMemcpyAsync(ctx->kappa_t_d, kappa_t, sizeof(double) * n_nu * n_t, cudaMemcpyHostToDevice,
+                               ctx->stream));
+    RT_CK(ctx, cudaMemcpyAsync(ctx->tg32, tg.data(), sizeof(float) * n_t, cudaMemcpyHostToDevice, ctx->stream));
+    RT_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->n_nu = n_nu;
+    ctx->t_sub = t_sub;
+    ctx->kappa_bf16 = 0;
+    ctx->n_t = n_t;
+    ctx->tgrid_h.assign(t_grid, t_grid + n_t);
+    ctx->kappa_t_h.assign(kappa_t, kappa_t + (size_t)n_nu * n_t);
+    ctx->nu_h.assign(nu_mid, nu_mid + n_nu);
+    ctx->kappa_h = kmax;
     ctx->have_table = true;
     return finalize(ctx);
 }

@@ -334,6 +334,11 @@ int rt_batch_create(rt_ctx *const *ctxs, int n, void *cuda_stream, rt_batch **ou
             return bfail(nullptr, RT_ERR_NOT_CONFIGURED, "context " + std::to_string(g) + " is NULL or not configured");
         }
         const rt::CtxView &v = b->views[g];
+        if (v.tdep) {
+            delete b;
+            return bfail(nullptr, RT_ERR_INVALID_ARG,
+                         "context " + std::to_string(g) + " has a temperature-dependent table (not batched)");
+        }
         if (g > 0 && (v.precision != b->views[0].precision || v.dev != b->views[0].dev)) {
             delete b;
             return bfail(nullptr, RT_ERR_INVALID_ARG, "all contexts of a batch need one precision and one device");

@@ -122,6 +122,14 @@ cudaError_t launch_ray_shape(int precision, Shape s, const TraceArgs &args, cuda
 cudaError_t launch_trace(int precision, Shape s, const TraceArgs &args, unsigned ntiles,
                          cudaStream_t stream, unsigned *grid_out);
 
+// Tracer with temperature-dependent opacity tables (rt_tdep.cu)
+constexpr int kMaxTdepPoints = 32;
+int tdep_shapes(int nr, Shape *out, int max_out);
+cudaError_t launch_tdep(Shape s, const TraceArgs &args, const float2 *kt2, const float *tg, int n_t,
+                        cudaStream_t stream, unsigned *grid_out);
+cudaError_t launch_build_tdep(int n_active, int nnu_pad, int n_t, const double *kappa_t, const int *order,
+                              float2 *kt2, cudaStream_t stream);
+
 // A configured context's device tables, for the batch launcher (rt_api.cu).
 struct CtxView {
     TraceArgs args;        // tables and sizes; field pointers, partials, validity word unset
@@ -130,6 +138,7 @@ struct CtxView {
     int dev;
     long long flat_cells;  // nrays * (nr + 1)
     long long ncells;
+    bool tdep;             // temperature-dependent opacity table (not batched)
 };
 }  // namespace rt
 struct rt_ctx;
@@ -149,6 +158,9 @@ struct CtxInfo {
     const double *nu_h;        // host copies of the table the tracer uses (kappa
     const double *kappa_h;     // after the optional BF16 rounding)
     unsigned long long table_fingerprint;  // of (n_nu, nu, kappa, t_sub, t_star)
+    int n_t;                   // > 0: temperature-dependent table on t_grid_h [n_t],
+    const double *t_grid_h;    // kappa_t_h [n_nu][n_t] (then kappa_h holds each bin's
+    const double *kappa_t_h;   // largest value)
     const float4 *rtab;        // [nr] (dr, Gq, Ga0, 0)
     const float *domega32;     // [nrays]
     const NuEntry *nu_tab;     // [nnu_pad], kappa-sorted active bins
@@ -166,10 +178,12 @@ void sur_free(SurState *s);
 int ctx_fail(rt_ctx *c, int status, const std::string &msg);
 
 // Set-up kernels (rt_setup.cu)
+// order_dev (may be null) receives the original index of every kappa-sorted bin
 cudaError_t launch_setup_bins(int n_nu, const double *nu_mid_dev, const double *kappa_dev,
                               double t_star, double r_star, int kappa_bf16,
                               double *f_bin_dev, NuEntry *nu_dev, float *kap_dev,
-                              double2 *nu64_dev, DevScalars *sc_dev, cudaStream_t stream);
+                              double2 *nu64_dev, DevScalars *sc_dev, cudaStream_t stream,
+                              int *order_dev = nullptr);
 cudaError_t launch_setup_geometry(int nr, int ntheta, int nphi, const double *r_if_dev,
                                   const double *theta_if_dev, const double *phi_if_dev,
                                   double t_star, float4 *rtab, RadRow64 *rtab64,

@@ -14,7 +14,7 @@ namespace {
 // then thread 0 compacts the bins with kappa > 0 into the tracer's table.
 __global__ void k_setup_bins(int n_nu, const double *nu_mid, const double *kappa, double t_star,
                              double r_star, int kappa_bf16, double *f_bin, NuEntry *nu,
-                             float *kap, double2 *nu64, DevScalars *sc)
+                             float *kap, double2 *nu64, DevScalars *sc, int *order_out)
 {
     __shared__ double s_f[RT_MAX_NU];
     __shared__ double s_k[RT_MAX_NU];
@@ -57,6 +57,7 @@ __global__ void k_setup_bins(int n_nu, const double *nu_mid, const double *kappa
     }
     for (int a = 0; a < na; ++a) {
         const int b = order[a];
+        if (order_out) order_out[a] = b;
         nu[a].nk = (float)(-s_k[b] * kLog2e);
         nu[a].lf = (float)log2(s_f[b] / fmax);
         kap[a] = (float)s_k[b];
@@ -164,11 +165,11 @@ __global__ void k_energy_reduce(const double2 *partials, long long ntiles, const
 cudaError_t launch_setup_bins(int n_nu, const double *nu_mid_dev, const double *kappa_dev,
                               double t_star, double r_star, int kappa_bf16, double *f_bin_dev,
                               NuEntry *nu_dev, float *kap_dev, double2 *nu64_dev,
-                              DevScalars *sc_dev, cudaStream_t stream)
+                              DevScalars *sc_dev, cudaStream_t stream, int *order_dev)
 {
     k_setup_bins<<<1, 32 * (RT_MAX_NU / 4), 0, stream>>>(n_nu, nu_mid_dev, kappa_dev, t_star, r_star,
                                               kappa_bf16, f_bin_dev, nu_dev, kap_dev, nu64_dev,
-                                              sc_dev);
+                                              sc_dev, order_dev);
     return cudaGetLastError();
 }
 

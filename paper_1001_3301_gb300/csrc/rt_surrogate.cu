@@ -1298,6 +1298,9 @@ int begin(rt_ctx *ctx, CtxInfo *in)
     if (!ctx) return RT_ERR_INVALID_ARG;
     ctx_info(ctx, in);
     if (!in->configured) return ctx_fail(ctx, RT_ERR_NOT_CONFIGURED, "call rt_set_star and rt_set_opacity_table first");
+    if (in->n_t > 0)
+        return ctx_fail(ctx, RT_ERR_INVALID_ARG,
+                        "the surrogate's inputs assume a temperature-independent table (rt_set_opacity_table)");
     if (cudaSetDevice(in->dev) != cudaSuccess) return ctx_fail(ctx, RT_ERR_CUDA, "cudaSetDevice");
     return RT_OK;
 }

@@ -1,0 +1,280 @@
+// Tracer with temperature-dependent opacity tables: kappa_i(T) per bin, linear in T
+// between the points of a temperature grid (the ends beyond it), zero above the
+// sublimation temperature. Each cell has its own kappa per bin, so the optical
+// depth of every bin is its own scan along the ray (Eq. 19; no single column serves
+// all bins as in rt_ray.cu):
+//   tau_i,in(k) = sum_{k' < k} kappa_i(T_k') rho_k' dr_k',
+// then the attenuated flux (Eq. 17) and the absorbed fraction of the cell
+// (Eqs. 31-32, 36) per (cell, bin) as in the per-bin loop of rt_device.cuh.
+//
+// One warp per ray, lane l owns cells [l C, (l+1) C). Per bin: every cell's kappa
+// from the table (one 8-byte shared-memory read of the bracketing pair), the lane's
+// compensated sum, a compensated warp scan of the lane sums, then a second pass over
+// the lane's cells carrying the exclusive prefix (no per-cell prefix is stored).
+// The bins are ordered by their largest tabulated kappa; the Taylor classes of the
+// absorbed fraction (1, 2, 3, 5 terms) come from that largest kappa and the warp's
+// largest column, the remaining bins take the per-cell select between the 5-term
+// series and 1 - ex2 (kappa's smallest value need not follow the same order).
+#include "rt_device.cuh"
+
+namespace rt {
+namespace {
+
+struct TdepTab {
+    const float2 *kt2;  // [nnu_pad][n_t] (kappa_j, kappa_{j+1}) of every sorted bin
+    const float *tg;    // [n_t] temperature grid (K)
+    int n_t;
+};
+
+template <int CLASS>
+__device__ __forceinline__ float absorbed(float y)  // 1 - 2^y, y = -dtau log2(e) <= 0
+{
+    if constexpr (CLASS <= 5) {
+        float p = (float)taylor_coeff(CLASS - 1);
+#pragma unroll
+        for (int k = CLASS - 2; k >= 0; --k) p = fmaf(p, y, (float)taylor_coeff(k));
+        return y * p;
+    } else {
+        float p = (float)taylor_coeff(4);
+#pragma unroll
+        for (int k = 3; k >= 0; --k) p = fmaf(p, y, (float)taylor_coeff(k));
+        const float small = y * p;
+        const float big = 1.0f - ex2_approx(y);
+        return y > -kYSplit ? small : big;
+    }
+}
+
+// Bins [i0, i1) of one class: scan, attenuation, absorption for the lane's cells.
+template <int CLASS, int C>
+__device__ __forceinline__ void tdep_range(int i0, int i1, const float *s_lf, const float2 *s_kt, int n_t,
+                                           const int (&jt)[C], const float (&wt)[C], const float (&d)[C],
+                                           float (&acc)[C], float (&acc0)[C], bool any_zero, int lane,
+                                           float &esc)
+{
+    for (int i = i0; i < i1; ++i) {
+        const float lf = s_lf[i];
+        const float2 *row = s_kt + i * n_t;
+        float kap[C], dt[C];
+        KahanSum run;
+        run.zero();
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            const float2 kk = row[jt[j]];
+            kap[j] = fmaf(wt[j], kk.y - kk.x, kk.x);
+            dt[j] = kap[j] * d[j];
+            run.add(dt[j]);
+        }
+        // compensated warp scan of the lane sums
+        KahanSum inc = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const KahanSum v = inc.shfl_up(o);
+            if (lane >= o) inc.add(v);
+        }
+        KahanSum pre = inc.shfl_up(1);
+        if (lane == 0) pre.zero();
+        if (lane == 31) esc += ex2_approx(fmaf(-(float)kLog2e, inc.value(), lf));
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            const float g = ex2_approx(fmaf(-(float)kLog2e, pre.value(), lf));
+            acc[j] = fmaf(g, absorbed<CLASS>(-(float)kLog2e * dt[j]), acc[j]);
+            if (any_zero) acc0[j] = fmaf(g, kap[j], acc0[j]);
+            pre.add(dt[j]);
+        }
+    }
+}
+
+template <int C, int W, int MINB>
+__global__ void __launch_bounds__(W * 32, MINB) k_ray_tdep(const TraceArgs p, const TdepTab t)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nr = p.nr;
+    const int c0 = lane * C;
+    const int nv = nr - c0 < 0 ? 0 : (nr - c0 > C ? C : nr - c0);
+
+    __shared__ float s_dr[C][32], s_gq[C][32], s_ga[C][32];
+    __shared__ float s_tg[32];
+    __shared__ KahanSum s_red[W][2];
+    extern __shared__ __align__(16) unsigned char smem[];
+    float4 *s_nu = reinterpret_cast<float4 *>(smem);                 // [nnu_pad] (nk_max, ., lf, .)
+    float *s_lf = reinterpret_cast<float *>(s_nu + p.nnu_pad);        // [nnu_pad]
+    float2 *s_kt = reinterpret_cast<float2 *>(s_lf + p.nnu_pad + 2);  // [nnu_pad][n_t], 8-byte aligned
+    s_kt = reinterpret_cast<float2 *>((reinterpret_cast<size_t>(s_kt) + 7) & ~size_t(7));
+
+    for (int i = tid; i < p.nnu_pad; i += W * 32) {
+        const NuEntry e = p.nu[i];
+        s_nu[i] = make_float4(e.nk, e.nk, e.lf, e.lf);
+        s_lf[i] = e.lf;
+    }
+    for (int i = tid; i < p.nnu_pad * t.n_t; i += W * 32) s_kt[i] = t.kt2[i];
+    for (int i = tid; i < t.n_t; i += W * 32) s_tg[i] = t.tg[i];
+    for (int i = tid; i < 32 * C; i += W * 32) {
+        const int l = i / C, j = i % C, k = l * C + j;
+        const float4 g = (k < nr) ? __ldg(&p.rtab[k]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        s_dr[j][l] = g.x;
+        s_gq[j][l] = g.y;
+        s_ga[j][l] = g.z;
+    }
+    __syncthreads();
+    const int nt = t.n_t;
+
+    KahanSum eabs, eesc;
+    eabs.zero();
+    eesc.zero();
+    for (unsigned ray = blockIdx.x * W + warp; ray < p.nrays; ray += gridDim.x * W) {
+        const size_t base = (size_t)ray * nr + c0;
+        float d[C], acc[C], acc0[C], wt[C];
+        int jt[C];
+        unsigned zero_m = 0;
+        bool bad = false;
+        float dmax = 0.0f;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            float rho = 0.0f, td = 0.0f;
+            if (j < nv) {
+                rho = __ldg(p.rho + base + j);
+                td = __ldg(p.tdust + base + j);
+                bad |= !(rho >= 0.0f && rho <= FLT_MAX) || (td != td);
+            }
+            const bool dust = j < nv && td <= p.t_sub;
+            d[j] = dust ? rho * s_dr[j][lane] : 0.0f;
+            if (dust && d[j] == 0.0f) zero_m |= 1u << j;
+            dmax = fmaxf(dmax, d[j]);
+            acc[j] = 0.0f;
+            acc0[j] = 0.0f;
+            // bracketing temperature points and the weight of the upper one
+            int lo = 0;
+            for (int s = 16; s > 0; s >>= 1)
+                if (lo + s < nt - 1 && s_tg[lo + s] <= td) lo += s;
+            const float w = (td - s_tg[lo]) / (s_tg[lo + 1] - s_tg[lo]);
+            jt[j] = lo;
+            wt[j] = fminf(fmaxf(w, 0.0f), 1.0f);
+        }
+        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicMax(p.bad_input, p.seq);
+        for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        const bool any_zero = __any_sync(0xffffffffu, zero_m != 0u);
+
+        const int na = p.n_active;
+        const BinClasses bc = classify_bins(s_nu, na, lane, dmax, 0.0f);
+        float esc = 0.0f;
+        tdep_range<1, C>(0, bc.b1, s_lf, s_kt, nt, jt, wt, d, acc, acc0, any_zero, lane, esc);
+        tdep_range<2, C>(bc.b1, bc.b2, s_lf, s_kt, nt, jt, wt, d, acc, acc0, any_zero, lane, esc);
+        tdep_range<3, C>(bc.b2, bc.b3, s_lf, s_kt, nt, jt, wt, d, acc, acc0, any_zero, lane, esc);
+        tdep_range<5, C>(bc.b3, bc.b5, s_lf, s_kt, nt, jt, wt, d, acc, acc0, any_zero, lane, esc);
+        tdep_range<6, C>(bc.b5, na, s_lf, s_kt, nt, jt, wt, d, acc, acc0, any_zero, lane, esc);
+
+        const float w = __ldg(p.domega32 + ray);
+        if (lane == 31) eesc.add(esc * w);
+        float lane_abs = 0.0f;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            const bool zc = (zero_m >> j) & 1u;
+            const float qv = zc ? 0.0f : s_gq[j][lane] * acc[j];
+            const float av = s_ga[j][lane] * (zc ? acc0[j] : (d[j] > 0.0f ? __fdividef(acc[j], d[j]) : 0.0f));
+            lane_abs += (j < nv && !zc) ? acc[j] : 0.0f;
+            if (j < nv) {
+                p.q[base + j] = qv;
+                p.a[base + j] = av;
+            }
+        }
+        eabs.add(lane_abs * w);
+    }
+
+    for (int o = 16; o > 0; o >>= 1) {
+        eabs.add(eabs.shfl_xor(o));
+        eesc.add(eesc.shfl_xor(o));
+    }
+    if (lane == 0) {
+        s_red[warp][0] = eabs;
+        s_red[warp][1] = eesc;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        KahanSum sa = s_red[0][0], se = s_red[0][1];
+        for (int w2 = 1; w2 < W; ++w2) {
+            sa.add(s_red[w2][0]);
+            se.add(s_red[w2][1]);
+        }
+        p.partials[blockIdx.x] = make_double2(to_double(sa), to_double(se));
+    }
+}
+
+// kt2[a][j] = (kappa[order[a]][j], kappa[order[a]][j + 1]) for the sorted active
+// bins; padding bins get zero opacity
+__global__ void k_build_tdep(int n_active, int nnu_pad, int n_t, const double *kappa_t, const int *order,
+                             float2 *kt2)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nnu_pad * n_t) return;
+    const int a = idx / n_t, j = idx % n_t;
+    if (a >= n_active) {
+        kt2[idx] = make_float2(0.0f, 0.0f);
+        return;
+    }
+    const double *row = kappa_t + (size_t)order[a] * n_t;
+    kt2[idx] = make_float2((float)row[j], (float)row[j + 1 < n_t ? j + 1 : j]);
+}
+
+template <int C, int W, int MINB>
+cudaError_t launch_tdep_shape(const TraceArgs &a, const TdepTab &t, cudaStream_t stream, unsigned *grid_out)
+{
+    const size_t smem = (size_t)a.nnu_pad * (16 + 4) + 8 + 16 + (size_t)a.nnu_pad * t.n_t * sizeof(float2);
+    auto kern = k_ray_tdep<C, W, MINB>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    unsigned grid = (unsigned)nsm * (unsigned)per_sm;
+    const unsigned need = (a.nrays + W - 1) / W;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    kern<<<grid, W * 32, smem, stream>>>(a, t);
+    *grid_out = grid;
+    return cudaGetLastError();
+}
+
+struct TdepEntry {
+    int c, w, minb;
+    cudaError_t (*fn)(const TraceArgs &, const TdepTab &, cudaStream_t, unsigned *);
+};
+#define RT_TD(C, W, MB) {C, W, MB, &launch_tdep_shape<C, W, MB>}
+const TdepEntry kTdepShapes[] = {RT_TD(2, 4, 8), RT_TD(4, 4, 8), RT_TD(8, 4, 6), RT_TD(8, 4, 4), RT_TD(16, 4, 3),
+                                 RT_TD(32, 4, 2)};
+#undef RT_TD
+
+}  // namespace
+
+int tdep_shapes(int nr, Shape *out, int max_out)
+{
+    int n = 0;
+    for (const TdepEntry &s : kTdepShapes)
+        if (32 * s.c >= nr && n < max_out) out[n++] = Shape{kKindRay, s.c, s.w, s.minb};
+    return n;
+}
+
+cudaError_t launch_tdep(Shape s, const TraceArgs &args, const float2 *kt2, const float *tg, int n_t,
+                        cudaStream_t stream, unsigned *grid_out)
+{
+    const TdepTab t{kt2, tg, n_t};
+    for (const TdepEntry &e : kTdepShapes)
+        if (e.c == s.cells_per_lane && e.w == s.warps && (s.min_blocks == 0 || e.minb == s.min_blocks) &&
+            32 * e.c >= args.nr)
+            return e.fn(args, t, stream, grid_out);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_build_tdep(int n_active, int nnu_pad, int n_t, const double *kappa_t, const int *order,
+                              float2 *kt2, cudaStream_t stream)
+{
+    const int n = nnu_pad * n_t;
+    k_build_tdep<<<(n + 255) / 256, 256, 0, stream>>>(n_active, nnu_pad, n_t, kappa_t, order, kt2);
+    return cudaGetLastError();
+}
+
+}  // namespace rt

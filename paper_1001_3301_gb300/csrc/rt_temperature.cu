@@ -31,8 +31,19 @@ namespace {
 
 // Planck mean of the table at temperature exp(y[n]); one warp per node, the bins'
 // band integrals in FP64. kp_out[n] = kappa_P (double) and lkp[n] = ln kappa_P.
+// kappa of bin row `row` at temperature t: linear between the bracketing points of
+// t_grid, the end values beyond (n_t == 1: constant)
+__device__ double kappa_at(const double *row, int n_t, const double *t_grid, double t)
+{
+    if (n_t <= 1 || t <= t_grid[0]) return row[0];
+    if (t >= t_grid[n_t - 1]) return row[n_t - 1];
+    int j = 0;
+    while (!(t < t_grid[j + 1])) ++j;
+    return row[j] + (row[j + 1] - row[j]) * ((t - t_grid[j]) / (t_grid[j + 1] - t_grid[j]));
+}
+
 __global__ void k_planck_mean(int n_nodes, const double *t_nodes, int n_nu, const double *nu_mid,
-                              const double *kappa, double *kp_out, float *lkp)
+                              const double *kappa, int n_t, const double *t_grid, double *kp_out, float *lkp)
 {
     const int lane = threadIdx.x & 31;
     const int node = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -44,7 +55,7 @@ __global__ void k_planck_mean(int n_nodes, const double *t_nodes, int n_nu, cons
         const double lo = (i == 0) ? 0.0 : 0.5 * (nu_mid[i - 1] + nu_mid[i]);
         const double hi = (i == n_nu - 1) ? INFINITY : 0.5 * (nu_mid[i] + nu_mid[i + 1]);
         const double b = planck_band_warp(lo / kt_h, hi / kt_h, lane);
-        num += kappa[i] * b;
+        num += kappa_at(kappa + (size_t)i * n_t, n_t, t_grid, t) * b;
         den += b;
     }
     if (lane == 0) {
@@ -108,7 +119,10 @@ __global__ void __launch_bounds__(256) k_dust_temperature(const TempArgs p)
         float L, dL;
         interp(s, 5.7037825f, p.y0, p.inv_dy, L, dL);
         float y = 0.25f * (logf(er + ar * expf(-L)) - p.ln_a);
-        for (int it = 0; it < 40; ++it) {
+        // Newton converges quadratically: once a step is below 1e-5 the next one
+        // reaches the FP32 resolution of ln T, so one more step ends the solve
+        bool close = false;
+        for (int it = 0; it < 24; ++it) {
             interp(s, y, p.y0, p.inv_dy, L, dL);
             const float src = ar * expf(-L);
             const float rhs = er + src;
@@ -117,7 +131,8 @@ __global__ void __launch_bounds__(256) k_dust_temperature(const TempArgs p)
             float dy = -f / fmaxf(fp, 0.5f);
             dy = fminf(fmaxf(dy, -2.0f), 2.0f);
             y += dy;
-            if (fabsf(dy) < 2e-7f) break;
+            if (close) break;
+            close = fabsf(dy) < 1e-5f;
         }
         p.t_out[c] = expf(y);
     }
@@ -134,16 +149,22 @@ int planck_means(const CtxInfo &in, const std::vector<double> &t_nodes, double *
                  cudaStream_t st, std::string &err)
 {
     const int n = (int)t_nodes.size();
-    double *tn = nullptr, *nu = nullptr, *ka = nullptr, *kp = nullptr;
+    // the table's opacities: one value per bin, or rows on a temperature grid
+    const int n_t = in.n_t > 0 ? in.n_t : 1;
+    const double *kap_h = in.n_t > 0 ? in.kappa_t_h : in.kappa_h;
+    double *tn = nullptr, *nu = nullptr, *ka = nullptr, *kp = nullptr, *tg = nullptr;
     bool ok = cudaMalloc(&tn, sizeof(double) * n) == cudaSuccess &&
               cudaMalloc(&nu, sizeof(double) * in.n_nu) == cudaSuccess &&
-              cudaMalloc(&ka, sizeof(double) * in.n_nu) == cudaSuccess &&
+              cudaMalloc(&ka, sizeof(double) * in.n_nu * n_t) == cudaSuccess &&
+              cudaMalloc(&tg, sizeof(double) * n_t) == cudaSuccess &&
               cudaMalloc(&kp, sizeof(double) * n) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(tn, t_nodes.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st) == cudaSuccess &&
          cudaMemcpyAsync(nu, in.nu_h, sizeof(double) * in.n_nu, cudaMemcpyHostToDevice, st) == cudaSuccess &&
-         cudaMemcpyAsync(ka, in.kappa_h, sizeof(double) * in.n_nu, cudaMemcpyHostToDevice, st) == cudaSuccess;
+         cudaMemcpyAsync(ka, kap_h, sizeof(double) * in.n_nu * n_t, cudaMemcpyHostToDevice, st) == cudaSuccess;
+    if (ok && in.n_t > 0)
+        ok = cudaMemcpyAsync(tg, in.t_grid_h, sizeof(double) * n_t, cudaMemcpyHostToDevice, st) == cudaSuccess;
     if (ok) {
-        k_planck_mean<<<(n + 7) / 8, 256, 0, st>>>(n, tn, in.n_nu, nu, ka, kp, lkp_dev);
+        k_planck_mean<<<(n + 7) / 8, 256, 0, st>>>(n, tn, in.n_nu, nu, ka, n_t, tg, kp, lkp_dev);
         ok = cudaGetLastError() == cudaSuccess;
     }
     if (ok && kp_host) ok = cudaMemcpyAsync(kp_host, kp, sizeof(double) * n, cudaMemcpyDeviceToHost, st) == cudaSuccess;
@@ -152,6 +173,7 @@ int planck_means(const CtxInfo &in, const std::vector<double> &t_nodes, double *
     cudaFree(tn);
     cudaFree(nu);
     cudaFree(ka);
+    cudaFree(tg);
     cudaFree(kp);
     return ok ? RT_OK : RT_ERR_CUDA;
 }

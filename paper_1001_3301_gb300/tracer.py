@@ -71,6 +71,17 @@ class Tracer:
                                        int(bool(kappa_bf16))), self._ctx)
         self.n_nu = len(nu)
 
+    def set_opacity_table_t(self, nu_mid, t_grid, kappa_t, t_sub: float):
+        """Temperature-dependent table: kappa_t [n_nu][n_t] on t_grid [n_t] (K)."""
+        nu = _f64(nu_mid)
+        tg = _f64(t_grid)
+        kt = np.ascontiguousarray(kappa_t, dtype=np.float64)
+        if kt.shape != (nu.size, tg.size):
+            raise ValueError("kappa_t must be [n_nu][n_t]")
+        check(lib.rt_set_opacity_table_t(self._ctx, nu.size, _dptr(nu), tg.size, _dptr(tg), _dptr(kt),
+                                         float(t_sub)), self._ctx)
+        self.n_nu = nu.size
+
     def set_star(self, t_star: float, r_star: float):
         check(lib.rt_set_star(self._ctx, float(t_star), float(r_star)), self._ctx)
 

@@ -160,6 +160,21 @@ def kappa_synth(nu: np.ndarray) -> np.ndarray:
 # ----------------------------------------------------------------------------
 # density (Sect. 3.1.1)
 # ----------------------------------------------------------------------------
+# temperature-dependent variant: ice mantles evaporating near 150 K remove 30 % of
+# the opacity (a smooth logistic step of width 15 K), on a log-spaced T grid
+T_GRID_LO_K, T_GRID_HI_K = 10.0, 1500.0
+
+
+def t_grid(n_t: int = 24) -> np.ndarray:
+    return np.geomspace(T_GRID_LO_K, T_GRID_HI_K, n_t)
+
+
+def kappa_synth_t(nu: np.ndarray, tg: np.ndarray) -> np.ndarray:
+    """kappa(nu, T) [n_nu][n_t] = kappa_synth(nu) (1 - 0.3 / (1 + e^{-(T - 150 K) / 15 K}))."""
+    s = 1.0 - 0.3 / (1.0 + np.exp(-(np.asarray(tg, dtype=np.float64) - 150.0) / 15.0))
+    return np.outer(kappa_synth(nu), s)
+
+
 def rho0_for_tau550(tau550: float, kappa550: float | None = None) -> float:
     """Midplane normalisation: tau550 = int_{r_min}^{r_max} rho0 (r_d/r) kappa dr
     along z = 0, i.e. rho0 = tau550 / (kappa550 r_d ln(r_max/r_min))."""
