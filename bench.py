@@ -66,6 +66,9 @@ def parse():
     p.add_argument("--batch", action="store_true",
                    help="instead of the throughput line of the 4-grid step: the 96-grid uneven "
                         "batch (one persistent launch per step, CUDA-graph replay)")
+    p.add_argument("--cpu-table", action="store_true",
+                   help="instead of the throughput line: oracle (1 core, all cores) and GPU throughput of "
+                        "the 2-D disk, the 3-D disk at tau 1 and 100, and the 512x256x512 disk")
     p.add_argument("--no-surrogate", action="store_true",
                    help="skip the learned-surrogate leg of the default line")
     p.add_argument("--surrogate", action="store_true",
@@ -199,6 +202,57 @@ def cpu_baseline(ws, target_s=12.0):
     return {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n_rays} evenly spaced rays x {w.grid.nr} cells x {len(w.nu)} bins of the tau550={w.tau550:g} grid "
                       f"({units:.3e} cell-nu updates, {dt:.1f} s, OpenMP over rays)"}
+
+
+def run_cpu_table(args, local):
+    """Oracle (1 core and all cores, bounded ray samples) and GPU tracer (full grid,
+    autotuned) throughput per workload, for the baseline table."""
+    import torch
+    import oracle
+    from paper_1001_3301_gb300 import Tracer, probe_alu_rates
+    torch.cuda.set_device(local)
+    oracle.build()
+    cores = oracle.max_threads()
+    ex2_clk, ffma_clk, mhz = probe_alu_rates()
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = ex2_clk * nsm * 2070e6
+    cases = [("C1 64x32x1 nu32 tau1", synth.disk2d()),
+             ("C2 256x128x256 nu79 tau1", synth.disk3d(256, 128, 256, n_nu=79, tau550=1.0, seed=1)),
+             ("C2 256x128x256 nu79 tau100", synth.disk3d(256, 128, 256, n_nu=79, tau550=100.0, seed=1)),
+             ("C3 512x256x512 nu79 tau1", synth.disk3d(512, 256, 512, n_nu=79, tau550=1.0, seed=2))]
+    rows = []
+    for name, w in cases:
+        nrays = w.grid.ntheta * w.grid.nphi
+        row = {"workload": name}
+        for label, nth in (("oracle_1core", 1), ("oracle_all_cores", cores)):
+            n = min(nrays, 8 * nth)
+            dt = oracle_sample(w, n, nth)
+            n = int(min(nrays, max(n, n * 3.0 / max(dt, 1e-3))))  # about 3 s of work
+            dt = oracle_sample(w, n, nth)
+            row[label] = n * w.grid.nr * len(w.nu) / dt
+        tr = Tracer.from_grid(w.grid)
+        tr.set_opacity_table(w.nu, w.kappa, w.t_sub)
+        tr.set_star(w.t_star, w.r_star)
+        r = torch.from_numpy(w.rho32()).cuda()
+        t = torch.from_numpy(w.tdust32()).cuda()
+        q, a = torch.empty_like(r), torch.empty_like(r)
+        tr.autotune(r, t, q, a, reps=2)
+        for _ in range(3):
+            tr.irradiate(r, t, q, a)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            tr.irradiate(r, t, q, a)
+        e1.record()
+        torch.cuda.synchronize()
+        v = w.grid.ncells * len(w.nu) / (e0.elapsed_time(e1) / args.steps * 1e-3)
+        row.update(gpu=v, gpu_roofline_frac=v / peak, tuning=list(tr.tuning()))
+        tr.close()
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    print(json.dumps({"mode": "cpu_table", "cores": cores, "ex2_per_sm_clk": ex2_clk, "ffma_per_sm_clk": ffma_clk,
+                      "rows": rows}), flush=True)
 
 
 def run_reference(args, rank, world):
@@ -366,7 +420,7 @@ def run_ours(args, rank, world, local):
         temp = {"ms_per_grid": t_ms, "cells_per_s": ncell / (t_ms * 1e-3),
                 "achieved_gbs": 8.0 * ncell / (t_ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm,
                 "frac_of_hbm": 8.0 * ncell / (t_ms * 1e-3) / 1e9 / hbm,
-                "median_t_k": float(t_out[1].median())}
+                "median_t_k": float(t_out[min(1, len(ws) - 1)].median())}
         del t_out
 
     # the tracer with a temperature-dependent table (24 temperatures) on the tau = 1 grid
@@ -693,6 +747,10 @@ def main():
     if args.precision_sweep:
         if rank == 0:
             run_precision_sweep(args, local)
+        return
+    if args.cpu_table:
+        if rank == 0:
+            run_cpu_table(args, local)
         return
     if args.surrogate:
         if rank == 0:

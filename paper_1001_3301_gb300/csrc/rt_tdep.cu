@@ -9,8 +9,9 @@
 //
 // One warp per ray, lane l owns cells [l C, (l+1) C). Per bin: every cell's kappa
 // from the table (one 8-byte shared-memory read of the bracketing pair), the lane's
-// compensated sum, a compensated warp scan of the lane sums, then a second pass over
-// the lane's cells carrying the exclusive prefix (no per-cell prefix is stored).
+// sum (C terms, plain FP32), a compensated warp scan of the lane sums, then a second
+// pass over the lane's cells carrying the exclusive prefix (no per-cell prefix is
+// stored).
 // The bins are ordered by their largest tabulated kappa; the Taylor classes of the
 // absorbed fraction (1, 2, 3, 5 terms) come from that largest kappa and the warp's
 // largest column, the remaining bins take the per-cell select between the 5-term
@@ -55,17 +56,18 @@ __device__ __forceinline__ void tdep_range(int i0, int i1, const float *s_lf, co
         const float lf = s_lf[i];
         const float2 *row = s_kt + i * n_t;
         float kap[C], dt[C];
-        KahanSum run;
-        run.zero();
+        float lane_sum = 0.0f;  // at most C terms: plain FP32 (error <= C ulp of the lane's share)
 #pragma unroll
         for (int j = 0; j < C; ++j) {
             const float2 kk = row[jt[j]];
             kap[j] = fmaf(wt[j], kk.y - kk.x, kk.x);
             dt[j] = kap[j] * d[j];
-            run.add(dt[j]);
+            lane_sum += dt[j];
         }
-        // compensated warp scan of the lane sums
-        KahanSum inc = run;
+        // compensated warp scan of the lane sums (the ray-long sum)
+        KahanSum inc;
+        inc.zero();
+        inc.add(lane_sum);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const KahanSum v = inc.shfl_up(o);
@@ -74,12 +76,16 @@ __device__ __forceinline__ void tdep_range(int i0, int i1, const float *s_lf, co
         KahanSum pre = inc.shfl_up(1);
         if (lane == 0) pre.zero();
         if (lane == 31) esc += ex2_approx(fmaf(-(float)kLog2e, inc.value(), lf));
+        // the lane's exclusive prefix: the warp offset (hi + lo) plus a plain partial sum
+        const float base_hi = pre.hi, base_lo = pre.lo;
+        float part = 0.0f;
 #pragma unroll
         for (int j = 0; j < C; ++j) {
-            const float g = ex2_approx(fmaf(-(float)kLog2e, pre.value(), lf));
+            const float tau = base_hi + (base_lo + part);
+            const float g = ex2_approx(fmaf(-(float)kLog2e, tau, lf));
             acc[j] = fmaf(g, absorbed<CLASS>(-(float)kLog2e * dt[j]), acc[j]);
             if (any_zero) acc0[j] = fmaf(g, kap[j], acc0[j]);
-            pre.add(dt[j]);
+            part += dt[j];
         }
     }
 }
@@ -250,11 +256,16 @@ const TdepEntry kTdepShapes[] = {RT_TD(2, 4, 8), RT_TD(4, 4, 8), RT_TD(8, 4, 6),
 
 }  // namespace
 
+// The shapes whose rays fill the warp: the fewest cells per lane that hold nr
+// (with each of its register caps); a wider one would leave lanes idle.
 int tdep_shapes(int nr, Shape *out, int max_out)
 {
+    int c_fit = 0;
+    for (const TdepEntry &s : kTdepShapes)
+        if (32 * s.c >= nr && (c_fit == 0 || s.c < c_fit)) c_fit = s.c;
     int n = 0;
     for (const TdepEntry &s : kTdepShapes)
-        if (32 * s.c >= nr && n < max_out) out[n++] = Shape{kKindRay, s.c, s.w, s.minb};
+        if (s.c == c_fit && n < max_out) out[n++] = Shape{kKindRay, s.c, s.w, s.minb};
     return n;
 }
 
