@@ -39,6 +39,13 @@ NR, NTH, NPH, NNU = 256, 128, 256, 79
 def workload_name(taus):
     return (f"disk3d {NR}x{NTH}x{NPH} (r,theta,phi), {NNU} nu bins, tau550 in "
             f"{{{','.join(f'{t:g}' for t in taus)}}}, env+20% lognormal, T_dust U(20,1600)")
+# algorithmic bytes per cell of the flux-limited-diffusion step (each array read or
+# written once per kernel; stencil neighbours from cache): set-up 28 (cell kernel:
+# rho, T, q, E in; F, storage, rhs out) + 36 (faces: 3 in; w[3], s, 1/dg, b out) + 8
+# (start-value copy); per refinement pass 40 (residual: b, s, w[3], 1/dg, x in;
+# r, d, p out) + 12 (accumulate: x, d in; x out); per iteration 24 (apply: p, s,
+# w[3] in; q out) + 28 (update: d, p, q, r, 1/dg in; d, r out) + 16 (direction)
+FLD_SETUP_B, FLD_PASS_B, FLD_ITER_B = 72, 52, 68
 # exp-class operations per (cell, bin) the method cannot avoid: e^{-tau_in}. The
 # absorbed fraction 1 - e^{-dtau} needs a second one only where dtau is not small.
 EXP_PER_CELL_NU = 1
@@ -69,6 +76,7 @@ def parse():
     p.add_argument("--cpu-table", action="store_true",
                    help="instead of the throughput line: oracle (1 core, all cores) and GPU throughput of "
                         "the 2-D disk, the 3-D disk at tau 1 and 100, and the 512x256x512 disk")
+    p.add_argument("--no-fld", action="store_true", help="skip the flux-limited-diffusion leg")
     p.add_argument("--no-surrogate", action="store_true",
                    help="skip the learned-surrogate leg of the default line")
     p.add_argument("--surrogate", action="store_true",
@@ -455,6 +463,46 @@ def run_ours(args, rank, world, local):
         trt.close()
         del qt, at
 
+    # one implicit flux-limited-diffusion step (Eqs. 7-15) on the tau = 1 grid, with
+    # that grid's q_abs as the source; HBM-bound: 96 B per cell for the set-up
+    # kernels and 72 B per cell per conjugate-gradient iteration
+    fld_line = None
+    if rank == 0 and not args.no_fld:
+        i1 = min(1, len(ws) - 1)
+        w1 = ws[i1]
+        tg_, e_, _ = synth.fld_fields(w1.grid, seed=1)
+        t_gas = torch.from_numpy(tg_.astype(np.float32)).cuda()
+        e_old = torch.from_numpy(e_.astype(np.float32)).cuda()
+        e_new = torch.empty_like(e_old)
+        dt_s, c_v, t_bg = 1e10, 1e8, 15.0
+        tr1 = tracers[i1]
+        for _ in range(2):
+            _, fst = tr1.fld_step(rho[i1], t_gas, q[i1], e_old, dt_s, c_v, t_bg, e_new=e_new, tol=1e-5,
+                                  max_iter=20000)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            _, fst = tr1.fld_step(rho[i1], t_gas, q[i1], e_old, dt_s, c_v, t_bg, e_new=e_new, tol=1e-5,
+                                  max_iter=20000)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        f_ms = e0.elapsed_time(e1) / args.steps
+        ncell = w1.grid.ncells
+        nbytes = (FLD_SETUP_B + FLD_PASS_B * fst["passes"] + FLD_ITER_B * fst["iterations"]) * ncell
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm = float(peaks.get("hbm_gbs") or 6678.0)
+        fld_line = {"workload": f"disk3d {NR}x{NTH}x{NPH}, tau550 = {w1.tau550:g}, dt = {dt_s:g} s, "
+                                f"c_v = {c_v:g}, T_bg = {t_bg:g} K, tol = 1e-5",
+                    "ms_per_step": f_ms, "iterations": fst["iterations"], "passes": fst["passes"], "rel_change": fst["rel_change"],
+                    "ms_per_iteration": f_ms / max(1, fst["iterations"]),
+                    "cells_per_s": ncell / (f_ms * 1e-3),
+                    "roofline": {"bound": "hbm", "unit": "GB/s", "achieved": nbytes / (f_ms * 1e-3) / 1e9,
+                                 "peak": hbm, "frac": nbytes / (f_ms * 1e-3) / 1e9 / hbm,
+                                 "bytes_per_cell": f"{FLD_SETUP_B} + {FLD_PASS_B} x {fst['passes']} passes + "
+                                                   f"{FLD_ITER_B} x {fst['iterations']} iterations"}}
+        del t_gas, e_old, e_new
+
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(ws)
@@ -494,6 +542,7 @@ def run_ours(args, rank, world, local):
             "energy_max_rel_err": max_energy_err,
             "dust_temperature": temp,
             "tdep": tdep,
+            "fld": fld_line,
             "surrogate": sur,
         }
         print(json.dumps(line), flush=True)

@@ -318,6 +318,54 @@ int rt_planck_mean_opacity(rt_ctx *ctx, double t, double *kappa_p);
 int rt_dust_temperature(rt_ctx *ctx, const float *a_rad, const float *e_rad, float *t_dust);
 
 /* ------------------------------------------------------------------------
+ * Flux-limited diffusion of the re-emitted radiation (Sect. 2.1, Eqs. 7-15).
+ * ------------------------------------------------------------------------ */
+
+/* rt_rosseland_mean_opacity -- kappa_R(T) with 1/kappa_R = sum_i w_i / kappa_i /
+ * sum_i w_i, w_i the integral of dB_nu/dT over bin i (the bin edges of Eq. 20), at
+ * temperature t (K, > 0), in FP64 on the device; 0 if a bin with weight has
+ * kappa_i = 0. The opacity of Eqs. 10-13. Synchronises the context's stream. */
+int rt_rosseland_mean_opacity(rt_ctx *ctx, double t, double *kappa_r);
+
+typedef struct rt_fld_stats {
+    int iterations;      /* conjugate-gradient iterations taken, all passes */
+    int passes;          /* refinement passes */
+    double rel_change;   /* max over cells of |correction| / |E'| of the last pass */
+} rt_fld_stats;
+
+/* rt_fld_step -- one backward-Euler step of Eqs. 8-15,
+ *     (E' - E) / dt = f_c (div(D grad E') + q_abs),
+ *     f_c = 1 / (c_v rho / (4 a T^3) + 1),                                (Eq. 9)
+ *     D = lambda c / (kappa_R rho), lambda = (2 + R) / (6 + 3 R + R^2),
+ *     R = |grad E| / (kappa_R rho E),                                      (Eqs. 10-13)
+ * with D, f_c and kappa_R(T) taken at the old state (kappa_R of the context's
+ * table, on 1 K .. 1e5 K, held constant outside) and D = c (2 s + g) /
+ * (6 s^2 + 3 s g + g^2), s = kappa_R rho, g = |grad E| / E, so that D stays finite
+ * as rho -> 0 (D = 0 where s = g = 0).
+ *   rho, t_gas  device [nphi][ntheta][nr] FP32: density (g cm^-3, >= 0) and gas =
+ *               dust temperature (K, > 0);
+ *   q_abs       device, same layout: the absorbed stellar power per volume
+ *               (erg s^-1 cm^-3, >= 0; the rt_irradiate output), the source of Eq. 15;
+ *   e_old       device, same layout: E_R at the start of the step (erg cm^-3, >= 0);
+ *   e_new       device, same layout, caller-allocated, not aliasing e_old: E_R after it;
+ *   dt (s) > 0 (1e300 gives the steady state), c_v (erg g^-1 K^-1) >= 0,
+ *   t_bg (K) >= 0: E = a t_bg^4 half a cell beyond the outer radius;
+ *   tol > 0, max_iter >= 1: mixed-precision iterative refinement (true residual in
+ *   FP32, Jacobi-preconditioned conjugate gradients for each correction, FP64
+ *   reductions) from E' = E_old until a pass changes no cell by more than tol
+ *   relative, or max_iter conjugate-gradient iterations in total.
+ *   stats       NULL or a host struct for the iteration count and final residual.
+ * Finite volumes: harmonic-mean face coefficients, no flux through the inner radius
+ * or the theta ends, periodic in phi when nphi > 1 (the wrap distance measured
+ * around the full circle). Synchronises the stream every 16 iterations. Errors:
+ * RT_ERR_NOT_CONFIGURED, RT_ERR_INVALID_ARG, RT_ERR_NONFINITE_INPUT (rho < 0,
+ * T <= 0, E_old < 0, q_abs < 0 or NaN/Inf; e_new is then unchanged),
+ * RT_ERR_TIMEOUT (tol not reached in max_iter; e_new holds the last iterate),
+ * RT_ERR_NO_MEMORY, RT_ERR_CUDA. */
+int rt_fld_step(rt_ctx *ctx, const float *rho, const float *t_gas, const float *q_abs, const float *e_old,
+                float *e_new, double dt, double c_v, double t_bg, double tol, int max_iter, rt_fld_stats *stats);
+
+/* ------------------------------------------------------------------------
  * Learned surrogate of the per-bin sum of one cell.
  *
  * Along a ray the tracer gives a cell with dust column N_in in front of it and

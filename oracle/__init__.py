@@ -49,6 +49,8 @@ def _configure(lib):
     lib.rto_irradiate_tdep.argtypes = ([ctypes.c_int] * 3 + [_D] * 3 + [ctypes.c_double] * 2 +
                                        [ctypes.c_int, _D, ctypes.c_int, _D, _D, ctypes.c_double] + [_D] * 8 +
                                        [ctypes.c_int])
+    lib.rto_rosseland_mean.restype = ctypes.c_double
+    lib.rto_rosseland_mean.argtypes = [ctypes.c_double, ctypes.c_int, _D, _D]
     lib.rto_planck_mean.restype = ctypes.c_double
     lib.rto_planck_mean.argtypes = [ctypes.c_double, ctypes.c_int, _D, _D]
     lib.rto_dust_temperature.restype = ctypes.c_int
@@ -124,6 +126,15 @@ def planck_mean(t: float, nu_mid, kappa) -> float:
     v = _load().rto_planck_mean(float(t), len(nu), _ptr(nu), _ptr(k))
     if v < 0:
         raise ValueError("rto_planck_mean: bad argument")
+    return v
+
+
+def rosseland_mean(t: float, nu_mid, kappa) -> float:
+    """kappa_R(T) of a bin table: sum W_i / sum (W_i / kappa_i), W_i = int dB/dT over bin i."""
+    nu, k = _f64(nu_mid), _f64(kappa)
+    v = _load().rto_rosseland_mean(float(t), len(nu), _ptr(nu), _ptr(k))
+    if v < 0:
+        raise ValueError("rto_rosseland_mean: bad argument")
     return v
 
 

@@ -147,6 +147,35 @@ double rto_planck_mean(double t, int n_nu, const double *nu_mid, const double *k
     return den > 0.0 ? num / den : 0.0;
 }
 
+/* Rosseland mean opacity of a bin table at temperature t (the kappa_R of the FLD
+ * diffusion constant, Eq. 11): 1/kappa_R = sum_i W_i / kappa_i / sum_i W_i with
+ * W_i = int over bin i of dB_nu/dT dnu. In x = h nu / (k T) the weight is
+ * int t^4 e^t / (e^t - 1)^2 dt, and by parts (d/dt of 1/(e^t - 1) is
+ * -e^t/(e^t - 1)^2) over [a, b]:
+ *     a^4/(e^a - 1) - b^4/(e^b - 1) + 4 int_a^b t^3/(e^t - 1) dt.
+ * A bin with kappa = 0 and weight > 0 makes the mean 0. Returns < 0 on a bad
+ * argument. */
+double rto_rosseland_mean(double t, int n_nu, const double *nu_mid, const double *kappa)
+{
+    if (!(t > 0.0) || n_nu < 1) return -1.0;
+    const double kt_over_h = RTO_K * t / RTO_H;
+    double num = 0.0, den = 0.0;
+    int opaque_gap = 0;
+    for (int i = 0; i < n_nu; ++i) {
+        double lo = (i == 0) ? 0.0 : 0.5 * (nu_mid[i - 1] + nu_mid[i]);
+        double hi = (i == n_nu - 1) ? INFINITY : 0.5 * (nu_mid[i] + nu_mid[i + 1]);
+        const double a = lo / kt_over_h, b = isinf(hi) ? INFINITY : hi / kt_over_h;
+        const double ea = (a > 0.0) ? pow(a, 4) / expm1(a) : 0.0;
+        const double eb = (isinf(b) || b > 700.0) ? 0.0 : pow(b, 4) / expm1(b);
+        const double w = ea - eb + 4.0 * rto_planck_band(a, b);
+        den += w;
+        if (kappa[i] > 0.0) num += w / kappa[i];
+        else if (w > 0.0) opaque_gap = 1;
+    }
+    if (opaque_gap || !(num > 0.0)) return 0.0;
+    return den / num;
+}
+
 /* Eq. 16 with frequency-dependent fluxes, per cell: the dust temperature T with
  *     a T^4 = E_R + a_rad / kappa_P(T),   a = 4 sigma / c,
  * (sum_i kappa_i F_i over the cell is q_abs / rho = c a_rad). kappa_P is evaluated

@@ -66,6 +66,10 @@ class RtSurrogateStats(ctypes.Structure):
                 ("e_esc", ctypes.c_double), ("rel_err", ctypes.c_double)]
 
 
+class RtFldStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("passes", ctypes.c_int), ("rel_change", ctypes.c_double)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.c_double
@@ -104,6 +108,8 @@ SIGNATURES = {
     "rt_probe_alu_rates": (_I, [_DP, _DP, _DP]),
     "rt_planck_mean_opacity": (_I, [_P, _D, _DP]),
     "rt_dust_temperature": (_I, [_P, _P, _P, _P]),
+    "rt_rosseland_mean_opacity": (_I, [_P, _D, _DP]),
+    "rt_fld_step": (_I, [_P, _P, _P, _P, _P, _P, _D, _D, _D, _D, _I, _P]),
     "rt_surrogate_train": (_I, [_P, ctypes.POINTER(RtTrainCfg), ctypes.POINTER(_P), ctypes.POINTER(_P), _I,
                                 ctypes.POINTER(RtTrainStats)]),
     "rt_irradiate_surrogate": (_I, [_P, _P, _P, _P, _P, ctypes.c_float, _I, ctypes.POINTER(RtSurrogateStats)]),

@@ -25,8 +25,9 @@ struct rt_ctx {
     long long nrays = 0, ncells = 0, L = 0;
     cudaStream_t stream = nullptr;
 
-    // geometry (device)
+    // geometry (device, and host copies of the axes)
     double *r_if = nullptr, *theta_if = nullptr, *phi_if = nullptr;
+    std::vector<double> r_if_h, theta_if_h, phi_if_h;
     float4 *rtab = nullptr;
     RadRow64 *rtab64 = nullptr;
     double *domega = nullptr;
@@ -65,6 +66,8 @@ struct rt_ctx {
     // Planck-mean table of the dust-temperature update (rt_temperature.cu)
     float *temp_lkp = nullptr;
     unsigned long long temp_fp = 0;
+    // workspace of the flux-limited-diffusion step (rt_fld.cu)
+    rt::FldState *fld = nullptr;
 
     // configuration state
     int n_nu = 0, kappa_bf16 = 0;
@@ -398,6 +401,11 @@ bool ctx_info(const rt_ctx *c, CtxInfo *o)
     o->stream = c->stream;
     o->configured = c->configured;
     o->nr = c->nr;
+    o->ntheta = c->ntheta;
+    o->nphi = c->nphi;
+    o->r_if_h = c->r_if_h.data();
+    o->theta_if_h = c->theta_if_h.data();
+    o->phi_if_h = c->phi_if_h.data();
     o->nrays = c->nrays;
     o->ncells = c->ncells;
     o->t_sub = c->t_sub;
@@ -421,6 +429,7 @@ bool ctx_info(const rt_ctx *c, CtxInfo *o)
 SurState *&ctx_surrogate(rt_ctx *c) { return c->sur; }
 float *&ctx_temp_table(rt_ctx *c) { return c->temp_lkp; }
 unsigned long long &ctx_temp_fingerprint(rt_ctx *c) { return c->temp_fp; }
+FldState *&ctx_fld(rt_ctx *c) { return c->fld; }
 
 int ctx_fail(rt_ctx *c, int status, const std::string &msg) { return fail(c, status, msg); }
 }  // namespace rt
@@ -452,6 +461,9 @@ int rt_create(const rt_grid_desc *g, void *cuda_stream, rt_ctx **out)
     c->nr = g->nr;
     c->ntheta = g->ntheta;
     c->nphi = g->nphi;
+    c->r_if_h.assign(g->r_if, g->r_if + g->nr + 1);
+    c->theta_if_h.assign(g->theta_if, g->theta_if + g->ntheta + 1);
+    c->phi_if_h.assign(g->phi_if, g->phi_if + g->nphi + 1);
     c->precision = g->precision;
     c->nrays = nrays;
     c->ncells = ncells;
@@ -791,6 +803,7 @@ void rt_destroy(rt_ctx *ctx)
     cudaSetDevice(ctx->dev);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->sur) rt::sur_free(ctx->sur);
+    if (ctx->fld) rt::fld_free(ctx->fld);
     if (ctx->s_in) {
         cudaStreamSynchronize(ctx->s_in);
         cudaStreamSynchronize(ctx->s_out);

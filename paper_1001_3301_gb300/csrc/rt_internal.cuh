@@ -151,7 +151,8 @@ struct CtxInfo {
     int dev;
     cudaStream_t stream;
     bool configured;
-    int nr;
+    int nr, ntheta, nphi;
+    const double *r_if_h, *theta_if_h, *phi_if_h;  // host copies of the cell interfaces
     long long nrays, ncells;
     double t_sub, t_star, r_star;
     int n_nu;
@@ -175,6 +176,10 @@ SurState *&ctx_surrogate(rt_ctx *c);   // owned by the context, freed by rt_dest
 float *&ctx_temp_table(rt_ctx *c);
 unsigned long long &ctx_temp_fingerprint(rt_ctx *c);
 void sur_free(SurState *s);
+// workspace of the flux-limited-diffusion step (rt_fld.cu), owned by the context
+struct FldState;
+FldState *&ctx_fld(rt_ctx *c);
+void fld_free(FldState *s);
 int ctx_fail(rt_ctx *c, int status, const std::string &msg);
 
 // Set-up kernels (rt_setup.cu)

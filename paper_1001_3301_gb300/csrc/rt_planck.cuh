@@ -44,5 +44,26 @@ __device__ double planck_band_warp(double a, double b, int lane)
     return s;
 }
 
+// Rosseland weight of the band [a, b]: int t^4 e^t / (e^t - 1)^2 dt, by parts
+// a^4/(e^a - 1) - b^4/(e^b - 1) + 4 int_a^b t^3/(e^t - 1) dt (result in every lane).
+__device__ double rosseland_band_warp(double a, double b, int lane)
+{
+    if (a > 700.0) return 0.0;
+    const double ea = a > 0.0 ? a * a * a * a / expm1(a) : 0.0;
+    const double eb = (isinf(b) || b > 700.0) ? 0.0 : b * b * b * b / expm1(b);
+    return ea - eb + 4.0 * planck_band_warp(a, b, lane);
+}
+
+// kappa of bin row `row` at temperature t: linear between the bracketing points of
+// t_grid, the end values beyond (n_t <= 1: the one value)
+__device__ double kappa_at(const double *row, int n_t, const double *t_grid, double t)
+{
+    if (n_t <= 1 || t <= t_grid[0]) return row[0];
+    if (t >= t_grid[n_t - 1]) return row[n_t - 1];
+    int j = 0;
+    while (!(t < t_grid[j + 1])) ++j;
+    return row[j] + (row[j + 1] - row[j]) * ((t - t_grid[j]) / (t_grid[j + 1] - t_grid[j]));
+}
+
 }  // namespace
 }  // namespace rt

@@ -31,17 +31,6 @@ namespace {
 
 // Planck mean of the table at temperature exp(y[n]); one warp per node, the bins'
 // band integrals in FP64. kp_out[n] = kappa_P (double) and lkp[n] = ln kappa_P.
-// kappa of bin row `row` at temperature t: linear between the bracketing points of
-// t_grid, the end values beyond (n_t == 1: constant)
-__device__ double kappa_at(const double *row, int n_t, const double *t_grid, double t)
-{
-    if (n_t <= 1 || t <= t_grid[0]) return row[0];
-    if (t >= t_grid[n_t - 1]) return row[n_t - 1];
-    int j = 0;
-    while (!(t < t_grid[j + 1])) ++j;
-    return row[j] + (row[j + 1] - row[j]) * ((t - t_grid[j]) / (t_grid[j + 1] - t_grid[j]));
-}
-
 __global__ void k_planck_mean(int n_nodes, const double *t_nodes, int n_nu, const double *nu_mid,
                               const double *kappa, int n_t, const double *t_grid, double *kp_out, float *lkp)
 {

@@ -12,7 +12,7 @@ import os
 import numpy as np
 
 from . import _lib
-from ._lib import (RT_SUR_NPARAMS, RtEnergy, RtGridDesc, RtSurrogateStats, RtTrainCfg, RtTrainStats, check,
+from ._lib import (RT_SUR_NPARAMS, RtEnergy, RtFldStats, RtGridDesc, RtSurrogateStats, RtTrainCfg, RtTrainStats, check,
                    lib)
 
 
@@ -179,6 +179,28 @@ class Tracer:
         check(lib.rt_dust_temperature(self._ctx, a_rad.data_ptr(), None if e_rad is None else e_rad.data_ptr(),
                                       t_dust.data_ptr()), self._ctx)
         return t_dust
+
+    # -- flux-limited diffusion (Eqs. 7-15) ----------------------------------------
+    def rosseland_mean_opacity(self, t: float) -> float:
+        """kappa_R(T) of the configured table (cm^2/g)."""
+        k = ctypes.c_double()
+        check(lib.rt_rosseland_mean_opacity(self._ctx, float(t), ctypes.byref(k)), self._ctx)
+        return k.value
+
+    def fld_step(self, rho, t_gas, q_abs, e_old, dt, c_v, t_bg, e_new=None, tol=1e-5, max_iter=20000):
+        """One implicit flux-limited-diffusion step of E_R (CUDA tensors of this grid);
+        returns (e_new, {"iterations", "passes", "rel_change"})."""
+        import torch
+        for f, name in ((rho, "rho"), (t_gas, "t_gas"), (q_abs, "q_abs"), (e_old, "e_old")):
+            self._check_field(f, name)
+        if e_new is None:
+            e_new = torch.empty(self.shape, dtype=torch.float32, device=e_old.device)
+        self._check_field(e_new, "e_new")
+        st = RtFldStats()
+        check(lib.rt_fld_step(self._ctx, rho.data_ptr(), t_gas.data_ptr(), q_abs.data_ptr(), e_old.data_ptr(),
+                              e_new.data_ptr(), float(dt), float(c_v), float(t_bg), float(tol), int(max_iter),
+                              ctypes.byref(st)), self._ctx)
+        return e_new, {"iterations": st.iterations, "passes": st.passes, "rel_change": st.rel_change}
 
     # -- learned surrogate (rt_surrogate_*) -------------------------------------
     def surrogate_train(self, rho_list, t_list, n_samples=0, batch=0, steps=0, lr=0.0, seed=1):

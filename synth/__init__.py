@@ -234,6 +234,23 @@ def tdust_random(grid: Grid, t_lo: float, t_hi: float, seed: int) -> np.ndarray:
     return (t_lo + (t_hi - t_lo) * u).reshape(grid.shape)
 
 
+def fld_fields(grid: Grid, seed: int = 1, t_in: float = 300.0, e_in: float = 1e-5, q_in: float = 1e-12):
+    """Old state of a radiation-diffusion step on ``grid`` [nphi][ntheta][nr] (float64):
+    gas temperature t_in (r/r_in)^-1/2 x lognormal(0.1), clipped to 10..1500 K;
+    radiation energy density e_in (r/r_in)^-2 x lognormal(0.3) (erg cm^-3);
+    source q_in (r/r_in)^-5/2 x U(0, 1) (erg s^-1 cm^-3)."""
+    r_c, _ = grid.centres()
+    x = np.broadcast_to(r_c / grid.r_if[0], grid.shape)
+    idx = np.arange(grid.ncells, dtype=np.uint64)
+    g1 = hash_normal(seed, 30, idx).reshape(grid.shape)
+    g2 = hash_normal(seed, 31, idx).reshape(grid.shape)
+    u = hash_u01(seed, 32, idx).reshape(grid.shape)
+    t = np.clip(t_in * x ** -0.5 * np.exp(0.1 * g1), 10.0, 1500.0)
+    e = e_in * x ** -2.0 * np.exp(0.3 * g2)
+    q = q_in * x ** -2.5 * u
+    return t, e, q
+
+
 def gas_mass(grid: Grid, rho: np.ndarray) -> float:
     """Total mass (g) of a cell-centred density field on a spherical grid."""
     dv_r = (grid.r_if[1:] ** 3 - grid.r_if[:-1] ** 3) / 3.0
