@@ -474,7 +474,7 @@ def run_ours(args, rank, world, local):
         t_gas = torch.from_numpy(tg_.astype(np.float32)).cuda()
         e_old = torch.from_numpy(e_.astype(np.float32)).cuda()
         e_new = torch.empty_like(e_old)
-        dt_s, c_v, t_bg = 1e10, 1e8, 15.0
+        dt_s, c_v, t_bg = 1e4, 1e8, 14.7   # the paper's FLD time step and outer boundary (Sect. 3.1.2)
         tr1 = tracers[i1]
         for _ in range(2):
             _, fst = tr1.fld_step(rho[i1], t_gas, q[i1], e_old, dt_s, c_v, t_bg, e_new=e_new, tol=1e-5,

@@ -453,6 +453,134 @@ __global__ void __launch_bounds__(256) k_cg_accumulate(const CgArgs a)
     if (grid_reduce<true>(a, (double)m, &tot)) a.scal[kCorr] = tot;
 }
 
+// --- the same kernels on four consecutive cells per thread (nr % 4 == 0: the four
+// cells share (j, l), every array offset is a multiple of 16 bytes) -----------------
+#define FLD_QUADS(c)                                                                          \
+    for (unsigned c = 4u * (blockIdx.x * blockDim.x + threadIdx.x); c < (unsigned)a.n;         \
+         c += 4u * gridDim.x * blockDim.x)
+
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+
+// A v on cells c .. c+3 of one ray
+__device__ __forceinline__ float4 apply_flux4(const CgArgs &a, const float *v, unsigned c)
+{
+    int k, j, l;
+    cell_ijk(c, a.nr, a.nth, a.div_nr, a.div_nth, k, j, l);
+    const unsigned n = (unsigned)a.n, plane = (unsigned)a.nr * (unsigned)a.nth;
+    const float4 vc = ld4(v + c), s = ld4(a.s + c), wr = ld4(a.w + c);
+    float4 acc = make_float4(s.x * vc.x, s.y * vc.y, s.z * vc.z, s.w * vc.w);
+    // radial faces: inside the quad, and to c-1 / c+4
+    acc.x = fmaf(wr.x, vc.x - vc.y, acc.x);
+    acc.y = fmaf(wr.y, vc.y - vc.z, acc.y);
+    acc.z = fmaf(wr.z, vc.z - vc.w, acc.z);
+    acc.y = fmaf(wr.x, vc.y - vc.x, acc.y);
+    acc.z = fmaf(wr.y, vc.z - vc.y, acc.z);
+    acc.w = fmaf(wr.z, vc.w - vc.z, acc.w);
+    if (k + 4 < a.nr) acc.w = fmaf(wr.w, vc.w - v[c + 4], acc.w);
+    if (k > 0) acc.x = fmaf(a.w[c - 1], vc.x - v[c - 1], acc.x);
+    auto face4 = [&](float4 w, float4 u) {
+        acc.x = fmaf(w.x, vc.x - u.x, acc.x);
+        acc.y = fmaf(w.y, vc.y - u.y, acc.y);
+        acc.z = fmaf(w.z, vc.z - u.z, acc.z);
+        acc.w = fmaf(w.w, vc.w - u.w, acc.w);
+    };
+    if (j + 1 < a.nth) face4(ld4(a.w + n + c), ld4(v + c + a.nr));
+    if (j > 0) face4(ld4(a.w + n + c - a.nr), ld4(v + c - a.nr));
+    if (a.nph > 1) {
+        const unsigned cb = l + 1 < a.nph ? c + plane : c - (unsigned)l * plane;
+        const unsigned ca = l > 0 ? c - plane : c + (unsigned)(a.nph - 1) * plane;
+        face4(ld4(a.w + 2 * n + c), ld4(v + cb));
+        face4(ld4(a.w + 2 * n + ca), ld4(v + ca));
+    }
+    return acc;
+}
+
+__global__ void __launch_bounds__(256) k_cg_residual4(const CgArgs a)
+{
+    KSum rz;
+    FLD_QUADS(c)
+    {
+        const float4 ax = apply_flux4(a, a.x, c), b = ld4(a.b + c), idg = ld4(a.idg + c);
+        const float4 r = make_float4(b.x - ax.x, b.y - ax.y, b.z - ax.z, b.w - ax.w);
+        const float4 z = make_float4(r.x * idg.x, r.y * idg.y, r.z * idg.z, r.w * idg.w);
+        st4(a.r + c, r);
+        st4(a.d + c, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+        st4(a.p + c, z);
+        rz.add(r.x * z.x);
+        rz.add(r.y * z.y);
+        rz.add(r.z * z.z);
+        rz.add(r.w * z.w);
+    }
+    double tot;
+    if (grid_reduce<false>(a, rz.value(), &tot)) {
+        a.scal[kRz] = tot;
+        a.scal[kRz0] = tot;
+        a.scal[kDone] = tot > 0.0 ? 0.0 : 1.0;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_cg_apply4(const CgArgs a)
+{
+    if (a.scal[kDone] != 0.0) return;
+    KSum pq;
+    FLD_QUADS(c)
+    {
+        const float4 q = apply_flux4(a, a.p, c), p = ld4(a.p + c);
+        st4(a.q + c, q);
+        pq.add(p.x * q.x);
+        pq.add(p.y * q.y);
+        pq.add(p.z * q.z);
+        pq.add(p.w * q.w);
+    }
+    double tot;
+    if (grid_reduce<false>(a, pq.value(), &tot)) {
+        a.scal[kAlpha] = tot > 0.0 ? a.scal[kRz] / tot : 0.0;
+        if (!(tot > 0.0)) a.scal[kDone] = 1.0;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_cg_update4(const CgArgs a)
+{
+    if (a.scal[kDone] != 0.0) return;
+    const float alpha = (float)a.scal[kAlpha];
+    KSum rz;
+    FLD_QUADS(c)
+    {
+        const float4 p = ld4(a.p + c), q = ld4(a.q + c), idg = ld4(a.idg + c);
+        float4 d = ld4(a.d + c), r = ld4(a.r + c);
+        d = make_float4(fmaf(alpha, p.x, d.x), fmaf(alpha, p.y, d.y), fmaf(alpha, p.z, d.z), fmaf(alpha, p.w, d.w));
+        r = make_float4(fmaf(-alpha, q.x, r.x), fmaf(-alpha, q.y, r.y), fmaf(-alpha, q.z, r.z),
+                        fmaf(-alpha, q.w, r.w));
+        st4(a.d + c, d);
+        st4(a.r + c, r);
+        rz.add(r.x * (r.x * idg.x));
+        rz.add(r.y * (r.y * idg.y));
+        rz.add(r.z * (r.z * idg.z));
+        rz.add(r.w * (r.w * idg.w));
+    }
+    double tot;
+    if (grid_reduce<false>(a, rz.value(), &tot)) {
+        a.scal[kBeta] = a.scal[kRz] > 0.0 ? tot / a.scal[kRz] : 0.0;
+        a.scal[kRz] = tot;
+        a.scal[kIters] += 1.0;
+        if (!(tot > kInnerDrop * kInnerDrop * a.scal[kRz0])) a.scal[kDone] = 1.0;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_cg_direction4(const CgArgs a)
+{
+    if (a.scal[kDone] != 0.0) return;
+    const float beta = (float)a.scal[kBeta];
+    FLD_QUADS(c)
+    {
+        const float4 r = ld4(a.r + c), idg = ld4(a.idg + c), p = ld4(a.p + c);
+        st4(a.p + c, make_float4(fmaf(beta, p.x, r.x * idg.x), fmaf(beta, p.y, r.y * idg.y),
+                                 fmaf(beta, p.z, r.z * idg.z), fmaf(beta, p.w, r.w * idg.w)));
+    }
+}
+
+#undef FLD_QUADS
 #undef FLD_CELLS
 
 int rosseland_nodes(const CtxInfo &in, const std::vector<double> &t_nodes, double *kr_host, float *lkr_dev,
@@ -617,15 +745,16 @@ int rt_fld_step(rt_ctx *ctx, const float *rho, const float *t_gas, const float *
         }
         fs->cap = n;
     }
-    if (fs->part_cap < grid) {
+    const int grid_max = 8 * nsm;  // 256-thread CTAs resident per SM are at most 8
+    if (fs->part_cap < grid_max) {
         cudaFree(fs->part);
         fs->part = nullptr;
         fs->part_cap = 0;
-        if (cudaMalloc(&fs->part, sizeof(double) * grid) != cudaSuccess) {
+        if (cudaMalloc(&fs->part, sizeof(double) * grid_max) != cudaSuccess) {
             cudaGetLastError();
             return ctx_fail(ctx, RT_ERR_NO_MEMORY, "FLD partials");
         }
-        fs->part_cap = grid;
+        fs->part_cap = grid_max;
     }
     if (!fs->scal) {
         if (cudaMalloc(&fs->scal, sizeof(double) * kNScal) != cudaSuccess ||
@@ -746,22 +875,45 @@ int rt_fld_step(rt_ctx *ctx, const float *rho, const float *t_gas, const float *
     int iters = 0, passes = 0;
     double corr = INFINITY;
     bool done = false;
+    // four cells per thread where a ray holds a multiple of four cells
+    const bool quads = nr % 4 == 0;
+    // grids of one full wave: the CTAs resident per SM (from each kernel's registers)
+    // times the SM count, capped by the work
+    auto wave = [&](const void *kern) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        const long long work = ((quads ? n / 4 : n) + 255) / 256;
+        return (int)std::max(1LL, std::min<long long>(work, (long long)per_sm * nsm));
+    };
+    const int g_res = quads ? wave((const void *)k_cg_residual4) : wave((const void *)k_cg_residual);
+    const int g_app = quads ? wave((const void *)k_cg_apply4) : wave((const void *)k_cg_apply);
+    const int g_upd = quads ? wave((const void *)k_cg_update4) : wave((const void *)k_cg_update);
+    const int g_dir = quads ? wave((const void *)k_cg_direction4) : wave((const void *)k_cg_direction);
+    const int g_acc = wave((const void *)k_cg_accumulate);
     while (!done) {
-        k_cg_residual<<<grid, 256, 0, st>>>(cg);
+        if (quads) k_cg_residual4<<<g_res, 256, 0, st>>>(cg);
+        else k_cg_residual<<<g_res, 256, 0, st>>>(cg);
         bool inner_done = false;
         while (!inner_done && iters < max_iter) {
             const int burst = std::min(kBurst, max_iter - iters);
             for (int i = 0; i < burst; ++i) {
-                k_cg_apply<<<grid, 256, 0, st>>>(cg);
-                k_cg_update<<<grid, 256, 0, st>>>(cg);
-                k_cg_direction<<<grid, 256, 0, st>>>(cg);
+                if (quads) {
+                    k_cg_apply4<<<g_app, 256, 0, st>>>(cg);
+                    k_cg_update4<<<g_upd, 256, 0, st>>>(cg);
+                    k_cg_direction4<<<g_dir, 256, 0, st>>>(cg);
+                } else {
+                    k_cg_apply<<<g_app, 256, 0, st>>>(cg);
+                    k_cg_update<<<g_upd, 256, 0, st>>>(cg);
+                    k_cg_direction<<<g_dir, 256, 0, st>>>(cg);
+                }
             }
             if (!sync_read(h_sc, nullptr))
                 return ctx_fail(ctx, RT_ERR_CUDA, std::string("FLD iteration: ") + cudaGetErrorString(cudaGetLastError()));
             iters = (int)h_sc[kIters];
             inner_done = h_sc[kDone] != 0.0;
         }
-        k_cg_accumulate<<<grid, 256, 0, st>>>(cg);
+        k_cg_accumulate<<<g_acc, 256, 0, st>>>(cg);
         if (!sync_read(h_sc, nullptr))
             return ctx_fail(ctx, RT_ERR_CUDA, std::string("FLD refinement: ") + cudaGetErrorString(cudaGetLastError()));
         ++passes;

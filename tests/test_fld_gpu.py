@@ -97,6 +97,7 @@ def _step_pair(torch, g, nu, kappa, rho, t, q, e0, dt, c_v, t_bg, t_grid=None):
 
 CASES = [
     # (nr, ntheta, nphi), dt (s): storage-dominated, mixed, steady state
+    ((20, 12, 8), 1e4),     # the paper's FLD time step
     ((20, 12, 8), 1e6),
     ((20, 12, 8), 1e10),
     ((20, 12, 8), 1e300),
