@@ -40,12 +40,18 @@ def workload_name(taus):
     return (f"disk3d {NR}x{NTH}x{NPH} (r,theta,phi), {NNU} nu bins, tau550 in "
             f"{{{','.join(f'{t:g}' for t in taus)}}}, env+20% lognormal, T_dust U(20,1600)")
 # algorithmic bytes per cell of the flux-limited-diffusion step (each array read or
-# written once per kernel; stencil neighbours from cache): set-up 28 (cell kernel:
+# written once per kernel; stencil neighbours from cache). Set-up: 28 (cell kernel:
 # rho, T, q, E in; F, storage, rhs out) + 36 (faces: 3 in; w[3], s, 1/dg, b out) + 8
-# (start-value copy); per refinement pass 40 (residual: b, s, w[3], 1/dg, x in;
-# r, d, p out) + 12 (accumulate: x, d in; x out); per iteration 24 (apply: p, s,
-# w[3] in; q out) + 28 (update: d, p, q, r, 1/dg in; d, r out) + 16 (direction)
+# (start-value copy) + 16 (Galerkin coarsening reads s, w[3]; the coarse levels are
+# 1/8, 1/64, ... of that). Jacobi iteration: 24 (apply: p, s, w[3] in; q out) + 28
+# (update: d, p, q, r, 1/dg in; d, r out) + 16 (direction); per pass 40 (residual) +
+# 12 (accumulate). Multigrid iteration: 24 (apply) + 24 (update: d, p, q, r in; d, r
+# out) + 12 (direction: z, p in; p out) + 24 (restriction: b, 1/dg, s, w[3] in) + 28
+# (prolongation: the same in, z out) + 8 (the coarser levels, 1/7 of the last two);
+# per pass 36 (residual: b, s, w[3], x in; r, d, p out) + 64 (one V-cycle and the
+# direction) + 12 (accumulate)
 FLD_SETUP_B, FLD_PASS_B, FLD_ITER_B = 72, 52, 68
+FLD_SETUP_MG_B, FLD_PASS_MG_B, FLD_ITER_MG_B = 88, 112, 120
 # exp-class operations per (cell, bin) the method cannot avoid: e^{-tau_in}. The
 # absorbed fraction 1 - e^{-dtau} needs a second one only where dtau is not small.
 EXP_PER_CELL_NU = 1
@@ -77,6 +83,11 @@ def parse():
                    help="instead of the throughput line: oracle (1 core, all cores) and GPU throughput of "
                         "the 2-D disk, the 3-D disk at tau 1 and 100, and the 512x256x512 disk")
     p.add_argument("--no-fld", action="store_true", help="skip the flux-limited-diffusion leg")
+    p.add_argument("--fld", action="store_true",
+                   help="print only the flux-limited-diffusion leg (trace the tau = 1 disk of --fld-grid, then "
+                        "time --steps FLD steps with its q_abs)")
+    p.add_argument("--fld-grid", default="256x128x256")
+    p.add_argument("--fld-dt", type=float, default=1e4, help="FLD time step (s); the paper's is 1e4")
     p.add_argument("--no-surrogate", action="store_true",
                    help="skip the learned-surrogate leg of the default line")
     p.add_argument("--surrogate", action="store_true",
@@ -464,44 +475,11 @@ def run_ours(args, rank, world, local):
         del qt, at
 
     # one implicit flux-limited-diffusion step (Eqs. 7-15) on the tau = 1 grid, with
-    # that grid's q_abs as the source; HBM-bound: 96 B per cell for the set-up
-    # kernels and 72 B per cell per conjugate-gradient iteration
+    # that grid's q_abs as the source
     fld_line = None
     if rank == 0 and not args.no_fld:
         i1 = min(1, len(ws) - 1)
-        w1 = ws[i1]
-        tg_, e_, _ = synth.fld_fields(w1.grid, seed=1)
-        t_gas = torch.from_numpy(tg_.astype(np.float32)).cuda()
-        e_old = torch.from_numpy(e_.astype(np.float32)).cuda()
-        e_new = torch.empty_like(e_old)
-        dt_s, c_v, t_bg = 1e4, 1e8, 14.7   # the paper's FLD time step and outer boundary (Sect. 3.1.2)
-        tr1 = tracers[i1]
-        for _ in range(2):
-            _, fst = tr1.fld_step(rho[i1], t_gas, q[i1], e_old, dt_s, c_v, t_bg, e_new=e_new, tol=1e-5,
-                                  max_iter=20000)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            _, fst = tr1.fld_step(rho[i1], t_gas, q[i1], e_old, dt_s, c_v, t_bg, e_new=e_new, tol=1e-5,
-                                  max_iter=20000)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        f_ms = e0.elapsed_time(e1) / args.steps
-        ncell = w1.grid.ncells
-        nbytes = (FLD_SETUP_B + FLD_PASS_B * fst["passes"] + FLD_ITER_B * fst["iterations"]) * ncell
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        hbm = float(peaks.get("hbm_gbs") or 6678.0)
-        fld_line = {"workload": f"disk3d {NR}x{NTH}x{NPH}, tau550 = {w1.tau550:g}, dt = {dt_s:g} s, "
-                                f"c_v = {c_v:g}, T_bg = {t_bg:g} K, tol = 1e-5",
-                    "ms_per_step": f_ms, "iterations": fst["iterations"], "passes": fst["passes"], "rel_change": fst["rel_change"],
-                    "ms_per_iteration": f_ms / max(1, fst["iterations"]),
-                    "cells_per_s": ncell / (f_ms * 1e-3),
-                    "roofline": {"bound": "hbm", "unit": "GB/s", "achieved": nbytes / (f_ms * 1e-3) / 1e9,
-                                 "peak": hbm, "frac": nbytes / (f_ms * 1e-3) / 1e9 / hbm,
-                                 "bytes_per_cell": f"{FLD_SETUP_B} + {FLD_PASS_B} x {fst['passes']} passes + "
-                                                   f"{FLD_ITER_B} x {fst['iterations']} iterations"}}
-        del t_gas, e_old, e_new
+        fld_line = run_fld(args, tracers[i1], ws[i1], rho[i1], q[i1], stream)
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -786,6 +764,65 @@ def run_batch(args, local):
                       "clocks": clk.summary()}), flush=True)
 
 
+def run_fld(args, tr, w, rho, q, stream):
+    """Time one implicit flux-limited-diffusion step (Eqs. 7-15) on the grid of ``tr``
+    with ``q`` (the tracer's q_abs) as source: gas temperature and old E_R from
+    ``synth.fld_fields``, the paper's outer boundary T0 = 14.7 K (Sect. 3.1.2),
+    c_v = 1e8 erg/(g K), tol 1e-5. HBM-bound: FLD_SETUP_B + FLD_PASS_B per pass +
+    FLD_ITER_B per iteration bytes per cell."""
+    import torch
+    tg_, e_, _ = synth.fld_fields(w.grid, seed=1)
+    t_gas = torch.from_numpy(tg_.astype(np.float32)).cuda()
+    e_old = torch.from_numpy(e_.astype(np.float32)).cuda()
+    e_new = torch.empty_like(e_old)
+    dt_s, c_v, t_bg = args.fld_dt, 1e8, 14.7
+    for _ in range(max(1, min(args.warmup, 2))):
+        _, fst = tr.fld_step(rho, t_gas, q, e_old, dt_s, c_v, t_bg, e_new=e_new, tol=1e-5, max_iter=20000)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        _, fst = tr.fld_step(rho, t_gas, q, e_old, dt_s, c_v, t_bg, e_new=e_new, tol=1e-5, max_iter=20000)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    f_ms = e0.elapsed_time(e1) / args.steps
+    ncell = w.grid.ncells
+    mg = fst["levels"] > 1
+    sb, pb, ib = (FLD_SETUP_MG_B, FLD_PASS_MG_B, FLD_ITER_MG_B) if mg else (FLD_SETUP_B, FLD_PASS_B, FLD_ITER_B)
+    nbytes = (sb + pb * fst["passes"] + ib * fst["iterations"]) * ncell
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    hbm = float(peaks.get("hbm_gbs") or 6678.0)
+    g = w.grid
+    return {"workload": f"disk3d {g.nr}x{g.ntheta}x{g.nphi}, tau550 = {w.tau550:g}, dt = {dt_s:g} s, "
+                        f"c_v = {c_v:g}, T_bg = {t_bg:g} K, tol = 1e-5",
+            "ms_per_step": f_ms, "iterations": fst["iterations"], "passes": fst["passes"],
+            "rel_change": fst["rel_change"], "ms_per_iteration": f_ms / max(1, fst["iterations"]),
+            "preconditioner": f"aggregation multigrid, {fst['levels']} levels" if mg else "Jacobi",
+            "cells_per_s": ncell / (f_ms * 1e-3),
+            "roofline": {"bound": "hbm", "unit": "GB/s", "achieved": nbytes / (f_ms * 1e-3) / 1e9,
+                         "peak": hbm, "frac": nbytes / (f_ms * 1e-3) / 1e9 / hbm,
+                         "bytes_per_cell": f"{sb} + {pb} x {fst['passes']} passes + "
+                                           f"{ib} x {fst['iterations']} iterations"}}
+
+
+def run_fld_only(args, local):
+    """--fld: trace the tau = 1 disk of --fld-grid, then time the FLD step on it."""
+    import torch
+    from paper_1001_3301_gb300 import Tracer
+    torch.cuda.set_device(local)
+    nr, nth, nph = _dims(args.fld_grid)
+    w = synth.disk3d(nr, nth, nph, n_nu=NNU, tau550=1.0, seed=1)
+    tr = Tracer.from_grid(w.grid)
+    tr.set_opacity_table(w.nu, w.kappa, w.t_sub)
+    tr.set_star(w.t_star, w.r_star)
+    rho = torch.from_numpy(w.rho32()).cuda()
+    td = torch.from_numpy(w.tdust32()).cuda()
+    q, _, _ = tr.irradiate(rho, td)
+    out = run_fld(args, tr, w, rho, q, torch.cuda.current_stream())
+    tr.close()
+    return out
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -804,6 +841,10 @@ def main():
     if args.surrogate:
         if rank == 0:
             print(json.dumps({"mode": "surrogate", **run_surrogate(args, local)}), flush=True)
+        return
+    if args.fld:
+        if rank == 0:
+            print(json.dumps({"mode": "fld", **run_fld_only(args, local)}), flush=True)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)

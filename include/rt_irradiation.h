@@ -331,6 +331,7 @@ typedef struct rt_fld_stats {
     int iterations;      /* conjugate-gradient iterations taken, all passes */
     int passes;          /* refinement passes */
     double rel_change;   /* max over cells of |correction| / |E'| of the last pass */
+    int levels;          /* multigrid levels of the preconditioner (1: Jacobi) */
 } rt_fld_stats;
 
 /* rt_fld_step -- one backward-Euler step of Eqs. 8-15,
@@ -351,9 +352,11 @@ typedef struct rt_fld_stats {
  *   dt (s) > 0 (1e300 gives the steady state), c_v (erg g^-1 K^-1) >= 0,
  *   t_bg (K) >= 0: E = a t_bg^4 half a cell beyond the outer radius;
  *   tol > 0, max_iter >= 1: mixed-precision iterative refinement (true residual in
- *   FP32, Jacobi-preconditioned conjugate gradients for each correction, FP64
- *   reductions) from E' = E_old until a pass changes no cell by more than tol
- *   relative, or max_iter conjugate-gradient iterations in total.
+ *   FP32, conjugate gradients for each correction, FP64 reductions) from
+ *   E' = E_old until a pass changes no cell by more than tol relative, or max_iter
+ *   conjugate-gradient iterations in total. Grids of more than 512 cells are
+ *   preconditioned by an aggregation-multigrid V-cycle (Galerkin coarse levels
+ *   halving every direction), smaller ones by Jacobi.
  *   stats       NULL or a host struct for the iteration count and final residual.
  * Finite volumes: harmonic-mean face coefficients, no flux through the inner radius
  * or the theta ends, periodic in phi when nphi > 1 (the wrap distance measured

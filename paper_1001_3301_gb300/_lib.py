@@ -67,7 +67,8 @@ class RtSurrogateStats(ctypes.Structure):
 
 
 class RtFldStats(ctypes.Structure):
-    _fields_ = [("iterations", ctypes.c_int), ("passes", ctypes.c_int), ("rel_change", ctypes.c_double)]
+    _fields_ = [("iterations", ctypes.c_int), ("passes", ctypes.c_int), ("rel_change", ctypes.c_double),
+                ("levels", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

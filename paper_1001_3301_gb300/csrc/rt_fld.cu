@@ -34,7 +34,9 @@ constexpr double kRossLnLo = 0.0, kRossLnHi = 11.512925464970229;  // ln 1 K .. 
 
 struct FldState {
     long long cap = 0;
-    float *buf = nullptr;  // F, tc, b0, w[3], s, 1/dg, b, d, r, p, q: 14 n floats
+    float *buf = nullptr;  // F, tc, b0, w[3], s, 1/dg, b, d, r, p, q, z: 15 n floats
+    float *mg_buf = nullptr;              // coarse levels: s, w[3], 1/dg, b, x each
+    std::vector<int> mg_dims;             // (nr, ntheta, nphi) of every level, finest first
     double *part = nullptr, *scal = nullptr;
     unsigned *bad = nullptr, *count = nullptr;
     int part_cap = 0;
@@ -256,11 +258,11 @@ __global__ void __launch_bounds__(256) k_fld_faces(const FldFaceArgs p)
 // left as the difference of large rounded numbers (a diagonal holding s + sum w
 // would bury s under the rounding of the face weights wherever diffusion dominates).
 // Mixed-precision iterative refinement: each pass computes the true residual
-// r = b - A x, solves A d = r by Jacobi-preconditioned CG from d = 0 until the
+// r = b - A x, solves A d = r by preconditioned CG from d = 0 until the
 // preconditioned residual norm fell by kInnerDrop, and adds d to x. FP32 recurrences
 // lose the true residual after a few hundred iterations; the restart from the true
 // residual recovers it, and the passes end when max |d| / |x| < tol.
-constexpr double kInnerDrop = 1e-4;
+constexpr double kInnerDrop = 1e-2;
 
 // device scalars of the solve
 enum : int {
@@ -581,6 +583,412 @@ __global__ void __launch_bounds__(256) k_cg_direction4(const CgArgs a)
 }
 
 #undef FLD_QUADS
+// --- aggregation multigrid preconditioner ---------------------------------------
+// Levels coarsen by 2 in every direction longer than one cell. The coarse operator
+// is the Galerkin product with piecewise-constant prolongation: the storage terms
+// of an aggregate add up, and a coarse face carries the sum of the fine faces that
+// cross from one aggregate into the next (faces inside an aggregate drop out), so
+// every level keeps the flux form. One V-cycle per CG iteration: a damped Jacobi
+// step from zero, the restricted residual, the coarser levels, the prolonged
+// correction and one more Jacobi step (symmetric, so CG keeps its guarantees);
+// 16 Jacobi sweeps on the coarsest level (<= 1024 cells, one CTA). The fine-level
+// intermediates are formed on the fly at the stencil's points, never stored.
+constexpr float kMgOmega = 0.8f;
+constexpr int kMgCoarseSweeps = 16;
+constexpr unsigned kMgCoarsest = 512;  // coarsen while a level has more cells
+
+struct MgLevel {
+    int nr, nth, nph;
+    FastDiv dnr, dnth;
+    unsigned n;
+    float *s, *w, *idg;  // operator in flux form, w [3][n]
+    float *b, *x;        // right-hand side and result of the level
+};
+
+struct MgPair {
+    MgLevel f, c;    // fine and coarse level
+    int sr, st, sp;  // log2 of the aggregation factors (0 or 1)
+    CgArgs cg;       // scalars and reduction scratch (the finest pair's up kernel)
+};
+
+template <class V>
+__device__ __forceinline__ float apply_lv(const MgLevel &L, const V &v, unsigned c, int k, int j, int l, float vc)
+{
+    const unsigned n = L.n, plane = (unsigned)L.nr * (unsigned)L.nth;
+    float acc = L.s[c] * vc;
+    if (k + 1 < L.nr) acc = fmaf(L.w[c], vc - v(c + 1), acc);
+    if (k > 0) acc = fmaf(L.w[c - 1], vc - v(c - 1), acc);
+    if (j + 1 < L.nth) acc = fmaf(L.w[n + c], vc - v(c + L.nr), acc);
+    if (j > 0) acc = fmaf(L.w[n + c - L.nr], vc - v(c - L.nr), acc);
+    if (L.nph > 1) {
+        const unsigned cb = l + 1 < L.nph ? c + plane : c - (unsigned)l * plane;
+        const unsigned ca = l > 0 ? c - plane : c + (unsigned)(L.nph - 1) * plane;
+        acc = fmaf(L.w[2 * n + c], vc - v(cb), acc);
+        acc = fmaf(L.w[2 * n + ca], vc - v(ca), acc);
+    }
+    return acc;
+}
+
+#define MG_LOOP(i, N) for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < (N); i += gridDim.x * blockDim.x)
+
+// coarse storage terms and face weights of an aggregate
+__global__ void __launch_bounds__(256) k_mg_coarsen(const MgPair P)
+{
+    const MgLevel &F = P.f, &C = P.c;
+    MG_LOOP(cc, C.n)
+    {
+        int K, J, L;
+        cell_ijk(cc, C.nr, C.nth, C.dnr, C.dnth, K, J, L);
+        float sum = 0.0f, wr = 0.0f, wt = 0.0f, wp = 0.0f;
+#pragma unroll
+        for (int dl = 0; dl < 2; ++dl)
+#pragma unroll
+            for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+                for (int dk = 0; dk < 2; ++dk) {
+                    const int l = (L << P.sp) + dl, j = (J << P.st) + dj, k = (K << P.sr) + dk;
+                    if (!((dl <= P.sp && l < F.nph) && (dj <= P.st && j < F.nth) && (dk <= P.sr && k < F.nr)))
+                        continue;
+                    const unsigned c = ((unsigned)l * F.nth + j) * F.nr + k;
+                    sum += F.s[c];
+                    if (k + 1 < F.nr && ((k + 1) >> P.sr) != (k >> P.sr)) wr += F.w[c];
+                    if (j + 1 < F.nth && ((j + 1) >> P.st) != (j >> P.st)) wt += F.w[F.n + c];
+                    if (F.nph > 1 && (((l + 1) % F.nph) >> P.sp) != (l >> P.sp)) wp += F.w[2 * F.n + c];
+                }
+        C.s[cc] = sum;
+        C.w[cc] = wr;
+        C.w[C.n + cc] = wt;
+        C.w[2 * C.n + cc] = wp;
+    }
+}
+
+// inverse diagonal of a level
+__global__ void __launch_bounds__(256) k_mg_diag(const MgLevel L)
+{
+    const unsigned n = L.n, plane = (unsigned)L.nr * (unsigned)L.nth;
+    MG_LOOP(c, n)
+    {
+        int k, j, l;
+        cell_ijk(c, L.nr, L.nth, L.dnr, L.dnth, k, j, l);
+        float d = L.s[c];
+        if (k + 1 < L.nr) d += L.w[c];
+        if (k > 0) d += L.w[c - 1];
+        if (j + 1 < L.nth) d += L.w[n + c];
+        if (j > 0) d += L.w[n + c - L.nr];
+        if (L.nph > 1) {
+            const unsigned ca = l > 0 ? c - plane : c + (unsigned)(L.nph - 1) * plane;
+            d += L.w[2 * n + c] + L.w[2 * n + ca];
+        }
+        L.idg[c] = d > 0.0f ? 1.0f / d : 0.0f;
+    }
+}
+
+// coarse right-hand side: the aggregate's sum of the fine residuals after the
+// first Jacobi step x0 = omega b / dg (the 2 x 2 x 2 loop unrolled, so that the
+// loads of all eight fine cells are in flight together)
+__global__ void __launch_bounds__(256) k_mg_down(const MgPair P)
+{
+    if (P.cg.scal[kDone] != 0.0) return;
+    const MgLevel &F = P.f, &C = P.c;
+    const float *idg = F.idg, *b = F.b;
+    auto x0 = [=](unsigned i) { return kMgOmega * idg[i] * b[i]; };
+    MG_LOOP(cc, C.n)
+    {
+        int K, J, L;
+        cell_ijk(cc, C.nr, C.nth, C.dnr, C.dnth, K, J, L);
+        float sum = 0.0f;
+#pragma unroll
+        for (int dl = 0; dl < 2; ++dl)
+#pragma unroll
+            for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+                for (int dk = 0; dk < 2; ++dk) {
+                    const int l = (L << P.sp) + dl, j = (J << P.st) + dj, k = (K << P.sr) + dk;
+                    const bool in = (dl <= P.sp && l < F.nph) && (dj <= P.st && j < F.nth) && (dk <= P.sr && k < F.nr);
+                    if (in) {
+                        const unsigned c = ((unsigned)l * F.nth + j) * F.nr + k;
+                        sum += b[c] - apply_lv(F, x0, c, k, j, l, x0(c));
+                    }
+                }
+        C.b[cc] = sum;
+    }
+}
+
+// the coarsest level (n <= 1024): kMgCoarseSweeps damped Jacobi sweeps from zero,
+// the level's operator staged in shared memory once
+__global__ void __launch_bounds__(256) k_mg_coarsest(const MgLevel L, const double *scal)
+{
+    if (scal[kDone] != 0.0) return;
+    __shared__ float xs[1024], ss[1024], wr[1024], wt[1024], wp[1024], id[1024], bs[1024];
+    const unsigned n = L.n;
+    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+        ss[i] = L.s[i];
+        wr[i] = L.w[i];
+        wt[i] = L.w[n + i];
+        wp[i] = L.w[2 * n + i];
+        id[i] = L.idg[i];
+        bs[i] = L.b[i];
+        xs[i] = kMgOmega * L.idg[i] * L.b[i];
+    }
+    __syncthreads();
+    const unsigned plane = (unsigned)L.nr * (unsigned)L.nth;
+    for (int sweep = 1; sweep < kMgCoarseSweeps; ++sweep) {
+        float nv[4];
+        int m = 0;
+        for (unsigned i = threadIdx.x; i < n; i += blockDim.x, ++m) {
+            int k, j, l;
+            cell_ijk(i, L.nr, L.nth, L.dnr, L.dnth, k, j, l);
+            const float xi = xs[i];
+            float acc = ss[i] * xi;
+            if (k + 1 < L.nr) acc = fmaf(wr[i], xi - xs[i + 1], acc);
+            if (k > 0) acc = fmaf(wr[i - 1], xi - xs[i - 1], acc);
+            if (j + 1 < L.nth) acc = fmaf(wt[i], xi - xs[i + L.nr], acc);
+            if (j > 0) acc = fmaf(wt[i - L.nr], xi - xs[i - L.nr], acc);
+            if (L.nph > 1) {
+                const unsigned cb = l + 1 < L.nph ? i + plane : i - (unsigned)l * plane;
+                const unsigned ca = l > 0 ? i - plane : i + (unsigned)(L.nph - 1) * plane;
+                acc = fmaf(wp[i], xi - xs[cb], acc);
+                acc = fmaf(wp[ca], xi - xs[ca], acc);
+            }
+            nv[m] = fmaf(kMgOmega * id[i], bs[i] - acc, xi);
+        }
+        __syncthreads();
+        m = 0;
+        for (unsigned i = threadIdx.x; i < n; i += blockDim.x, ++m) xs[i] = nv[m];
+        __syncthreads();
+    }
+    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) L.x[i] = xs[i];
+}
+
+// prolonged correction and the second Jacobi step: x = x1 + omega (b - A x1) / dg,
+// x1 = omega b / dg + x_coarse[aggregate]. On the finest pair (top) x is z = M^-1 r
+// and its r.z closes the CG step: init sets rz0 and beta = 0, otherwise beta, rz,
+// the iteration count and the convergence flag.
+__global__ void __launch_bounds__(256) k_mg_up(const MgPair P, int top, int init)
+{
+    if (P.cg.scal[kDone] != 0.0) return;
+    const MgLevel &F = P.f, &C = P.c;
+    const unsigned n = F.n, plane = (unsigned)F.nr * (unsigned)F.nth;
+    const float *idg = F.idg, *b = F.b, *xc = C.x;
+    auto x1 = [&](unsigned i, int k, int j, int l) {
+        return fmaf(kMgOmega * idg[i], b[i], xc[((unsigned)(l >> P.sp) * C.nth + (j >> P.st)) * C.nr + (k >> P.sr)]);
+    };
+    KSum rz;
+    MG_LOOP(c, n)
+    {
+        int k, j, l;
+        cell_ijk(c, F.nr, F.nth, F.dnr, F.dnth, k, j, l);
+        const float vc = x1(c, k, j, l);
+        float acc = F.s[c] * vc;
+        if (k + 1 < F.nr) acc = fmaf(F.w[c], vc - x1(c + 1, k + 1, j, l), acc);
+        if (k > 0) acc = fmaf(F.w[c - 1], vc - x1(c - 1, k - 1, j, l), acc);
+        if (j + 1 < F.nth) acc = fmaf(F.w[n + c], vc - x1(c + F.nr, k, j + 1, l), acc);
+        if (j > 0) acc = fmaf(F.w[n + c - F.nr], vc - x1(c - F.nr, k, j - 1, l), acc);
+        if (F.nph > 1) {
+            const int lb = l + 1 < F.nph ? l + 1 : 0, la = l > 0 ? l - 1 : F.nph - 1;
+            const unsigned cb = c + (unsigned)(lb - l) * plane, ca = c + (unsigned)(la - l) * plane;
+            acc = fmaf(F.w[2 * n + c], vc - x1(cb, k, j, lb), acc);
+            acc = fmaf(F.w[2 * n + ca], vc - x1(ca, k, j, la), acc);
+        }
+        const float xv = fmaf(kMgOmega * idg[c], b[c] - acc, vc);
+        F.x[c] = xv;
+        if (top) rz.add(b[c] * xv);
+    }
+    if (!top) return;
+    double tot;
+    if (grid_reduce<false>(P.cg, rz.value(), &tot)) {
+        double *sc = P.cg.scal;
+        if (init) {
+            sc[kRz] = tot;
+            sc[kRz0] = tot;
+            sc[kBeta] = 0.0;
+            sc[kDone] = tot > 0.0 ? 0.0 : 1.0;
+        } else {
+            sc[kBeta] = sc[kRz] > 0.0 ? tot / sc[kRz] : 0.0;
+            sc[kRz] = tot;
+            sc[kIters] += 1.0;
+            if (!(tot > kInnerDrop * kInnerDrop * sc[kRz0])) sc[kDone] = 1.0;
+        }
+    }
+}
+
+// Finest level with nr % 4 == 0: four cells of one ray per thread, 128-bit loads.
+// A v on the quad c .. c+3 at (k .. k+3, j, l), the value of the quad at the same k
+// of row (j', l') from vrow(c0, k, j', l') and of one cell from vone(i, k', j, l).
+template <class VR, class V1>
+__device__ __forceinline__ float4 apply_quad(const MgLevel &F, const VR &vrow, const V1 &vone, unsigned c, int k,
+                                             int j, int l, float4 vc)
+{
+    const unsigned n = F.n, plane = (unsigned)F.nr * (unsigned)F.nth;
+    const float4 s = ld4(F.s + c), wr = ld4(F.w + c);
+    float4 acc = make_float4(s.x * vc.x, s.y * vc.y, s.z * vc.z, s.w * vc.w);
+    acc.x = fmaf(wr.x, vc.x - vc.y, acc.x);
+    acc.y = fmaf(wr.y, vc.y - vc.z, acc.y);
+    acc.z = fmaf(wr.z, vc.z - vc.w, acc.z);
+    acc.y = fmaf(wr.x, vc.y - vc.x, acc.y);
+    acc.z = fmaf(wr.y, vc.z - vc.y, acc.z);
+    acc.w = fmaf(wr.z, vc.w - vc.z, acc.w);
+    if (k + 4 < F.nr) acc.w = fmaf(wr.w, vc.w - vone(c + 4, k + 4, j, l), acc.w);
+    if (k > 0) acc.x = fmaf(F.w[c - 1], vc.x - vone(c - 1, k - 1, j, l), acc.x);
+    auto face4 = [&](float4 w, float4 u) {
+        acc.x = fmaf(w.x, vc.x - u.x, acc.x);
+        acc.y = fmaf(w.y, vc.y - u.y, acc.y);
+        acc.z = fmaf(w.z, vc.z - u.z, acc.z);
+        acc.w = fmaf(w.w, vc.w - u.w, acc.w);
+    };
+    if (j + 1 < F.nth) face4(ld4(F.w + n + c), vrow(c + F.nr, k, j + 1, l));
+    if (j > 0) face4(ld4(F.w + n + c - F.nr), vrow(c - F.nr, k, j - 1, l));
+    if (F.nph > 1) {
+        const int lb = l + 1 < F.nph ? l + 1 : 0, la = l > 0 ? l - 1 : F.nph - 1;
+        const unsigned cb = c + (unsigned)(lb - l) * plane, ca = c + (unsigned)(la - l) * plane;
+        face4(ld4(F.w + 2 * n + c), vrow(cb, k, j, lb));
+        face4(ld4(F.w + 2 * n + ca), vrow(ca, k, j, la));
+    }
+    return acc;
+}
+
+// k_mg_down on the finest level: one thread per pair of coarse cells (K0, K0 + 1)
+// of one coarse row, i.e. the four-cell quads of the fine rows in the aggregate
+__global__ void __launch_bounds__(256) k_mg_down4(const MgPair P)
+{
+    if (P.cg.scal[kDone] != 0.0) return;
+    const MgLevel &F = P.f, &C = P.c;
+    const float *idg = F.idg, *b = F.b;
+    auto vrow = [=](unsigned c0, int, int, int) {
+        const float4 d = ld4(idg + c0), bb = ld4(b + c0);
+        return make_float4(kMgOmega * d.x * bb.x, kMgOmega * d.y * bb.y, kMgOmega * d.z * bb.z, kMgOmega * d.w * bb.w);
+    };
+    auto vone = [=](unsigned i, int, int, int) { return kMgOmega * idg[i] * b[i]; };
+    const unsigned nq = (unsigned)(F.nr / 4) * (unsigned)C.nth * (unsigned)C.nph;
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < nq; t += gridDim.x * blockDim.x) {
+        const unsigned qr = (unsigned)(F.nr / 4);
+        const unsigned rest = t / qr;
+        const int m = (int)(t - rest * qr);
+        const int J = (int)(rest % (unsigned)C.nth), L = (int)(rest / (unsigned)C.nth);
+        const int k = 4 * m;
+        float lo = 0.0f, hi = 0.0f;
+        for (int l = L << P.sp; l < min((L + 1) << P.sp, F.nph); ++l)
+            for (int j = J << P.st; j < min((J + 1) << P.st, F.nth); ++j) {
+                const unsigned c = ((unsigned)l * F.nth + j) * F.nr + k;
+                const float4 vc = vrow(c, k, j, l), bb = ld4(b + c);
+                const float4 ax = apply_quad(F, vrow, vone, c, k, j, l, vc);
+                lo += (bb.x - ax.x) + (bb.y - ax.y);
+                hi += (bb.z - ax.z) + (bb.w - ax.w);
+            }
+        const unsigned cc = ((unsigned)L * C.nth + J) * C.nr + 2 * m;
+        C.b[cc] = lo;
+        C.b[cc + 1] = hi;
+    }
+}
+
+// k_mg_up on the finest level (top), four cells per thread
+__global__ void __launch_bounds__(256) k_mg_up4(const MgPair P, int init)
+{
+    if (P.cg.scal[kDone] != 0.0) return;
+    const MgLevel &F = P.f, &C = P.c;
+    const float *idg = F.idg, *b = F.b, *xc = C.x;
+    const int st = P.st, sp = P.sp, cnr = C.nr, cnth = C.nth;
+    auto crow = [=](int j, int l) { return ((unsigned)(l >> sp) * cnth + (j >> st)) * cnr; };
+    auto vrow = [=](unsigned c0, int k, int j, int l) {
+        const unsigned K0 = crow(j, l) + (k >> 1);
+        const float2 x2 = make_float2(xc[K0], xc[K0 + 1]);
+        const float4 d = ld4(idg + c0), bb = ld4(b + c0);
+        return make_float4(fmaf(kMgOmega * d.x, bb.x, x2.x), fmaf(kMgOmega * d.y, bb.y, x2.x),
+                           fmaf(kMgOmega * d.z, bb.z, x2.y), fmaf(kMgOmega * d.w, bb.w, x2.y));
+    };
+    auto vone = [=](unsigned i, int k, int j, int l) { return fmaf(kMgOmega * idg[i], b[i], xc[crow(j, l) + (k >> 1)]); };
+    KSum rz;
+    for (unsigned c = 4u * (blockIdx.x * blockDim.x + threadIdx.x); c < F.n; c += 4u * gridDim.x * blockDim.x) {
+        int k, j, l;
+        cell_ijk(c, F.nr, F.nth, F.dnr, F.dnth, k, j, l);
+        const float4 vc = vrow(c, k, j, l);
+        const float4 ax = apply_quad(F, vrow, vone, c, k, j, l, vc);
+        const float4 d = ld4(idg + c), bb = ld4(b + c);
+        const float4 z = make_float4(fmaf(kMgOmega * d.x, bb.x - ax.x, vc.x), fmaf(kMgOmega * d.y, bb.y - ax.y, vc.y),
+                                     fmaf(kMgOmega * d.z, bb.z - ax.z, vc.z), fmaf(kMgOmega * d.w, bb.w - ax.w, vc.w));
+        st4(F.x + c, z);
+        rz.add(bb.x * z.x);
+        rz.add(bb.y * z.y);
+        rz.add(bb.z * z.z);
+        rz.add(bb.w * z.w);
+    }
+    double tot;
+    if (grid_reduce<false>(P.cg, rz.value(), &tot)) {
+        double *sc = P.cg.scal;
+        if (init) {
+            sc[kRz] = tot;
+            sc[kRz0] = tot;
+            sc[kBeta] = 0.0;
+            sc[kDone] = tot > 0.0 ? 0.0 : 1.0;
+        } else {
+            sc[kBeta] = sc[kRz] > 0.0 ? tot / sc[kRz] : 0.0;
+            sc[kRz] = tot;
+            sc[kIters] += 1.0;
+            if (!(tot > kInnerDrop * kInnerDrop * sc[kRz0])) sc[kDone] = 1.0;
+        }
+    }
+}
+
+#undef MG_LOOP
+
+// CG steps of the multigrid path (the preconditioned residual z comes from k_mg_up)
+// r = b - A x, d = 0, p = 0
+__global__ void __launch_bounds__(256) k_cg_residual_mg(const CgArgs a)
+{
+    FLD_CELLS(c)
+    {
+        a.r[c] = a.b[c] - apply_flux(a, a.x, c);
+        a.d[c] = 0.0f;
+        a.p[c] = 0.0f;
+    }
+}
+
+// d += alpha p, r -= alpha q (four cells per thread; n % 4 == 0)
+__global__ void __launch_bounds__(256) k_cg_update_mg4(const CgArgs a)
+{
+    if (a.scal[kDone] != 0.0) return;
+    const float alpha = (float)a.scal[kAlpha];
+    for (unsigned c = 4u * (blockIdx.x * blockDim.x + threadIdx.x); c < (unsigned)a.n; c += 4u * gridDim.x * blockDim.x) {
+        const float4 p = ld4(a.p + c), q = ld4(a.q + c);
+        float4 d = ld4(a.d + c), r = ld4(a.r + c);
+        d = make_float4(fmaf(alpha, p.x, d.x), fmaf(alpha, p.y, d.y), fmaf(alpha, p.z, d.z), fmaf(alpha, p.w, d.w));
+        r = make_float4(fmaf(-alpha, q.x, r.x), fmaf(-alpha, q.y, r.y), fmaf(-alpha, q.z, r.z),
+                        fmaf(-alpha, q.w, r.w));
+        st4(a.d + c, d);
+        st4(a.r + c, r);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_cg_update_mg(const CgArgs a)
+{
+    if (a.scal[kDone] != 0.0) return;
+    const float alpha = (float)a.scal[kAlpha];
+    FLD_CELLS(c)
+    {
+        a.d[c] = fmaf(alpha, a.p[c], a.d[c]);
+        a.r[c] = fmaf(-alpha, a.q[c], a.r[c]);
+    }
+}
+
+// p = z + beta p (z: the finest level's multigrid result)
+__global__ void __launch_bounds__(256) k_cg_direction_mg4(const CgArgs a, const float *z)
+{
+    if (a.scal[kDone] != 0.0) return;
+    const float beta = (float)a.scal[kBeta];
+    for (unsigned c = 4u * (blockIdx.x * blockDim.x + threadIdx.x); c < (unsigned)a.n; c += 4u * gridDim.x * blockDim.x) {
+        const float4 zz = ld4(z + c), p = ld4(a.p + c);
+        st4(a.p + c, make_float4(fmaf(beta, p.x, zz.x), fmaf(beta, p.y, zz.y), fmaf(beta, p.z, zz.z),
+                                 fmaf(beta, p.w, zz.w)));
+    }
+}
+
+__global__ void __launch_bounds__(256) k_cg_direction_mg(const CgArgs a, const float *z)
+{
+    if (a.scal[kDone] != 0.0) return;
+    const float beta = (float)a.scal[kBeta];
+    FLD_CELLS(c) a.p[c] = fmaf(beta, a.p[c], z[c]);
+}
+
 #undef FLD_CELLS
 
 int rosseland_nodes(const CtxInfo &in, const std::vector<double> &t_nodes, double *kr_host, float *lkr_dev,
@@ -684,6 +1092,7 @@ void fld_free(FldState *s)
 {
     if (!s) return;
     cudaFree(s->buf);
+    cudaFree(s->mg_buf);
     cudaFree(s->part);
     cudaFree(s->scal);
     cudaFree(s->bad);
@@ -739,7 +1148,7 @@ int rt_fld_step(rt_ctx *ctx, const float *rho, const float *t_gas, const float *
         cudaFree(fs->buf);
         fs->buf = nullptr;
         fs->cap = 0;
-        if (cudaMalloc(&fs->buf, sizeof(float) * 14 * (size_t)n) != cudaSuccess) {
+        if (cudaMalloc(&fs->buf, sizeof(float) * 15 * (size_t)n) != cudaSuccess) {
             cudaGetLastError();
             return ctx_fail(ctx, RT_ERR_NO_MEMORY, "FLD workspace");
         }
@@ -780,6 +1189,23 @@ int rt_fld_step(rt_ctx *ctx, const float *rho, const float *t_gas, const float *
             return ctx_fail(ctx, RT_ERR_CUDA, "FLD geometry tables");
         }
     }
+    if (fs->mg_dims.empty()) {  // multigrid levels: halve every direction longer than one cell
+        int a = nr, b2 = nth, c3 = nph;
+        size_t coarse = 0;
+        fs->mg_dims = {a, b2, c3};
+        while ((unsigned long long)a * b2 * c3 > kMgCoarsest && (a > 1 || b2 > 1 || c3 > 1)) {
+            a = a > 1 ? (a + 1) / 2 : 1;
+            b2 = b2 > 1 ? (b2 + 1) / 2 : 1;
+            c3 = c3 > 1 ? (c3 + 1) / 2 : 1;
+            fs->mg_dims.insert(fs->mg_dims.end(), {a, b2, c3});
+            coarse += (size_t)a * b2 * c3;
+        }
+        if (coarse > 0 && cudaMalloc(&fs->mg_buf, sizeof(float) * 7 * coarse) != cudaSuccess) {
+            cudaGetLastError();
+            fs->mg_dims.clear();
+            return ctx_fail(ctx, RT_ERR_NO_MEMORY, "FLD multigrid levels");
+        }
+    }
     if (!fs->lkr_valid || fs->lkr_fp != in.table_fingerprint) {
         if (!fs->lkr && cudaMalloc(&fs->lkr, sizeof(float) * kRossNodes) != cudaSuccess) {
             cudaGetLastError();
@@ -797,7 +1223,7 @@ int rt_fld_step(rt_ctx *ctx, const float *rho, const float *t_gas, const float *
     const double L = in.r_if_h[nr];
     const double a_rad = radiation_constant();
     float *F = fs->buf, *tc = F + n, *b0 = tc + n, *w = b0 + n, *sv = w + 3 * n, *idg = sv + n, *b = idg + n;
-    float *d = b + n, *r = d + n, *p = r + n, *q = p + n;
+    float *d = b + n, *r = d + n, *p = r + n, *q = p + n, *z = q + n;
 
     FldCellArgs ca;
     ca.g = g;
@@ -849,6 +1275,65 @@ int rt_fld_step(rt_ctx *ctx, const float *rho, const float *t_gas, const float *
     cg.scal = fs->scal;
     cg.count = fs->count;
 
+    // multigrid levels and pairs (level 0: the fine operator, b = r, x = z)
+    const int n_lv = (int)fs->mg_dims.size() / 3;
+    const bool use_mg = n_lv > 1;
+    std::vector<MgLevel> lv(n_lv);
+    {
+        float *cursor = fs->mg_buf;
+        for (int i = 0; i < n_lv; ++i) {
+            MgLevel &L = lv[i];
+            L.nr = fs->mg_dims[3 * i];
+            L.nth = fs->mg_dims[3 * i + 1];
+            L.nph = fs->mg_dims[3 * i + 2];
+            L.dnr = FastDiv::make((unsigned)L.nr);
+            L.dnth = FastDiv::make((unsigned)L.nth);
+            L.n = (unsigned)L.nr * (unsigned)L.nth * (unsigned)L.nph;
+            if (i == 0) {
+                L.s = sv;
+                L.w = w;
+                L.idg = idg;
+                L.b = r;
+                L.x = z;
+            } else {
+                L.s = cursor;
+                L.w = L.s + L.n;
+                L.idg = L.w + 3 * (size_t)L.n;
+                L.b = L.idg + L.n;
+                L.x = L.b + L.n;
+                cursor = L.x + L.n;
+            }
+        }
+    }
+    std::vector<MgPair> pairs(n_lv > 0 ? n_lv - 1 : 0);
+    for (int i = 0; i + 1 < n_lv; ++i) {
+        pairs[i].f = lv[i];
+        pairs[i].c = lv[i + 1];
+        pairs[i].sr = lv[i].nr > 1 ? 1 : 0;
+        pairs[i].st = lv[i].nth > 1 ? 1 : 0;
+        pairs[i].sp = lv[i].nph > 1 ? 1 : 0;
+        pairs[i].cg = cg;
+    }
+    auto work_grid = [&](const void *kern, unsigned cells) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        return (int)std::max(1LL, std::min<long long>((cells + 255) / 256, (long long)per_sm * nsm));
+    };
+    // the finest pair in four-cell form where the rays hold a multiple of four cells
+    const bool quad0 = nr % 4 == 0 && use_mg;
+    auto mg_apply = [&](int init) {
+        if (quad0) k_mg_down4<<<work_grid((const void *)k_mg_down4, lv[1].n / 2), 256, 0, st>>>(pairs[0]);
+        else k_mg_down<<<work_grid((const void *)k_mg_down, lv[1].n), 256, 0, st>>>(pairs[0]);
+        for (int i = 1; i + 1 < n_lv; ++i)
+            k_mg_down<<<work_grid((const void *)k_mg_down, lv[i + 1].n), 256, 0, st>>>(pairs[i]);
+        k_mg_coarsest<<<1, 256, 0, st>>>(lv[n_lv - 1], fs->scal);
+        for (int i = n_lv - 2; i >= 1; --i)
+            k_mg_up<<<work_grid((const void *)k_mg_up, lv[i].n), 256, 0, st>>>(pairs[i], 0, init);
+        if (quad0) k_mg_up4<<<work_grid((const void *)k_mg_up4, lv[0].n / 4), 256, 0, st>>>(pairs[0], init);
+        else k_mg_up<<<work_grid((const void *)k_mg_up, lv[0].n), 256, 0, st>>>(pairs[0], 1, init);
+    };
+
     auto sync_read = [&](double *h_sc, unsigned *h_bad) {
         bool ok = cudaGetLastError() == cudaSuccess &&
                   cudaMemcpyAsync(h_sc, fs->scal, sizeof(double) * kNScal, cudaMemcpyDeviceToHost, st) == cudaSuccess;
@@ -861,6 +1346,10 @@ int rt_fld_step(rt_ctx *ctx, const float *rho, const float *t_gas, const float *
               cudaMemsetAsync(fs->scal, 0, sizeof(double) * kNScal, st) == cudaSuccess;
     k_fld_cell<<<grid, 256, 0, st>>>(ca);
     k_fld_faces<<<grid, 256, 0, st>>>(fa);
+    for (int i = 0; i + 1 < n_lv; ++i) {  // coarse operators of this step
+        k_mg_coarsen<<<work_grid((const void *)k_mg_coarsen, lv[i + 1].n), 256, 0, st>>>(pairs[i]);
+        k_mg_diag<<<work_grid((const void *)k_mg_diag, lv[i + 1].n), 256, 0, st>>>(lv[i + 1]);
+    }
     ok = ok && sync_read(h_sc, &h_bad);
     if (!ok) return ctx_fail(ctx, RT_ERR_CUDA, std::string("FLD set-up: ") + cudaGetErrorString(cudaGetLastError()));
     if (h_bad)
@@ -892,13 +1381,34 @@ int rt_fld_step(rt_ctx *ctx, const float *rho, const float *t_gas, const float *
     const int g_dir = quads ? wave((const void *)k_cg_direction4) : wave((const void *)k_cg_direction);
     const int g_acc = wave((const void *)k_cg_accumulate);
     while (!done) {
-        if (quads) k_cg_residual4<<<g_res, 256, 0, st>>>(cg);
-        else k_cg_residual<<<g_res, 256, 0, st>>>(cg);
+        if (cudaMemsetAsync(fs->scal + kDone, 0, sizeof(double), st) != cudaSuccess)
+            return ctx_fail(ctx, RT_ERR_CUDA, "FLD pass start");
+        if (use_mg) {
+            k_cg_residual_mg<<<g_res, 256, 0, st>>>(cg);
+            mg_apply(1);
+            if (quads) k_cg_direction_mg4<<<g_dir, 256, 0, st>>>(cg, z);
+            else k_cg_direction_mg<<<g_dir, 256, 0, st>>>(cg, z);
+        } else if (quads) {
+            k_cg_residual4<<<g_res, 256, 0, st>>>(cg);
+        } else {
+            k_cg_residual<<<g_res, 256, 0, st>>>(cg);
+        }
         bool inner_done = false;
         while (!inner_done && iters < max_iter) {
             const int burst = std::min(kBurst, max_iter - iters);
             for (int i = 0; i < burst; ++i) {
-                if (quads) {
+                if (use_mg) {
+                    if (quads) {
+                        k_cg_apply4<<<g_app, 256, 0, st>>>(cg);
+                        k_cg_update_mg4<<<g_upd, 256, 0, st>>>(cg);
+                    } else {
+                        k_cg_apply<<<g_app, 256, 0, st>>>(cg);
+                        k_cg_update_mg<<<g_upd, 256, 0, st>>>(cg);
+                    }
+                    mg_apply(0);
+                    if (quads) k_cg_direction_mg4<<<g_dir, 256, 0, st>>>(cg, z);
+                    else k_cg_direction_mg<<<g_dir, 256, 0, st>>>(cg, z);
+                } else if (quads) {
                     k_cg_apply4<<<g_app, 256, 0, st>>>(cg);
                     k_cg_update4<<<g_upd, 256, 0, st>>>(cg);
                     k_cg_direction4<<<g_dir, 256, 0, st>>>(cg);
@@ -921,6 +1431,7 @@ int rt_fld_step(rt_ctx *ctx, const float *rho, const float *t_gas, const float *
         done = corr < tol || iters >= max_iter || isinf(corr);
     }
     if (stats) {
+        stats->levels = use_mg ? n_lv : 1;
         stats->iterations = iters;
         stats->passes = passes;
         stats->rel_change = corr;

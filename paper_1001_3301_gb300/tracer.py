@@ -189,7 +189,7 @@ class Tracer:
 
     def fld_step(self, rho, t_gas, q_abs, e_old, dt, c_v, t_bg, e_new=None, tol=1e-5, max_iter=20000):
         """One implicit flux-limited-diffusion step of E_R (CUDA tensors of this grid);
-        returns (e_new, {"iterations", "passes", "rel_change"})."""
+        returns (e_new, {"iterations", "passes", "rel_change", "levels"})."""
         import torch
         for f, name in ((rho, "rho"), (t_gas, "t_gas"), (q_abs, "q_abs"), (e_old, "e_old")):
             self._check_field(f, name)
@@ -200,7 +200,8 @@ class Tracer:
         check(lib.rt_fld_step(self._ctx, rho.data_ptr(), t_gas.data_ptr(), q_abs.data_ptr(), e_old.data_ptr(),
                               e_new.data_ptr(), float(dt), float(c_v), float(t_bg), float(tol), int(max_iter),
                               ctypes.byref(st)), self._ctx)
-        return e_new, {"iterations": st.iterations, "passes": st.passes, "rel_change": st.rel_change}
+        return e_new, {"iterations": st.iterations, "passes": st.passes, "rel_change": st.rel_change,
+                       "levels": st.levels}
 
     # -- learned surrogate (rt_surrogate_*) -------------------------------------
     def surrogate_train(self, rho_list, t_list, n_samples=0, batch=0, steps=0, lr=0.0, seed=1):

@@ -96,7 +96,8 @@ def _step_pair(torch, g, nu, kappa, rho, t, q, e0, dt, c_v, t_bg, t_grid=None):
 
 
 CASES = [
-    # (nr, ntheta, nphi), dt (s): storage-dominated, mixed, steady state
+    # (nr, ntheta, nphi), dt (s): storage-dominated, mixed, steady state; grids above
+    # 512 cells take the multigrid-preconditioned path, smaller ones Jacobi
     ((20, 12, 8), 1e4),     # the paper's FLD time step
     ((20, 12, 8), 1e6),
     ((20, 12, 8), 1e10),
@@ -105,6 +106,8 @@ CASES = [
     ((33, 7, 1), 1e10),     # axisymmetric
     ((16, 6, 2), 1e10),     # two phi cells: both faces between the same pair
     ((24, 1, 1), 1e10),     # one theta cell: radial only
+    ((40, 24, 16), 1e4),    # three multigrid levels, four-cell kernels
+    ((41, 23, 9), 1e4),     # three multigrid levels, odd sizes (one-cell aggregates at the ends)
 ]
 
 
@@ -116,6 +119,7 @@ def test_fld_step_matches_oracle(torch, shape, dt):
     got, ref, st = _step_pair(torch, w.grid, w.nu, w.kappa, w.rho, t, q, e0, dt, 1e8, 15.0)
     rel = np.abs(got / ref - 1)
     assert st["rel_change"] < TOL
+    assert (st["levels"] > 1) == (nr * nth * nph > 512)
     assert rel.max() < RTOL_E, (rel.max(), st)
 
 
