@@ -44,6 +44,13 @@ struct FldState {
     float *lkr = nullptr;  // ln kappa_R on the ln T nodes
     unsigned long long lkr_fp = 0;
     bool lkr_valid = false;
+    // the solve runs on a private stream (after the context's stream), so that its
+    // inner-iteration bursts can be captured and replayed as a CUDA graph
+    cudaStream_t gs = nullptr;
+    cudaEvent_t ev_in = nullptr;
+    cudaGraphExec_t burst = nullptr;
+    const void *burst_x = nullptr, *burst_buf = nullptr;  // what the captured launches point at
+    bool no_graph = false;
 };
 
 namespace {
@@ -1099,6 +1106,9 @@ void fld_free(FldState *s)
     cudaFree(s->count);
     cudaFree(s->geo);
     cudaFree(s->lkr);
+    if (s->burst) cudaGraphExecDestroy(s->burst);
+    if (s->ev_in) cudaEventDestroy(s->ev_in);
+    if (s->gs) cudaStreamDestroy(s->gs);
     delete s;
 }
 
@@ -1135,9 +1145,19 @@ int rt_fld_step(rt_ctx *ctx, const float *rho, const float *t_gas, const float *
     if (e_new == e_old) return ctx_fail(ctx, RT_ERR_INVALID_ARG, "e_new must not alias e_old");
     if (in.ncells >= (1LL << 31) - 1) return ctx_fail(ctx, RT_ERR_INVALID_ARG, "FLD step needs fewer than 2^31 cells");
     if (cudaSetDevice(in.dev) != cudaSuccess) return ctx_fail(ctx, RT_ERR_CUDA, "cudaSetDevice");
-    cudaStream_t st = in.stream;
     FldState *&fs = ctx_fld(ctx);
     if (!fs) fs = new FldState();
+    if (!fs->gs) {
+        if (cudaStreamCreateWithFlags(&fs->gs, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&fs->ev_in, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return ctx_fail(ctx, RT_ERR_CUDA, "FLD stream");
+        }
+    }
+    // everything below runs on the private stream, after the context stream's work so far
+    if (cudaEventRecord(fs->ev_in, in.stream) != cudaSuccess || cudaStreamWaitEvent(fs->gs, fs->ev_in, 0) != cudaSuccess)
+        return ctx_fail(ctx, RT_ERR_CUDA, "FLD stream order");
+    cudaStream_t st = fs->gs;
     const long long n = in.ncells;
     const int nr = in.nr, nth = in.ntheta, nph = in.nphi;
     int nsm = 0;
@@ -1322,16 +1342,21 @@ int rt_fld_step(rt_ctx *ctx, const float *rho, const float *t_gas, const float *
     };
     // the finest pair in four-cell form where the rays hold a multiple of four cells
     const bool quad0 = nr % 4 == 0 && use_mg;
+    std::vector<int> g_down(n_lv, 1), g_up(n_lv, 1);
+    for (int i = 0; i + 1 < n_lv; ++i) {
+        g_down[i] = (i == 0 && quad0) ? work_grid((const void *)k_mg_down4, lv[1].n / 2)
+                                      : work_grid((const void *)k_mg_down, lv[i + 1].n);
+        g_up[i] = (i == 0 && quad0) ? work_grid((const void *)k_mg_up4, lv[0].n / 4)
+                                    : work_grid((const void *)k_mg_up, lv[i].n);
+    }
     auto mg_apply = [&](int init) {
-        if (quad0) k_mg_down4<<<work_grid((const void *)k_mg_down4, lv[1].n / 2), 256, 0, st>>>(pairs[0]);
-        else k_mg_down<<<work_grid((const void *)k_mg_down, lv[1].n), 256, 0, st>>>(pairs[0]);
-        for (int i = 1; i + 1 < n_lv; ++i)
-            k_mg_down<<<work_grid((const void *)k_mg_down, lv[i + 1].n), 256, 0, st>>>(pairs[i]);
+        if (quad0) k_mg_down4<<<g_down[0], 256, 0, st>>>(pairs[0]);
+        else k_mg_down<<<g_down[0], 256, 0, st>>>(pairs[0]);
+        for (int i = 1; i + 1 < n_lv; ++i) k_mg_down<<<g_down[i], 256, 0, st>>>(pairs[i]);
         k_mg_coarsest<<<1, 256, 0, st>>>(lv[n_lv - 1], fs->scal);
-        for (int i = n_lv - 2; i >= 1; --i)
-            k_mg_up<<<work_grid((const void *)k_mg_up, lv[i].n), 256, 0, st>>>(pairs[i], 0, init);
-        if (quad0) k_mg_up4<<<work_grid((const void *)k_mg_up4, lv[0].n / 4), 256, 0, st>>>(pairs[0], init);
-        else k_mg_up<<<work_grid((const void *)k_mg_up, lv[0].n), 256, 0, st>>>(pairs[0], 1, init);
+        for (int i = n_lv - 2; i >= 1; --i) k_mg_up<<<g_up[i], 256, 0, st>>>(pairs[i], 0, init);
+        if (quad0) k_mg_up4<<<g_up[0], 256, 0, st>>>(pairs[0], init);
+        else k_mg_up<<<g_up[0], 256, 0, st>>>(pairs[0], 1, init);
     };
 
     auto sync_read = [&](double *h_sc, unsigned *h_bad) {
@@ -1380,6 +1405,29 @@ int rt_fld_step(rt_ctx *ctx, const float *rho, const float *t_gas, const float *
     const int g_upd = quads ? wave((const void *)k_cg_update4) : wave((const void *)k_cg_update);
     const int g_dir = quads ? wave((const void *)k_cg_direction4) : wave((const void *)k_cg_direction);
     const int g_acc = wave((const void *)k_cg_accumulate);
+    // one inner iteration: q = A p, the updates, z = M^-1 r and r.z, the new direction
+    auto iteration = [&]() {
+        if (use_mg) {
+            if (quads) {
+                k_cg_apply4<<<g_app, 256, 0, st>>>(cg);
+                k_cg_update_mg4<<<g_upd, 256, 0, st>>>(cg);
+            } else {
+                k_cg_apply<<<g_app, 256, 0, st>>>(cg);
+                k_cg_update_mg<<<g_upd, 256, 0, st>>>(cg);
+            }
+            mg_apply(0);
+            if (quads) k_cg_direction_mg4<<<g_dir, 256, 0, st>>>(cg, z);
+            else k_cg_direction_mg<<<g_dir, 256, 0, st>>>(cg, z);
+        } else if (quads) {
+            k_cg_apply4<<<g_app, 256, 0, st>>>(cg);
+            k_cg_update4<<<g_upd, 256, 0, st>>>(cg);
+            k_cg_direction4<<<g_dir, 256, 0, st>>>(cg);
+        } else {
+            k_cg_apply<<<g_app, 256, 0, st>>>(cg);
+            k_cg_update<<<g_upd, 256, 0, st>>>(cg);
+            k_cg_direction<<<g_dir, 256, 0, st>>>(cg);
+        }
+    };
     while (!done) {
         if (cudaMemsetAsync(fs->scal + kDone, 0, sizeof(double), st) != cudaSuccess)
             return ctx_fail(ctx, RT_ERR_CUDA, "FLD pass start");
@@ -1396,27 +1444,32 @@ int rt_fld_step(rt_ctx *ctx, const float *rho, const float *t_gas, const float *
         bool inner_done = false;
         while (!inner_done && iters < max_iter) {
             const int burst = std::min(kBurst, max_iter - iters);
-            for (int i = 0; i < burst; ++i) {
-                if (use_mg) {
-                    if (quads) {
-                        k_cg_apply4<<<g_app, 256, 0, st>>>(cg);
-                        k_cg_update_mg4<<<g_upd, 256, 0, st>>>(cg);
-                    } else {
-                        k_cg_apply<<<g_app, 256, 0, st>>>(cg);
-                        k_cg_update_mg<<<g_upd, 256, 0, st>>>(cg);
-                    }
-                    mg_apply(0);
-                    if (quads) k_cg_direction_mg4<<<g_dir, 256, 0, st>>>(cg, z);
-                    else k_cg_direction_mg<<<g_dir, 256, 0, st>>>(cg, z);
-                } else if (quads) {
-                    k_cg_apply4<<<g_app, 256, 0, st>>>(cg);
-                    k_cg_update4<<<g_upd, 256, 0, st>>>(cg);
-                    k_cg_direction4<<<g_dir, 256, 0, st>>>(cg);
-                } else {
-                    k_cg_apply<<<g_app, 256, 0, st>>>(cg);
-                    k_cg_update<<<g_upd, 256, 0, st>>>(cg);
-                    k_cg_direction<<<g_dir, 256, 0, st>>>(cg);
+            if (burst == kBurst && !fs->no_graph && (!fs->burst || fs->burst_x != e_new || fs->burst_buf != fs->buf)) {
+                // (re)capture the burst: its launches point at e_new and the workspace
+                if (fs->burst) cudaGraphExecDestroy(fs->burst);
+                fs->burst = nullptr;
+                cudaGraph_t graph = nullptr;
+                bool cap = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+                if (cap) {
+                    for (int i = 0; i < kBurst; ++i) iteration();
+                    cap = cudaStreamEndCapture(st, &graph) == cudaSuccess && graph;
                 }
+                if (cap) cap = cudaGraphInstantiate(&fs->burst, graph, 0) == cudaSuccess;
+                if (graph) cudaGraphDestroy(graph);
+                if (!cap) {  // run the bursts as plain launches from now on
+                    cudaGetLastError();
+                    if (fs->burst) cudaGraphExecDestroy(fs->burst);
+                    fs->burst = nullptr;
+                    fs->no_graph = true;
+                }
+                fs->burst_x = e_new;
+                fs->burst_buf = fs->buf;
+            }
+            if (burst == kBurst && fs->burst && !fs->no_graph) {
+                if (cudaGraphLaunch(fs->burst, st) != cudaSuccess)
+                    return ctx_fail(ctx, RT_ERR_CUDA, "FLD graph launch");
+            } else {
+                for (int i = 0; i < burst; ++i) iteration();
             }
             if (!sync_read(h_sc, nullptr))
                 return ctx_fail(ctx, RT_ERR_CUDA, std::string("FLD iteration: ") + cudaGetErrorString(cudaGetLastError()));
