@@ -11,7 +11,7 @@
 // from the table (one 8-byte shared-memory read of the bracketing pair), the lane's
 // sum (C terms, plain FP32), a compensated warp scan of the lane sums, then a second
 // pass over the lane's cells carrying the exclusive prefix (no per-cell prefix is
-// stored).
+// stored). The per-cell arithmetic runs on pairs of cells in f32x2 registers.
 // The bins are ordered by their largest tabulated kappa; the Taylor classes of the
 // absorbed fraction (1, 2, 3, 5 terms) come from that largest kappa and the warp's
 // largest column, the remaining bins take the per-cell select between the 5-term
@@ -27,47 +27,35 @@ struct TdepTab {
     int n_t;
 };
 
-template <int CLASS>
-__device__ __forceinline__ float absorbed(float y)  // 1 - 2^y, y = -dtau log2(e) <= 0
-{
-    if constexpr (CLASS <= 5) {
-        float p = (float)taylor_coeff(CLASS - 1);
-#pragma unroll
-        for (int k = CLASS - 2; k >= 0; --k) p = fmaf(p, y, (float)taylor_coeff(k));
-        return y * p;
-    } else {
-        float p = (float)taylor_coeff(4);
-#pragma unroll
-        for (int k = 3; k >= 0; --k) p = fmaf(p, y, (float)taylor_coeff(k));
-        const float small = y * p;
-        const float big = 1.0f - ex2_approx(y);
-        return y > -kYSplit ? small : big;
-    }
-}
-
-// Bins [i0, i1) of one class: scan, attenuation, absorption for the lane's cells.
+// Bins [i0, i1) of one class: scan, attenuation, absorption for the lane's cells,
+// two cells per f32x2 register pair (packed FMA/ADD/MUL on the column, the exponent,
+// the absorbed fraction and the accumulators; the two cells' kappa come from
+// different table rows, so the interpolation itself stays scalar).
 template <int CLASS, int C>
 __device__ __forceinline__ void tdep_range(int i0, int i1, const float *s_lf, const float2 *s_kt, int n_t,
-                                           const int (&jt)[C], const float (&wt)[C], const float (&d)[C],
-                                           float (&acc)[C], float (&acc0)[C], bool any_zero, int lane,
+                                           const int (&jt)[C], const float (&wt)[C], const float2 (&d2)[C / 2],
+                                           float2 (&a2)[C / 2], float2 (&a02)[C / 2], bool any_zero, int lane,
                                            float &esc)
 {
+    const float2 nl2e = f2(-(float)kLog2e);
     for (int i = i0; i < i1; ++i) {
         const float lf = s_lf[i];
         const float2 *row = s_kt + i * n_t;
-        float kap[C], dt[C];
-        float lane_sum = 0.0f;  // at most C terms: plain FP32 (error <= C ulp of the lane's share)
+        auto kappa2 = [&](int m) {  // the two cells' kappa of this bin
+            const float2 k0 = row[jt[2 * m]], k1 = row[jt[2 * m + 1]];
+            return make_float2(fmaf(wt[2 * m], k0.y - k0.x, k0.x), fmaf(wt[2 * m + 1], k1.y - k1.x, k1.x));
+        };
+        float2 dt2[C / 2];
+        float2 ls2 = f2(0.0f);  // the lane's sum, at most C terms in two halves (plain FP32)
 #pragma unroll
-        for (int j = 0; j < C; ++j) {
-            const float2 kk = row[jt[j]];
-            kap[j] = fmaf(wt[j], kk.y - kk.x, kk.x);
-            dt[j] = kap[j] * d[j];
-            lane_sum += dt[j];
+        for (int m = 0; m < C / 2; ++m) {
+            dt2[m] = __fmul2_rn(kappa2(m), d2[m]);
+            ls2 = __fadd2_rn(ls2, dt2[m]);
         }
         // compensated warp scan of the lane sums (the ray-long sum)
         KahanSum inc;
         inc.zero();
-        inc.add(lane_sum);
+        inc.add(ls2.x + ls2.y);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const KahanSum v = inc.shfl_up(o);
@@ -77,15 +65,25 @@ __device__ __forceinline__ void tdep_range(int i0, int i1, const float *s_lf, co
         if (lane == 0) pre.zero();
         if (lane == 31) esc += ex2_approx(fmaf(-(float)kLog2e, inc.value(), lf));
         // the lane's exclusive prefix: the warp offset (hi + lo) plus a plain partial sum
-        const float base_hi = pre.hi, base_lo = pre.lo;
+        const float2 bhi = f2(pre.hi), blo = f2(pre.lo), lf2 = f2(lf);
         float part = 0.0f;
 #pragma unroll
-        for (int j = 0; j < C; ++j) {
-            const float tau = base_hi + (base_lo + part);
-            const float g = ex2_approx(fmaf(-(float)kLog2e, tau, lf));
-            acc[j] = fmaf(g, absorbed<CLASS>(-(float)kLog2e * dt[j]), acc[j]);
-            if (any_zero) acc0[j] = fmaf(g, kap[j], acc0[j]);
-            part += dt[j];
+        for (int m = 0; m < C / 2; ++m) {
+            const float2 p2 = make_float2(part, part + dt2[m].x);
+            const float2 tau = __fadd2_rn(bhi, __fadd2_rn(blo, p2));
+            const float2 g = ex2_approx2(__ffma2_rn(nl2e, tau, lf2));
+            const float2 y = __fmul2_rn(nl2e, dt2[m]);  // -dtau log2(e)
+            float2 om;                                   // 1 - 2^y
+            if constexpr (CLASS <= 5) {
+                om = taylor_fraction<CLASS>(y);
+            } else {
+                const float2 big = __ffma2_rn(ex2_approx2(y), f2(-1.0f), f2(1.0f));
+                const float2 small = taylor_fraction<5>(y);
+                om = make_float2(y.x > -kYSplit ? small.x : big.x, y.y > -kYSplit ? small.y : big.y);
+            }
+            a2[m] = __ffma2_rn(g, om, a2[m]);
+            if (any_zero) a02[m] = __ffma2_rn(g, kappa2(m), a02[m]);  // (rare: re-read, not kept)
+            part = p2.y + dt2[m].y;
         }
     }
 }
@@ -129,7 +127,8 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray_tdep(const TraceArgs p, co
     eesc.zero();
     for (unsigned ray = blockIdx.x * W + warp; ray < p.nrays; ray += gridDim.x * W) {
         const size_t base = (size_t)ray * nr + c0;
-        float d[C], acc[C], acc0[C], wt[C];
+        Cells<float, C> d, acc, acc0;
+        float wt[C];
         int jt[C];
         unsigned zero_m = 0;
         bool bad = false;
@@ -143,11 +142,12 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray_tdep(const TraceArgs p, co
                 bad |= !(rho >= 0.0f && rho <= FLT_MAX) || (td != td);
             }
             const bool dust = j < nv && td <= p.t_sub;
-            d[j] = dust ? rho * s_dr[j][lane] : 0.0f;
-            if (dust && d[j] == 0.0f) zero_m |= 1u << j;
-            dmax = fmaxf(dmax, d[j]);
-            acc[j] = 0.0f;
-            acc0[j] = 0.0f;
+            const float dj = dust ? rho * s_dr[j][lane] : 0.0f;
+            d.set(j, dj);
+            if (dust && dj == 0.0f) zero_m |= 1u << j;
+            dmax = fmaxf(dmax, dj);
+            acc.set(j, 0.0f);
+            acc0.set(j, 0.0f);
             // bracketing temperature points and the weight of the upper one
             int lo = 0;
             for (int s = 16; s > 0; s >>= 1)
@@ -163,11 +163,11 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray_tdep(const TraceArgs p, co
         const int na = p.n_active;
         const BinClasses bc = classify_bins(s_nu, na, lane, dmax, 0.0f);
         float esc = 0.0f;
-        tdep_range<1, C>(0, bc.b1, s_lf, s_kt, nt, jt, wt, d, acc, acc0, any_zero, lane, esc);
-        tdep_range<2, C>(bc.b1, bc.b2, s_lf, s_kt, nt, jt, wt, d, acc, acc0, any_zero, lane, esc);
-        tdep_range<3, C>(bc.b2, bc.b3, s_lf, s_kt, nt, jt, wt, d, acc, acc0, any_zero, lane, esc);
-        tdep_range<5, C>(bc.b3, bc.b5, s_lf, s_kt, nt, jt, wt, d, acc, acc0, any_zero, lane, esc);
-        tdep_range<6, C>(bc.b5, na, s_lf, s_kt, nt, jt, wt, d, acc, acc0, any_zero, lane, esc);
+        tdep_range<1, C>(0, bc.b1, s_lf, s_kt, nt, jt, wt, d.v, acc.v, acc0.v, any_zero, lane, esc);
+        tdep_range<2, C>(bc.b1, bc.b2, s_lf, s_kt, nt, jt, wt, d.v, acc.v, acc0.v, any_zero, lane, esc);
+        tdep_range<3, C>(bc.b2, bc.b3, s_lf, s_kt, nt, jt, wt, d.v, acc.v, acc0.v, any_zero, lane, esc);
+        tdep_range<5, C>(bc.b3, bc.b5, s_lf, s_kt, nt, jt, wt, d.v, acc.v, acc0.v, any_zero, lane, esc);
+        tdep_range<6, C>(bc.b5, na, s_lf, s_kt, nt, jt, wt, d.v, acc.v, acc0.v, any_zero, lane, esc);
 
         const float w = __ldg(p.domega32 + ray);
         if (lane == 31) eesc.add(esc * w);
@@ -175,9 +175,10 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray_tdep(const TraceArgs p, co
 #pragma unroll
         for (int j = 0; j < C; ++j) {
             const bool zc = (zero_m >> j) & 1u;
-            const float qv = zc ? 0.0f : s_gq[j][lane] * acc[j];
-            const float av = s_ga[j][lane] * (zc ? acc0[j] : (d[j] > 0.0f ? __fdividef(acc[j], d[j]) : 0.0f));
-            lane_abs += (j < nv && !zc) ? acc[j] : 0.0f;
+            const float aj = acc.get(j), dj = d.get(j);
+            const float qv = zc ? 0.0f : s_gq[j][lane] * aj;
+            const float av = s_ga[j][lane] * (zc ? acc0.get(j) : (dj > 0.0f ? __fdividef(aj, dj) : 0.0f));
+            lane_abs += (j < nv && !zc) ? aj : 0.0f;
             if (j < nv) {
                 p.q[base + j] = qv;
                 p.a[base + j] = av;
