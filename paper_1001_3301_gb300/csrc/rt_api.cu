@@ -49,7 +49,7 @@ struct rt_ctx {
     // device staging for the host-buffer entry point, and its copy pipeline
     float *h_rho = nullptr, *h_t = nullptr, *h_q = nullptr, *h_a = nullptr;
     cudaStream_t s_in = nullptr, s_out = nullptr;
-    cudaEvent_t ev_in[8] = {}, ev_done[8] = {}, ev_start = nullptr;
+    cudaEvent_t ev_in[8] = {}, ev_done[8] = {}, ev_start = nullptr;  // kHostChunks entries
 
     // host copies of the table as the tracer uses it, and its fingerprint
     std::vector<double> nu_h, kappa_h;
@@ -87,6 +87,7 @@ namespace {
 thread_local std::string g_create_err;
 
 constexpr int kHostChunks = 8;  // most ray chunks of the host-buffer pipeline
+static_assert(sizeof(rt_ctx::ev_in) / sizeof(cudaEvent_t) == kHostChunks, "one event pair per chunk");
 
 int fail(rt_ctx *ctx, int status, const std::string &msg)
 {
@@ -674,6 +675,8 @@ int rt_irradiate_host(rt_ctx *ctx, const float *rho, const float *t_dust, float 
         RT_CK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_in[k], 0));
         st = trace_range(ctx, ctx->h_rho, ctx->h_t, ctx->h_q, ctx->h_a, ctx->shape, r0, r1, ctx->stream, &npart);
         if (st != RT_OK) return st;
+        if (k == nch - 1 && !energy)  // the validity word, ahead of the last copies out
+            RT_CK(ctx, cudaMemcpyAsync(ctx->bad_h, ctx->bad, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
         RT_CK(ctx, cudaEventRecord(ctx->ev_done[k], ctx->stream));
         RT_CK(ctx, cudaStreamWaitEvent(ctx->s_out, ctx->ev_done[k], 0));
         RT_CK(ctx, cudaMemcpyAsync(q_abs + off, ctx->h_q + off, n, cudaMemcpyDeviceToHost, ctx->s_out));
@@ -687,10 +690,8 @@ int rt_irradiate_host(rt_ctx *ctx, const float *rho, const float *t_dust, float 
         RT_CK(ctx, cudaStreamSynchronize(ctx->s_out));
         return st;
     }
+    // s_out's last copies follow the last trace and the validity word (event order)
     RT_CK(ctx, cudaStreamSynchronize(ctx->s_out));
-    RT_CK(ctx, cudaStreamSynchronize(ctx->stream));
-    RT_CK(ctx, cudaMemcpyAsync(ctx->bad_h, ctx->bad, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
-    RT_CK(ctx, cudaStreamSynchronize(ctx->stream));
     if (*ctx->bad_h == ctx->seq)
         return fail(ctx, RT_ERR_NONFINITE_INPUT, "input field holds NaN/Inf/negative density or NaN temperature");
     return RT_OK;
