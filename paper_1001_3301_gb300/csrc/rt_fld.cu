@@ -855,8 +855,10 @@ __device__ __forceinline__ float4 apply_quad(const MgLevel &F, const VR &vrow, c
 }
 
 // k_mg_down on the finest level: one thread per pair of coarse cells (K0, K0 + 1)
-// of one coarse row, i.e. the four-cell quads of the fine rows in the aggregate
-__global__ void __launch_bounds__(256) k_mg_down4(const MgPair P)
+// of one coarse row, i.e. the four-cell quads of the fine rows in the aggregate.
+// (Five CTAs per SM: 48 registers and a few bytes of spill measured 1.2 % faster per
+// FLD step than four CTAs at 54 registers; the same for k_mg_up4.)
+__global__ void __launch_bounds__(256, 5) k_mg_down4(const MgPair P)
 {
     if (P.cg.scal[kDone] != 0.0) return;
     const MgLevel &F = P.f, &C = P.c;
@@ -889,7 +891,7 @@ __global__ void __launch_bounds__(256) k_mg_down4(const MgPair P)
 }
 
 // k_mg_up on the finest level (top), four cells per thread
-__global__ void __launch_bounds__(256) k_mg_up4(const MgPair P, int init)
+__global__ void __launch_bounds__(256, 5) k_mg_up4(const MgPair P, int init)
 {
     if (P.cg.scal[kDone] != 0.0) return;
     const MgLevel &F = P.f, &C = P.c;
