@@ -56,7 +56,7 @@ FLD_SETUP_MG_B, FLD_PASS_MG_B, FLD_ITER_MG_B = 88, 112, 120
 # absorbed fraction 1 - e^{-dtau} needs a second one only where dtau is not small.
 EXP_PER_CELL_NU = 1
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_ray_disk3d_256x128x256_nu79.md")
-KERNEL_SOURCES = ("rt_ray.cu", "rt_device.cuh")
+KERNEL_SOURCES = ("rt_ray.cu", "rt_ray.cuh", "rt_device.cuh")
 
 
 def parse():

@@ -236,14 +236,19 @@ int rt_batch_run(rt_batch *b, const float *const *rho, const float *const *t_dus
  * values (energies are still filled). */
 int rt_batch_energy(rt_batch *b, rt_energy *energies);
 
-/* rt_batch_autotune -- time every compiled tile shape of the batch's precision on
- * the given fields (overwriting q_abs and a_rad), keep the fastest and rebuild the
- * graph. reps >= 1. Synchronises. rt_batch_get_tuning reports the shape in use
- * (kind is always RT_KERNEL_TILE). */
+/* rt_batch_autotune -- time every compiled shape of the batch's precision on the
+ * given fields (overwriting q_abs and a_rad), keep the fastest and rebuild the
+ * graph. reps >= 1. Synchronises. The shapes are tiles of the flattened grids
+ * (RT_KERNEL_TILE, any nr) and, where every grid has nr <= 32 cells_per_lane,
+ * warp-per-ray bodies (RT_KERNEL_RAY; 8, 16 or 32 lanes per ray chosen per grid).
+ * rt_batch_get_tuning reports the shape in use; rt_batch_set_tuning selects one
+ * (RT_ERR_INVALID_ARG if no such shape is compiled for the batch's precision or a
+ * grid's rays do not fit it; min_blocks_per_sm 0 = any) and rebuilds the graph. */
 int rt_batch_autotune(rt_batch *b, const float *const *rho, const float *const *t_dust,
                       float *const *q_abs, float *const *a_rad, int reps);
 int rt_batch_get_tuning(const rt_batch *b, int *kind, int *cells_per_lane, int *warps_per_block,
                         int *min_blocks_per_sm);
+int rt_batch_set_tuning(rt_batch *b, int kind, int cells_per_lane, int warps_per_block, int min_blocks_per_sm);
 
 /* rt_batch_last_error -- text of the batch's last failure ("" if none). */
 const char *rt_batch_last_error(const rt_batch *b);

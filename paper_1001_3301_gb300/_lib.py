@@ -101,6 +101,7 @@ SIGNATURES = {
     "rt_batch_autotune": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
                                ctypes.POINTER(_P), _I]),
     "rt_batch_get_tuning": (_I, [_P] + [ctypes.POINTER(_I)] * 4),
+    "rt_batch_set_tuning": (_I, [_P, _I, _I, _I, _I]),
     "rt_batch_last_error": (ctypes.c_char_p, [_P]),
     "rt_batch_destroy": (None, [_P]),
     "rt_irradiate_static": (_I, [ctypes.POINTER(RtGridDesc), _D, _D, _I, _DP, _DP, _D, _I,

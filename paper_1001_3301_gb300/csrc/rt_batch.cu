@@ -8,13 +8,17 @@
 // partial per (grid, CTA). A second small kernel reduces the partials of every
 // grid in FP64. Both kernels and the partials reset form a CUDA graph built once;
 // each run only replaces the field pointers in the tracer node and replays it.
-// The tile shape comes from rt_batch_autotune (timed on the caller's buffers) or,
+// Two kernel families: the tile body of rt_tile.cuh (any nr; work units are tiles),
+// and the warp-per-ray body of rt_ray.cuh (every grid with nr <= 32 C; work units
+// are warp-slots of 32 / G rays, G = 8, 16 or 32 lanes per ray chosen per grid).
+// The shape comes from rt_batch_autotune (timed on the caller's buffers) or,
 // before that, from a fixed default.
 #include <string.h>
 
 #include <string>
 #include <vector>
 
+#include "rt_ray.cuh"
 #include "rt_tile.cuh"
 
 namespace rt {
@@ -22,8 +26,8 @@ namespace {
 
 struct BatchParams {
     const TraceArgs *grids;          // [n] tables and sizes of every grid
-    const unsigned *grid_tile_begin; // [n+1] first global tile of every grid
-    const unsigned *cta_begin;       // [G+1] first global tile of every CTA
+    const unsigned *grid_tile_begin; // [n+1] first global work unit (tile or warp-slot) of every grid
+    const unsigned *cta_begin;       // [G+1] first global work unit of every CTA
     double2 *partials;               // [n * G] (absorbed, escaped) per grid and CTA
     unsigned seq;                    // call number, stored in the validity word on bad input
     int n;
@@ -72,6 +76,65 @@ __global__ void __launch_bounds__(W * 32, MINB) k_batch(const __grid_constant__ 
     }
 }
 
+// Lanes per ray of grid p for C cells per lane: the fewest of 8, 16, 32 that hold
+// the ray (nr <= 32 C for every grid of a ray-kind batch).
+__host__ __device__ __forceinline__ int ray_lanes_for(int nr, int C)
+{
+    return nr <= 8 * C ? 8 : (nr <= 16 * C ? 16 : 32);
+}
+
+// The warp-per-ray batch: each CTA walks its range of warp-slots grid by grid,
+// staging the grid's descriptor and tables in shared memory at every change.
+template <int C, int W, int MODE, int MINB>
+__global__ void __launch_bounds__(W * 32, MINB) k_batch_ray(const __grid_constant__ BatchParams bp)
+{
+    __shared__ TraceArgs s_p;
+    __shared__ RayShared<C> rs;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const unsigned T0 = bp.cta_begin[blockIdx.x], T1 = bp.cta_begin[blockIdx.x + 1];
+    if (T0 >= T1) return;
+    const int warp = threadIdx.x >> 5;
+    int lo = 0, hi = bp.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (bp.grid_tile_begin[mid + 1] > T0) hi = mid;
+        else lo = mid + 1;
+    }
+    unsigned t = T0;
+    for (int g = lo; t < T1 && g < bp.n; ++g) {
+        const unsigned gb = bp.grid_tile_begin[g], ge = bp.grid_tile_begin[g + 1];
+        const unsigned seg_end = T1 < ge ? T1 : ge;
+        if (seg_end <= t) continue;
+        __syncthreads();  // everyone is done with the previous grid's tables
+        if (threadIdx.x == 0) {
+            s_p = bp.grids[g];
+            s_p.rho = bp.rho[g];
+            s_p.tdust = bp.tdust[g];
+            s_p.q = bp.q[g];
+            s_p.a = bp.a[g];
+            s_p.seq = bp.seq;
+        }
+        __syncthreads();
+        const int G = ray_lanes_for(s_p.nr, C);
+        float *s_kap = reinterpret_cast<float *>(smem);
+        float4 *s_nu = reinterpret_cast<float4 *>(s_kap + s_p.nnu_pad);
+        float4 *s_mom = s_nu + s_p.nnu_pad;
+        ray_tables<C, W>(s_p, G, rs, s_kap, s_nu, s_mom);
+        __syncthreads();
+        KahanSum eabs, eesc;
+        eabs.zero();
+        eesc.zero();
+        const unsigned w0 = t - gb + warp, w1 = seg_end - gb;
+        if (G == 8) ray_slots<C, W, MODE, 8>(s_p, w0, w1, W, rs, s_kap, s_nu, s_mom, eabs, eesc);
+        else if (G == 16) ray_slots<C, W, MODE, 16>(s_p, w0, w1, W, rs, s_kap, s_nu, s_mom, eabs, eesc);
+        else ray_slots<C, W, MODE, 32>(s_p, w0, w1, W, rs, s_kap, s_nu, s_mom, eabs, eesc);
+        block_energy<W>(eabs, eesc);
+        if (threadIdx.x == 0)
+            bp.partials[(size_t)g * gridDim.x + blockIdx.x] = make_double2(to_double(eabs), to_double(eesc));
+        t = seg_end;
+    }
+}
+
 // One block per grid: FP64 sum of its partials and the energy bookkeeping of
 // rt_energy (the same formulas as the single-grid reduction).
 __global__ void k_batch_energy(const double2 *partials, unsigned G, const DevScalars *const *sc,
@@ -109,18 +172,22 @@ __global__ void k_batch_energy(const double2 *partials, unsigned G, const DevSca
 using BatchKernel = void (*)(BatchParams);
 
 struct BatchShape {
+    int kind;  // RT_KERNEL_TILE or RT_KERNEL_RAY
     int precision, c, w, minb;
     BatchKernel kern;
 };
 
-#define RT_BSHAPE(P, C, W, MB) {P, C, W, MB, &k_batch<C, W, P, MB>}
+#define RT_BSHAPE(P, C, W, MB) {RT_KERNEL_TILE, P, C, W, MB, &k_batch<C, W, P, MB>}
+#define RT_BRAY(P, C, W, MB) {RT_KERNEL_RAY, P, C, W, MB, &k_batch_ray<C, W, P, MB>}
 const BatchShape kBatchShapes[] = {
     RT_BSHAPE(RT_FP32_KAHAN, 2, 4, 8), RT_BSHAPE(RT_FP32_KAHAN, 4, 4, 8), RT_BSHAPE(RT_FP32_KAHAN, 4, 8, 4),
     RT_BSHAPE(RT_FP32_KAHAN, 8, 4, 6), RT_BSHAPE(RT_FP32_KAHAN, 8, 4, 5), RT_BSHAPE(RT_FP32_KAHAN, 8, 8, 3),
-    RT_BSHAPE(RT_FP32_PLAIN, 4, 4, 8), RT_BSHAPE(RT_FP32_PLAIN, 8, 4, 6), RT_BSHAPE(RT_FP64, 2, 4, 8),
-    RT_BSHAPE(RT_FP64, 4, 4, 4),
+    RT_BRAY(RT_FP32_KAHAN, 8, 4, 6),   RT_BRAY(RT_FP32_KAHAN, 16, 4, 3), RT_BRAY(RT_FP32_KAHAN, 16, 4, 4),
+    RT_BSHAPE(RT_FP32_PLAIN, 4, 4, 8), RT_BSHAPE(RT_FP32_PLAIN, 8, 4, 6), RT_BRAY(RT_FP32_PLAIN, 16, 4, 4),
+    RT_BSHAPE(RT_FP64, 2, 4, 8),       RT_BSHAPE(RT_FP64, 4, 4, 4),
 };
 #undef RT_BSHAPE
+#undef RT_BRAY
 
 }  // namespace
 }  // namespace rt
@@ -185,13 +252,25 @@ size_t tile_smem(const rt::TraceArgs &a, const BatchShape &s)
     return (size_t)(TS * 6 * 4 + 3 * nrs * 4 + (long long)a.nnu_pad * 4 + (long long)a.nnu_pad * (16 + 32) + 16);
 }
 
-// Shape-dependent plan: tile ranges per CTA balanced by cost, partials, graph.
+// whether every grid of the batch fits the warp-per-ray body of shape s
+bool ray_fits(const rt_batch *b, const BatchShape &s)
+{
+    for (const rt::CtxView &v : b->views)
+        if (v.args.nr > 32 * s.c) return false;
+    return true;
+}
+
+// Shape-dependent plan: work-unit ranges per CTA balanced by cost, partials, graph.
+// Units are tiles of 32 W C flattened cells (tile kind) or warp-slots of 32 / G rays
+// (ray kind); either costs about (bins + 6) per cell of 32 C (tile: 32 W C) cells.
 int plan(rt_batch *b, const BatchShape *s)
 {
     const int n = b->n;
+    const bool ray = s->kind == RT_KERNEL_RAY;
     const long long T = 32LL * s->w * s->c;
     size_t smem = 0;
-    for (const rt::CtxView &v : b->views) smem = std::max(smem, tile_smem(v.args, *s));
+    for (const rt::CtxView &v : b->views)
+        smem = std::max(smem, ray ? rt::ray_bin_smem(v.args.nnu_pad) + 16 : tile_smem(v.args, *s));
     if (smem > 48 * 1024)
         RT_BCK(b, cudaFuncSetAttribute(s->kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int nsm = 0, per_sm = 0;
@@ -203,7 +282,13 @@ int plan(rt_batch *b, const BatchShape *s)
     std::vector<unsigned> gtb(n + 1, 0);
     std::vector<double> cost_before(n + 1, 0.0);
     for (int g = 0; g < n; ++g) {
-        const long long nt = (b->views[g].flat_cells + T - 1) / T;
+        long long nt;
+        if (ray) {
+            const int R = 32 / rt::ray_lanes_for(b->views[g].args.nr, s->c);
+            nt = ((long long)b->views[g].args.nrays + R - 1) / R;
+        } else {
+            nt = (b->views[g].flat_cells + T - 1) / T;
+        }
         gtb[g + 1] = gtb[g] + (unsigned)nt;
         cost_before[g + 1] = cost_before[g] + (double)nt * (b->views[g].args.nnu_pad + 6);
     }
@@ -386,9 +471,13 @@ int rt_batch_create(rt_ctx *const *ctxs, int n, void *cuda_stream, rt_batch **ou
     // default shape: 8-cell tiles (4-cell for FP64)
     const BatchShape *def = nullptr;
     for (const BatchShape &s : rt::kBatchShapes)
-        if (s.precision == b->precision && !def) def = &s;
+        if (s.precision == b->precision && s.kind == RT_KERNEL_TILE && !def) def = &s;
     for (const BatchShape &s : rt::kBatchShapes)
-        if (s.precision == b->precision && s.c == (b->precision == RT_FP64 ? 4 : 8) && s.w == 4) { def = &s; break; }
+        if (s.precision == b->precision && s.kind == RT_KERNEL_TILE && s.c == (b->precision == RT_FP64 ? 4 : 8) &&
+            s.w == 4) {
+            def = &s;
+            break;
+        }
     int st = plan(b, def);
     if (st != RT_OK) {
         rt::set_thread_error(b->err);
@@ -440,6 +529,7 @@ int rt_batch_autotune(rt_batch *b, const float *const *rho, const float *const *
     int st = RT_OK;
     for (const BatchShape &s : rt::kBatchShapes) {
         if (s.precision != b->precision) continue;
+        if (s.kind == RT_KERNEL_RAY && !ray_fits(b, s)) continue;
         st = plan(b, &s);
         if (st != RT_OK) break;
         st = rt_batch_run(b, rho, t_dust, q_abs, a_rad);  // warm-up
@@ -463,11 +553,26 @@ int rt_batch_get_tuning(const rt_batch *b, int *kind, int *cells_per_lane, int *
                         int *min_blocks_per_sm)
 {
     if (!b || !kind || !cells_per_lane || !warps_per_block || !min_blocks_per_sm) return RT_ERR_INVALID_ARG;
-    *kind = RT_KERNEL_TILE;
+    *kind = b->shape->kind;
     *cells_per_lane = b->shape->c;
     *warps_per_block = b->shape->w;
     *min_blocks_per_sm = b->shape->minb;
     return RT_OK;
+}
+
+int rt_batch_set_tuning(rt_batch *b, int kind, int cells_per_lane, int warps_per_block, int min_blocks_per_sm)
+{
+    if (!b) return RT_ERR_INVALID_ARG;
+    RT_BCK(b, cudaSetDevice(b->dev));
+    for (const BatchShape &s : rt::kBatchShapes) {
+        if (s.precision != b->precision || s.kind != kind || s.c != cells_per_lane || s.w != warps_per_block ||
+            (min_blocks_per_sm != 0 && s.minb != min_blocks_per_sm))
+            continue;
+        if (s.kind == RT_KERNEL_RAY && !ray_fits(b, s))
+            return bfail(b, RT_ERR_INVALID_ARG, "a grid of the batch has more radial cells than 32 cells_per_lane");
+        return plan(b, &s);
+    }
+    return bfail(b, RT_ERR_INVALID_ARG, "no such batch shape for this precision");
 }
 
 const char *rt_batch_last_error(const rt_batch *b) { return b ? b->err.c_str() : rt_last_error(nullptr); }

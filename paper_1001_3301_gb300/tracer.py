@@ -415,6 +415,11 @@ class Batch:
                                           self._ptrs(q_abs, "q_abs"), self._ptrs(a_rad, "a_rad"), int(reps)))
         return self.tuning()
 
+    def set_tuning(self, kind: int, cells_per_lane: int, warps: int, min_blocks: int = 0):
+        """Select a compiled batch shape (kind 0 = tiles, 1 = warp per ray) and rebuild the graph."""
+        self._check(lib.rt_batch_set_tuning(self._b, int(kind), int(cells_per_lane), int(warps), int(min_blocks)))
+        return self.tuning()
+
     def tuning(self):
         v = [ctypes.c_int() for _ in range(4)]
         self._check(lib.rt_batch_get_tuning(self._b, *[ctypes.byref(x) for x in v]))

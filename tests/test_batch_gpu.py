@@ -67,7 +67,7 @@ def test_batch_against_oracle_every_shape(torch):
             _parity.assert_parity(w, qq.double().cpu().numpy(), aa.double().cpu().numpy(), e, o,
                                   label=w.name)
         shape = b.autotune(rho, td, q, a, reps=2)
-        assert shape[0] == 0
+        assert shape[0] in (0, 1)
         for rep in range(2):  # graph replays after the autotuner rebuilt the plan
             for x in q + a:
                 x.fill_(float("nan"))
@@ -76,6 +76,38 @@ def test_batch_against_oracle_every_shape(torch):
             for w, o, qq, aa, e in zip(ws, orcs, q, a, es):
                 _parity.assert_parity(w, qq.double().cpu().numpy(), aa.double().cpu().numpy(), e, o,
                                       label=f"{w.name} rep {rep}")
+    for tr in trs:
+        tr.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 16, 4, 3), (1, 16, 4, 4), (1, 8, 4, 6)])
+def test_batch_warp_per_ray_shapes(torch, shape):
+    """The warp-per-ray batch body (8, 16 or 32 lanes per ray chosen per grid)
+    against the oracle; shapes whose rays cannot hold a grid are refused."""
+    from paper_1001_3301_gb300 import Batch, RtError
+    specs = SMALL if shape[1] == 16 else [s for s in SMALL if s["nr"] <= 256]
+    ws = _make(specs)
+    trs = _tracers(ws)
+    rho, td, q, a = _fields(torch, ws)
+    orcs = [_parity.oracle_for(w) for w in ws]
+    with Batch(trs) as b:
+        assert b.set_tuning(*shape) == shape
+        for rep in range(2):
+            for x in q + a:
+                x.fill_(float("nan"))
+            b.run(rho, td, q, a)
+            es = b.energy()
+            for w, o, qq, aa, e in zip(ws, orcs, q, a, es):
+                _parity.assert_parity(w, qq.double().cpu().numpy(), aa.double().cpu().numpy(), e, o,
+                                      label=f"{w.name} {shape} rep {rep}")
+    if shape[1] == 8:  # the 512-cell rays do not fit 32 lanes x 8 cells
+        big = _make([s for s in SMALL if s["nr"] > 256][:2])
+        trs2 = _tracers(big)
+        with Batch(trs2) as b2:
+            with pytest.raises(RtError, match="INVALID"):
+                b2.set_tuning(*shape)
+        for tr in trs2:
+            tr.close()
     for tr in trs:
         tr.close()
 
