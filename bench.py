@@ -405,8 +405,12 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
+            # the step's grids in flight together (copies of one grid overlap the
+            # trace and copies of the others), then every grid's outputs on the host
             for i, tr in enumerate(tracers):
-                tr.irradiate_host(h_rho[i], h_td[i], h_q[i], h_a[i])
+                tr.irradiate_host_async(h_rho[i], h_td[i], h_q[i], h_a[i])
+            for tr in tracers:
+                tr.host_wait()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         if dist:

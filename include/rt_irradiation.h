@@ -154,6 +154,20 @@ int rt_irradiate(rt_ctx *ctx, const float *rho, const float *t_dust, float *q_ab
 int rt_irradiate_host(rt_ctx *ctx, const float *rho, const float *t_dust, float *q_abs,
                       float *a_rad, rt_energy *energy);
 
+/* rt_irradiate_host_async -- rt_irradiate_host without the wait: the copies in, the
+ * trace and the copies out are enqueued and the call returns, so that the calls of
+ * several contexts overlap on the link. The host buffers must stay untouched (rho,
+ * t_dust) and unread (q_abs, a_rad) until rt_host_wait(ctx) returns. One call is in
+ * flight per context: a new host call on the context first waits for the previous
+ * one (and returns its RT_ERR_NONFINITE_INPUT, if any). Errors: as
+ * rt_irradiate_host, except that invalid input is reported by rt_host_wait. */
+int rt_irradiate_host_async(rt_ctx *ctx, const float *rho, const float *t_dust, float *q_abs, float *a_rad);
+
+/* rt_host_wait -- wait until the last rt_irradiate_host_async of the context has
+ * copied its outputs back; RT_ERR_NONFINITE_INPUT if its input fields held invalid
+ * values. RT_OK at once if no asynchronous call is pending. */
+int rt_host_wait(rt_ctx *ctx);
+
 /* rt_energy_last -- energy sums of the most recent trace on this context (runs the
  * FP64 reduction of its per-tile partial sums, synchronises the stream).
  * Errors: RT_ERR_NOT_CONFIGURED (nothing traced yet), RT_ERR_CUDA,

@@ -85,6 +85,8 @@ SIGNATURES = {
     "rt_set_opacity_table_t": (_I, [_P, _I, _DP, _I, _DP, _DP, _D]),
     "rt_irradiate": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(RtEnergy)]),
     "rt_irradiate_host": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(RtEnergy)]),
+    "rt_irradiate_host_async": (_I, [_P, _P, _P, _P, _P]),
+    "rt_host_wait": (_I, [_P]),
     "rt_energy_last": (_I, [_P, ctypes.POINTER(RtEnergy)]),
     "rt_get_bins": (_I, [_P, _DP]),
     "rt_set_tuning": (_I, [_P, _I, _I, _I, _I]),

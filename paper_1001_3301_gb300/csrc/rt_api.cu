@@ -50,6 +50,8 @@ struct rt_ctx {
     float *h_rho = nullptr, *h_t = nullptr, *h_q = nullptr, *h_a = nullptr;
     cudaStream_t s_in = nullptr, s_out = nullptr;
     cudaEvent_t ev_in[8] = {}, ev_done[8] = {}, ev_start = nullptr;  // kHostChunks entries
+    cudaEvent_t ev_out = nullptr;  // the last host call's copies out are done
+    bool host_pending = false;     // an asynchronous host call has not been waited for
 
     // host copies of the table as the tracer uses it, and its fingerprint
     std::vector<double> nu_h, kappa_h;
@@ -624,12 +626,14 @@ int rt_irradiate(rt_ctx *ctx, const float *rho, const float *t_dust, float *q_ab
     return read_energy(ctx, energy);
 }
 
-int rt_irradiate_host(rt_ctx *ctx, const float *rho, const float *t_dust, float *q_abs,
-                      float *a_rad, rt_energy *energy)
+namespace {
+// Enqueue the host-buffer pipeline of one call (no synchronisation). With energy
+// the validity word is left to read_energy; otherwise it is copied to bad_h ahead
+// of the last copies out, and ev_out marks the end of the call's copies.
+int host_enqueue(rt_ctx *ctx, const float *rho, const float *t_dust, float *q_abs, float *a_rad, bool energy)
 {
     int st = check_call(ctx, rho, t_dust, q_abs, a_rad);
     if (st != RT_OK) return st;
-    const size_t bytes = sizeof(float) * (size_t)ctx->ncells;
     if (!ctx->h_rho) {
         bool ok = dalloc(&ctx->h_rho, ctx->ncells) == cudaSuccess &&
                   dalloc(&ctx->h_t, ctx->ncells) == cudaSuccess &&
@@ -640,7 +644,6 @@ int rt_irradiate_host(rt_ctx *ctx, const float *rho, const float *t_dust, float 
             return fail(ctx, RT_ERR_NO_MEMORY, "cannot allocate device staging buffers");
         }
     }
-    (void)bytes;
     // Pipeline over ray chunks: the copies in of chunk k+1 (stream s_in) and out of
     // chunk k-1 (stream s_out, the other direction of the link) overlap the trace of
     // chunk k on the context's stream.
@@ -650,8 +653,10 @@ int rt_irradiate_host(rt_ctx *ctx, const float *rho, const float *t_dust, float 
         for (int k = 0; ok && k < kHostChunks; ++k)
             ok = cudaEventCreateWithFlags(&ctx->ev_in[k], cudaEventDisableTiming) == cudaSuccess &&
                  cudaEventCreateWithFlags(&ctx->ev_done[k], cudaEventDisableTiming) == cudaSuccess;
-        ok = ok && cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) == cudaSuccess;
         if (!ok) return cuda_fail(ctx, "host pipeline streams", cudaGetLastError());
+        RT_CK(ctx, cudaEventRecord(ctx->ev_out, ctx->s_out));
     }
     const long long cells_min = 1LL << 20;  // at least ~1 M cells per chunk
     int nch = (int)std::min<long long>(kHostChunks, std::max<long long>(1, ctx->ncells / cells_min));
@@ -662,7 +667,9 @@ int rt_irradiate_host(rt_ctx *ctx, const float *rho, const float *t_dust, float 
     st = ensure_partials(ctx, bound);
     if (st != RT_OK) return st;
     ++ctx->seq;
-    // the staging buffers are free once earlier work on the context's stream is done
+    // the staging buffers are free once earlier traces (context stream) and the
+    // previous call's copies out (ev_out) are done
+    RT_CK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_out, 0));
     RT_CK(ctx, cudaEventRecord(ctx->ev_start, ctx->stream));
     RT_CK(ctx, cudaStreamWaitEvent(ctx->s_in, ctx->ev_start, 0));
     long long npart = 0;
@@ -682,19 +689,59 @@ int rt_irradiate_host(rt_ctx *ctx, const float *rho, const float *t_dust, float 
         RT_CK(ctx, cudaMemcpyAsync(q_abs + off, ctx->h_q + off, n, cudaMemcpyDeviceToHost, ctx->s_out));
         RT_CK(ctx, cudaMemcpyAsync(a_rad + off, ctx->h_a + off, n, cudaMemcpyDeviceToHost, ctx->s_out));
     }
+    RT_CK(ctx, cudaEventRecord(ctx->ev_out, ctx->s_out));
     ctx->last_ntiles = npart;
     ctx->traced = true;
-    if (energy) {
-        st = read_energy(ctx, energy);
-        if (st != RT_OK && st != RT_ERR_NONFINITE_INPUT) return st;
-        RT_CK(ctx, cudaStreamSynchronize(ctx->s_out));
-        return st;
-    }
-    // s_out's last copies follow the last trace and the validity word (event order)
-    RT_CK(ctx, cudaStreamSynchronize(ctx->s_out));
+    return RT_OK;
+}
+
+// Wait for the copies out of the last host call; its validity word was copied ahead
+// of them.
+int host_wait(rt_ctx *ctx)
+{
+    RT_CK(ctx, cudaEventSynchronize(ctx->ev_out));
+    ctx->host_pending = false;
     if (*ctx->bad_h == ctx->seq)
         return fail(ctx, RT_ERR_NONFINITE_INPUT, "input field holds NaN/Inf/negative density or NaN temperature");
     return RT_OK;
+}
+}  // namespace
+
+int rt_irradiate_host(rt_ctx *ctx, const float *rho, const float *t_dust, float *q_abs,
+                      float *a_rad, rt_energy *energy)
+{
+    if (ctx && ctx->host_pending) {
+        const int w = host_wait(ctx);
+        if (w != RT_OK && w != RT_ERR_NONFINITE_INPUT) return w;
+    }
+    int st = host_enqueue(ctx, rho, t_dust, q_abs, a_rad, energy != nullptr);
+    if (st != RT_OK) return st;
+    if (energy) {
+        st = read_energy(ctx, energy);
+        if (st != RT_OK && st != RT_ERR_NONFINITE_INPUT) return st;
+        RT_CK(ctx, cudaEventSynchronize(ctx->ev_out));
+        return st;
+    }
+    return host_wait(ctx);
+}
+
+int rt_irradiate_host_async(rt_ctx *ctx, const float *rho, const float *t_dust, float *q_abs, float *a_rad)
+{
+    if (ctx && ctx->host_pending) {  // one call in flight per context: the last one's validity word
+        const int w = host_wait(ctx);
+        if (w != RT_OK) return w;
+    }
+    const int st = host_enqueue(ctx, rho, t_dust, q_abs, a_rad, false);
+    if (st == RT_OK) ctx->host_pending = true;
+    return st;
+}
+
+int rt_host_wait(rt_ctx *ctx)
+{
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (!ctx->host_pending) return RT_OK;
+    RT_CK(ctx, cudaSetDevice(ctx->dev));
+    return host_wait(ctx);
 }
 
 int rt_energy_last(rt_ctx *ctx, rt_energy *out)
@@ -815,6 +862,7 @@ void rt_destroy(rt_ctx *ctx)
             if (ctx->ev_done[k]) cudaEventDestroy(ctx->ev_done[k]);
         }
         if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
+        if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
     }
     free_all(ctx);
     delete ctx;

@@ -123,6 +123,18 @@ class Tracer:
         check(lib.rt_irradiate_host(self._ctx, *ptrs, ctypes.byref(e) if energy else None), self._ctx)
         return Energy(e) if energy else None
 
+    def irradiate_host_async(self, rho, t_dust, q_abs, a_rad):
+        """Host-buffer variant that returns once the copies and the trace are enqueued;
+        keep the buffers alive and untouched until host_wait()."""
+        ptrs = []
+        for x, name in ((rho, "rho"), (t_dust, "t_dust"), (q_abs, "q_abs"), (a_rad, "a_rad")):
+            ptrs.append(_host_ptr(x, self.nr * self.ntheta * self.nphi, name))
+        check(lib.rt_irradiate_host_async(self._ctx, *ptrs), self._ctx)
+
+    def host_wait(self):
+        """Wait for the last irradiate_host_async's outputs (raises on invalid input)."""
+        check(lib.rt_host_wait(self._ctx), self._ctx)
+
     def energy_last(self) -> Energy:
         e = RtEnergy()
         check(lib.rt_energy_last(self._ctx, ctypes.byref(e)), self._ctx)

@@ -356,6 +356,47 @@ def test_host_path_pipelined_chunks():
     tr.close()
 
 
+def test_host_path_async_overlapped_contexts():
+    """Asynchronous host calls of several contexts in flight together, twice in a
+    row on the same buffers (the second call's traces must wait for the first
+    call's copies out of the staging buffers): outputs equal the device path bit for
+    bit; invalid input is reported by host_wait, and the context stays usable."""
+    import torch
+    from paper_1001_3301_gb300 import RtError, Tracer
+    ws = [synth.disk3d(160, 64, 112, n_nu=32, tau550=t, seed=20 + i) for i, t in enumerate((0.3, 3.0, 30.0))]
+    trs, ref, host = [], [], []
+    for w in ws:
+        tr = Tracer.from_grid(w.grid)
+        tr.set_opacity_table(w.nu, w.kappa, w.t_sub)
+        tr.set_star(w.t_star, w.r_star)
+        q, a, _ = tr.irradiate(torch.from_numpy(w.rho32()).cuda(), torch.from_numpy(w.tdust32()).cuda())
+        ref.append((q.cpu(), a.cpu()))
+        trs.append(tr)
+        host.append([torch.from_numpy(w.rho32()).pin_memory(), torch.from_numpy(w.tdust32()).pin_memory(),
+                     torch.empty(w.grid.shape, dtype=torch.float32).pin_memory(),
+                     torch.empty(w.grid.shape, dtype=torch.float32).pin_memory()])
+    for rep in range(2):
+        for h in host:
+            h[2].fill_(-1.0)
+        for _ in range(2):
+            for tr, h in zip(trs, host):
+                tr.irradiate_host_async(*h)
+        for tr in trs:
+            tr.host_wait()
+        for (q, a), h in zip(ref, host):
+            assert torch.equal(h[2], q) and torch.equal(h[3], a)
+    bad = host[1][0].clone().pin_memory()
+    bad.view(-1)[5] = float("nan")
+    trs[1].irradiate_host_async(bad, host[1][1], host[1][2], host[1][3])
+    with pytest.raises(RtError, match="NONFINITE"):
+        trs[1].host_wait()
+    trs[1].host_wait()  # nothing pending any more
+    trs[1].irradiate_host(*host[1])
+    assert torch.equal(host[1][2], ref[1][0])
+    for tr in trs:
+        tr.close()
+
+
 def test_autotune_and_streams():
     import torch
     from paper_1001_3301_gb300 import Tracer
