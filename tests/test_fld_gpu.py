@@ -108,6 +108,8 @@ CASES = [
     ((24, 1, 1), 1e10),     # one theta cell: radial only
     ((40, 24, 16), 1e4),    # three multigrid levels, four-cell kernels
     ((41, 23, 9), 1e4),     # three multigrid levels, odd sizes (one-cell aggregates at the ends)
+    ((48, 24, 1), 1e4),     # multigrid on an axisymmetric grid (no phi aggregation)
+    ((3000, 1, 1), 1e4),    # multigrid along r only (four levels)
 ]
 
 
