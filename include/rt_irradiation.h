@@ -379,7 +379,8 @@ typedef struct rt_fld_stats {
  *   stats       NULL or a host struct for the iteration count and final residual.
  * Finite volumes: harmonic-mean face coefficients, no flux through the inner radius
  * or the theta ends, periodic in phi when nphi > 1 (the wrap distance measured
- * around the full circle). Synchronises the stream every 16 iterations. Errors:
+ * around the full circle). Runs on a private stream ordered after the context's
+ * stream and synchronises it every 8 iterations; returns with e_new complete. Errors:
  * RT_ERR_NOT_CONFIGURED, RT_ERR_INVALID_ARG, RT_ERR_NONFINITE_INPUT (rho < 0,
  * T <= 0, E_old < 0, q_abs < 0 or NaN/Inf; e_new is then unchanged),
  * RT_ERR_TIMEOUT (tol not reached in max_iter; e_new holds the last iterate),
