@@ -376,7 +376,8 @@ typedef struct rt_fld_stats {
  *   conjugate-gradient iterations in total. Grids of more than 512 cells are
  *   preconditioned by an aggregation-multigrid V-cycle (Galerkin coarse levels
  *   halving every direction), smaller ones by Jacobi.
- *   stats       NULL or a host struct for the iteration count and final residual.
+ *   stats       NULL or a host struct: iterations, refinement passes, the last
+ *               pass's relative change and the number of multigrid levels.
  * Finite volumes: harmonic-mean face coefficients, no flux through the inner radius
  * or the theta ends, periodic in phi when nphi > 1 (the wrap distance measured
  * around the full circle). Runs on a private stream ordered after the context's
