@@ -225,7 +225,7 @@ def cpu_baseline(ws, target_s=12.0):
 
 def run_cpu_table(args, local):
     """Oracle (1 core and all cores, bounded ray samples) and GPU tracer (full grid,
-    autotuned) throughput per workload, for the baseline table."""
+    autotuned) throughput per workload, as one table."""
     import torch
     import oracle
     from paper_1001_3301_gb300 import Tracer, probe_alu_rates
