@@ -12,7 +12,8 @@
 // (Catmull-Rom tangents); outside the range it is held constant. Each cell solves
 // 4 y + ln a = ln(E_R + a_rad e^{-L(y)}), y = ln T, L = ln kappa_P, by Newton's
 // method in FP32 (the derivative 4 + w L'(y), 0 <= w <= 1, is positive wherever
-// the mean grows slower than T^4).
+// the mean grows slower than T^4). Where E_R = 0 the equation is
+// 4 y + ln a - ln a_rad + L(y) = 0, solved without an exp or a log per step.
 #include <math.h>
 
 #include <string>
@@ -104,24 +105,40 @@ __global__ void __launch_bounds__(256) k_dust_temperature(const TempArgs p)
             p.t_out[c] = 0.0f;
             continue;
         }
-        // start from 300 K's opacity, then Newton on F(y) = 4 y + ln a - ln(E_R + a_rad e^{-L})
+        // start from 300 K's opacity, then Newton on F(y) = 4 y + ln a - ln(E_R + a_rad e^{-L});
+        // with E_R = 0 that is F = 4 y + ln a - ln a_rad + L(y): no exp or log per step
         float L, dL;
         interp(s, 5.7037825f, p.y0, p.inv_dy, L, dL);
-        float y = 0.25f * (logf(er + ar * expf(-L)) - p.ln_a);
         // Newton converges quadratically: once a step is below 1e-5 the next one
         // reaches the FP32 resolution of ln T, so one more step ends the solve
         bool close = false;
-        for (int it = 0; it < 24; ++it) {
-            interp(s, y, p.y0, p.inv_dy, L, dL);
-            const float src = ar * expf(-L);
-            const float rhs = er + src;
-            const float f = 4.0f * y + p.ln_a - logf(rhs);
-            const float fp = 4.0f + dL * src / rhs;
-            float dy = -f / fmaxf(fp, 0.5f);
-            dy = fminf(fmaxf(dy, -2.0f), 2.0f);
-            y += dy;
-            if (close) break;
-            close = fabsf(dy) < 1e-5f;
+        float y;
+        if (!(er > 0.0f)) {
+            const float c0 = p.ln_a - logf(ar);
+            y = -0.25f * (c0 + L);
+            for (int it = 0; it < 24; ++it) {
+                interp(s, y, p.y0, p.inv_dy, L, dL);
+                const float f = 4.0f * y + c0 + L;
+                float dy = -__fdividef(f, fmaxf(4.0f + dL, 0.5f));  // the step, not the root: fast divide
+                dy = fminf(fmaxf(dy, -2.0f), 2.0f);
+                y += dy;
+                if (close) break;
+                close = fabsf(dy) < 1e-5f;
+            }
+        } else {
+            y = 0.25f * (logf(er + ar * expf(-L)) - p.ln_a);
+            for (int it = 0; it < 24; ++it) {
+                interp(s, y, p.y0, p.inv_dy, L, dL);
+                const float src = ar * expf(-L);
+                const float rhs = er + src;
+                const float f = 4.0f * y + p.ln_a - logf(rhs);
+                const float fp = 4.0f + dL * __fdividef(src, rhs);
+                float dy = -__fdividef(f, fmaxf(fp, 0.5f));
+                dy = fminf(fmaxf(dy, -2.0f), 2.0f);
+                y += dy;
+                if (close) break;
+                close = fabsf(dy) < 1e-5f;
+            }
         }
         p.t_out[c] = expf(y);
     }
