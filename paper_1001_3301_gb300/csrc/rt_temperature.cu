@@ -13,7 +13,8 @@
 // 4 y + ln a = ln(E_R + a_rad e^{-L(y)}), y = ln T, L = ln kappa_P, by Newton's
 // method in FP32 (the derivative 4 + w L'(y), 0 <= w <= 1, is positive wherever
 // the mean grows slower than T^4). Where E_R = 0 the equation is
-// 4 y + ln a - ln a_rad + L(y) = 0, solved without an exp or a log per step.
+// 4 y + L(y) = ln a_rad - ln a: a cell reads y from the tabulated inverse of the left
+// side (built once per table) and polishes it with a Newton step.
 #include <math.h>
 
 #include <string>
@@ -55,11 +56,54 @@ __global__ void k_planck_mean(int n_nodes, const double *t_nodes, int n_nu, cons
     }
 }
 
+// The inverse of X(y) = 4 y + L(y) (y = ln T, L = ln kappa_P by the interpolation the
+// cells use, held constant outside the table) on kTempNodes uniform points of X between
+// X(y_lo) and X(y_hi): with E_R = 0, Eq. 16 reads X(y) = ln a_rad - ln a, so a cell's ln T
+// is this table at its X, polished by a Newton step. One CTA; bisection in FP64.
+// inv[n] = y, inv[n + 0..1] after the table: X(y_lo), X(y_hi).
+__device__ double interp_d(const float *s, double y, double y0, double inv_dy)
+{
+    double u = (y - y0) * inv_dy;
+    if (!(u > 0.0)) return s[0];
+    if (u >= (double)(kTempNodes - 1)) return s[kTempNodes - 1];
+    const int k = min((int)u, kTempNodes - 2);
+    const double t = u - (double)k;
+    const double p0 = s[k], p1 = s[k + 1];
+    const double m0 = 0.5 * (p1 - s[k > 0 ? k - 1 : 0]) * (k > 0 ? 1.0 : 2.0);
+    const double m1 = 0.5 * (s[k + 2 < kTempNodes ? k + 2 : kTempNodes - 1] - p0) * (k + 2 < kTempNodes ? 1.0 : 2.0);
+    const double t2 = t * t, t3 = t2 * t;
+    return (2.0 * t3 - 3.0 * t2 + 1.0) * p0 + (t3 - 2.0 * t2 + t) * m0 + (-2.0 * t3 + 3.0 * t2) * p1 + (t3 - t2) * m1;
+}
+
+__global__ void __launch_bounds__(1024) k_inverse_table(const float *lkp, float *inv, double y0, double y1)
+{
+    __shared__ float s[kTempNodes];
+    for (int i = threadIdx.x; i < kTempNodes; i += blockDim.x) s[i] = lkp[i];
+    __syncthreads();
+    const double inv_dy = (kTempNodes - 1) / (y1 - y0);
+    const double x_lo = 4.0 * y0 + s[0], x_hi = 4.0 * y1 + s[kTempNodes - 1];
+    for (int i = threadIdx.x; i < kTempNodes; i += blockDim.x) {
+        const double x = x_lo + (x_hi - x_lo) * i / (kTempNodes - 1);
+        double lo = y0, hi = y1;
+        for (int it = 0; it < 64; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (4.0 * mid + interp_d(s, mid, y0, inv_dy) < x) lo = mid;
+            else hi = mid;
+        }
+        inv[i] = (float)(0.5 * (lo + hi));
+    }
+    if (threadIdx.x == 0) {
+        inv[kTempNodes] = (float)x_lo;
+        inv[kTempNodes + 1] = (float)x_hi;
+    }
+}
+
 struct TempArgs {
     const float *a_rad;
     const float *e_rad;   // may be null (E_R = 0)
     float *t_out;
     const float *lkp;     // [kTempNodes] ln kappa_P on the uniform ln T grid
+    const float *inv;     // [kTempNodes + 2] ln T on the uniform grid of 4 ln T + ln kappa_P
     long long n;
     float y0, inv_dy;     // grid origin and 1 / spacing
     float ln_a;           // ln of the radiation constant a = 4 sigma / c
@@ -94,8 +138,9 @@ __device__ __forceinline__ void interp(const float *s, float y, float y0, float 
 
 __global__ void __launch_bounds__(256) k_dust_temperature(const TempArgs p)
 {
-    __shared__ float s[kTempNodes];
+    __shared__ float s[kTempNodes], s_inv[kTempNodes + 2];
     for (int i = threadIdx.x; i < kTempNodes; i += blockDim.x) s[i] = p.lkp[i];
+    for (int i = threadIdx.x; i < kTempNodes + 2; i += blockDim.x) s_inv[i] = p.inv[i];
     __syncthreads();
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < p.n;
          c += (long long)gridDim.x * blockDim.x) {
@@ -105,28 +150,35 @@ __global__ void __launch_bounds__(256) k_dust_temperature(const TempArgs p)
             p.t_out[c] = 0.0f;
             continue;
         }
-        // start from 300 K's opacity, then Newton on F(y) = 4 y + ln a - ln(E_R + a_rad e^{-L});
-        // with E_R = 0 that is F = 4 y + ln a - ln a_rad + L(y): no exp or log per step
-        float L, dL;
-        interp(s, 5.7037825f, p.y0, p.inv_dy, L, dL);
-        // Newton converges quadratically: once a step is below 1e-5 the next one
-        // reaches the FP32 resolution of ln T, so one more step ends the solve
-        bool close = false;
-        float y;
+        float L, dL, y;
         if (!(er > 0.0f)) {
-            const float c0 = p.ln_a - logf(ar);
-            y = -0.25f * (c0 + L);
+            // X(y) = 4 y + L(y) = ln a_rad - ln a: the inverse table, then Newton steps
+            // until one is below 2e-6 (quadratic convergence: one step from the table)
+            const float x = logf(ar) - p.ln_a;
+            const float x_lo = s_inv[kTempNodes], x_hi = s_inv[kTempNodes + 1];
+            if (x <= x_lo) {
+                y = 0.25f * (x - s[0]);
+            } else if (x >= x_hi) {
+                y = 0.25f * (x - s[kTempNodes - 1]);
+            } else {
+                float yi, dyi;
+                interp(s_inv, x, x_lo, (float)(kTempNodes - 1) / (x_hi - x_lo), yi, dyi);
+                y = yi;
+            }
             for (int it = 0; it < 24; ++it) {
                 interp(s, y, p.y0, p.inv_dy, L, dL);
-                const float f = 4.0f * y + c0 + L;
-                float dy = -__fdividef(f, fmaxf(4.0f + dL, 0.5f));  // the step, not the root: fast divide
+                float dy = -__fdividef(4.0f * y + L - x, fmaxf(4.0f + dL, 0.5f));  // the step, not the root: fast divide
                 dy = fminf(fmaxf(dy, -2.0f), 2.0f);
                 y += dy;
-                if (close) break;
-                close = fabsf(dy) < 1e-5f;
+                if (fabsf(dy) < 2e-6f) break;
             }
         } else {
+            // Newton on F(y) = 4 y + ln a - ln(E_R + a_rad e^{-L}) from 300 K's opacity;
+            // it converges quadratically: once a step is below 1e-5 the next one reaches
+            // the FP32 resolution of ln T, so one more step ends the solve
+            interp(s, 5.7037825f, p.y0, p.inv_dy, L, dL);
             y = 0.25f * (logf(er + ar * expf(-L)) - p.ln_a);
+            bool close = false;
             for (int it = 0; it < 24; ++it) {
                 interp(s, y, p.y0, p.inv_dy, L, dL);
                 const float src = ar * expf(-L);
@@ -215,7 +267,7 @@ int rt_dust_temperature(rt_ctx *ctx, const float *a_rad, const float *e_rad, flo
     float *&lkp = ctx_temp_table(ctx);
     unsigned long long &fp = ctx_temp_fingerprint(ctx);
     if (!lkp || fp != in.table_fingerprint) {
-        if (!lkp && cudaMalloc(&lkp, sizeof(float) * kTempNodes) != cudaSuccess) {
+        if (!lkp && cudaMalloc(&lkp, sizeof(float) * (2 * kTempNodes + 2)) != cudaSuccess) {
             lkp = nullptr;
             cudaGetLastError();
             return ctx_fail(ctx, RT_ERR_NO_MEMORY, "Planck-mean table");
@@ -226,6 +278,8 @@ int rt_dust_temperature(rt_ctx *ctx, const float *a_rad, const float *e_rad, flo
         std::string err;
         const int rc = planck_means(in, tn, nullptr, lkp, in.stream, err);
         if (rc != RT_OK) return ctx_fail(ctx, rc, err);
+        k_inverse_table<<<1, 1024, 0, in.stream>>>(lkp, lkp + kTempNodes, kTempLnLo, kTempLnHi);
+        if (cudaGetLastError() != cudaSuccess) return ctx_fail(ctx, RT_ERR_CUDA, "inverse temperature table");
         fp = in.table_fingerprint;
     }
     const double sigma = 2.0 * pow(kPi, 5) * pow(kKB, 4) / (15.0 * kH * kH * kH * kC * kC);
@@ -234,6 +288,7 @@ int rt_dust_temperature(rt_ctx *ctx, const float *a_rad, const float *e_rad, flo
     p.e_rad = e_rad;
     p.t_out = t_dust;
     p.lkp = lkp;
+    p.inv = lkp + kTempNodes;
     p.n = in.ncells;
     p.y0 = (float)kTempLnLo;
     p.inv_dy = (float)((kTempNodes - 1) / (kTempLnHi - kTempLnLo));
