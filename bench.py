@@ -42,16 +42,16 @@ def workload_name(taus):
 # algorithmic bytes per cell of the flux-limited-diffusion step (each array read or
 # written once per kernel; stencil neighbours from cache). Set-up: 28 (cell kernel:
 # rho, T, q, E in; F, storage, rhs out) + 36 (faces: 3 in; w[3], s, 1/dg, b out) + 8
-# (start-value copy) + 16 (Galerkin coarsening reads s, w[3]; the coarse levels are
-# 1/8, 1/64, ... of that). Jacobi iteration: 24 (apply: p, s, w[3] in; q out) + 28
-# (update: d, p, q, r, 1/dg in; d, r out) + 16 (direction); per pass 40 (residual) +
-# 12 (accumulate). Multigrid iteration: 24 (apply) + 24 (update: d, p, q, r in; d, r
-# out) + 12 (direction: z, p in; p out) + 24 (restriction: b, 1/dg, s, w[3] in) + 28
-# (prolongation: the same in, z out) + 8 (the coarser levels, 1/7 of the last two);
-# per pass 36 (residual: b, s, w[3], x in; r, d, p out) + 64 (one V-cycle and the
-# direction) + 12 (accumulate)
+# (start-value copy); with multigrid also 10 (BF16 copies of s, w[3], 1/dg) + 16 (the
+# Galerkin coarsening reads s, w[3]; the coarse levels are 1/8, 1/64, ... of that).
+# Jacobi iteration: 24 (apply: p, s, w[3] in; q out) + 28 (update: d, p, q, r, 1/dg in;
+# d, r out) + 16 (direction); per pass 40 (residual) + 12 (accumulate). Multigrid
+# iteration: 24 (apply) + 24 (update: d, p, q, r in; d, r out) + 12 (direction: z, p in;
+# p out) + 14 (restriction: b in FP32, 1/dg, s, w[3] in BF16) + 18 (prolongation: the
+# same in, z out) + 8 (the coarser levels); per pass 36 (residual: b, s, w[3], x in; r,
+# d, p out) + 52 (one V-cycle and the direction) + 12 (accumulate)
 FLD_SETUP_B, FLD_PASS_B, FLD_ITER_B = 72, 52, 68
-FLD_SETUP_MG_B, FLD_PASS_MG_B, FLD_ITER_MG_B = 88, 112, 120
+FLD_SETUP_MG_B, FLD_PASS_MG_B, FLD_ITER_MG_B = 98, 100, 100
 # exp-class operations per (cell, bin) the method cannot avoid: e^{-tau_in}. The
 # absorbed fraction 1 - e^{-dtau} needs a second one only where dtau is not small.
 EXP_PER_CELL_NU = 1

@@ -18,6 +18,7 @@
 // refinement (FP32 vectors, FP64 reductions, every scalar of the iteration kept on
 // the device), from E_old, until the last refinement changed no cell by more than
 // tol relative.
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include <algorithm>
@@ -34,7 +35,8 @@ constexpr double kRossLnLo = 0.0, kRossLnHi = 11.512925464970229;  // ln 1 K .. 
 
 struct FldState {
     long long cap = 0;
-    float *buf = nullptr;  // F, tc, b0, w[3], s, 1/dg, b, d, r, p, q, z: 15 n floats
+    float *buf = nullptr;  // F, tc, b0, w[3], s, 1/dg, b, d, r, p, q, z: 15 n floats, then BF16
+                           // copies of s, w[3], 1/dg (5 n halves) for the finest V-cycle
     float *mg_buf = nullptr;              // coarse levels: s, w[3], 1/dg, b, x each
     std::vector<int> mg_dims;             // (nr, ntheta, nphi) of every level, finest first
     double *part = nullptr, *scal = nullptr;
@@ -206,6 +208,7 @@ struct FldFaceArgs {
     const float *F, *tc, *b0;
     float e_bg;               // a T_bg^4
     float *w, *s, *idg, *b;   // w [3][n]: to the k+1, j+1 and l+1 neighbours
+    unsigned short *hs, *hw, *hidg;  // BF16 copies of s, w, 1/dg (the finest V-cycle's operator)
     long long n;
 };
 
@@ -250,12 +253,18 @@ __global__ void __launch_bounds__(256) k_fld_faces(const FldFaceArgs p)
             faces += wp;
             faces += harm(Fc, p.F[c + (long long)(la - l) * plane]) * area / g.dphc[la];
         }
+        const float idg = 1.0f / (sc + faces);
         p.w[c] = wr;
         p.w[n + c] = wt;
         p.w[2 * n + c] = wp;
         p.s[c] = sc;
-        p.idg[c] = 1.0f / (sc + faces);
+        p.idg[c] = idg;
         p.b[c] = rhs;
+        p.hw[c] = __bfloat16_as_ushort(__float2bfloat16_rn(wr));
+        p.hw[n + c] = __bfloat16_as_ushort(__float2bfloat16_rn(wt));
+        p.hw[2 * n + c] = __bfloat16_as_ushort(__float2bfloat16_rn(wp));
+        p.hs[c] = __bfloat16_as_ushort(__float2bfloat16_rn(sc));
+        p.hidg[c] = __bfloat16_as_ushort(__float2bfloat16_rn(idg));
     }
 }
 
@@ -616,10 +625,19 @@ struct MgLevel {
     float *b, *x;        // right-hand side and result of the level
 };
 
+// BF16 copies of the finest level's operator. The V-cycle is a preconditioner: it
+// needs a symmetric positive definite approximation of A, not A itself (CG applies
+// the FP32 operator), so the finest level's restriction and prolongation read these
+// (BF16 keeps FP32's exponent range; s, w and 1/dg move 10 bytes per cell, not 20).
+struct HalfOp {
+    const unsigned short *s, *w, *idg;
+};
+
 struct MgPair {
     MgLevel f, c;    // fine and coarse level
     int sr, st, sp;  // log2 of the aggregation factors (0 or 1)
     CgArgs cg;       // scalars and reduction scratch (the finest pair's up kernel)
+    HalfOp h;        // the finest level's BF16 operator (finest pair, four-cell kernels)
 };
 
 template <class V>
@@ -823,15 +841,24 @@ __global__ void __launch_bounds__(256) k_mg_up(const MgPair P, int top, int init
     }
 }
 
-// Finest level with nr % 4 == 0: four cells of one ray per thread, 128-bit loads.
-// A v on the quad c .. c+3 at (k .. k+3, j, l), the value of the quad at the same k
-// of row (j', l') from vrow(c0, k, j', l') and of one cell from vone(i, k', j, l).
+// Finest level with nr % 4 == 0: four cells of one ray per thread; the BF16 operator
+// in 64-bit loads. A_h v on the quad c .. c+3 at (k .. k+3, j, l), the value of the quad
+// at the same k of row (j', l') from vrow(c0, k, j', l') and of one cell from
+// vone(i, k', j, l).
+__device__ __forceinline__ float4 ldh4(const unsigned short *p)
+{
+    const uint2 u = *reinterpret_cast<const uint2 *>(p);
+    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u), __uint_as_float(u.y << 16),
+                       __uint_as_float(u.y & 0xffff0000u));
+}
+__device__ __forceinline__ float ldh1(const unsigned short *p) { return __uint_as_float((unsigned)*p << 16); }
+
 template <class VR, class V1>
-__device__ __forceinline__ float4 apply_quad(const MgLevel &F, const VR &vrow, const V1 &vone, unsigned c, int k,
-                                             int j, int l, float4 vc)
+__device__ __forceinline__ float4 apply_quad(const MgLevel &F, const HalfOp &h, const VR &vrow, const V1 &vone,
+                                             unsigned c, int k, int j, int l, float4 vc)
 {
     const unsigned n = F.n, plane = (unsigned)F.nr * (unsigned)F.nth;
-    const float4 s = ld4(F.s + c), wr = ld4(F.w + c);
+    const float4 s = ldh4(h.s + c), wr = ldh4(h.w + c);
     float4 acc = make_float4(s.x * vc.x, s.y * vc.y, s.z * vc.z, s.w * vc.w);
     acc.x = fmaf(wr.x, vc.x - vc.y, acc.x);
     acc.y = fmaf(wr.y, vc.y - vc.z, acc.y);
@@ -840,20 +867,20 @@ __device__ __forceinline__ float4 apply_quad(const MgLevel &F, const VR &vrow, c
     acc.z = fmaf(wr.y, vc.z - vc.y, acc.z);
     acc.w = fmaf(wr.z, vc.w - vc.z, acc.w);
     if (k + 4 < F.nr) acc.w = fmaf(wr.w, vc.w - vone(c + 4, k + 4, j, l), acc.w);
-    if (k > 0) acc.x = fmaf(F.w[c - 1], vc.x - vone(c - 1, k - 1, j, l), acc.x);
+    if (k > 0) acc.x = fmaf(ldh1(h.w + c - 1), vc.x - vone(c - 1, k - 1, j, l), acc.x);
     auto face4 = [&](float4 w, float4 u) {
         acc.x = fmaf(w.x, vc.x - u.x, acc.x);
         acc.y = fmaf(w.y, vc.y - u.y, acc.y);
         acc.z = fmaf(w.z, vc.z - u.z, acc.z);
         acc.w = fmaf(w.w, vc.w - u.w, acc.w);
     };
-    if (j + 1 < F.nth) face4(ld4(F.w + n + c), vrow(c + F.nr, k, j + 1, l));
-    if (j > 0) face4(ld4(F.w + n + c - F.nr), vrow(c - F.nr, k, j - 1, l));
+    if (j + 1 < F.nth) face4(ldh4(h.w + n + c), vrow(c + F.nr, k, j + 1, l));
+    if (j > 0) face4(ldh4(h.w + n + c - F.nr), vrow(c - F.nr, k, j - 1, l));
     if (F.nph > 1) {
         const int lb = l + 1 < F.nph ? l + 1 : 0, la = l > 0 ? l - 1 : F.nph - 1;
         const unsigned cb = c + (unsigned)(lb - l) * plane, ca = c + (unsigned)(la - l) * plane;
-        face4(ld4(F.w + 2 * n + c), vrow(cb, k, j, lb));
-        face4(ld4(F.w + 2 * n + ca), vrow(ca, k, j, la));
+        face4(ldh4(h.w + 2 * n + c), vrow(cb, k, j, lb));
+        face4(ldh4(h.w + 2 * n + ca), vrow(ca, k, j, la));
     }
     return acc;
 }
@@ -866,12 +893,13 @@ __global__ void __launch_bounds__(256, 5) k_mg_down4(const MgPair P)
 {
     if (P.cg.scal[kDone] != 0.0) return;
     const MgLevel &F = P.f, &C = P.c;
-    const float *idg = F.idg, *b = F.b;
+    const unsigned short *idg = P.h.idg;
+    const float *b = F.b;
     auto vrow = [=](unsigned c0, int, int, int) {
-        const float4 d = ld4(idg + c0), bb = ld4(b + c0);
+        const float4 d = ldh4(idg + c0), bb = ld4(b + c0);
         return make_float4(kMgOmega * d.x * bb.x, kMgOmega * d.y * bb.y, kMgOmega * d.z * bb.z, kMgOmega * d.w * bb.w);
     };
-    auto vone = [=](unsigned i, int, int, int) { return kMgOmega * idg[i] * b[i]; };
+    auto vone = [=](unsigned i, int, int, int) { return kMgOmega * ldh1(idg + i) * b[i]; };
     const unsigned nq = (unsigned)(F.nr / 4) * (unsigned)C.nth * (unsigned)C.nph;
     for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < nq; t += gridDim.x * blockDim.x) {
         const unsigned qr = (unsigned)(F.nr / 4);
@@ -884,7 +912,7 @@ __global__ void __launch_bounds__(256, 5) k_mg_down4(const MgPair P)
             for (int j = J << P.st; j < min((J + 1) << P.st, F.nth); ++j) {
                 const unsigned c = ((unsigned)l * F.nth + j) * F.nr + k;
                 const float4 vc = vrow(c, k, j, l), bb = ld4(b + c);
-                const float4 ax = apply_quad(F, vrow, vone, c, k, j, l, vc);
+                const float4 ax = apply_quad(F, P.h, vrow, vone, c, k, j, l, vc);
                 lo += (bb.x - ax.x) + (bb.y - ax.y);
                 hi += (bb.z - ax.z) + (bb.w - ax.w);
             }
@@ -899,24 +927,27 @@ __global__ void __launch_bounds__(256, 5) k_mg_up4(const MgPair P, int init)
 {
     if (P.cg.scal[kDone] != 0.0) return;
     const MgLevel &F = P.f, &C = P.c;
-    const float *idg = F.idg, *b = F.b, *xc = C.x;
+    const unsigned short *idg = P.h.idg;
+    const float *b = F.b, *xc = C.x;
     const int st = P.st, sp = P.sp, cnr = C.nr, cnth = C.nth;
     auto crow = [=](int j, int l) { return ((unsigned)(l >> sp) * cnth + (j >> st)) * cnr; };
     auto vrow = [=](unsigned c0, int k, int j, int l) {
         const unsigned K0 = crow(j, l) + (k >> 1);
         const float2 x2 = make_float2(xc[K0], xc[K0 + 1]);
-        const float4 d = ld4(idg + c0), bb = ld4(b + c0);
+        const float4 d = ldh4(idg + c0), bb = ld4(b + c0);
         return make_float4(fmaf(kMgOmega * d.x, bb.x, x2.x), fmaf(kMgOmega * d.y, bb.y, x2.x),
                            fmaf(kMgOmega * d.z, bb.z, x2.y), fmaf(kMgOmega * d.w, bb.w, x2.y));
     };
-    auto vone = [=](unsigned i, int k, int j, int l) { return fmaf(kMgOmega * idg[i], b[i], xc[crow(j, l) + (k >> 1)]); };
+    auto vone = [=](unsigned i, int k, int j, int l) {
+        return fmaf(kMgOmega * ldh1(idg + i), b[i], xc[crow(j, l) + (k >> 1)]);
+    };
     KSum rz;
     for (unsigned c = 4u * (blockIdx.x * blockDim.x + threadIdx.x); c < F.n; c += 4u * gridDim.x * blockDim.x) {
         int k, j, l;
         cell_ijk(c, F.nr, F.nth, F.dnr, F.dnth, k, j, l);
         const float4 vc = vrow(c, k, j, l);
-        const float4 ax = apply_quad(F, vrow, vone, c, k, j, l, vc);
-        const float4 d = ld4(idg + c), bb = ld4(b + c);
+        const float4 ax = apply_quad(F, P.h, vrow, vone, c, k, j, l, vc);
+        const float4 d = ldh4(idg + c), bb = ld4(b + c);
         const float4 z = make_float4(fmaf(kMgOmega * d.x, bb.x - ax.x, vc.x), fmaf(kMgOmega * d.y, bb.y - ax.y, vc.y),
                                      fmaf(kMgOmega * d.z, bb.z - ax.z, vc.z), fmaf(kMgOmega * d.w, bb.w - ax.w, vc.w));
         st4(F.x + c, z);
@@ -1174,7 +1205,7 @@ int rt_fld_step(rt_ctx *ctx, const float *rho, const float *t_gas, const float *
         cudaFree(fs->buf);
         fs->buf = nullptr;
         fs->cap = 0;
-        if (cudaMalloc(&fs->buf, sizeof(float) * 15 * (size_t)n) != cudaSuccess) {
+        if (cudaMalloc(&fs->buf, sizeof(float) * 18 * (size_t)n) != cudaSuccess) {
             cudaGetLastError();
             return ctx_fail(ctx, RT_ERR_NO_MEMORY, "FLD workspace");
         }
@@ -1250,6 +1281,7 @@ int rt_fld_step(rt_ctx *ctx, const float *rho, const float *t_gas, const float *
     const double a_rad = radiation_constant();
     float *F = fs->buf, *tc = F + n, *b0 = tc + n, *w = b0 + n, *sv = w + 3 * n, *idg = sv + n, *b = idg + n;
     float *d = b + n, *r = d + n, *p = r + n, *q = p + n, *z = q + n;
+    unsigned short *hs = reinterpret_cast<unsigned short *>(z + n), *hw = hs + n, *hidg = hw + 3 * n;
 
     FldCellArgs ca;
     ca.g = g;
@@ -1280,6 +1312,9 @@ int rt_fld_step(rt_ctx *ctx, const float *rho, const float *t_gas, const float *
     fa.s = sv;
     fa.idg = idg;
     fa.b = b;
+    fa.hs = hs;
+    fa.hw = hw;
+    fa.hidg = hidg;
     fa.n = n;
     CgArgs cg;
     cg.nr = nr;
@@ -1339,6 +1374,7 @@ int rt_fld_step(rt_ctx *ctx, const float *rho, const float *t_gas, const float *
         pairs[i].st = lv[i].nth > 1 ? 1 : 0;
         pairs[i].sp = lv[i].nph > 1 ? 1 : 0;
         pairs[i].cg = cg;
+        pairs[i].h = HalfOp{hs, hw, hidg};
     }
     auto work_grid = [&](const void *kern, unsigned cells) {
         int per_sm = 0;
