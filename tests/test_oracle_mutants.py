@@ -1,5 +1,7 @@
 """Plant plausible slips in copies of the oracle (on the CPU) and check that the
-pins in ``test_oracle_pins.py`` catch every one of them.
+pins in ``test_oracle_pins.py`` (tracer), ``test_temperature_cpu.py`` (Planck mean,
+Eq. 16), ``test_fld_cpu.py`` (Rosseland mean) and ``test_tdep_cpu.py`` (kappa(nu, T)
+tables) catch every one of them.
 
 A pin set that lets a dropped term, a wrong sign, an off-by-one or a transposed
 index through would not be pinning anything; this test makes that claim
@@ -15,7 +17,10 @@ import subprocess
 import pytest
 
 import oracle
+from tests import test_fld_cpu as fld_pins
 from tests import test_oracle_pins as pins
+from tests import test_tdep_cpu as tdep_pins
+from tests import test_temperature_cpu as temp_pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "rt_oracle.c")
 
@@ -39,6 +44,25 @@ MUTANTS = [
     ("escape_lost", "rto_add(&esc, lum * exp(-tau));", "rto_add(&esc, lum * exp(-tau) * 0.999);"),
     ("no_mask_on_force", "A[k] += lum * att * kap * dr * rto_phi(dtau);",
      "A[k] += lum * att * kappa[i] * dr * rto_phi(dtau);"),
+    # Planck and Rosseland means (Eqs. 11, 16)
+    ("planck_unweighted", "num += kappa[i] * f[i];\n        den += f[i];", "num += kappa[i];\n        den += 1.0;"),
+    ("rosseland_arithmetic", "if (kappa[i] > 0.0) num += w / kappa[i];", "if (kappa[i] > 0.0) num += w * kappa[i];"),
+    ("rosseland_planck_weight", "const double w = ea - eb + 4.0 * rto_planck_band(a, b);",
+     "const double w = rto_planck_band(a, b);"),
+    ("rosseland_boundary_sign", "const double w = ea - eb + 4.0 * rto_planck_band(a, b);",
+     "const double w = eb - ea + 4.0 * rto_planck_band(a, b);"),
+    ("rosseland_window_ignored", "else if (w > 0.0) opaque_gap = 1;", "else if (w > 0.0) opaque_gap = 0;"),
+    # dust temperature (Eq. 16)
+    ("temperature_without_er", "const double f = a_rad_const * tt * tt * tt * tt - er - ar / kp;",
+     "const double f = a_rad_const * tt * tt * tt * tt - ar / kp;"),
+    ("temperature_kappa_times", "- er - ar / kp;", "- er - ar * kp;"),
+    ("temperature_no_clamp", "const double tk = tt < t_lo ? t_lo : (tt > t_hi ? t_hi : tt);",
+     "const double tk = tt;"),
+    # kappa(nu, T) tables: linear in T between grid points, held beyond the ends
+    ("kappa_at_left_row", "return row[j] + (row[j + 1] - row[j]) * w;", "return row[j];"),
+    ("kappa_at_weight_flipped", "const double w = (t - t_grid[j]) / (t_grid[j + 1] - t_grid[j]);",
+     "const double w = (t_grid[j + 1] - t) / (t_grid[j + 1] - t_grid[j]);"),
+    ("kappa_at_extrapolated_below", "if (n_t == 1 || t <= t_grid[0]) return row[0];", "if (n_t == 1) return row[0];"),
 ]
 
 PIN_CALLS = [
@@ -53,6 +77,18 @@ PIN_CALLS = [
     ("fluxdiff", lambda: pins.test_flux_difference_form()),
     ("layout", lambda: pins.test_layout_theta_phi_distinct()),
     ("sublimated", lambda: pins.test_sublimated_cells_are_transparent()),
+    ("planck_one_bin", lambda: temp_pins.test_planck_mean_of_one_bin_is_its_opacity()),
+    ("planck_power_law", lambda: temp_pins.test_planck_mean_of_a_power_law(300.0)),
+    ("t_radiation_only", lambda: temp_pins.test_radiation_only_closed_form()),
+    ("t_eq16", lambda: temp_pins.test_solution_satisfies_eq16()),
+    ("t_thin_sphere", lambda: temp_pins.test_gray_thin_sphere_equilibrium()),
+    ("t_clamp", lambda: temp_pins.test_planck_mean_is_held_outside_the_table_range()),
+    ("rosseland_power_law", lambda: fld_pins.test_rosseland_mean_of_a_power_law(300.0)),
+    ("rosseland_window", lambda: fld_pins.test_rosseland_mean_of_a_transparent_window()),
+    ("tdep_constant", lambda: tdep_pins.test_constant_table_is_the_plain_tracer()),
+    ("tdep_row_below", lambda: tdep_pins.test_uniform_temperature_uses_the_interpolated_row(5.0)),
+    ("tdep_row_inside", lambda: tdep_pins.test_uniform_temperature_uses_the_interpolated_row(97.0)),
+    ("tdep_two_zone", lambda: tdep_pins.test_two_zone_gray_ray()),
 ]
 
 

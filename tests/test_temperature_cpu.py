@@ -89,3 +89,19 @@ def test_gray_and_frequency_agree_when_thin():
     np.testing.assert_allclose(rf.a_rad, rg.a_rad, rtol=1e-12)
     tf = oracle.dust_temperature(rf.a_rad, None, nu, kap)
     np.testing.assert_allclose(tf, oracle.dust_temperature(rg.a_rad, None, nu, kap), rtol=1e-12)
+
+
+def test_planck_mean_is_held_outside_the_table_range():
+    """kappa_P is evaluated at T clamped to [t_lo, t_hi]: a cell whose solution lies
+    below t_lo solves a T^4 = a_rad / kappa_P(t_lo) exactly, one above t_hi
+    a T^4 = a_rad / kappa_P(t_hi)."""
+    nu = synth.nu_bins(24)
+    kap = synth.kappa_synth(nu)
+    t_lo, t_hi = 20.0, 400.0
+    kp_lo = oracle.planck_mean(t_lo, nu, kap)
+    kp_hi = oracle.planck_mean(t_hi, nu, kap)
+    assert kp_lo != pytest.approx(kp_hi, rel=1e-3)
+    # a_rad chosen so the clamped solutions are 5 K and 2000 K
+    ar = np.array([A_RAD * 5.0 ** 4 * kp_lo, A_RAD * 2000.0 ** 4 * kp_hi])
+    t = oracle.dust_temperature(ar, None, nu, kap, t_lo=t_lo, t_hi=t_hi)
+    np.testing.assert_allclose(t, [5.0, 2000.0], rtol=1e-12)
