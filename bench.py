@@ -52,11 +52,16 @@ def workload_name(taus):
 # d, p out) + 52 (one V-cycle and the direction) + 12 (accumulate)
 FLD_SETUP_B, FLD_PASS_B, FLD_ITER_B = 72, 52, 68
 FLD_SETUP_MG_B, FLD_PASS_MG_B, FLD_ITER_MG_B = 98, 100, 100
-# exp-class operations per (cell, bin) the method cannot avoid: e^{-tau_in}. The
-# absorbed fraction 1 - e^{-dtau} needs a second one only where dtau is not small.
+# exp-class operations per (cell, bin) traced bin by bin: e^{-tau_in}. The absorbed
+# fraction 1 - e^{-dtau} needs a second one only where dtau is not small.
 EXP_PER_CELL_NU = 1
+# bins with kappa_i N_max <= THIN_X (N_max the largest total column of the rays one
+# warp traces) enter the tracer's power series instead (no exponential per cell)
+THIN_X = 0.5
+# algorithmic bytes per cell of the tracer: rho, T_dust in, q_abs, a_rad out (FP32)
+TRACE_BYTES_PER_CELL = 16
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_ray_disk3d_256x128x256_nu79.md")
-KERNEL_SOURCES = ("rt_ray.cu", "rt_ray.cuh", "rt_device.cuh")
+KERNEL_SOURCES = ("rt_ray.cu", "rt_ray.cuh", "rt_device.cuh", "rt_internal.cuh")
 
 
 def parse():
@@ -184,6 +189,30 @@ def traffic_from_profile(src_hash: str):
     return t if (h == src_hash and t is not None) else None
 
 
+def exact_exp_ops(w, shape):
+    """Exp-class operations of one tracer launch on grid w that the series cannot
+    replace: one per (cell, bin) outside the thin prefix of the cell's warp (the bins
+    with kappa_i N_max <= THIN_X, N_max the largest total column of the warp's rays).
+    The tile kernel traces every bin."""
+    nr = w.grid.nr
+    nbins = int(np.count_nonzero(w.kappa > 0))
+    if shape[0] != 1:
+        return w.grid.ncells * nbins
+    c = shape[1]
+    g = 8 if 8 * c >= nr else (16 if 16 * c >= nr else 32)   # lanes per ray
+    r = 32 // g                                               # rays per warp
+    dust = w.tdust32() <= w.t_sub
+    col = np.where(dust, w.rho32().astype(np.float64), 0.0) * np.diff(w.grid.r_if)
+    ntot = col.reshape(-1, nr).sum(axis=1)
+    pad = (-len(ntot)) % r
+    nmax = np.concatenate([ntot, np.zeros(pad)]).reshape(-1, r).max(axis=1)
+    kap = np.sort(w.kappa[w.kappa > 0])
+    bt = np.searchsorted(kap, THIN_X / np.maximum(nmax, 1e-300), side="right")
+    rays = np.full(len(nmax), r)
+    rays[-1] = r - pad
+    return int(np.sum((nbins - bt) * rays)) * nr
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
@@ -235,6 +264,7 @@ def run_cpu_table(args, local):
     ex2_clk, ffma_clk, mhz = probe_alu_rates()
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     peak = ex2_clk * nsm * 2070e6
+    hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs") or 6678.0)
     cases = [("C1 64x32x1 nu32 tau1", synth.disk2d()),
              ("C2 256x128x256 nu79 tau1", synth.disk3d(256, 128, 256, n_nu=79, tau550=1.0, seed=1)),
              ("C2 256x128x256 nu79 tau100", synth.disk3d(256, 128, 256, n_nu=79, tau550=100.0, seed=1)),
@@ -265,8 +295,11 @@ def run_cpu_table(args, local):
             tr.irradiate(r, t, q, a)
         e1.record()
         torch.cuda.synchronize()
-        v = w.grid.ncells * len(w.nu) / (e0.elapsed_time(e1) / args.steps * 1e-3)
-        row.update(gpu=v, gpu_roofline_frac=v / peak, tuning=list(tr.tuning()))
+        t_s = e0.elapsed_time(e1) / args.steps * 1e-3
+        v = w.grid.ncells * len(w.nu) / t_s
+        t_floor = max(TRACE_BYTES_PER_CELL * w.grid.ncells / (hbm * 1e9),
+                      exact_exp_ops(w, tr.tuning()) / peak)
+        row.update(gpu=v, gpu_roofline_frac=t_floor / t_s, tuning=list(tr.tuning()))
         tr.close()
         rows.append(row)
         print(json.dumps(row), flush=True)
@@ -337,7 +370,6 @@ def run_ours(args, rank, world, local):
         tr.set_tuning(*shape)
 
     units_per_step = sum(w.grid.ncells * len(w.nu) for w in ws)
-    exp_ops_per_launch = [EXP_PER_CELL_NU * w.grid.ncells * len(w.nu) for w in ws]
 
     def step(ev=None):
         for i, tr in enumerate(tracers):
@@ -380,16 +412,39 @@ def run_ours(args, rank, world, local):
     energies = [tr.energy_last() for tr in tracers]
     max_energy_err = max(abs(e.rel_err) for e in energies)
 
-    # roofline of the tracer kernel: exp-class ops per launch / average launch time
+    # roofline of the tracer kernel. Two floors per launch: HBM (16 B per cell) and
+    # MUFU (one ex2 per (cell, bin) outside the thin series); the larger binds, and
+    # the fraction is that floor over the average launch time.
     avg_launch_s = statistics.mean(x for row in launch_ms for x in row) * 1e-3
-    achieved = statistics.mean(exp_ops_per_launch) / avg_launch_s / 1e9
     ex2_clk, ffma_clk, probe_mhz = probe_alu_rates()
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     clocks = clk.summary()
     mhz = clocks["sm_mhz"] or probe_mhz
     peak = ex2_clk * nsm * mhz * 1e6 / 1e9
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    hbm_peak = float(peaks.get("hbm_gbs") or 6678.0)
+    bytes_per_launch = statistics.mean(TRACE_BYTES_PER_CELL * w.grid.ncells for w in ws)
+    exact_ops = statistics.mean(exact_exp_ops(w, shape) for w in ws)
+    t_hbm = bytes_per_launch / (hbm_peak * 1e9)
+    t_mufu = exact_ops / (peak * 1e9)
+    achieved = exact_ops / avg_launch_s / 1e9
     src_hash = kernel_source_hash()
     traffic = traffic_from_profile(src_hash)
+    if t_hbm >= t_mufu:
+        roofline = {"bound": "hbm", "unit": "GB/s", "achieved": bytes_per_launch / avg_launch_s / 1e9,
+                    "peak": hbm_peak, "frac": t_hbm / avg_launch_s,
+                    "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        roofline = {"bound": "alu", "unit": "Gop/s (MUFU ex2)", "achieved": achieved, "peak": peak,
+                    "frac": t_mufu / avg_launch_s,
+                    "peak_basis": f"measured {ex2_clk:.2f} ex2/SM/clk x {nsm} SMs x {mhz:.0f} MHz"}
+    roofline.update({
+        "traffic": traffic, "kernel": "k_ray" if shape[0] == 1 else "k_trace",
+        "avg_launch_ms": avg_launch_s * 1e3, "algorithmic_bytes_per_launch": bytes_per_launch,
+        "mufu": {"exact_ex2_per_launch": exact_ops, "achieved_gops": achieved, "peak_gops": peak,
+                 "frac": t_mufu / avg_launch_s,
+                 "peak_basis": f"measured {ex2_clk:.2f} ex2/SM/clk x {nsm} SMs x {mhz:.0f} MHz"},
+        "ffma_per_sm_clk": ffma_clk, "kernel_source_sha256": src_hash})
 
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None
@@ -509,13 +564,7 @@ def run_ours(args, rank, world, local):
                                         "warps": shape[2], "min_blocks_per_sm": shape[3]},
                        "l2": f"no flush: inputs+outputs {16 * sum(w.grid.ncells for w in ws) / 1e6:.0f} MB per step exceed the 129 MB L2",
                        "replicas_per_rank": 1},
-            "roofline": {"bound": "alu", "unit": "Gop/s (MUFU ex2)", "achieved": achieved,
-                         "peak": peak, "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_ray" if shape[0] == 1 else "k_trace",
-                         "ops_per_cell_nu": EXP_PER_CELL_NU,
-                         "avg_launch_ms": avg_launch_s * 1e3,
-                         "peak_basis": f"measured {ex2_clk:.2f} ex2/SM/clk x {nsm} SMs x {mhz:.0f} MHz",
-                         "ffma_per_sm_clk": ffma_clk, "kernel_source_sha256": src_hash},
+            "roofline": roofline,
             "cpu_baseline": base,
             "e2e": e2e,
             "gpu_launches": len(ws) * args.steps,

@@ -485,7 +485,7 @@ int rt_create(const rt_grid_desc *g, void *cuda_stream, rt_ctx **out)
     ok = ok && dalloc(&c->kappa, RT_MAX_NU) == cudaSuccess;
     ok = ok && dalloc(&c->f_bin, RT_MAX_NU) == cudaSuccess;
     ok = ok && dalloc(&c->nu_tab, RT_MAX_NU + rt::kNuPad) == cudaSuccess;
-    ok = ok && dalloc(&c->kap, RT_MAX_NU + rt::kNuPad) == cudaSuccess;
+    ok = ok && dalloc(&c->kap, rt::kKapBuffer) == cudaSuccess;
     ok = ok && dalloc(&c->nu64, RT_MAX_NU + rt::kNuPad) == cudaSuccess;
     ok = ok && dalloc(&c->sc, 1) == cudaSuccess;
     ok = ok && dalloc(&c->order_d, RT_MAX_NU) == cudaSuccess;

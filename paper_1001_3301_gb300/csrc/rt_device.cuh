@@ -277,11 +277,15 @@ __device__ __forceinline__ void bin_range(int i0, int i1, const float4 *s_nu, co
 struct BinClasses {
     int b1, b2, b3, b5, bb;
 };
+// from > 0: only bins from the 32-bin chunk holding `from` on are looked at, and the
+// bins before that chunk count as inside every class (exact for every boundary at or
+// above `from`, which is how the thin-series caller uses them).
 __device__ __forceinline__ BinClasses classify_bins(const float4 *s_nu, int n_active, int lane,
-                                                     float dmax, float dmin)
+                                                     float dmax, float dmin, int from = 0)
 {
-    BinClasses c{0, 0, 0, 0, 0};
-    for (int c0 = 0; c0 < n_active; c0 += 32) {
+    const int start = from & ~31;
+    BinClasses c{start, start, start, start, start};
+    for (int c0 = start; c0 < n_active; c0 += 32) {
         const int i = c0 + lane;
         const float ak = (i < n_active) ? -s_nu[i].x : INFINITY;
         const float ym = ak * dmax, yn = ak * dmin;
@@ -293,6 +297,70 @@ __device__ __forceinline__ BinClasses classify_bins(const float4 *s_nu, int n_ac
     }
     c.bb = c.bb > c.b5 ? c.bb : c.b5;
     return c;
+}
+
+// Bins optically thin along every ray a warp holds: kappa_i N_max <= kThinX, N_max the
+// largest total column of those rays. With the bins sorted by kappa ascending they
+// are a prefix; the count is warp-uniform.
+constexpr float kThinY = (float)(kThinX * kLog2e);  // the bound in the units of -nk
+__device__ __forceinline__ int thin_count(const float4 *s_nu, int n_active, int lane, float nmax)
+{
+    int bt = 0;
+    for (int c0 = 0; c0 < n_active; c0 += 32) {
+        const int i = c0 + lane;
+        const float ak = (i < n_active) ? -s_nu[i].x : INFINITY;
+        bt += __popc(__ballot_sync(0xffffffffu, ak * nmax <= kThinY));
+    }
+    return bt;
+}
+
+// The bins i < b of a thin prefix (Eqs. 17, 19 and 31-32 summed over them) as one
+// series. With Phi(u) = sum_{i<b} w_i e^{-kappa_i u}, a cell with column N in front of
+// it and dN in it absorbs Phi(N) - Phi(N + dN). Expanding e^{-kappa u} in powers of
+// kappa u and writing a = s (N + dN), c = s N (s = kappa_{b-1}, so a, c <= kThinX):
+//   Phi(N) - Phi(N + dN) = dN s sum_{k>=1} C_k h_{k-1}(a, c),
+//   h_{k-1}(a, c) = sum_{j<k} a^j c^{k-1-j} = (a^k - c^k) / (a - c),
+// with C_k the row's coefficients. The sum over k is the divided difference of
+// P(u) = sum_k C_k u^k between a and c, evaluated by the paired Horner recurrence
+// (no a - c cancellation); all terms of one power carry one sign and |a|, |c| <=
+// kThinX, so the alternating sum loses at most a factor e^{2 kThinX} of precision.
+// row: the table row b (s, C_1 .. C_kThinTerms).
+template <int C>
+__device__ __forceinline__ void thin_series(const float *row, const float2 (&n2)[C / 2],
+                                            const float2 (&d2)[C / 2], float2 (&a2)[C / 2])
+{
+    static_assert(kThinTerms >= 2, "paired Horner form needs two terms");
+    const float s = __ldg(row);
+    float c[kThinTerms + 1];
+#pragma unroll
+    for (int k = 1; k <= kThinTerms; ++k) c[k] = __ldg(row + k);
+    const float2 s2 = f2(s);
+#pragma unroll
+    for (int m = 0; m < C / 2; ++m) {
+        const float2 cc = __fmul2_rn(s2, n2[m]);
+        const float2 aa = __ffma2_rn(s2, d2[m], cc);
+        float2 dd = f2(c[kThinTerms]);
+        float2 pc = __ffma2_rn(dd, cc, f2(c[kThinTerms - 1]));
+#pragma unroll
+        for (int k = kThinTerms - 2; k >= 1; --k) {
+            dd = __ffma2_rn(dd, aa, pc);
+            pc = __ffma2_rn(pc, cc, f2(c[k]));
+        }
+        dd = __ffma2_rn(dd, aa, pc);
+        a2[m] = __ffma2_rn(__fmul2_rn(d2[m], dd), s2, a2[m]);
+    }
+}
+
+// Escaping part of the thin bins of a row for a ray of total column n:
+// sum_{i<b} w_i e^{-kappa_i n} = S_0 - sum_{k>=1} C_k (s n)^k with S_0 = sum_{i<b} w_i
+// (the row's last entry); s n <= kThinX keeps the result above e^{-kThinX} S_0.
+__device__ __forceinline__ float thin_escape(const float *row, float n)
+{
+    const float u = __ldg(row) * n;
+    float p = __ldg(row + kThinTerms);
+#pragma unroll
+    for (int k = kThinTerms - 1; k >= 1; --k) p = fmaf(p, u, __ldg(row + k));
+    return fmaf(-p, u, __ldg(row + kThinTerms + 1));
 }
 
 // solid angle of ray r of this launch, in the mode's precision

@@ -31,6 +31,20 @@ struct alignas(8) NuEntry {
     float lf;
 };
 
+// Bins optically thin along every ray a warp holds (kappa_i N_total <= kThinX) are
+// summed as one power series in the column instead of bin by bin (thin_series in
+// rt_device.cuh). Its coefficients live in the buffer of the kappa table, after
+// it: row b = 1..n_active holds s_b = kappa_{b-1} (column units) and then
+// C_k(b) = (-1)^{k+1} / k! sum_{i<b} w_i (kappa_i / s_b)^k for k = 1..kThinTerms,
+// then S_0(b) = sum_{i<b} w_i; w_i = F_i / F_max, bins in the kappa-sorted order.
+// With x = kThinX the first omitted term is below x^kThinTerms / kThinTerms! = 1e-7
+// of the leading one.
+constexpr int kThinTerms = 8;
+constexpr int kThinStride = 12;                                       // floats per row (>= kThinTerms + 2)
+constexpr int kKapTable = RT_MAX_NU + kNuPad;                         // floats of the kappa table
+constexpr int kKapBuffer = kKapTable + (RT_MAX_NU + 1) * kThinStride;  // with the series rows
+constexpr float kThinX = 0.5f;
+
 // Scalars of one configured grid, resident in device memory.
 struct DevScalars {
     double f_max;          // largest bin flux F_i (erg s^-1 cm^-2)

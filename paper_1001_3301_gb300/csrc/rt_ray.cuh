@@ -10,11 +10,12 @@
 //   - dN = [T <= t_sub] rho dr per cell, and its exclusive prefix N_in along the
 //     ray (Eq. 19, tau = 0 at the inner radius): compensated lane sums, then a
 //     compensated warp scan;
-//   - the per-bin loop of rt_device.cuh (Eqs. 17, 20, 31-32) into one accumulator
-//     per cell, with the warp's bin classes chosen from its largest and smallest
-//     column;
+//   - the bins optically thin along all the warp's rays as one power series in the
+//     column (thin_series), the others by the per-bin loop of rt_device.cuh
+//     (Eqs. 17, 20, 31-32), into one accumulator per cell, with the warp's bin
+//     classes chosen from its largest and smallest column;
 //   - escaping power sum_i F_i/F_max e^{-kappa_i N_total} (Eqs. 33-35), the lanes
-//     sharing the bins;
+//     sharing the bins outside the thin series (that part from the series row);
 //   - q_abs = Gq acc and a_rad = q/(rho c) = Ga0 acc / dN (Sect. 5; the rho -> 0
 //     limit where dN = 0 with dust), stored as 16-byte vectors;
 //   - energy sums per lane.
@@ -164,13 +165,21 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
             dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
         }
         const int na = p.n_active;
-        const BinClasses bc = classify_bins(s_nu, na, lane, dmax, dmin);
-        moment_range<1, C>(0, bc.b1, s_nu, s_mom, N.v, D.v, acc.v);
-        moment_range<2, C>(bc.b1, bc.b2, s_nu, s_mom, N.v, D.v, acc.v);
-        bin_range<3, C>(bc.b2, bc.b3, s_nu, N.v, D.v, acc.v);
-        bin_range<5, C>(bc.b3, bc.b5, s_nu, N.v, D.v, acc.v);
-        bin_range<6, C>(bc.b5, bc.bb, s_nu, N.v, D.v, acc.v);
-        bin_range<7, C>(bc.bb, na, s_nu, N.v, D.v, acc.v);
+        // bins thin along all the warp's rays: one series for the lot, the rest bin by bin
+        float nmax = ntot;
+        for (int o = G; o < 32; o <<= 1) nmax = fmaxf(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+        const int bt = thin_count(s_nu, na, lane, nmax);
+        const float *thin_row = p.kap + kKapTable + bt * kThinStride;
+        if (bt > 0) thin_series<C>(thin_row, N.v, D.v, acc.v);
+        const BinClasses bc = classify_bins(s_nu, na, lane, dmax, dmin, bt);
+        const int t1 = max(bc.b1, bt), t2 = max(bc.b2, bt), t3 = max(bc.b3, bt), t5 = max(bc.b5, bt);
+        const int tb = max(bc.bb, bt);
+        moment_range<1, C>(bt, t1, s_nu, s_mom, N.v, D.v, acc.v);
+        moment_range<2, C>(t1, t2, s_nu, s_mom, N.v, D.v, acc.v);
+        bin_range<3, C>(t2, t3, s_nu, N.v, D.v, acc.v);
+        bin_range<5, C>(t3, t5, s_nu, N.v, D.v, acc.v);
+        bin_range<6, C>(t5, tb, s_nu, N.v, D.v, acc.v);
+        bin_range<7, C>(tb, na, s_nu, N.v, D.v, acc.v);
 
         // cells with dust but no column: the rho -> 0 force limit sum_i kappa_i g_i
         if (__any_sync(0xffffffffu, zero_m != 0u)) {
@@ -189,9 +198,12 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
         const float w = live ? __ldg(p.domega32 + ray) : 0.0f;
         {
             float s = 0.0f;
-            for (int i = ll; i < p.nnu_pad; i += G) s += ex2_approx(fmaf(s_nu[i].x, ntot, s_nu[i].z));
+            for (int i = bt + ll; i < p.nnu_pad; i += G) s += ex2_approx(fmaf(s_nu[i].x, ntot, s_nu[i].z));
             for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (ll == 0) eesc.add(s * w);
+            if (ll == 0) {
+                if (bt > 0) s += thin_escape(thin_row, ntot);
+                eesc.add(s * w);
+            }
         }
 
         // outputs and the lane's absorbed power

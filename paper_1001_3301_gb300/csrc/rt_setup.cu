@@ -78,6 +78,49 @@ __global__ void k_setup_bins(int n_nu, const double *nu_mid, const double *kappa
     sc->nnu_pad = pad;
 }
 
+// Series rows of the bins thin along whole rays (layout at kThinTerms in
+// rt_internal.cuh), one block of one warp per row b = 0..RT_MAX_NU: s_b = kappa_{b-1},
+// C_k(b) = (-1)^{k+1} / k! sum_{i<b} w_i (kappa_i / s_b)^k and S_0(b) = sum_{i<b} w_i,
+// in FP64 from the FP32 table the tracer uses (kappa_i = -nk_i ln 2, w_i = 2^lf_i).
+__global__ void k_thin_table(const NuEntry *nu, const DevScalars *sc, float *thin)
+{
+    const int b = blockIdx.x, lane = threadIdx.x;
+    const int na = sc->n_active;
+    float *row = thin + (size_t)b * kThinStride;
+    if (b == 0 || b > na) {
+        if (lane < kThinStride) row[lane] = 0.0f;
+        return;
+    }
+    const double s = -(double)nu[b - 1].nk * kLn2;
+    double m[kThinTerms + 1];
+#pragma unroll
+    for (int k = 0; k <= kThinTerms; ++k) m[k] = 0.0;
+    for (int i = lane; i < b; i += 32) {
+        const double r = -(double)nu[i].nk * kLn2 / s;
+        double p = exp2((double)nu[i].lf);
+        m[0] += p;
+#pragma unroll
+        for (int k = 1; k <= kThinTerms; ++k) {
+            p *= r;
+            m[k] += p;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k <= kThinTerms; ++k)
+        for (int o = 16; o > 0; o >>= 1) m[k] += __shfl_xor_sync(0xffffffffu, m[k], o);
+    if (lane == 0) {
+        row[0] = (float)s;
+        double fact = 1.0;
+#pragma unroll
+        for (int k = 1; k <= kThinTerms; ++k) {
+            fact *= k;
+            row[k] = (float)(((k & 1) ? m[k] : -m[k]) / fact);
+        }
+        row[kThinTerms + 1] = (float)m[0];
+        for (int k = kThinTerms + 2; k < kThinStride; ++k) row[k] = 0.0f;
+    }
+}
+
 // Per-radius and per-ray tables. Gq = 3 R*^2 F_max / (r+^3 - r-^3) turns the
 // per-ray sum of F_i/F_max e^-tau (1-e^-dtau) into power per volume; Ga0 = Gq dr / c
 // is the rho -> 0 force factor.
@@ -170,6 +213,10 @@ cudaError_t launch_setup_bins(int n_nu, const double *nu_mid_dev, const double *
     k_setup_bins<<<1, 32 * (RT_MAX_NU / 4), 0, stream>>>(n_nu, nu_mid_dev, kappa_dev, t_star, r_star,
                                               kappa_bf16, f_bin_dev, nu_dev, kap_dev, nu64_dev,
                                               sc_dev, order_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    static_assert(kThinStride >= kThinTerms + 2, "a row holds s, C_1..C_K and S_0");
+    k_thin_table<<<RT_MAX_NU + 1, 32, 0, stream>>>(nu_dev, sc_dev, kap_dev + kKapTable);
     return cudaGetLastError();
 }
 

@@ -38,7 +38,7 @@ struct StaticScratch {
     double kappa[RT_MAX_NU];
     double f_bin[RT_MAX_NU];
     rt::NuEntry nu_tab[RT_MAX_NU + rt::kNuPad];
-    float kap[RT_MAX_NU + rt::kNuPad];
+    float kap[rt::kKapBuffer];  // kappa table, then the thin-ray series rows
     double2 nu64[RT_MAX_NU + rt::kNuPad];
     float4 rtab[kStaticMaxNr];
     rt::RadRow64 rtab64[kStaticMaxNr];

@@ -88,6 +88,33 @@ def test_disk3d_reduced(tau):
     assert stats["n_mask"] > 1000
 
 
+def _thin_counts(w, x=0.5):
+    """Per ray, the bins with kappa_i N_total <= x (the ones the series takes when
+    the ray's warp holds no thicker ray)."""
+    col = np.where(w.tdust32() <= w.t_sub, w.rho32().astype(np.float64), 0.0) * np.diff(w.grid.r_if)
+    ntot = col.reshape(-1, w.grid.nr).sum(axis=1)
+    kap = np.sort(w.kappa[w.kappa > 0])
+    return np.searchsorted(kap, x / np.maximum(ntot, 1e-300), side="right"), len(kap)
+
+
+@pytest.mark.parametrize("tau", [1e-4, 1e3])
+def test_thin_series_extremes(tau):
+    """The power series over the bins optically thin along whole rays: at
+    tau550 = 1e-4 every bin of every ray goes through it; at 1e3 the midplane rays
+    keep only the far-infrared bins in it and trace the rest bin by bin. Both
+    segment widths (32 and 16 lanes per ray, one and two rays per warp)."""
+    w = _w3(256, 24, 4, 79, tau=tau, seed=5)
+    bt, na = _thin_counts(w)
+    if tau < 1:
+        assert np.all(bt == na)
+    else:
+        assert bt.min() < na // 2 and bt.max() > 0
+    orc = _parity.oracle_for(w)
+    for shape in [(1, 8, 4, 6), (1, 16, 4, 3)]:
+        q, a, e = _parity.run_gpu(w, "fp32_kahan", shape=shape)
+        _parity.assert_parity(w, q, a, e, orc, label=f"tau={tau} {shape}")
+
+
 # --------------------------------------------------------------------------
 # full 256 x 128 x 256, 79-bin size in the bench's launch configuration:
 # sampled rays against the oracle, energy of the whole grid
