@@ -228,10 +228,11 @@ typedef struct rt_batch rt_batch;
 
 /* rt_batch_create -- plan one persistent launch over several grids of any size
  * (each a configured context; all of one precision and one device; each below
- * 2^31 - 2^16 flattened cells). The grids' tiles are concatenated and split over
- * the CTAs by cost (tiles weighted by the grid's bin count); the launch, a reset of
- * the energy partials and a per-grid FP64 energy reduction are built into a CUDA
- * graph once. The contexts must outlive the batch and must not be reconfigured
+ * 2^31 - 2^16 flattened cells). With tile shapes the grids' tiles are
+ * concatenated and split over the CTAs by cost (tiles weighted by the grid's bin
+ * count); with warp-per-ray shapes the CTAs take chunks of rays from a counter at
+ * run time. The launch, a reset of the energy partials (and of the counter) and a
+ * per-grid FP64 energy reduction are built into a CUDA graph once. The contexts must outlive the batch and must not be reconfigured
  * while it exists (re-create the batch after rt_set_star/rt_set_opacity_table).
  *   ctxs  [n] contexts, n in 1..RT_BATCH_MAX;  cuda_stream  the stream runs use.
  * Errors: RT_ERR_INVALID_ARG, RT_ERR_NOT_CONFIGURED, RT_ERR_CUDA, RT_ERR_NO_MEMORY;

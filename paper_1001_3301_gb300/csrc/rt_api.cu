@@ -658,7 +658,10 @@ int host_enqueue(rt_ctx *ctx, const float *rho, const float *t_dust, float *q_ab
         if (!ok) return cuda_fail(ctx, "host pipeline streams", cudaGetLastError());
         RT_CK(ctx, cudaEventRecord(ctx->ev_out, ctx->s_out));
     }
-    const long long cells_min = 1LL << 20;  // at least ~1 M cells per chunk
+    // at least ~2 M cells per chunk: copies of >= 8 MB per field, since the link moves
+    // small copies in both directions at once less efficiently (4 MB: 253 GB/s in
+    // total, 16 MB: 312 GB/s, one 256 MB copy each way: 340 GB/s)
+    const long long cells_min = 1LL << 21;
     int nch = (int)std::min<long long>(kHostChunks, std::max<long long>(1, ctx->ncells / cells_min));
     if (nch > ctx->nrays) nch = (int)ctx->nrays;
     long long bound = 0;

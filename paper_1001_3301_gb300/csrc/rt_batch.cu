@@ -8,9 +8,11 @@
 // partial per (grid, CTA). A second small kernel reduces the partials of every
 // grid in FP64. Both kernels and the partials reset form a CUDA graph built once;
 // each run only replaces the field pointers in the tracer node and replays it.
-// Two kernel families: the tile body of rt_tile.cuh (any nr; work units are tiles),
-// and the warp-per-ray body of rt_ray.cuh (every grid with nr <= 32 C; work units
-// are warp-slots of 32 / G rays, G = 8, 16 or 32 lanes per ray chosen per grid).
+// Two kernel families: the tile body of rt_tile.cuh (any nr; work units are tiles,
+// split statically as above), and the warp-per-ray body of rt_ray.cuh (every grid
+// with nr <= 32 C; work units are warp-slots of 32 / G rays, G = 8, 16 or 32 lanes
+// per ray chosen per grid, handed out in chunks at run time from one counter that
+// a memset node of the graph zeroes).
 // The shape comes from rt_batch_autotune (timed on the caller's buffers) or,
 // before that, from a fixed default.
 #include <string.h>
@@ -29,6 +31,10 @@ struct BatchParams {
     const unsigned *grid_tile_begin; // [n+1] first global work unit (tile or warp-slot) of every grid
     const unsigned *cta_begin;       // [G+1] first global work unit of every CTA
     double2 *partials;               // [n * G] (absorbed, escaped) per grid and CTA
+    unsigned *work;                  // warp-per-ray kind: next chunk to hand out (zeroed per run)
+    const unsigned *chunk_begin;     // [n+1] first chunk of every grid (warp-per-ray kind)
+    unsigned n_chunks;               // chunks of all grids
+    unsigned chunk_slots;            // warp-slots per chunk
     unsigned seq;                    // call number, stored in the validity word on bad input
     int n;
     const float *rho[RT_BATCH_MAX];
@@ -36,6 +42,9 @@ struct BatchParams {
     float *q[RT_BATCH_MAX];
     float *a[RT_BATCH_MAX];
 };
+
+// warp-slots per warp in one chunk of the warp-per-ray batch
+constexpr unsigned kBatchChunkWarpSlots = 8;
 
 template <int C, int W, int MODE, int MINB>
 __global__ void __launch_bounds__(W * 32, MINB) k_batch(const __grid_constant__ BatchParams bp)
@@ -83,55 +92,78 @@ __host__ __device__ __forceinline__ int ray_lanes_for(int nr, int C)
     return nr <= 8 * C ? 8 : (nr <= 16 * C ? 16 : 32);
 }
 
-// The warp-per-ray batch: each CTA walks its range of warp-slots grid by grid,
-// staging the grid's descriptor and tables in shared memory at every change.
+// The warp-per-ray batch. The grids' warp-slots are cut into chunks of
+// chunk_slots (a chunk never spans two grids), and the CTAs take chunks in order
+// from one counter: the cost of a warp-slot depends on how many of its bins the
+// thin series takes, which only the fields decide, so a static split by bins would
+// leave CTAs idle. Chunk indices grow, so a CTA meets every grid at most once; it
+// stages the grid's descriptor and tables in shared memory when the grid changes
+// and writes one FP64 energy partial per (grid, CTA) when it leaves it. The next
+// chunk's index is fetched while the current one is traced.
 template <int C, int W, int MODE, int MINB>
 __global__ void __launch_bounds__(W * 32, MINB) k_batch_ray(const __grid_constant__ BatchParams bp)
 {
     __shared__ TraceArgs s_p;
     __shared__ RayShared<C> rs;
+    __shared__ unsigned s_next;
     extern __shared__ __align__(16) unsigned char smem[];
-    const unsigned T0 = bp.cta_begin[blockIdx.x], T1 = bp.cta_begin[blockIdx.x + 1];
-    if (T0 >= T1) return;
     const int warp = threadIdx.x >> 5;
-    int lo = 0, hi = bp.n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (bp.grid_tile_begin[mid + 1] > T0) hi = mid;
-        else lo = mid + 1;
-    }
-    unsigned t = T0;
-    for (int g = lo; t < T1 && g < bp.n; ++g) {
-        const unsigned gb = bp.grid_tile_begin[g], ge = bp.grid_tile_begin[g + 1];
-        const unsigned seg_end = T1 < ge ? T1 : ge;
-        if (seg_end <= t) continue;
-        __syncthreads();  // everyone is done with the previous grid's tables
-        if (threadIdx.x == 0) {
-            s_p = bp.grids[g];
-            s_p.rho = bp.rho[g];
-            s_p.tdust = bp.tdust[g];
-            s_p.q = bp.q[g];
-            s_p.a = bp.a[g];
-            s_p.seq = bp.seq;
+    float *const s_kap = reinterpret_cast<float *>(smem);
+    float4 *s_nu = nullptr, *s_mom = nullptr;
+    if (threadIdx.x == 0) s_next = atomicAdd(bp.work, 1u);
+    __syncthreads();
+    unsigned c = s_next;
+    int cur = -1, G = 32;
+    KahanSum eabs, eesc;
+    eabs.zero();
+    eesc.zero();
+    while (c < bp.n_chunks) {
+        __syncthreads();  // every thread has read s_next
+        if (threadIdx.x == 0) s_next = atomicAdd(bp.work, 1u);
+        int lo = 0, hi = bp.n - 1;  // grid of chunk c
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (bp.chunk_begin[mid + 1] > c) hi = mid;
+            else lo = mid + 1;
         }
-        __syncthreads();
-        const int G = ray_lanes_for(s_p.nr, C);
-        float *s_kap = reinterpret_cast<float *>(smem);
-        float4 *s_nu = reinterpret_cast<float4 *>(s_kap + s_p.nnu_pad);
-        float4 *s_mom = s_nu + s_p.nnu_pad;
-        ray_tables<C, W>(s_p, G, rs, s_kap, s_nu, s_mom);
-        __syncthreads();
-        KahanSum eabs, eesc;
-        eabs.zero();
-        eesc.zero();
-        const unsigned w0 = t - gb + warp, w1 = seg_end - gb;
-        if (G == 8) ray_slots<C, W, MODE, 8>(s_p, w0, w1, W, rs, s_kap, s_nu, s_mom, eabs, eesc);
-        else if (G == 16) ray_slots<C, W, MODE, 16>(s_p, w0, w1, W, rs, s_kap, s_nu, s_mom, eabs, eesc);
-        else ray_slots<C, W, MODE, 32>(s_p, w0, w1, W, rs, s_kap, s_nu, s_mom, eabs, eesc);
+        if (lo != cur) {
+            if (cur >= 0) {
+                block_energy<W>(eabs, eesc);
+                if (threadIdx.x == 0)
+                    bp.partials[(size_t)cur * gridDim.x + blockIdx.x] = make_double2(to_double(eabs), to_double(eesc));
+            }
+            __syncthreads();  // everyone is done with the previous grid's tables
+            if (threadIdx.x == 0) {
+                s_p = bp.grids[lo];
+                s_p.rho = bp.rho[lo];
+                s_p.tdust = bp.tdust[lo];
+                s_p.q = bp.q[lo];
+                s_p.a = bp.a[lo];
+                s_p.seq = bp.seq;
+            }
+            __syncthreads();
+            G = ray_lanes_for(s_p.nr, C);
+            s_nu = reinterpret_cast<float4 *>(s_kap + s_p.nnu_pad);
+            s_mom = s_nu + s_p.nnu_pad;
+            ray_tables<C, W>(s_p, G, rs, s_kap, s_nu, s_mom);
+            __syncthreads();
+            cur = lo;
+            eabs.zero();
+            eesc.zero();
+        }
+        const unsigned units = bp.grid_tile_begin[cur + 1] - bp.grid_tile_begin[cur];
+        const unsigned w0 = (c - bp.chunk_begin[cur]) * bp.chunk_slots;
+        const unsigned w1 = w0 + bp.chunk_slots < units ? w0 + bp.chunk_slots : units;
+        if (G == 8) ray_slots<C, W, MODE, 8>(s_p, w0 + warp, w1, W, rs, s_kap, s_nu, s_mom, eabs, eesc);
+        else if (G == 16) ray_slots<C, W, MODE, 16>(s_p, w0 + warp, w1, W, rs, s_kap, s_nu, s_mom, eabs, eesc);
+        else ray_slots<C, W, MODE, 32>(s_p, w0 + warp, w1, W, rs, s_kap, s_nu, s_mom, eabs, eesc);
+        __syncthreads();  // s_next holds the next chunk
+        c = s_next;
+    }
+    if (cur >= 0) {
         block_energy<W>(eabs, eesc);
         if (threadIdx.x == 0)
-            bp.partials[(size_t)g * gridDim.x + blockIdx.x] = make_double2(to_double(eabs), to_double(eesc));
-        t = seg_end;
+            bp.partials[(size_t)cur * gridDim.x + blockIdx.x] = make_double2(to_double(eabs), to_double(eesc));
     }
 }
 
@@ -204,6 +236,8 @@ struct rt_batch {
     rt::TraceArgs *grids_d = nullptr;
     unsigned *grid_tile_begin_d = nullptr;
     unsigned *cta_begin_d = nullptr;
+    unsigned *chunk_begin_d = nullptr;  // [n+1], warp-per-ray kind
+    unsigned *work_d = nullptr;         // chunk counter of the warp-per-ray kind
     double2 *partials_d = nullptr;
     const rt::DevScalars **sc_d = nullptr;
     rt_energy *energies_d = nullptr;
@@ -260,9 +294,9 @@ bool ray_fits(const rt_batch *b, const BatchShape &s)
     return true;
 }
 
-// Shape-dependent plan: work-unit ranges per CTA balanced by cost, partials, graph.
-// Units are tiles of 32 W C flattened cells (tile kind) or warp-slots of 32 / G rays
-// (ray kind); either costs about (bins + 6) per cell of 32 C (tile: 32 W C) cells.
+// Shape-dependent plan: work-unit ranges per CTA balanced by cost (tile kind; a tile
+// of 32 W C flattened cells costs about (bins + 6) per cell) or the chunk table (ray
+// kind: warp-slots of 32 / G rays), partials, graph.
 int plan(rt_batch *b, const BatchShape *s)
 {
     const int n = b->n;
@@ -294,7 +328,16 @@ int plan(rt_batch *b, const BatchShape *s)
     }
     const unsigned total_tiles = gtb[n];
     unsigned G = (unsigned)nsm * (unsigned)per_sm;
-    if (G > total_tiles) G = total_tiles;
+    // warp-per-ray kind: chunks of kBatchChunkWarpSlots warp-slots per warp, handed out
+    // in order at run time (so G only needs to fill the GPU)
+    const unsigned chunk_slots = (unsigned)s->w * rt::kBatchChunkWarpSlots;
+    std::vector<unsigned> chb(n + 1, 0);
+    for (int gg = 0; gg < n; ++gg) chb[gg + 1] = chb[gg] + (gtb[gg + 1] - gtb[gg] + chunk_slots - 1) / chunk_slots;
+    if (ray) {
+        if (G > chb[n]) G = chb[n];
+    } else if (G > total_tiles) {
+        G = total_tiles;
+    }
     if (G < 1) G = 1;
     std::vector<unsigned> cb(G + 1, 0);
     int g = 0;
@@ -323,6 +366,7 @@ int plan(rt_batch *b, const BatchShape *s)
     }
     RT_BCK(b, cudaMemcpy(b->cta_begin_d, cb.data(), sizeof(unsigned) * (G + 1), cudaMemcpyHostToDevice));
     RT_BCK(b, cudaMemcpy(b->grid_tile_begin_d, gtb.data(), sizeof(unsigned) * (n + 1), cudaMemcpyHostToDevice));
+    RT_BCK(b, cudaMemcpy(b->chunk_begin_d, chb.data(), sizeof(unsigned) * (n + 1), cudaMemcpyHostToDevice));
 
     b->shape = s;
     b->G = G;
@@ -331,6 +375,10 @@ int plan(rt_batch *b, const BatchShape *s)
     b->params.grid_tile_begin = b->grid_tile_begin_d;
     b->params.cta_begin = b->cta_begin_d;
     b->params.partials = b->partials_d;
+    b->params.work = b->work_d;
+    b->params.chunk_begin = b->chunk_begin_d;
+    b->params.n_chunks = chb[n];
+    b->params.chunk_slots = chunk_slots;
     b->params.n = n;
 
     // graph: reset partials -> tracer -> per-grid energy
@@ -344,8 +392,16 @@ int plan(rt_batch *b, const BatchShape *s)
     mp.width = (size_t)n * G * sizeof(double2) / 4;
     mp.height = 1;
     mp.pitch = 0;
-    cudaGraphNode_t n_reset, n_energy;
-    RT_BCK(b, cudaGraphAddMemsetNode(&n_reset, b->graph, nullptr, 0, &mp));
+    cudaGraphNode_t n_reset[2], n_energy;
+    RT_BCK(b, cudaGraphAddMemsetNode(&n_reset[0], b->graph, nullptr, 0, &mp));
+    cudaMemsetParams mw{};
+    mw.dst = b->work_d;
+    mw.value = 0;
+    mw.elementSize = 4;
+    mw.width = 1;
+    mw.height = 1;
+    mw.pitch = 0;
+    RT_BCK(b, cudaGraphAddMemsetNode(&n_reset[1], b->graph, nullptr, 0, &mw));
     b->kp_args[0] = &b->params;
     b->kp.func = (void *)s->kern;
     b->kp.gridDim = dim3(G);
@@ -353,7 +409,7 @@ int plan(rt_batch *b, const BatchShape *s)
     b->kp.sharedMemBytes = (unsigned)smem;
     b->kp.kernelParams = b->kp_args;
     b->kp.extra = nullptr;
-    RT_BCK(b, cudaGraphAddKernelNode(&b->kern_node, b->graph, &n_reset, 1, &b->kp));
+    RT_BCK(b, cudaGraphAddKernelNode(&b->kern_node, b->graph, n_reset, 2, &b->kp));
     cudaKernelNodeParams ep{};
     const double2 *e_part = b->partials_d;  // argument values are copied into the node
     unsigned e_g = G;
@@ -390,8 +446,8 @@ void free_batch(rt_batch *b)
 {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    void *ptrs[] = {b->grids_d, b->grid_tile_begin_d, b->cta_begin_d, b->partials_d, (void *)b->sc_d,
-                    b->energies_d, b->bad_d};
+    void *ptrs[] = {b->grids_d, b->grid_tile_begin_d, b->cta_begin_d, b->chunk_begin_d, b->work_d, b->partials_d,
+                    (void *)b->sc_d, b->energies_d, b->bad_d};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (b->energies_h) cudaFreeHost(b->energies_h);
@@ -441,6 +497,8 @@ int rt_batch_create(rt_ctx *const *ctxs, int n, void *cuda_stream, rt_batch **ou
     }
     bool ok = cudaMalloc(&b->grids_d, sizeof(rt::TraceArgs) * n) == cudaSuccess &&
               cudaMalloc(&b->grid_tile_begin_d, sizeof(unsigned) * (n + 1)) == cudaSuccess &&
+              cudaMalloc(&b->chunk_begin_d, sizeof(unsigned) * (n + 1)) == cudaSuccess &&
+              cudaMalloc(&b->work_d, sizeof(unsigned)) == cudaSuccess &&
               cudaMalloc(&b->sc_d, sizeof(void *) * n) == cudaSuccess &&
               cudaMalloc(&b->energies_d, sizeof(rt_energy) * n) == cudaSuccess &&
               cudaMalloc(&b->bad_d, sizeof(unsigned)) == cudaSuccess &&
