@@ -106,10 +106,11 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
                 }
             }
         } else {
+            // cells past the ray's end: no density, no dust (their column is 0 with any t_sub)
 #pragma unroll
             for (int j = 0; j < C; ++j) {
                 rho[j] = 0.0f;
-                td[j] = 0.0f;
+                td[j] = INFINITY;
                 if (j < nv) {
                     rho[j] = __ldg(p.rho + base + j);
                     td[j] = __ldg(p.tdust + base + j);
@@ -126,14 +127,13 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
 #pragma unroll
         for (int j = 0; j < C; ++j) {
             const bool dust = td[j] <= p.t_sub;
-            const float d = (j < nv && dust) ? rho[j] * rs.dr[j][lane] : 0.0f;
+            const float d = dust ? rho[j] * rs.dr[j][lane] : 0.0f;
             D.set(j, d);
-            if (j < nv) {
-                bad |= !(rho[j] >= 0.0f && rho[j] <= FLT_MAX) || (td[j] != td[j]);
-                if (dust && d == 0.0f) zero_m |= 1u << j;
-            }
+            bad |= !(rho[j] >= 0.0f && rho[j] <= FLT_MAX) || (td[j] != td[j]);
+            if (dust && d == 0.0f) zero_m |= 1u << j;
             lsum.add(d);
         }
+        zero_m &= nv >= 32 ? 0xffffffffu : (1u << nv) - 1u;  // cells of the ray only
         if (__any_sync(0xffffffffu, bad) && lane == 0) atomicMax(p.bad_input, p.seq);
 
         // exclusive prefix along the ray: scan of the lane sums within the segment
@@ -171,15 +171,17 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
         const int bt = thin_count(s_nu, na, lane, nmax);
         const float *thin_row = p.kap + kKapTable + bt * kThinStride;
         if (bt > 0) thin_series<C>(thin_row, N.v, D.v, acc.v);
-        const BinClasses bc = classify_bins(s_nu, na, lane, dmax, dmin, bt);
-        const int t1 = max(bc.b1, bt), t2 = max(bc.b2, bt), t3 = max(bc.b3, bt), t5 = max(bc.b5, bt);
-        const int tb = max(bc.bb, bt);
-        moment_range<1, C>(bt, t1, s_nu, s_mom, N.v, D.v, acc.v);
-        moment_range<2, C>(t1, t2, s_nu, s_mom, N.v, D.v, acc.v);
-        bin_range<3, C>(t2, t3, s_nu, N.v, D.v, acc.v);
-        bin_range<5, C>(t3, t5, s_nu, N.v, D.v, acc.v);
-        bin_range<6, C>(t5, tb, s_nu, N.v, D.v, acc.v);
-        bin_range<7, C>(tb, na, s_nu, N.v, D.v, acc.v);
+        if (bt < na) {  // warp-uniform
+            const BinClasses bc = classify_bins(s_nu, na, lane, dmax, dmin, bt);
+            const int t1 = max(bc.b1, bt), t2 = max(bc.b2, bt), t3 = max(bc.b3, bt), t5 = max(bc.b5, bt);
+            const int tb = max(bc.bb, bt);
+            moment_range<1, C>(bt, t1, s_nu, s_mom, N.v, D.v, acc.v);
+            moment_range<2, C>(t1, t2, s_nu, s_mom, N.v, D.v, acc.v);
+            bin_range<3, C>(t2, t3, s_nu, N.v, D.v, acc.v);
+            bin_range<5, C>(t3, t5, s_nu, N.v, D.v, acc.v);
+            bin_range<6, C>(t5, tb, s_nu, N.v, D.v, acc.v);
+            bin_range<7, C>(tb, na, s_nu, N.v, D.v, acc.v);
+        }
 
         // cells with dust but no column: the rho -> 0 force limit sum_i kappa_i g_i
         if (__any_sync(0xffffffffu, zero_m != 0u)) {
@@ -198,7 +200,7 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
         const float w = live ? __ldg(p.domega32 + ray) : 0.0f;
         {
             float s = 0.0f;
-            for (int i = bt + ll; i < p.nnu_pad; i += G) s += ex2_approx(fmaf(s_nu[i].x, ntot, s_nu[i].z));
+            for (int i = bt + ll; i < na; i += G) s += ex2_approx(fmaf(s_nu[i].x, ntot, s_nu[i].z));
             for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             if (ll == 0) {
                 if (bt > 0) s += thin_escape(thin_row, ntot);
@@ -207,15 +209,16 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
         }
 
         // outputs and the lane's absorbed power
+        // (a cell with no column, past the ray or without dust or density, absorbed 0)
         float qv[C], av[C];
         float lane_abs = 0.0f;
 #pragma unroll
         for (int j = 0; j < C; ++j) {
             const float aj = acc.get(j), dj = D.get(j);
             const bool zc = (zero_m >> j) & 1u;
-            qv[j] = zc ? 0.0f : rs.gq[j][lane] * aj;
+            qv[j] = rs.gq[j][lane] * aj;
             av[j] = rs.ga[j][lane] * (zc ? dj : (dj > 0.0f ? __fdividef(aj, dj) : 0.0f));
-            lane_abs += (j < nv && !zc) ? aj : 0.0f;
+            lane_abs += aj;
         }
         eabs.add(lane_abs * w);
         if (vec && nv == C) {
