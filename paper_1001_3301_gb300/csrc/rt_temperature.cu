@@ -26,6 +26,11 @@
 namespace rt {
 
 constexpr int kTempNodes = 1024;
+// the context's table buffer: lkp [kTempNodes], inv [kTempNodes + 2], then (16-byte
+// aligned) the cubic coefficients of both, [kTempNodes - 1] float4 each
+constexpr int kTempCoefLkp = ((2 * kTempNodes + 2 + 3) / 4) * 4;
+constexpr int kTempCoefInv = kTempCoefLkp + 4 * (kTempNodes - 1);
+constexpr int kTempTableFloats = kTempCoefInv + 4 * (kTempNodes - 1);
 constexpr double kTempLnLo = 0.0;                    // ln 1 K
 constexpr double kTempLnHi = 11.512925464970229;     // ln 1e5 K
 
@@ -98,102 +103,164 @@ __global__ void __launch_bounds__(1024) k_inverse_table(const float *lkp, float 
     }
 }
 
+// Per-interval cubic coefficients of a node table (the cubic Hermite interpolation of
+// interp_d, with the same tangents): on interval k, t in [0, 1],
+//   f = c0 + t (c1 + t (c2 + t c3)),  c0 = p0, c1 = m0, c2 = 3 (p1 - p0) - 2 m0 - m1,
+//   c3 = 2 (p0 - p1) + m0 + m1,
+// so a cell evaluates one interval with one 16-byte load and three FMAs.
+__global__ void k_hermite_coeffs(const float *s, float4 *c)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < kTempNodes - 1; k += gridDim.x * blockDim.x) {
+        const double p0 = s[k], p1 = s[k + 1];
+        const double m0 = 0.5 * (p1 - s[k > 0 ? k - 1 : 0]) * (k > 0 ? 1.0 : 2.0);
+        const double m1 = 0.5 * (s[k + 2 < kTempNodes ? k + 2 : kTempNodes - 1] - p0) * (k + 2 < kTempNodes ? 1.0 : 2.0);
+        c[k] = make_float4((float)p0, (float)m0, (float)(3.0 * (p1 - p0) - 2.0 * m0 - m1),
+                           (float)(2.0 * (p0 - p1) + m0 + m1));
+    }
+}
+
 struct TempArgs {
     const float *a_rad;
     const float *e_rad;   // may be null (E_R = 0)
     float *t_out;
     const float *lkp;     // [kTempNodes] ln kappa_P on the uniform ln T grid
     const float *inv;     // [kTempNodes + 2] ln T on the uniform grid of 4 ln T + ln kappa_P
+    const float4 *c_lkp;  // [kTempNodes - 1] cubic coefficients of lkp per interval
+    const float4 *c_inv;  // [kTempNodes - 1] the same of inv
+    int vec;              // a_rad, e_rad (if any) and t_out are 16-byte aligned
     long long n;
     float y0, inv_dy;     // grid origin and 1 / spacing
     float ln_a;           // ln of the radiation constant a = 4 sigma / c
 };
 
-// ln kappa_P(e^y) and its derivative by cubic Hermite interpolation
-__device__ __forceinline__ void interp(const float *s, float y, float y0, float inv_dy, float &L, float &dL)
+// ln kappa_P(e^y) and its derivative from the per-interval coefficients; lo, hi: the
+// node values held outside the table.
+__device__ __forceinline__ void interp_c(const float4 *c, float lo, float hi, float y, float y0, float inv_dy,
+                                         float &L, float &dL)
 {
-    float u = (y - y0) * inv_dy;
+    const float u = (y - y0) * inv_dy;
     if (!(u > 0.0f)) {  // below the table (or NaN): constant
-        L = s[0];
+        L = lo;
         dL = 0.0f;
         return;
     }
     if (u >= (float)(kTempNodes - 1)) {
-        L = s[kTempNodes - 1];
+        L = hi;
         dL = 0.0f;
         return;
     }
     const int k = min((int)u, kTempNodes - 2);
     const float t = u - (float)k;
-    const float p0 = s[k], p1 = s[k + 1];
-    const float m0 = 0.5f * (p1 - s[k > 0 ? k - 1 : 0]) * (k > 0 ? 1.0f : 2.0f);
-    const float m1 = 0.5f * (s[k + 2 < kTempNodes ? k + 2 : kTempNodes - 1] - p0) * (k + 2 < kTempNodes ? 1.0f : 2.0f);
-    const float t2 = t * t, t3 = t2 * t;
-    L = (2.0f * t3 - 3.0f * t2 + 1.0f) * p0 + (t3 - 2.0f * t2 + t) * m0 + (-2.0f * t3 + 3.0f * t2) * p1 +
-        (t3 - t2) * m1;
-    dL = ((6.0f * t2 - 6.0f * t) * p0 + (3.0f * t2 - 4.0f * t + 1.0f) * m0 + (-6.0f * t2 + 6.0f * t) * p1 +
-          (3.0f * t2 - 2.0f * t) * m1) *
-         inv_dy;
+    const float4 q = __ldg(c + k);
+    L = fmaf(fmaf(fmaf(q.w, t, q.z), t, q.y), t, q.x);
+    dL = fmaf(fmaf(3.0f * q.w, t, 2.0f * q.z), t, q.y) * inv_dy;
 }
 
+// e^y for |y| up to ~88 from the hardware 2^x: y log2(e) is formed as hi + lo with an
+// FMA (Dekker's product, log2(e) split into two floats), so the rounding of the
+// product does not grow with |y|; e^y = 2^hi (1 + lo ln 2) to about 2^-22.
+__device__ __forceinline__ float exp_ex2(float y)
+{
+    constexpr float kL2eHi = 1.44269502162933349609375f;  // log2(e) rounded to float
+    constexpr float kL2eLo = 1.92596298909109e-8f;        // log2(e) - kL2eHi
+    const float hi = y * kL2eHi;
+    const float lo = fmaf(y, kL2eHi, -hi) + y * kL2eLo;
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(hi));
+    return fmaf(r, lo * 0.69314718055994530942f, r);
+}
+
+// ln x for x > 0 from the hardware log2 (absolute error ~2^-22 in log2 x)
+__device__ __forceinline__ float log_lg2(float x)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r * 0.69314718055994530942f;
+}
+
+// The table ends and the inverse table's grid, read once per thread.
+struct TempConsts {
+    float l_lo, l_hi, i_lo, i_hi, x_lo, x_hi, inv_dx;
+};
+
+// T of one cell (Eq. 16): a T^4 = E_R + a_rad / kappa_P(T); 0 where both sources vanish.
+__device__ __forceinline__ float cell_temperature(const TempArgs &p, const TempConsts &k, float ar, float er)
+{
+    ar = fmaxf(ar, 0.0f);
+    er = fmaxf(er, 0.0f);
+    if (!(ar > 0.0f) && !(er > 0.0f)) return 0.0f;
+    float L, dL, y;
+    if (!(er > 0.0f)) {
+        // X(y) = 4 y + L(y) = ln a_rad - ln a: the inverse table, then Newton steps until one
+        // is below 2e-6 (quadratic convergence: normally the step from the table and one
+        // more that confirms it)
+        const float x = log_lg2(ar) - p.ln_a;
+        if (x <= k.x_lo) {
+            y = 0.25f * (x - k.l_lo);
+        } else if (x >= k.x_hi) {
+            y = 0.25f * (x - k.l_hi);
+        } else {
+            float yi, dyi;
+            interp_c(p.c_inv, k.i_lo, k.i_hi, x, k.x_lo, k.inv_dx, yi, dyi);
+            y = yi;
+        }
+        for (int it = 0; it < 24; ++it) {
+            interp_c(p.c_lkp, k.l_lo, k.l_hi, y, p.y0, p.inv_dy, L, dL);
+            float dy = -__fdividef(4.0f * y + L - x, fmaxf(4.0f + dL, 0.5f));  // the step, not the root: fast divide
+            dy = fminf(fmaxf(dy, -2.0f), 2.0f);
+            y += dy;
+            if (fabsf(dy) < 2e-6f) break;
+        }
+        return exp_ex2(y);
+    }
+    // Newton on F(y) = 4 y + ln a - ln(E_R + a_rad e^{-L}) from 300 K's opacity; it
+    // converges quadratically: once a step is below 1e-5 the next one reaches the FP32
+    // resolution of ln T, so one more step ends the solve
+    interp_c(p.c_lkp, k.l_lo, k.l_hi, 5.7037825f, p.y0, p.inv_dy, L, dL);
+    y = 0.25f * (logf(er + ar * expf(-L)) - p.ln_a);
+    bool close = false;
+    for (int it = 0; it < 24; ++it) {
+        interp_c(p.c_lkp, k.l_lo, k.l_hi, y, p.y0, p.inv_dy, L, dL);
+        const float src = ar * expf(-L);
+        const float rhs = er + src;
+        const float f = 4.0f * y + p.ln_a - logf(rhs);
+        const float fp = 4.0f + dL * __fdividef(src, rhs);
+        float dy = -__fdividef(f, fmaxf(fp, 0.5f));
+        dy = fminf(fmaxf(dy, -2.0f), 2.0f);
+        y += dy;
+        if (close) break;
+        close = fabsf(dy) < 1e-5f;
+    }
+    return expf(y);
+}
+
+// Four cells per thread and iteration, moved as 16-byte vectors where the fields allow
+// (p.vec): one load in flight per thread would leave HBM latency-bound.
 __global__ void __launch_bounds__(256) k_dust_temperature(const TempArgs p)
 {
-    __shared__ float s[kTempNodes], s_inv[kTempNodes + 2];
-    for (int i = threadIdx.x; i < kTempNodes; i += blockDim.x) s[i] = p.lkp[i];
-    for (int i = threadIdx.x; i < kTempNodes + 2; i += blockDim.x) s_inv[i] = p.inv[i];
-    __syncthreads();
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < p.n;
-         c += (long long)gridDim.x * blockDim.x) {
-        const float ar = fmaxf(p.a_rad[c], 0.0f);
-        const float er = p.e_rad ? fmaxf(p.e_rad[c], 0.0f) : 0.0f;
-        if (!(ar > 0.0f) && !(er > 0.0f)) {
-            p.t_out[c] = 0.0f;
-            continue;
-        }
-        float L, dL, y;
-        if (!(er > 0.0f)) {
-            // X(y) = 4 y + L(y) = ln a_rad - ln a: the inverse table, then Newton steps
-            // until one is below 2e-6 (quadratic convergence: one step from the table)
-            const float x = logf(ar) - p.ln_a;
-            const float x_lo = s_inv[kTempNodes], x_hi = s_inv[kTempNodes + 1];
-            if (x <= x_lo) {
-                y = 0.25f * (x - s[0]);
-            } else if (x >= x_hi) {
-                y = 0.25f * (x - s[kTempNodes - 1]);
-            } else {
-                float yi, dyi;
-                interp(s_inv, x, x_lo, (float)(kTempNodes - 1) / (x_hi - x_lo), yi, dyi);
-                y = yi;
-            }
-            for (int it = 0; it < 24; ++it) {
-                interp(s, y, p.y0, p.inv_dy, L, dL);
-                float dy = -__fdividef(4.0f * y + L - x, fmaxf(4.0f + dL, 0.5f));  // the step, not the root: fast divide
-                dy = fminf(fmaxf(dy, -2.0f), 2.0f);
-                y += dy;
-                if (fabsf(dy) < 2e-6f) break;
-            }
-        } else {
-            // Newton on F(y) = 4 y + ln a - ln(E_R + a_rad e^{-L}) from 300 K's opacity;
-            // it converges quadratically: once a step is below 1e-5 the next one reaches
-            // the FP32 resolution of ln T, so one more step ends the solve
-            interp(s, 5.7037825f, p.y0, p.inv_dy, L, dL);
-            y = 0.25f * (logf(er + ar * expf(-L)) - p.ln_a);
-            bool close = false;
-            for (int it = 0; it < 24; ++it) {
-                interp(s, y, p.y0, p.inv_dy, L, dL);
-                const float src = ar * expf(-L);
-                const float rhs = er + src;
-                const float f = 4.0f * y + p.ln_a - logf(rhs);
-                const float fp = 4.0f + dL * __fdividef(src, rhs);
-                float dy = -__fdividef(f, fmaxf(fp, 0.5f));
-                dy = fminf(fmaxf(dy, -2.0f), 2.0f);
-                y += dy;
-                if (close) break;
-                close = fabsf(dy) < 1e-5f;
-            }
-        }
-        p.t_out[c] = expf(y);
+    TempConsts k;
+    k.l_lo = __ldg(p.lkp);
+    k.l_hi = __ldg(p.lkp + kTempNodes - 1);
+    k.i_lo = __ldg(p.inv);
+    k.i_hi = __ldg(p.inv + kTempNodes - 1);
+    k.x_lo = __ldg(p.inv + kTempNodes);
+    k.x_hi = __ldg(p.inv + kTempNodes + 1);
+    k.inv_dx = (float)(kTempNodes - 1) / (k.x_hi - k.x_lo);
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long n4 = p.vec ? p.n / 4 : 0;
+    for (long long v = tid; v < n4; v += stride) {
+        const float4 a4 = __ldg(reinterpret_cast<const float4 *>(p.a_rad) + v);
+        const float4 e4 = p.e_rad ? __ldg(reinterpret_cast<const float4 *>(p.e_rad) + v) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 t4;
+        t4.x = cell_temperature(p, k, a4.x, e4.x);
+        t4.y = cell_temperature(p, k, a4.y, e4.y);
+        t4.z = cell_temperature(p, k, a4.z, e4.z);
+        t4.w = cell_temperature(p, k, a4.w, e4.w);
+        reinterpret_cast<float4 *>(p.t_out)[v] = t4;
     }
+    for (long long c = 4 * n4 + tid; c < p.n; c += stride)
+        p.t_out[c] = cell_temperature(p, k, p.a_rad[c], p.e_rad ? p.e_rad[c] : 0.0f);
 }
 
 }  // namespace
@@ -267,7 +334,7 @@ int rt_dust_temperature(rt_ctx *ctx, const float *a_rad, const float *e_rad, flo
     float *&lkp = ctx_temp_table(ctx);
     unsigned long long &fp = ctx_temp_fingerprint(ctx);
     if (!lkp || fp != in.table_fingerprint) {
-        if (!lkp && cudaMalloc(&lkp, sizeof(float) * (2 * kTempNodes + 2)) != cudaSuccess) {
+        if (!lkp && cudaMalloc(&lkp, sizeof(float) * kTempTableFloats) != cudaSuccess) {
             lkp = nullptr;
             cudaGetLastError();
             return ctx_fail(ctx, RT_ERR_NO_MEMORY, "Planck-mean table");
@@ -279,6 +346,8 @@ int rt_dust_temperature(rt_ctx *ctx, const float *a_rad, const float *e_rad, flo
         const int rc = planck_means(in, tn, nullptr, lkp, in.stream, err);
         if (rc != RT_OK) return ctx_fail(ctx, rc, err);
         k_inverse_table<<<1, 1024, 0, in.stream>>>(lkp, lkp + kTempNodes, kTempLnLo, kTempLnHi);
+        k_hermite_coeffs<<<4, 256, 0, in.stream>>>(lkp, reinterpret_cast<float4 *>(lkp + kTempCoefLkp));
+        k_hermite_coeffs<<<4, 256, 0, in.stream>>>(lkp + kTempNodes, reinterpret_cast<float4 *>(lkp + kTempCoefInv));
         if (cudaGetLastError() != cudaSuccess) return ctx_fail(ctx, RT_ERR_CUDA, "inverse temperature table");
         fp = in.table_fingerprint;
     }
@@ -289,13 +358,16 @@ int rt_dust_temperature(rt_ctx *ctx, const float *a_rad, const float *e_rad, flo
     p.t_out = t_dust;
     p.lkp = lkp;
     p.inv = lkp + kTempNodes;
+    p.c_lkp = reinterpret_cast<const float4 *>(lkp + kTempCoefLkp);
+    p.c_inv = reinterpret_cast<const float4 *>(lkp + kTempCoefInv);
+    p.vec = ((reinterpret_cast<size_t>(a_rad) | reinterpret_cast<size_t>(e_rad) | reinterpret_cast<size_t>(t_dust)) % 16) == 0;
     p.n = in.ncells;
     p.y0 = (float)kTempLnLo;
     p.inv_dy = (float)((kTempNodes - 1) / (kTempLnHi - kTempLnLo));
     p.ln_a = (float)log(4.0 * sigma / kC);
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, in.dev);
-    long long blocks = (in.ncells + 255) / 256;
+    long long blocks = (in.ncells / 4 + 255) / 256;
     if (blocks > 8LL * nsm) blocks = 8LL * nsm;
     if (blocks < 1) blocks = 1;
     k_dust_temperature<<<(unsigned)blocks, 256, 0, in.stream>>>(p);
