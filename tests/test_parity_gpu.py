@@ -365,7 +365,7 @@ def test_host_path_pipelined_chunks():
     the energy (partials grouped differently) to rounding."""
     import torch
     from paper_1001_3301_gb300 import Tracer
-    w = synth.disk3d(256, 96, 160, n_nu=32, tau550=10.0, seed=8)   # 3.9 M cells: 3 chunks
+    w = synth.disk3d(256, 128, 192, n_nu=32, tau550=10.0, seed=8)   # 6.3 M cells: 3 chunks
     tr = Tracer.from_grid(w.grid)
     tr.set_opacity_table(w.nu, w.kappa, w.t_sub)
     tr.set_star(w.t_star, w.r_star)
