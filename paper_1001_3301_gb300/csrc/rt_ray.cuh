@@ -153,17 +153,6 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
         }
         const float ntot = __shfl_sync(0xffffffffu, pre.value(), G - 1, G);
 
-        // the warp's largest and smallest non-zero column decide each bin's class
-        float dmax = 0.0f, dmin = INFINITY;
-#pragma unroll
-        for (int j = 0; j < C; ++j) {
-            dmax = fmaxf(dmax, D.get(j));
-            if (D.get(j) > 0.0f) dmin = fminf(dmin, D.get(j));
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-            dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
-        }
         const int na = p.n_active;
         // bins thin along all the warp's rays: one series for the lot, the rest bin by bin
         float nmax = ntot;
@@ -172,6 +161,17 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
         const float *thin_row = p.kap + kKapTable + bt * kThinStride;
         if (bt > 0) thin_series<C>(thin_row, N.v, D.v, acc.v);
         if (bt < na) {  // warp-uniform
+            // the warp's largest and smallest non-zero column decide each bin's class
+            float dmax = 0.0f, dmin = INFINITY;
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                dmax = fmaxf(dmax, D.get(j));
+                if (D.get(j) > 0.0f) dmin = fminf(dmin, D.get(j));
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+                dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+            }
             const BinClasses bc = classify_bins(s_nu, na, lane, dmax, dmin, bt);
             const int t1 = max(bc.b1, bt), t2 = max(bc.b2, bt), t3 = max(bc.b3, bt), t5 = max(bc.b5, bt);
             const int tb = max(bc.bb, bt);
