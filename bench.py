@@ -213,6 +213,33 @@ def exact_exp_ops(w, shape):
     return int(np.sum((nbins - bt) * rays)) * nr
 
 
+def roofline_summary(bytes_per_launch, exact_ops, cell_nu_per_launch, avg_launch_s, hbm_peak_gbs,
+                     ex2_peak_gops, ex2_basis):
+    """The tracer's roofline object. Two floors per launch: HBM (16 B per cell at the
+    measured copy bandwidth) and MUFU (one ex2 per (cell, bin) outside the thin series,
+    at the measured ex2 rate); the larger binds, and `frac` is that floor over the
+    average launch time. `mufu` gives the second floor, and `one_ex2_per_cell_nu` the
+    rate against one exponential per cell-nu (the bound the method had before the
+    series; above 1 where the series removes exponentials)."""
+    t_hbm = bytes_per_launch / (hbm_peak_gbs * 1e9)
+    t_mufu = exact_ops / (ex2_peak_gops * 1e9)
+    if t_hbm >= t_mufu:
+        out = {"bound": "hbm", "unit": "GB/s", "achieved": bytes_per_launch / avg_launch_s / 1e9,
+               "peak": hbm_peak_gbs, "frac": t_hbm / avg_launch_s,
+               "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        out = {"bound": "alu", "unit": "Gop/s (MUFU ex2)", "achieved": exact_ops / avg_launch_s / 1e9,
+               "peak": ex2_peak_gops, "frac": t_mufu / avg_launch_s, "peak_basis": ex2_basis}
+    out.update({
+        "avg_launch_ms": avg_launch_s * 1e3, "algorithmic_bytes_per_launch": bytes_per_launch,
+        "mufu": {"exact_ex2_per_launch": exact_ops, "achieved_gops": exact_ops / avg_launch_s / 1e9,
+                 "peak_gops": ex2_peak_gops, "frac": t_mufu / avg_launch_s, "peak_basis": ex2_basis},
+        "one_ex2_per_cell_nu": {"cell_nu_per_s": cell_nu_per_launch / avg_launch_s,
+                                "peak_cell_nu_per_s": ex2_peak_gops * 1e9,
+                                "frac": cell_nu_per_launch / avg_launch_s / (ex2_peak_gops * 1e9)}})
+    return out
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
@@ -412,39 +439,24 @@ def run_ours(args, rank, world, local):
     energies = [tr.energy_last() for tr in tracers]
     max_energy_err = max(abs(e.rel_err) for e in energies)
 
-    # roofline of the tracer kernel. Two floors per launch: HBM (16 B per cell) and
-    # MUFU (one ex2 per (cell, bin) outside the thin series); the larger binds, and
-    # the fraction is that floor over the average launch time.
+    # roofline of the tracer kernel (roofline_summary: the binding floor and both bases)
     avg_launch_s = statistics.mean(x for row in launch_ms for x in row) * 1e-3
     ex2_clk, ffma_clk, probe_mhz = probe_alu_rates()
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     clocks = clk.summary()
     mhz = clocks["sm_mhz"] or probe_mhz
-    peak = ex2_clk * nsm * mhz * 1e6 / 1e9
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    hbm_peak = float(peaks.get("hbm_gbs") or 6678.0)
-    bytes_per_launch = statistics.mean(TRACE_BYTES_PER_CELL * w.grid.ncells for w in ws)
-    exact_ops = statistics.mean(exact_exp_ops(w, shape) for w in ws)
-    t_hbm = bytes_per_launch / (hbm_peak * 1e9)
-    t_mufu = exact_ops / (peak * 1e9)
-    achieved = exact_ops / avg_launch_s / 1e9
+    peak = ex2_clk * nsm * mhz * 1e6 / 1e9   # Gop/s of ex2 (also the temperature-table leg's bound)
     src_hash = kernel_source_hash()
-    traffic = traffic_from_profile(src_hash)
-    if t_hbm >= t_mufu:
-        roofline = {"bound": "hbm", "unit": "GB/s", "achieved": bytes_per_launch / avg_launch_s / 1e9,
-                    "peak": hbm_peak, "frac": t_hbm / avg_launch_s,
-                    "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
-    else:
-        roofline = {"bound": "alu", "unit": "Gop/s (MUFU ex2)", "achieved": achieved, "peak": peak,
-                    "frac": t_mufu / avg_launch_s,
-                    "peak_basis": f"measured {ex2_clk:.2f} ex2/SM/clk x {nsm} SMs x {mhz:.0f} MHz"}
-    roofline.update({
-        "traffic": traffic, "kernel": "k_ray" if shape[0] == 1 else "k_trace",
-        "avg_launch_ms": avg_launch_s * 1e3, "algorithmic_bytes_per_launch": bytes_per_launch,
-        "mufu": {"exact_ex2_per_launch": exact_ops, "achieved_gops": achieved, "peak_gops": peak,
-                 "frac": t_mufu / avg_launch_s,
-                 "peak_basis": f"measured {ex2_clk:.2f} ex2/SM/clk x {nsm} SMs x {mhz:.0f} MHz"},
-        "ffma_per_sm_clk": ffma_clk, "kernel_source_sha256": src_hash})
+    roofline = roofline_summary(
+        bytes_per_launch=statistics.mean(TRACE_BYTES_PER_CELL * w.grid.ncells for w in ws),
+        exact_ops=statistics.mean(exact_exp_ops(w, shape) for w in ws),
+        cell_nu_per_launch=statistics.mean(w.grid.ncells * len(w.nu) for w in ws),
+        avg_launch_s=avg_launch_s, hbm_peak_gbs=float(peaks.get("hbm_gbs") or 6678.0),
+        ex2_peak_gops=peak,
+        ex2_basis=f"measured {ex2_clk:.2f} ex2/SM/clk x {nsm} SMs x {mhz:.0f} MHz")
+    roofline.update({"traffic": traffic_from_profile(src_hash), "kernel": "k_ray" if shape[0] == 1 else "k_trace",
+                     "ffma_per_sm_clk": ffma_clk, "kernel_source_sha256": src_hash})
 
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None

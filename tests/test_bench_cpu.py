@@ -49,3 +49,21 @@ def test_exact_exp_ops_limits():
     big = synth.Workload(w.name, w.grid, w.nu, w.kappa, w.rho * 1e30, w.tdust, tau550=1e30)
     nbins = int(np.count_nonzero(w.kappa > 0))
     assert bench.exact_exp_ops(big, (1, 8, 4, 6)) == w.grid.ncells * nbins
+
+
+def test_roofline_summary_picks_the_binding_floor():
+    """HBM binds when its time per launch is the larger one, MUFU otherwise; frac is the
+    binding floor's time over the launch time, and the two other bases ride along."""
+    # 134 MB at 6678 GB/s = 20.1 us against 1e8 ex2 at 1e4 Gop/s = 10 us: HBM binds
+    r = bench.roofline_summary(bytes_per_launch=134217728, exact_ops=1e8, cell_nu_per_launch=6.627e8,
+                               avg_launch_s=80e-6, hbm_peak_gbs=6678.0, ex2_peak_gops=1e4, ex2_basis="x")
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["frac"] == pytest.approx(134217728 / 6678e9 / 80e-6)
+    assert r["achieved"] / r["peak"] == pytest.approx(r["frac"])
+    assert r["mufu"]["frac"] == pytest.approx(1e8 / 1e13 / 80e-6)
+    assert r["one_ex2_per_cell_nu"]["frac"] == pytest.approx(6.627e8 / 80e-6 / 1e13)
+    # three times the exponentials: MUFU binds
+    r = bench.roofline_summary(bytes_per_launch=134217728, exact_ops=3e8, cell_nu_per_launch=6.627e8,
+                               avg_launch_s=80e-6, hbm_peak_gbs=6678.0, ex2_peak_gops=1e4, ex2_basis="x")
+    assert r["bound"] == "alu" and r["frac"] == pytest.approx(3e8 / 1e13 / 80e-6)
+    assert r["achieved"] / r["peak"] == pytest.approx(r["frac"])
