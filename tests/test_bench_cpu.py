@@ -67,3 +67,14 @@ def test_roofline_summary_picks_the_binding_floor():
                                avg_launch_s=80e-6, hbm_peak_gbs=6678.0, ex2_peak_gops=1e4, ex2_basis="x")
     assert r["bound"] == "alu" and r["frac"] == pytest.approx(3e8 / 1e13 / 80e-6)
     assert r["achieved"] / r["peak"] == pytest.approx(r["frac"])
+
+
+def test_thin_bound_matches_the_library():
+    """bench.THIN_X mirrors the tracer's kThinX (rt_internal.cuh): the count of
+    exponentials above is only right while the two agree."""
+    import os
+    import re
+    src = open(os.path.join(os.path.dirname(bench.__file__), "paper_1001_3301_gb300", "csrc",
+                            "rt_internal.cuh")).read()
+    m = re.search(r"constexpr float kThinX = ([0-9.eE+-]+)f;", src)
+    assert m and float(m.group(1)) == bench.THIN_X
