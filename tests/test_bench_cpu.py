@@ -78,3 +78,10 @@ def test_thin_bound_matches_the_library():
                             "rt_internal.cuh")).read()
     m = re.search(r"constexpr float kThinX = ([0-9.eE+-]+)f;", src)
     assert m and float(m.group(1)) == bench.THIN_X
+
+
+def test_cpu_baseline_samples_every_grid_of_the_step():
+    ws = [synth.disk3d(32, 8, 4, n_nu=16, tau550=t, seed=1) for t in (0.1, 100.0)]
+    r = bench.cpu_baseline(ws, target_s=0.05)
+    assert r["kind"] == "oracle" and r["value"] > 0 and r["cores"] >= 1
+    assert "tau550=0.1" in r["sample"] and "tau550=100" in r["sample"]
