@@ -51,7 +51,11 @@ extern "C" {
 /* ---- precision of the optical-depth scan and of the per-bin arithmetic --- */
 #define RT_FP32_KAHAN 0  /* FP32 bins; column density scanned in compensated
                             (double-float) FP32 and carried across tiles in the
-                            same form. The default. */
+                            same form. The default. In both FP32 modes the
+                            warp-per-ray kernel sums the bins optically thin along
+                            all rays of a warp (kappa_i N_total <= 1/2) as one
+                            power series in the column, truncated below 1e-7 of
+                            the value, instead of bin by bin. */
 #define RT_FP32_PLAIN 1  /* FP32 bins; plain FP32 running sum (precision study) */
 #define RT_FP64       2  /* FP64 scan and FP64 per-bin arithmetic (libm-grade exp
                             and expm1); outputs still rounded to float32 */
