@@ -130,11 +130,12 @@ int trace_shapes(int precision, Shape *out, int max_out);      // tile kernel
 int ray_shapes(int precision, int nr, Shape *out, int max_out);  // ray kernel, 32 C >= nr
 long long trace_tile_cells(Shape s);
 cudaError_t launch_ray_shape(int precision, Shape s, const TraceArgs &args, cudaStream_t stream,
-                             unsigned *grid_out);
+                             unsigned *grid_out, unsigned max_grid = 0);
 // Launches the persistent tracer over `ntiles` tiles; *grid_out receives the
-// number of CTAs (= energy partials written).
+// number of CTAs (= energy partials written). max_grid > 0 caps that number before
+// the launch (the kernels are persistent: any grid of >= 1 CTA covers the work).
 cudaError_t launch_trace(int precision, Shape s, const TraceArgs &args, unsigned ntiles,
-                         cudaStream_t stream, unsigned *grid_out);
+                         cudaStream_t stream, unsigned *grid_out, unsigned max_grid = 0);
 
 // Tracer with temperature-dependent opacity tables (rt_tdep.cu)
 constexpr int kMaxTdepPoints = 32;

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray(const TraceArgs p)
 }
 
 template <int C, int W, int MODE, int MINB, int G>
-cudaError_t launch_ray_g(const TraceArgs &a, cudaStream_t stream, unsigned *grid_out)
+cudaError_t launch_ray_g(const TraceArgs &a, cudaStream_t stream, unsigned *grid_out, unsigned max_grid)
 {
     constexpr int R = 32 / G;
     const size_t smem = ray_bin_smem(a.nnu_pad) + 16;
@@ -60,6 +60,7 @@ cudaError_t launch_ray_g(const TraceArgs &a, cudaStream_t stream, unsigned *grid
     unsigned grid = (unsigned)nsm * (unsigned)per_sm;
     const unsigned need = (a.nrays + W * R - 1) / (W * R);
     if (grid > need) grid = need;
+    if (max_grid > 0 && grid > max_grid) grid = max_grid;
     if (grid < 1) grid = 1;
     kern<<<grid, W * 32, smem, stream>>>(a);
     *grid_out = grid;
@@ -68,16 +69,16 @@ cudaError_t launch_ray_g(const TraceArgs &a, cudaStream_t stream, unsigned *grid
 
 // The fewest lanes per ray that still hold the ray: 8, 16 or 32 (G C >= nr).
 template <int C, int W, int MODE, int MINB>
-cudaError_t launch_ray(const TraceArgs &a, unsigned, cudaStream_t stream, unsigned *grid_out)
+cudaError_t launch_ray(const TraceArgs &a, unsigned, cudaStream_t stream, unsigned *grid_out, unsigned max_grid)
 {
-    if (8 * C >= a.nr) return launch_ray_g<C, W, MODE, MINB, 8>(a, stream, grid_out);
-    if (16 * C >= a.nr) return launch_ray_g<C, W, MODE, MINB, 16>(a, stream, grid_out);
-    return launch_ray_g<C, W, MODE, MINB, 32>(a, stream, grid_out);
+    if (8 * C >= a.nr) return launch_ray_g<C, W, MODE, MINB, 8>(a, stream, grid_out, max_grid);
+    if (16 * C >= a.nr) return launch_ray_g<C, W, MODE, MINB, 16>(a, stream, grid_out, max_grid);
+    return launch_ray_g<C, W, MODE, MINB, 32>(a, stream, grid_out, max_grid);
 }
 
 struct RayEntry {
     int precision, c, w, minb;
-    cudaError_t (*fn)(const TraceArgs &, unsigned, cudaStream_t, unsigned *);
+    cudaError_t (*fn)(const TraceArgs &, unsigned, cudaStream_t, unsigned *, unsigned);
 };
 
 #define RT_RAY(P, C, W, MB) {P, C, W, MB, &launch_ray<C, W, P, MB>}
@@ -101,12 +102,12 @@ int ray_shapes(int precision, int nr, Shape *out, int max_out)
 }
 
 cudaError_t launch_ray_shape(int precision, Shape s, const TraceArgs &args, cudaStream_t stream,
-                             unsigned *grid_out)
+                             unsigned *grid_out, unsigned max_grid)
 {
     for (const RayEntry &e : kRayShapes)
         if (e.precision == precision && e.c == s.cells_per_lane && e.w == s.warps &&
             (s.min_blocks == 0 || e.minb == s.min_blocks) && 32 * e.c >= args.nr)
-            return e.fn(args, 0, stream, grid_out);
+            return e.fn(args, 0, stream, grid_out, max_grid);
     return cudaErrorInvalidValue;
 }
 

@@ -28,7 +28,7 @@ constexpr int kStaticMaxNr = RT_STATIC_MAX_NR;
 constexpr int kStaticMaxTheta = RT_STATIC_MAX_NTHETA;
 constexpr int kStaticMaxPhi = RT_STATIC_MAX_NPHI;
 constexpr long long kStaticMaxRays = RT_STATIC_MAX_RAYS;
-constexpr int kStaticMaxCtas = 8192;  // energy partials: >= SMs x 32 resident CTAs for <= 256 SMs
+constexpr int kStaticMaxCtas = 8192;  // energy partials; the launch is capped at this many CTAs
 
 struct StaticScratch {
     double r_if[kStaticMaxNr + 1];
@@ -214,8 +214,8 @@ extern "C" int rt_irradiate_static(const rt_grid_desc *g, double t_star, double 
     const long long T = rt::trace_tile_cells(shape);
     const unsigned ntiles = (unsigned)((nrays * (g->nr + 1) + T - 1) / T);
     unsigned grid = 0;
-    RT_SCK(rt::launch_trace(g->precision, shape, args, ntiles, stream, &grid));
-    if (grid > (unsigned)kStaticMaxCtas) return fail(RT_ERR_CUDA, "static scratch: too many CTAs");
+    // the grid is capped before the launch: one energy partial per CTA, kStaticMaxCtas of them
+    RT_SCK(rt::launch_trace(g->precision, shape, args, ntiles, stream, &grid, (unsigned)kStaticMaxCtas));
 
     if (energy) {
         unsigned bad = 0;

@@ -51,7 +51,8 @@ __global__ void __launch_bounds__(W * 32, MINB) k_trace(const TraceArgs p)
 // Launch one chunk with a persistent grid of (SMs x resident CTAs) CTAs, or fewer
 // when there are fewer tiles. Returns the grid size (energy partials written).
 template <int C, int W, int MODE, int MINB>
-cudaError_t launch_shape(const TraceArgs &a, unsigned ntiles, cudaStream_t stream, unsigned *grid_out)
+cudaError_t launch_shape(const TraceArgs &a, unsigned ntiles, cudaStream_t stream, unsigned *grid_out,
+                         unsigned max_grid)
 {
     const size_t smem = trace_smem_bytes<C, W, MODE>(a);
     auto kern = k_trace<C, W, MODE, MINB>;
@@ -67,13 +68,14 @@ cudaError_t launch_shape(const TraceArgs &a, unsigned ntiles, cudaStream_t strea
     if (per_sm < 1) per_sm = 1;
     unsigned grid = (unsigned)nsm * (unsigned)per_sm;
     if (grid > ntiles) grid = ntiles;
+    if (max_grid > 0 && grid > max_grid) grid = max_grid;
     if (grid < 1) grid = 1;
     kern<<<grid, W * 32, smem, stream>>>(a);
     *grid_out = grid;
     return cudaGetLastError();
 }
 
-using LaunchFn = cudaError_t (*)(const TraceArgs &, unsigned, cudaStream_t, unsigned *);
+using LaunchFn = cudaError_t (*)(const TraceArgs &, unsigned, cudaStream_t, unsigned *, unsigned);
 struct ShapeEntry {
     int precision, c, w, minb;
     LaunchFn fn;
@@ -115,12 +117,12 @@ int trace_shapes(int precision, Shape *out, int max_out)
 long long trace_tile_cells(Shape s) { return 32LL * s.warps * s.cells_per_lane; }
 
 cudaError_t launch_trace(int precision, Shape s, const TraceArgs &args, unsigned ntiles,
-                         cudaStream_t stream, unsigned *grid_out)
+                         cudaStream_t stream, unsigned *grid_out, unsigned max_grid)
 {
-    if (s.kind == kKindRay) return launch_ray_shape(precision, s, args, stream, grid_out);
+    if (s.kind == kKindRay) return launch_ray_shape(precision, s, args, stream, grid_out, max_grid);
     const ShapeEntry *e = find_shape(precision, s.cells_per_lane, s.warps, s.min_blocks);
     if (!e) return cudaErrorInvalidValue;
-    return e->fn(args, ntiles, stream, grid_out);
+    return e->fn(args, ntiles, stream, grid_out, max_grid);
 }
 
 }  // namespace rt
