@@ -71,6 +71,12 @@ struct KahanSum {
         lo = lo + o.lo + e;
     }
     __device__ float value() const { return hi + lo; }
+    // the pair nearest to an FP64 value: hi its float rounding, lo the rest
+    __device__ void set(double d)
+    {
+        hi = (float)d;
+        lo = (float)(d - (double)hi);
+    }
     __device__ KahanSum shfl_up(int d, int width = 32) const
     {
         KahanSum r;
@@ -94,6 +100,7 @@ struct PlainSum {  // one accumulator, no compensation
     __device__ void add(Real v) { hi += v; }
     __device__ void add(const PlainSum &o) { hi += o.hi; }
     __device__ Real value() const { return hi; }
+    __device__ void set(double d) { hi = (Real)d; }
     __device__ PlainSum shfl_up(int d, int width = 32) const
     {
         PlainSum r;
@@ -373,6 +380,7 @@ __device__ __forceinline__ auto solid_angle(const TraceArgs &p, unsigned r)
 
 __device__ __forceinline__ double to_double(const KahanSum &s) { return (double)s.hi + (double)s.lo; }
 __device__ __forceinline__ double to_double(const PlainSum<double> &s) { return s.hi; }
+__device__ __forceinline__ double to_double(const PlainSum<float> &s) { return (double)s.hi; }
 
 // acc += part * w for a compensated (hi, lo) part, or a plain FP64 one
 __device__ __forceinline__ void add_weighted(KahanSum &acc, const KahanSum &part, float w)

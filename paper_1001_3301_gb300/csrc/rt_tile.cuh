@@ -71,8 +71,13 @@ __device__ __forceinline__ void trace_tile_range(const TraceArgs &p, unsigned t_
 
     __shared__ Sum s_wsum[W];
     __shared__ int s_whead[W];
-    __shared__ Sum s_cpart[W];  // first tile: per-warp shares of the re-summed column
-    __shared__ Sum s_carry[2];  // column handed from tile to tile (double buffered)
+    // The column of the ray that enters a tile crosses tile (and, for the first tile
+    // of a CTA, block) boundaries in FP64: the re-summed part in front of the CTA's
+    // first tile is added up in FP64, and the carry from tile to tile is held as an
+    // FP64 value. Inside a tile the mode's own sum (compensated FP32 by default)
+    // continues from it.
+    __shared__ double s_cpart[W];  // first tile: per-warp shares of the re-summed column
+    __shared__ double s_carry[2];  // column handed from tile to tile (double buffered)
 
     __syncthreads();  // a previous range of this CTA may still read the tables
 
@@ -132,13 +137,12 @@ __device__ __forceinline__ void trace_tile_range(const TraceArgs &p, unsigned t_
         int nreal, k0;
         tile_bounds(t_begin, f0, f1, m0, nreal, k0);
         const unsigned ray0 = p.r1div.div(f0);
-        Sum c;
-        c.zero();
+        double c = 0.0;
         const int kc = k0 < nr ? k0 : nr;
         const float *rr = p.rho + (size_t)ray0 * nr;
         const float *tt = p.tdust + (size_t)ray0 * nr;
-        for (int k = tid; k < kc; k += W * 32) c.add(column(__ldg(rr + k), __ldg(tt + k), k));
-        for (int o = 16; o > 0; o >>= 1) c.add(c.shfl_xor(o));
+        for (int k = tid; k < kc; k += W * 32) c += (double)column(__ldg(rr + k), __ldg(tt + k), k);
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
         if (lane == 0) s_cpart[warp] = c;
     }
 
@@ -215,10 +219,11 @@ __device__ __forceinline__ void trace_tile_range(const TraceArgs &p, unsigned t_
         __syncthreads();
         Sum pre;
         if (t == t_begin) {
-            pre.zero();
-            for (int w = 0; w < W; ++w) pre.add(s_cpart[w]);
+            double c0 = 0.0;
+            for (int w = 0; w < W; ++w) c0 += s_cpart[w];
+            pre.set(c0);
         } else {
-            pre = s_carry[buf];
+            pre.set(s_carry[buf]);
         }
         for (int w = 0; w < warp; ++w) {
             if (s_whead[w]) pre = s_wsum[w];
@@ -233,7 +238,7 @@ __device__ __forceinline__ void trace_tile_range(const TraceArgs &p, unsigned t_
             pre.add(D.get(j));
         }
         // the column at the end of this tile continues into the next one
-        if (tid == W * 32 - 1) s_carry[buf ^ 1] = pre;
+        if (tid == W * 32 - 1) s_carry[buf ^ 1] = to_double(pre);
 
         // frequency loop (escape cells carry D = 0 and absorb nothing here)
         Cells<Real, C> acc;

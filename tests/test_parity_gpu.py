@@ -116,6 +116,29 @@ def test_thin_series_extremes(tau):
 
 
 # --------------------------------------------------------------------------
+# deep rays: 2048 and 4096 cells at tau550 = 100, longer than any warp-per-ray
+# shape holds, so every ray spans many tiles and the column crosses tiles and CTAs
+# through the FP64 carry of the tile kernel
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("nr", [2048, 4096])
+@pytest.mark.parametrize("precision,rtol", [("fp32_kahan", 1e-5), ("fp64", 3e-7)])
+def test_deep_rays_tile_kernel(nr, precision, rtol):
+    from paper_1001_3301_gb300 import Tracer
+    # 7 polar cells (one centred on the midplane) x 64 azimuths: 448 rays, more tiles
+    # than the persistent grid has CTAs, so CTAs also hand the column from tile to tile
+    w = _w3(nr, 7, 64, 79, tau=100.0, seed=nr)
+    orc = oracle.irradiate_workload(w, nthreads=oracle.max_threads())
+    with Tracer.from_grid(w.grid, precision) as tr:
+        shapes = tr.tunings()
+    assert shapes and all(s[0] == 0 for s in shapes)  # no warp-per-ray shape holds these rays
+    for shape in shapes:
+        q, a, e = _parity.run_gpu(w, precision, shape=shape)
+        _parity.assert_parity(w, q, a, e, orc, rtol_q=rtol, rtol_a=rtol,
+                              rtol_energy=1e-6 if precision != "fp64" else 1e-9,
+                              label=f"nr={nr} {precision} {shape}")
+
+
+# --------------------------------------------------------------------------
 # full 256 x 128 x 256, 79-bin size in the bench's launch configuration:
 # sampled rays against the oracle, energy of the whole grid
 # --------------------------------------------------------------------------
