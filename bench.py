@@ -1,9 +1,11 @@
 """Throughput of the frequency-dependent irradiation ray tracer on GB300.
 
-One step traces the four grids of the 3-D disk-plus-envelope workload
-(256 x 128 x 256 cells, 79 frequency bins, midplane tau550 = 0.1, 1, 10, 100;
-seeded synthetic inputs) through the C ABI. The metric is cell x frequency-bin
-updates per second. Prints one JSON line.
+One step traces every grid of the 3-D disk-plus-envelope workload through the C
+ABI (rt_irradiate, then the FP64 energy reduction of Eqs. 33-35 on the device):
+by default the 512 x 256 x 512 grid (r, theta, phi; 67.1 M cells), 79 frequency
+bins, midplane tau550 = 1 and 100, seeded synthetic inputs. The metric is cell x
+frequency-bin updates per second. The 256 x 128 x 256 four-grid step (tau550 = 0.1,
+1, 10, 100) rides along as a secondary object. Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -34,11 +36,23 @@ import synth  # noqa: E402
 
 METRIC = "ray-traced cell·freq updates/s (plain vs MLP surrogate @≤1e-3 err); % roofline"
 UNIT = "cell·nu updates/s"
-TAUS = (0.1, 1.0, 10.0, 100.0)
-NR, NTH, NPH, NNU = 256, 128, 256, 79
-def workload_name(taus):
-    return (f"disk3d {NR}x{NTH}x{NPH} (r,theta,phi), {NNU} nu bins, tau550 in "
-            f"{{{','.join(f'{t:g}' for t in taus)}}}, env+20% lognormal, T_dust U(20,1600)")
+# the disk-plus-envelope workloads: grid, bins, midplane optical depths, seed
+WORKLOADS = {
+    "c3": {"nr": 512, "ntheta": 256, "nphi": 512, "n_nu": 79, "taus": (1.0, 100.0), "seed": 2},
+    "c2": {"nr": 256, "ntheta": 128, "nphi": 256, "n_nu": 79, "taus": (0.1, 1.0, 10.0, 100.0), "seed": 1},
+}
+NNU = 79
+# the 256 x 128 x 256 grid of the steps after the tracer (dust temperature, kappa(nu, T)
+# tracer, flux-limited diffusion) and of the secondary tracer object
+NR, NTH, NPH = 256, 128, 256
+
+
+def workload_name(spec, taus):
+    return (f"disk3d {spec['nr']}x{spec['ntheta']}x{spec['nphi']} (r,theta,phi), {spec['n_nu']} nu bins, "
+            f"tau550 in {{{','.join(f'{t:g}' for t in taus)}}}, env+20% lognormal, T_dust U(20,1600), "
+            f"seed {spec['seed']}")
+
+
 # algorithmic bytes per cell of the flux-limited-diffusion step (each array read or
 # written once per kernel; stencil neighbours from cache). Set-up: 28 (cell kernel:
 # rho, T, q, E in; F, storage, rhs out) + 36 (faces: 3 in; w[3], s, 1/dg, b out) + 8
@@ -58,9 +72,16 @@ EXP_PER_CELL_NU = 1
 # bins with kappa_i N_max <= THIN_X (N_max the largest total column of the rays one
 # warp traces) enter the tracer's power series instead (no exponential per cell)
 THIN_X = 0.5
+# FMA-pipe operations of the power series per cell (paired Horner form of
+# kThinTerms = 8 terms: 2 K + 1), and per (cell, bin) traced bin by bin at the least
+# (the exponent's FMA and the accumulation)
+SERIES_FMA_PER_CELL = 17
+EXACT_FMA_PER_PAIR = 2
 # algorithmic bytes per cell of the tracer: rho, T_dust in, q_abs, a_rad out (FP32)
 TRACE_BYTES_PER_CELL = 16
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_ray_disk3d_256x128x256_nu79.md")
+# the roofline fraction the tracer is meant to reach on its binding floor
+ROOFLINE_TARGET = 0.6
+PROFILE_DIR = os.path.join(ROOT, "profiles")
 KERNEL_SOURCES = ("rt_ray.cu", "rt_ray.cuh", "rt_device.cuh", "rt_internal.cuh")
 
 
@@ -73,8 +94,13 @@ def parse():
     p.add_argument("--precision", default="fp32_kahan")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--grids", default=",".join(str(t) for t in TAUS),
-                   help="comma-separated tau550 values of the grids in one step")
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default="c3",
+                   help="c3: the 512x256x512 grid at tau550 = 1 and 100 (default); c2: the 256x128x256 "
+                        "grid at tau550 = 0.1, 1, 10, 100")
+    p.add_argument("--grids", default=None,
+                   help="comma-separated tau550 values of the grids in one step (default: the workload's)")
+    p.add_argument("--no-secondary", action="store_true",
+                   help="skip the secondary tracer object (the other workload of WORKLOADS)")
     p.add_argument("--shape", default=None,
                    help="force the tracer shape 'kind,cells_per_lane,warps,min_blocks' (skips the autotuner)")
     p.add_argument("--precision-sweep", action="store_true",
@@ -111,8 +137,13 @@ def dist_env():
     return rank, world, local
 
 
-def workloads(seed_offset=0, taus=TAUS):
-    return [synth.disk3d(NR, NTH, NPH, n_nu=NNU, tau550=t, seed=1 + seed_offset) for t in taus]
+def workloads(spec, taus, seed_offset=0):
+    return [synth.disk3d(spec["nr"], spec["ntheta"], spec["nphi"], n_nu=spec["n_nu"], tau550=t,
+                         seed=spec["seed"] + seed_offset) for t in taus]
+
+
+def step_taus(args, spec):
+    return tuple(float(x) for x in args.grids.split(",")) if args.grids else tuple(spec["taus"])
 
 
 # --------------------------------------------------------------------------
@@ -172,11 +203,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_from_profile(src_hash: str):
-    """DRAM bytes per launch of the tracer from the committed ncu summary, only if
-    it was taken on the current kernel source."""
+def profile_summary_path(spec):
+    return os.path.join(PROFILE_DIR, f"k_ray_disk3d_{spec['nr']}x{spec['ntheta']}x{spec['nphi']}_nu{spec['n_nu']}.md")
+
+
+def traffic_from_profile(path: str, src_hash: str):
+    """DRAM bytes per launch of the tracer from a committed ncu summary, only if it
+    was taken on the current kernel source."""
     try:
-        txt = open(PROFILE_SUMMARY).read()
+        txt = open(path).read()
     except OSError:
         return None
     h = None
@@ -213,31 +248,73 @@ def exact_exp_ops(w, shape):
     return int(np.sum((nbins - bt) * rays)) * nr
 
 
-def roofline_summary(bytes_per_launch, exact_ops, cell_nu_per_launch, avg_launch_s, hbm_peak_gbs,
-                     ex2_peak_gops, ex2_basis):
-    """The tracer's roofline object. Two floors per launch: HBM (16 B per cell at the
-    measured copy bandwidth) and MUFU (one ex2 per (cell, bin) outside the thin series,
-    at the measured ex2 rate); the larger binds, and `frac` is that floor over the
-    average launch time. `mufu` gives the second floor, and `one_ex2_per_cell_nu` the
-    rate against one exponential per cell-nu (the bound the method had before the
-    series; above 1 where the series removes exponentials)."""
-    t_hbm = bytes_per_launch / (hbm_peak_gbs * 1e9)
-    t_mufu = exact_ops / (ex2_peak_gops * 1e9)
-    if t_hbm >= t_mufu:
-        out = {"bound": "hbm", "unit": "GB/s", "achieved": bytes_per_launch / avg_launch_s / 1e9,
-               "peak": hbm_peak_gbs, "frac": t_hbm / avg_launch_s,
-               "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
-    else:
-        out = {"bound": "alu", "unit": "Gop/s (MUFU ex2)", "achieved": exact_ops / avg_launch_s / 1e9,
-               "peak": ex2_peak_gops, "frac": t_mufu / avg_launch_s, "peak_basis": ex2_basis}
-    out.update({
-        "avg_launch_ms": avg_launch_s * 1e3, "algorithmic_bytes_per_launch": bytes_per_launch,
-        "mufu": {"exact_ex2_per_launch": exact_ops, "achieved_gops": exact_ops / avg_launch_s / 1e9,
-                 "peak_gops": ex2_peak_gops, "frac": t_mufu / avg_launch_s, "peak_basis": ex2_basis},
-        "one_ex2_per_cell_nu": {"cell_nu_per_s": cell_nu_per_launch / avg_launch_s,
+def series_fma_ops(w, shape):
+    """FMA-pipe operations of one tracer launch on grid w that its arithmetic needs at
+    the least: the power series (SERIES_FMA_PER_CELL per cell) in every warp whose rays
+    leave some bin in it, and EXACT_FMA_PER_PAIR per (cell, bin) traced bin by bin."""
+    nr = w.grid.nr
+    nbins = int(np.count_nonzero(w.kappa > 0))
+    exact = exact_exp_ops(w, shape)
+    if shape[0] != 1:
+        return EXACT_FMA_PER_PAIR * exact
+    c = shape[1]
+    g = 8 if 8 * c >= nr else (16 if 16 * c >= nr else 32)
+    r = 32 // g
+    dust = w.tdust32() <= w.t_sub
+    col = np.where(dust, w.rho32().astype(np.float64), 0.0) * np.diff(w.grid.r_if)
+    ntot = col.reshape(-1, nr).sum(axis=1)
+    pad = (-len(ntot)) % r
+    nmax = np.concatenate([ntot, np.zeros(pad)]).reshape(-1, r).max(axis=1)
+    kap = np.sort(w.kappa[w.kappa > 0])
+    bt = np.searchsorted(kap, THIN_X / np.maximum(nmax, 1e-300), side="right")
+    rays = np.full(len(nmax), r)
+    rays[-1] = r - pad
+    series_cells = int(np.sum(rays[bt > 0])) * nr if nbins else 0
+    return SERIES_FMA_PER_CELL * series_cells + EXACT_FMA_PER_PAIR * exact
+
+
+def roofline_summary(grids, hbm_peak_gbs, ex2_peak_gops, ffma_peak_gops, ex2_basis, ffma_basis):
+    """The tracer's roofline object over the launches of one step.
+
+    grids: one dict per grid of the step with the algorithmic work of one launch
+    (bytes: 16 B per cell; ex2: exponentials outside the thin series; fma: FMA-pipe
+    operations at the least; cell_nu) and its mean CUDA-event launch time launch_s.
+    The headline is HBM (16 B per cell, the per-unit figure of the scope): achieved
+    = bytes / launch time, frac = achieved / the measured copy bandwidth. Beside it
+    the two other floors (MUFU ex2 at the measured ex2 rate, FP32 FMA at the measured
+    FFMA rate) and the binding floor per grid (the largest of the three times) summed
+    over the step, against the launch time, and the target fraction."""
+    t_launch = sum(g["launch_s"] for g in grids)
+    by = sum(g["bytes"] for g in grids)
+    ex = sum(g["ex2"] for g in grids)
+    fm = sum(g["fma"] for g in grids)
+    t_h = [g["bytes"] / (hbm_peak_gbs * 1e9) for g in grids]
+    t_m = [g["ex2"] / (ex2_peak_gops * 1e9) for g in grids]
+    t_f = [g["fma"] / (ffma_peak_gops * 1e9) for g in grids]
+    names = []
+    t_bind = 0.0
+    for h, m, f in zip(t_h, t_m, t_f):
+        t_bind += max(h, m, f)
+        names.append("hbm" if h >= max(m, f) else ("mufu" if m >= f else "fp32"))
+    achieved = by / t_launch / 1e9
+    bind_frac = t_bind / t_launch
+    return {
+        "bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": hbm_peak_gbs,
+        "frac": achieved / hbm_peak_gbs,
+        "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+        "avg_launch_ms": t_launch / len(grids) * 1e3, "algorithmic_bytes_per_launch": by / len(grids),
+        "per_grid_launch_ms": [g["launch_s"] * 1e3 for g in grids],
+        "mufu": {"exact_ex2_per_launch": ex / len(grids), "achieved_gops": ex / t_launch / 1e9,
+                 "peak_gops": ex2_peak_gops, "frac": sum(t_m) / t_launch, "peak_basis": ex2_basis},
+        "fp32": {"fma_ops_per_launch": fm / len(grids), "achieved_gops": fm / t_launch / 1e9,
+                 "peak_gops": ffma_peak_gops, "frac": sum(t_f) / t_launch, "peak_basis": ffma_basis},
+        "binding_floor": {"per_grid": names, "frac": bind_frac,
+                          "floor_ms_per_launch": t_bind / len(grids) * 1e3},
+        "target_frac": ROOFLINE_TARGET,
+        "target_met": bool(bind_frac >= ROOFLINE_TARGET),
+        "one_ex2_per_cell_nu": {"cell_nu_per_s": sum(g["cell_nu"] for g in grids) / t_launch,
                                 "peak_cell_nu_per_s": ex2_peak_gops * 1e9,
-                                "frac": cell_nu_per_launch / avg_launch_s / (ex2_peak_gops * 1e9)}})
-    return out
+                                "frac": sum(g["cell_nu"] for g in grids) / t_launch / (ex2_peak_gops * 1e9)}}
 
 
 def kernel_source_hash():
@@ -344,31 +421,42 @@ def run_cpu_table(args, local):
                       "rows": rows}), flush=True)
 
 
+# seconds of OpenMP oracle work per step of the reference arm
+REF_STEP_S = 1.0
+
+
 def run_reference(args, rank, world):
+    """The FP64 oracle on the host cores, on the GPU arm's workload: per step an evenly
+    spaced sample of rays of every grid of the step, as many as fill about REF_STEP_S
+    seconds of OpenMP work (the same sampling as the cpu_baseline leg)."""
     if rank != 0:
         return
-    ws = workloads(taus=tuple(float(x) for x in args.grids.split(",")))
+    spec = WORKLOADS[args.workload]
+    taus = step_taus(args, spec)
+    ws = workloads(spec, taus)
     import oracle
     oracle.build()
     cores = oracle.max_threads()
-    n_rays = 64
+    nrays = ws[0].grid.ntheta * ws[0].grid.nphi
+    probe = min(2048, nrays)
+    dt = oracle_sample(ws[0], probe, cores)
+    n_rays = int(min(nrays, max(256, probe * REF_STEP_S / max(dt, 1e-3) / len(ws))))
     for _ in range(max(args.warmup, 0)):
         for w in ws:
             oracle_sample(w, n_rays, cores)
-    t0 = time.perf_counter()
+    dt = 0.0
     for _ in range(args.steps):
         for w in ws:
-            oracle_sample(w, n_rays, cores)
-    dt = time.perf_counter() - t0
-    units = args.steps * len(ws) * n_rays * NR * NNU
+            dt += oracle_sample(w, n_rays, cores)
+    units = args.steps * sum(n_rays * w.grid.nr * len(w.nu) for w in ws)
     value = units / dt
+    sample = (f"per step {n_rays} evenly spaced rays x {spec['nr']} cells x {spec['n_nu']} bins of each of the "
+              f"{len(ws)} grids (OpenMP over rays)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": workload_name([w.tau550 for w in ws]), "sample_per_step":
-                                            f"{n_rays} rays of each of the 4 grids"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"per step {n_rays} rays x {NR} cells x {NNU} bins of each tau grid"},
+            "data": "synthetic", "config": {"workload": workload_name(spec, taus), "sample_per_step": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -376,21 +464,14 @@ def run_reference(args, rank, world):
 # --------------------------------------------------------------------------
 # the GPU arm
 # --------------------------------------------------------------------------
-def run_ours(args, rank, world, local):
+def setup_tracers(ws, precision, shape_arg):
+    """One context per grid, fields resident on the device, launch shape from the
+    autotuner per grid (untimed) or forced."""
     import torch
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_1001_3301_gb300 import Tracer, probe_alu_rates
-
-    taus = tuple(float(x) for x in args.grids.split(","))
-    ws = workloads(seed_offset=rank, taus=taus)
-    stream = torch.cuda.current_stream()
+    from paper_1001_3301_gb300 import Tracer
     tracers, rho, td, q, a = [], [], [], [], []
     for w in ws:
-        tr = Tracer.from_grid(w.grid, args.precision)
+        tr = Tracer.from_grid(w.grid, precision)
         tr.set_opacity_table(w.nu, w.kappa, w.t_sub)
         tr.set_star(w.t_star, w.r_star)
         tracers.append(tr)
@@ -398,79 +479,129 @@ def run_ours(args, rank, world, local):
         td.append(torch.from_numpy(w.tdust32()).cuda())
         q.append(torch.empty(w.grid.shape, dtype=torch.float32, device="cuda"))
         a.append(torch.empty(w.grid.shape, dtype=torch.float32, device="cuda"))
-    # launch shape from the autotuner (untimed; cached for same-shape grids)
-    if args.shape:
-        shape = tuple(int(x) for x in args.shape.split(","))
-    else:
-        shape = tracers[0].autotune(rho[0], td[0], q[0], a[0], reps=3)
-    for tr in tracers:
-        tr.set_tuning(*shape)
+    shapes = []
+    for i, tr in enumerate(tracers):
+        if shape_arg:
+            tr.set_tuning(*shape_arg)
+        else:
+            tr.autotune(rho[i], td[i], q[i], a[i], reps=3)
+        shapes.append(tuple(tr.tuning()))
+    return {"tracers": tracers, "rho": rho, "td": td, "q": q, "a": a, "shapes": shapes, "ws": ws}
 
-    units_per_step = sum(w.grid.ncells * len(w.nu) for w in ws)
+
+def time_step(st, steps, warmup, stream, dist=None, sampler=None):
+    """Warm-up, then `steps` timed steps: every grid traced (rt_irradiate) and its FP64
+    energy reduction enqueued (rt_energy_reduce). Returns the step time (max over
+    ranks) and each grid's mean CUDA-event launch time of the tracer kernel."""
+    import torch
+    tr, rho, td, q, a = st["tracers"], st["rho"], st["td"], st["q"], st["a"]
 
     def step(ev=None):
-        for i, tr in enumerate(tracers):
+        for i, t in enumerate(tr):
             if ev is not None:
                 ev[i][0].record(stream)
-            tr.irradiate(rho[i], td[i], q[i], a[i])
+            t.irradiate(rho[i], td[i], q[i], a[i])
             if ev is not None:
                 ev[i][1].record(stream)
+            t.energy_reduce()
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
-    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in ws]
-           for _ in range(args.steps)]
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in tr] for _ in range(steps)]
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    if sampler is not None:
+        sampler.__enter__()
         time.sleep(0.3)
+    try:
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
         t_start.record(stream)
-        for s in range(args.steps):
+        for s in range(steps):
             step(evs[s])
         t_end.record(stream)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
+    finally:
+        if sampler is not None:
+            sampler.__exit__(None, None, None)
     ms = t_start.elapsed_time(t_end)
-    launch_ms = [[evs[s][i][0].elapsed_time(evs[s][i][1]) for i in range(len(ws))]
-                 for s in range(args.steps)]
+    launch_ms = [statistics.mean(evs[s][i][0].elapsed_time(evs[s][i][1]) for s in range(steps))
+                 for i in range(len(tr))]
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    ms_per_step = ms / args.steps
+    return ms / steps, launch_ms
+
+
+def tracer_roofline(st, launch_ms, ex2_peak, ffma_peak, hbm, ex2_basis, ffma_basis):
+    grids = []
+    for w, shape, lm in zip(st["ws"], st["shapes"], launch_ms):
+        grids.append({"bytes": TRACE_BYTES_PER_CELL * w.grid.ncells, "ex2": exact_exp_ops(w, shape),
+                      "fma": series_fma_ops(w, shape), "cell_nu": w.grid.ncells * len(w.nu),
+                      "launch_s": lm * 1e-3})
+    return roofline_summary(grids, hbm, ex2_peak, ffma_peak, ex2_basis, ffma_basis)
+
+
+def close_tracers(st):
+    if not st:
+        return
+    for tr in st["tracers"]:
+        tr.close()
+    st.clear()
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1001_3301_gb300 import probe_alu_rates
+
+    spec = WORKLOADS[args.workload]
+    taus = step_taus(args, spec)
+    ws = workloads(spec, taus, seed_offset=rank)
+    stream = torch.cuda.current_stream()
+    shape_arg = tuple(int(x) for x in args.shape.split(",")) if args.shape else None
+    prim = setup_tracers(ws, args.precision, shape_arg)
+    prim_shapes = list(prim["shapes"])
+    units_per_step = sum(w.grid.ncells * len(w.nu) for w in ws)
+    clk = ClockSampler(local)
+    ms_per_step, launch_ms = time_step(prim, args.steps, args.warmup, stream, dist, sampler=clk)
     value = world * units_per_step / (ms_per_step * 1e-3)
 
-    # energy and correctness check of the last step (untimed)
-    energies = [tr.energy_last() for tr in tracers]
+    # energy and input check of the last step (untimed read of what the step reduced)
+    energies = [tr.energy_last() for tr in prim["tracers"]]
     max_energy_err = max(abs(e.rel_err) for e in energies)
 
-    # roofline of the tracer kernel (roofline_summary: the binding floor and both bases)
-    avg_launch_s = statistics.mean(x for row in launch_ms for x in row) * 1e-3
+    # roofline of the tracer kernel: HBM headline, MUFU and FP32 floors, binding floor
     ex2_clk, ffma_clk, probe_mhz = probe_alu_rates()
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     clocks = clk.summary()
     mhz = clocks["sm_mhz"] or probe_mhz
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    peak = ex2_clk * nsm * mhz * 1e6 / 1e9   # Gop/s of ex2 (also the temperature-table leg's bound)
+    hbm = float(peaks.get("hbm_gbs") or 6678.0)
+    ex2_peak = ex2_clk * nsm * mhz * 1e6 / 1e9     # Gop/s of ex2 (also the temperature-table leg's bound)
+    ffma_peak = ffma_clk * nsm * mhz * 1e6 / 1e9   # Gop/s of FFMA
+    ex2_basis = f"measured {ex2_clk:.2f} ex2/SM/clk x {nsm} SMs x {mhz:.0f} MHz"
+    ffma_basis = f"measured {ffma_clk:.1f} FFMA/SM/clk x {nsm} SMs x {mhz:.0f} MHz"
     src_hash = kernel_source_hash()
-    roofline = roofline_summary(
-        bytes_per_launch=statistics.mean(TRACE_BYTES_PER_CELL * w.grid.ncells for w in ws),
-        exact_ops=statistics.mean(exact_exp_ops(w, shape) for w in ws),
-        cell_nu_per_launch=statistics.mean(w.grid.ncells * len(w.nu) for w in ws),
-        avg_launch_s=avg_launch_s, hbm_peak_gbs=float(peaks.get("hbm_gbs") or 6678.0),
-        ex2_peak_gops=peak,
-        ex2_basis=f"measured {ex2_clk:.2f} ex2/SM/clk x {nsm} SMs x {mhz:.0f} MHz")
-    roofline.update({"traffic": traffic_from_profile(src_hash), "kernel": "k_ray" if shape[0] == 1 else "k_trace",
-                     "ffma_per_sm_clk": ffma_clk, "kernel_source_sha256": src_hash})
+    roofline = tracer_roofline(prim, launch_ms, ex2_peak, ffma_peak, hbm, ex2_basis, ffma_basis)
+    kinds = {s[0] for s in prim_shapes}
+    roofline.update({"traffic": traffic_from_profile(profile_summary_path(spec), src_hash),
+                     "kernel": "k_ray" if kinds == {1} else ("k_trace" if kinds == {0} else "k_ray/k_trace"),
+                     "ffma_per_sm_clk": ffma_clk, "ex2_per_sm_clk": ex2_clk, "kernel_source_sha256": src_hash})
 
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None
     if not args.no_e2e:
+        tracers = prim["tracers"]
         h_rho = [torch.from_numpy(w.rho32()).pin_memory() for w in ws]
         h_td = [torch.from_numpy(w.tdust32()).pin_memory() for w in ws]
         h_q = [torch.empty(w.grid.shape, dtype=torch.float32).pin_memory() for w in ws]
@@ -496,42 +627,76 @@ def run_ours(args, rank, world, local):
             dt = float(t.item())
         nbytes = sum(4 * w.grid.ncells for w in ws)
         e2e = {"value": world * units_per_step * args.steps / dt, "unit": UNIT,
-               "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": 2 * nbytes}
+               "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": 2 * nbytes,
+               "entry_point": "rt_irradiate_host_async + rt_host_wait (pinned host buffers)"}
+        del h_rho, h_td, h_q, h_a
 
-    # the dust-temperature update (Eq. 16) on the step's grids, fed by their a_rad
-    # (untimed above; timed here on its own, 8 bytes per cell against HBM)
+    # the other workload's tracer step (rank 0), and the 256 x 128 x 256 tau = 1 grid
+    # that the steps after the tracer run on
+    sec = None
+    sec_st = None
+    c2 = prim if args.workload == "c2" else None
+    if rank == 0 and not args.no_secondary:
+        other = "c2" if args.workload == "c3" else "c3"
+        ospec = WORKLOADS[other]
+        if other == "c3":   # free the primary grids first
+            close_tracers(prim)
+            torch.cuda.empty_cache()
+            c2 = None
+        sec_st = setup_tracers(workloads(ospec, ospec["taus"]), args.precision, None)
+        s_ms, s_launch = time_step(sec_st, args.steps, args.warmup, stream)
+        s_units = sum(w.grid.ncells * len(w.nu) for w in sec_st["ws"])
+        s_roof = tracer_roofline(sec_st, s_launch, ex2_peak, ffma_peak, hbm, ex2_basis, ffma_basis)
+        s_roof["traffic"] = traffic_from_profile(profile_summary_path(ospec), src_hash)
+        sec = {"workload": workload_name(ospec, ospec["taus"]), "value": s_units / (s_ms * 1e-3), "unit": UNIT,
+               "ms_per_step": s_ms, "steps": args.steps, "launch_shapes": [list(x) for x in sec_st["shapes"]],
+               "energy_max_rel_err": max(abs(t.energy_last().rel_err) for t in sec_st["tracers"]),
+               "roofline": s_roof}
+        if other == "c2":
+            c2 = sec_st
+    if rank == 0 and c2 is None and not (args.no_fld and args.no_secondary):
+        c2 = setup_tracers(workloads(WORKLOADS["c2"], (1.0,)), args.precision, None)
+    i1 = 0
+    if c2:
+        i1 = next((i for i, w in enumerate(c2["ws"]) if w.tau550 == 1.0), 0)
+
+    # the dust-temperature update (Eq. 16) on the 256 x 128 x 256 grids, fed by their
+    # a_rad (timed on its own, 8 bytes per cell against HBM)
     temp = None
-    if rank == 0:
-        t_out = [torch.empty(w.grid.shape, dtype=torch.float32, device="cuda") for w in ws]
-        for i, tr in enumerate(tracers):
-            tr.dust_temperature(a[i], None, t_out[i])
+    if rank == 0 and c2:
+        for i, tr in enumerate(c2["tracers"]):
+            tr.irradiate(c2["rho"][i], c2["td"][i], c2["q"][i], c2["a"][i])
+        t_out = [torch.empty(w.grid.shape, dtype=torch.float32, device="cuda") for w in c2["ws"]]
+        for i, tr in enumerate(c2["tracers"]):
+            tr.dust_temperature(c2["a"][i], None, t_out[i])
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            for i, tr in enumerate(tracers):
-                tr.dust_temperature(a[i], None, t_out[i])
+            for i, tr in enumerate(c2["tracers"]):
+                tr.dust_temperature(c2["a"][i], None, t_out[i])
         e1.record(stream)
         torch.cuda.synchronize()
-        t_ms = e0.elapsed_time(e1) / (args.steps * len(ws))
-        ncell = ws[0].grid.ncells
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        hbm = float(peaks.get("hbm_gbs") or 6678.0)
-        temp = {"ms_per_grid": t_ms, "cells_per_s": ncell / (t_ms * 1e-3),
+        t_ms = e0.elapsed_time(e1) / (args.steps * len(c2["ws"]))
+        ncell = c2["ws"][0].grid.ncells
+        temp = {"workload": f"disk3d {NR}x{NTH}x{NPH}, a_rad of the tracer, "
+                            f"tau550 in {{{','.join(f'{w.tau550:g}' for w in c2['ws'])}}}",
+                "ms_per_grid": t_ms, "cells_per_s": ncell / (t_ms * 1e-3),
                 "achieved_gbs": 8.0 * ncell / (t_ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm,
                 "frac_of_hbm": 8.0 * ncell / (t_ms * 1e-3) / 1e9 / hbm,
-                "median_t_k": float(t_out[min(1, len(ws) - 1)].median())}
+                "median_t_k": float(t_out[i1].median())}
         del t_out
 
     # the tracer with a temperature-dependent table (24 temperatures) on the tau = 1 grid
     tdep = None
-    if rank == 0:
-        w1 = ws[min(1, len(ws) - 1)]
+    if rank == 0 and c2:
+        from paper_1001_3301_gb300 import Tracer
+        w1 = c2["ws"][i1]
         tg = synth.t_grid(24)
         trt = Tracer.from_grid(w1.grid)
         trt.set_opacity_table_t(w1.nu, tg, synth.kappa_synth_t(w1.nu, tg), w1.t_sub)
         trt.set_star(w1.t_star, w1.r_star)
-        ri, ti = rho[min(1, len(ws) - 1)], td[min(1, len(ws) - 1)]
+        ri, ti = c2["rho"][i1], c2["td"][i1]
         qt, at = torch.empty_like(ri), torch.empty_like(ri)
         sh_t = trt.autotune(ri, ti, qt, at, reps=2)
         for _ in range(3):
@@ -549,8 +714,8 @@ def run_ours(args, rank, world, local):
         _, _, et = trt.irradiate(ri, ti, qt, at, energy=True)
         tdep = {"workload": f"disk3d {NR}x{NTH}x{NPH}, {NNU} bins x 24 temperatures, tau550 = {w1.tau550:g}",
                 "ms": t_ms, "cell_nu_per_s": units / (t_ms * 1e-3),
-                "roofline": {"bound": "alu", "unit": "Gop/s (MUFU ex2)", "achieved": ach, "peak": peak,
-                             "frac": ach / peak},
+                "roofline": {"bound": "alu", "unit": "Gop/s (MUFU ex2)", "achieved": ach, "peak": ex2_peak,
+                             "frac": ach / ex2_peak},
                 "launch_shape": list(sh_t), "energy_rel_err": et.rel_err}
         trt.close()
         del qt, at
@@ -558,20 +723,17 @@ def run_ours(args, rank, world, local):
     # one implicit flux-limited-diffusion step (Eqs. 7-15) on the tau = 1 grid, with
     # that grid's q_abs as the source
     fld_line = None
-    if rank == 0 and not args.no_fld:
-        i1 = min(1, len(ws) - 1)
-        fld_line = run_fld(args, tracers[i1], ws[i1], rho[i1], q[i1], stream)
+    if rank == 0 and c2 and not args.no_fld:
+        fld_line = run_fld(args, c2["tracers"][i1], c2["ws"][i1], c2["rho"][i1], c2["q"][i1], stream)
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(ws)
+    for st in (prim, sec_st, c2):
+        close_tracers(st)
+    torch.cuda.empty_cache()
     sur = None
     if rank == 0 and world == 1 and not args.no_surrogate:
-        for tr in tracers:  # free the step's grids first
-            tr.close()
-        tracers = []
-        del rho, td, q, a
-        torch.cuda.empty_cache()
         sur = run_surrogate(args, local)
 
     if rank == 0:
@@ -580,27 +742,29 @@ def run_ours(args, rank, world, local):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded disk+envelope density, uniform dust temperatures, synthetic kappa_nu)",
-            "config": {"workload": workload_name(taus), "precision": args.precision, "grids_per_step": len(ws),
-                       "cells_per_step": sum(w.grid.ncells for w in ws), "nu_bins": NNU,
-                       "launch_shape": {"kernel": ["tile", "ray"][shape[0]], "cells_per_lane": shape[1],
-                                        "warps": shape[2], "min_blocks_per_sm": shape[3]},
-                       "l2": f"no flush: inputs+outputs {16 * sum(w.grid.ncells for w in ws) / 1e6:.0f} MB per step exceed the 129 MB L2",
+            "config": {"workload": workload_name(spec, taus), "precision": args.precision,
+                       "grids_per_step": len(ws), "cells_per_step": sum(w.grid.ncells for w in ws),
+                       "nu_bins": spec["n_nu"],
+                       "step": "per grid: rt_irradiate (tracer kernel) + rt_energy_reduce (FP64 energy reduction)",
+                       "launch_shapes": [{"kernel": ["tile", "ray"][sh[0]], "cells_per_lane": sh[1], "warps": sh[2],
+                                          "min_blocks_per_sm": sh[3]} for sh in prim_shapes],
+                       "l2": f"no flush: inputs+outputs {16 * sum(w.grid.ncells for w in ws) / 1e6:.0f} MB per step "
+                             f"exceed the 129 MB L2",
                        "replicas_per_rank": 1},
             "roofline": roofline,
             "cpu_baseline": base,
             "e2e": e2e,
-            "gpu_launches": len(ws) * args.steps,
+            "gpu_launches": 2 * len(ws) * args.steps,
             "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                        "reasons": clocks["reasons"]},
             "energy_max_rel_err": max_energy_err,
+            "secondary": sec,
             "dust_temperature": temp,
             "tdep": tdep,
             "fld": fld_line,
             "surrogate": sur,
         }
         print(json.dumps(line), flush=True)
-    for tr in tracers:
-        tr.close()
     if dist:
         dist.destroy_process_group()
 

@@ -178,6 +178,16 @@ int rt_host_wait(rt_ctx *ctx);
  * RT_ERR_NONFINITE_INPUT (that trace saw invalid input; *out is still filled). */
 int rt_energy_last(rt_ctx *ctx, rt_energy *out);
 
+/* rt_energy_reduce -- enqueue, on the context's stream, the FP64 reduction of the
+ * most recent trace's per-tile partial sums into the energy sums E_abs, E_esc and
+ * their balance against L* (Eqs. 33-35; Eq. 18 for L*), kept in device memory the
+ * context owns; no synchronisation, nothing is returned to the host. A step that
+ * needs the energy on the device every time and on the host only now and then
+ * calls this after rt_irradiate and rt_energy_last when it reads them (which runs
+ * the same reduction again). Errors: RT_ERR_NOT_CONFIGURED (nothing traced yet),
+ * RT_ERR_CUDA. */
+int rt_energy_reduce(rt_ctx *ctx);
+
 /* rt_get_bins -- copy the per-bin stellar surface fluxes F_i (erg s^-1 cm^-2, FP64,
  * Eq. 20) that the device computed for the current star and table into host
  * f_bin[n_nu]. Synchronises. Errors: RT_ERR_NOT_CONFIGURED, RT_ERR_CUDA. */

@@ -88,6 +88,7 @@ SIGNATURES = {
     "rt_irradiate_host_async": (_I, [_P, _P, _P, _P, _P]),
     "rt_host_wait": (_I, [_P]),
     "rt_energy_last": (_I, [_P, ctypes.POINTER(RtEnergy)]),
+    "rt_energy_reduce": (_I, [_P]),
     "rt_get_bins": (_I, [_P, _DP]),
     "rt_set_tuning": (_I, [_P, _I, _I, _I, _I]),
     "rt_get_tuning": (_I, [_P] + [ctypes.POINTER(_I)] * 4),

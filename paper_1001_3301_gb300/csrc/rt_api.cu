@@ -755,6 +755,16 @@ int rt_energy_last(rt_ctx *ctx, rt_energy *out)
     return read_energy(ctx, out);
 }
 
+int rt_energy_reduce(rt_ctx *ctx)
+{
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (!ctx->traced) return fail(ctx, RT_ERR_NOT_CONFIGURED, "nothing traced yet");
+    RT_CK(ctx, cudaSetDevice(ctx->dev));
+    cudaError_t e = rt::launch_energy_reduce(ctx->partials, ctx->last_ntiles, ctx->sc, ctx->energy_d, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, "energy reduce", e);
+    return RT_OK;
+}
+
 int rt_get_bins(rt_ctx *ctx, double *f_bin)
 {
     if (!ctx || !f_bin) return RT_ERR_INVALID_ARG;

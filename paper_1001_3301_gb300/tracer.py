@@ -140,6 +140,10 @@ class Tracer:
         check(lib.rt_energy_last(self._ctx, ctypes.byref(e)), self._ctx)
         return Energy(e)
 
+    def energy_reduce(self):
+        """Enqueue the FP64 energy reduction of the last trace (device only, no sync)."""
+        check(lib.rt_energy_reduce(self._ctx), self._ctx)
+
     def bins(self) -> np.ndarray:
         out = np.empty(self.n_nu, dtype=np.float64)
         check(lib.rt_get_bins(self._ctx, _dptr(out)), self._ctx)

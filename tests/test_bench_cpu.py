@@ -51,22 +51,79 @@ def test_exact_exp_ops_limits():
     assert bench.exact_exp_ops(big, (1, 8, 4, 6)) == w.grid.ncells * nbins
 
 
-def test_roofline_summary_picks_the_binding_floor():
-    """HBM binds when its time per launch is the larger one, MUFU otherwise; frac is the
-    binding floor's time over the launch time, and the two other bases ride along."""
-    # 134 MB at 6678 GB/s = 20.1 us against 1e8 ex2 at 1e4 Gop/s = 10 us: HBM binds
-    r = bench.roofline_summary(bytes_per_launch=134217728, exact_ops=1e8, cell_nu_per_launch=6.627e8,
-                               avg_launch_s=80e-6, hbm_peak_gbs=6678.0, ex2_peak_gops=1e4, ex2_basis="x")
+def _brute_fma(w, shape):
+    """Series FMAs per cell in every warp that leaves some bin in the series, plus
+    EXACT_FMA_PER_PAIR per (cell, bin) traced bin by bin."""
+    g = w.grid
+    kap = w.kappa[w.kappa > 0]
+    exact = _brute(w, shape)
+    if shape[0] != 1:
+        return bench.EXACT_FMA_PER_PAIR * exact
+    c = shape[1]
+    lanes = 8 if 8 * c >= g.nr else (16 if 16 * c >= g.nr else 32)
+    r = 32 // lanes
+    rho = w.rho32().astype(np.float64).reshape(-1, g.nr)
+    td = w.tdust32().reshape(-1, g.nr)
+    dr = np.diff(g.r_if)
+    cells = 0
+    for first in range(0, rho.shape[0], r):
+        rays = range(first, min(first + r, rho.shape[0]))
+        nmax = max(sum(rho[j, k] * dr[k] for k in range(g.nr) if td[j, k] <= w.t_sub) for j in rays)
+        if any(kk * nmax <= bench.THIN_X for kk in kap):
+            cells += len(rays) * g.nr
+    return bench.SERIES_FMA_PER_CELL * cells + bench.EXACT_FMA_PER_PAIR * exact
+
+
+@pytest.mark.parametrize("tau,shape", [(10.0, (1, 8, 4, 6)), (1e4, (1, 4, 4, 8)), (0.3, (0, 8, 4, 6))])
+def test_series_fma_ops_matches_brute_force(tau, shape):
+    w = synth.disk3d(40, 6, 5, n_nu=16, tau550=tau, seed=4)
+    assert bench.series_fma_ops(w, shape) == _brute_fma(w, shape)
+
+
+def _grid(launch_s, ex2, fma=0.0, nbytes=134217728):
+    return {"bytes": nbytes, "ex2": ex2, "fma": fma, "cell_nu": 6.627e8, "launch_s": launch_s}
+
+
+def test_roofline_summary_headline_and_floors():
+    """The headline is HBM (16 B per cell over the launch time, against the measured
+    copy bandwidth) whatever binds; the binding floor per grid is the largest of the
+    HBM, MUFU and FP32 times, summed over the step against the summed launch time."""
+    peaks = dict(hbm_peak_gbs=6678.0, ex2_peak_gops=1e4, ffma_peak_gops=4e4, ex2_basis="x", ffma_basis="y")
+    # grid 1: 134 MB at 6678 GB/s = 20.1 us against 1e8 ex2 at 1e4 Gop/s = 10 us (HBM binds);
+    # grid 2: 3e8 ex2 = 30 us (MUFU binds); grid 3: 1.2e9 FMA at 4e4 Gop/s = 30 us (FP32 binds)
+    r = bench.roofline_summary([_grid(80e-6, 1e8), _grid(100e-6, 3e8), _grid(60e-6, 0.0, 1.2e9)], **peaks)
+    t_h = 134217728 / 6678e9
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
-    assert r["frac"] == pytest.approx(134217728 / 6678e9 / 80e-6)
+    assert r["frac"] == pytest.approx(3 * t_h / 240e-6)
     assert r["achieved"] / r["peak"] == pytest.approx(r["frac"])
-    assert r["mufu"]["frac"] == pytest.approx(1e8 / 1e13 / 80e-6)
-    assert r["one_ex2_per_cell_nu"]["frac"] == pytest.approx(6.627e8 / 80e-6 / 1e13)
-    # three times the exponentials: MUFU binds
-    r = bench.roofline_summary(bytes_per_launch=134217728, exact_ops=3e8, cell_nu_per_launch=6.627e8,
-                               avg_launch_s=80e-6, hbm_peak_gbs=6678.0, ex2_peak_gops=1e4, ex2_basis="x")
-    assert r["bound"] == "alu" and r["frac"] == pytest.approx(3e8 / 1e13 / 80e-6)
-    assert r["achieved"] / r["peak"] == pytest.approx(r["frac"])
+    assert r["binding_floor"]["per_grid"] == ["hbm", "mufu", "fp32"]
+    assert r["binding_floor"]["frac"] == pytest.approx((t_h + 30e-6 + 30e-6) / 240e-6)
+    assert r["mufu"]["frac"] == pytest.approx(4e8 / 1e13 / 240e-6)
+    assert r["fp32"]["frac"] == pytest.approx(1.2e9 / 4e13 / 240e-6)
+    assert r["one_ex2_per_cell_nu"]["frac"] == pytest.approx(3 * 6.627e8 / 240e-6 / 1e13)
+    assert r["target_frac"] == bench.ROOFLINE_TARGET
+    assert r["target_met"] == (r["binding_floor"]["frac"] >= bench.ROOFLINE_TARGET)
+
+
+def test_series_fma_constants_match_the_library():
+    """SERIES_FMA_PER_CELL is the paired Horner form's 2 K + 1 operations for the
+    library's kThinTerms = K."""
+    import os
+    import re
+    src = open(os.path.join(os.path.dirname(bench.__file__), "paper_1001_3301_gb300", "csrc",
+                            "rt_internal.cuh")).read()
+    m = re.search(r"constexpr int kThinTerms = ([0-9]+);", src)
+    assert m and 2 * int(m.group(1)) + 1 == bench.SERIES_FMA_PER_CELL
+
+
+def test_workloads_and_reference_config():
+    """The default step is the 512 x 256 x 512 grid at tau550 = 1 and 100 (seed 2);
+    the reference arm names the same workload."""
+    spec = bench.WORKLOADS["c3"]
+    assert (spec["nr"], spec["ntheta"], spec["nphi"], spec["n_nu"]) == (512, 256, 512, 79)
+    assert spec["taus"] == (1.0, 100.0) and spec["seed"] == 2
+    name = bench.workload_name(spec, spec["taus"])
+    assert "512x256x512" in name and "tau550 in {1,100}" in name
 
 
 def test_thin_bound_matches_the_library():
