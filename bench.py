@@ -224,53 +224,53 @@ def traffic_from_profile(path: str, src_hash: str):
     return t if (h == src_hash and t is not None) else None
 
 
-def exact_exp_ops(w, shape):
-    """Exp-class operations of one tracer launch on grid w that the series cannot
-    replace: one per (cell, bin) outside the thin prefix of the cell's warp (the bins
-    with kappa_i N_max <= THIN_X, N_max the largest total column of the warp's rays).
-    The tile kernel traces every bin."""
-    nr = w.grid.nr
-    nbins = int(np.count_nonzero(w.kappa > 0))
-    if shape[0] != 1:
-        return w.grid.ncells * nbins
-    c = shape[1]
+def _warp_partition(w, shape):
+    """Per warp of the warp-per-ray kernel (R = 32 / G rays of nr cells, G lanes of C
+    cells each): the cells it traces, the bins its thin series takes (bt: kappa_i N_max
+    <= THIN_X, N_max the largest total column of its rays) and the end of its tier
+    (bt2: kappa_i c_max <= THIN_X, c_max the largest column of one lane's C cells; the
+    tier is used when it adds bins and either a thin row exists or it adds >= 4)."""
+    nr, c = w.grid.nr, shape[1]
     g = 8 if 8 * c >= nr else (16 if 16 * c >= nr else 32)   # lanes per ray
     r = 32 // g                                               # rays per warp
     dust = w.tdust32() <= w.t_sub
-    col = np.where(dust, w.rho32().astype(np.float64), 0.0) * np.diff(w.grid.r_if)
-    ntot = col.reshape(-1, nr).sum(axis=1)
-    pad = (-len(ntot)) % r
-    nmax = np.concatenate([ntot, np.zeros(pad)]).reshape(-1, r).max(axis=1)
+    col = (np.where(dust, w.rho32().astype(np.float64), 0.0) * np.diff(w.grid.r_if)).reshape(-1, nr)
+    nrays = col.shape[0]
+    pad = (-nrays) % r
+    colp = np.concatenate([col, np.zeros((pad, nr))]).reshape(-1, r, nr)
+    nmax = colp.sum(axis=2).max(axis=1)
+    chunks = np.zeros((colp.shape[0], r, g * c))
+    chunks[:, :, :nr] = colp
+    cmax = chunks.reshape(colp.shape[0], r, g, c).sum(axis=3).max(axis=(1, 2))
     kap = np.sort(w.kappa[w.kappa > 0])
     bt = np.searchsorted(kap, THIN_X / np.maximum(nmax, 1e-300), side="right")
+    bc = np.searchsorted(kap, THIN_X / np.maximum(cmax, 1e-300), side="right")
+    use = (bc > bt) & ((bt > 0) | (bc >= 4))
+    bt2 = np.where(use, bc, bt)
     rays = np.full(len(nmax), r)
     rays[-1] = r - pad
-    return int(np.sum((nbins - bt) * rays)) * nr
+    return rays * nr, bt, bt2, len(kap)
+
+
+def exact_exp_ops(w, shape):
+    """Exponentials of one tracer launch on grid w that its series cannot replace:
+    one per (cell, bin) beyond the warp's tier (bt2), one per (lane, bin) of the tier
+    (the tier's bins are expanded about each lane's first column), none for the thin
+    series. The tile kernel traces every (cell, bin) bin by bin."""
+    if shape[0] != 1:
+        return w.grid.ncells * int(np.count_nonzero(w.kappa > 0))
+    cells, bt, bt2, na = _warp_partition(w, shape)
+    return int(np.sum((na - bt2) * cells) + 32 * np.sum(bt2 - bt))
 
 
 def series_fma_ops(w, shape):
     """FMA-pipe operations of one tracer launch on grid w that its arithmetic needs at
-    the least: the power series (SERIES_FMA_PER_CELL per cell) in every warp whose rays
-    leave some bin in it, and EXACT_FMA_PER_PAIR per (cell, bin) traced bin by bin."""
-    nr = w.grid.nr
-    nbins = int(np.count_nonzero(w.kappa > 0))
-    exact = exact_exp_ops(w, shape)
+    the least: the power series (SERIES_FMA_PER_CELL per cell) in every warp that
+    sums some bin in it, and EXACT_FMA_PER_PAIR per (cell, bin) traced bin by bin."""
     if shape[0] != 1:
-        return EXACT_FMA_PER_PAIR * exact
-    c = shape[1]
-    g = 8 if 8 * c >= nr else (16 if 16 * c >= nr else 32)
-    r = 32 // g
-    dust = w.tdust32() <= w.t_sub
-    col = np.where(dust, w.rho32().astype(np.float64), 0.0) * np.diff(w.grid.r_if)
-    ntot = col.reshape(-1, nr).sum(axis=1)
-    pad = (-len(ntot)) % r
-    nmax = np.concatenate([ntot, np.zeros(pad)]).reshape(-1, r).max(axis=1)
-    kap = np.sort(w.kappa[w.kappa > 0])
-    bt = np.searchsorted(kap, THIN_X / np.maximum(nmax, 1e-300), side="right")
-    rays = np.full(len(nmax), r)
-    rays[-1] = r - pad
-    series_cells = int(np.sum(rays[bt > 0])) * nr if nbins else 0
-    return SERIES_FMA_PER_CELL * series_cells + EXACT_FMA_PER_PAIR * exact
+        return EXACT_FMA_PER_PAIR * exact_exp_ops(w, shape)
+    cells, bt, bt2, na = _warp_partition(w, shape)
+    return int(SERIES_FMA_PER_CELL * np.sum(cells[bt2 > 0]) + EXACT_FMA_PER_PAIR * np.sum((na - bt2) * cells))
 
 
 def roofline_summary(grids, hbm_peak_gbs, ex2_peak_gops, ffma_peak_gops, ex2_basis, ffma_basis):

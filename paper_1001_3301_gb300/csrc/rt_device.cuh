@@ -41,6 +41,14 @@ __device__ __forceinline__ float2 ex2_approx2(float2 x)
 
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 
+// the hardware reciprocal (relative error below 2^-22; 0 for +-Inf, flushes subnormals)
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Knuth's TwoSum: s + e == a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
@@ -202,8 +210,10 @@ __device__ __forceinline__ void fill_moments(float4 *s_mom, int i, float nk)
     s_mom[2 * i + 1] = make_float4(c2, c2, c3, c3);
 }
 
+// n0: a column the cells' n2 are counted from (the exponent is nk (n0 + n2) + lf,
+// taken as nk n2 + (nk n0 + lf)); 0 where n2 is the whole column.
 template <int NT, int C>
-__device__ __forceinline__ void moment_range(int i0, int i1, const float4 *s_nu, const float4 *s_mom,
+__device__ __forceinline__ void moment_range(int i0, int i1, const float4 *s_nu, const float4 *s_mom, float n0,
                                              const float2 (&n2)[C / 2], const float2 (&d2)[C / 2],
                                              float2 (&a2)[C / 2])
 {
@@ -217,7 +227,7 @@ __device__ __forceinline__ void moment_range(int i0, int i1, const float4 *s_nu,
 #pragma unroll(NT <= 2 ? 2 : 1)
     for (int i = i0; i < i1; ++i) {
         const float4 e = s_nu[i];
-        const float2 nk = make_float2(e.x, e.y), lf = make_float2(e.z, e.w);
+        const float2 nk = make_float2(e.x, e.y), lf = f2(fmaf(e.x, n0, e.z));
         const float4 m01 = s_mom[2 * i];
         const float2 c0 = make_float2(m01.x, m01.y), c1 = make_float2(m01.z, m01.w);
         float2 c2 = f2(0.0f);
@@ -245,13 +255,13 @@ __device__ __forceinline__ void moment_range(int i0, int i1, const float4 *s_nu,
 // Bin classes per warp: 1, 2, 3, 5 = Taylor with that many terms, 6 = mixed,
 // 7 = MUFU. Classes 1-3 run in the moment form above; bin_range serves 5-7.
 template <int CLASS, int C>
-__device__ __forceinline__ void bin_range(int i0, int i1, const float4 *s_nu, const float2 (&n2)[C / 2],
+__device__ __forceinline__ void bin_range(int i0, int i1, const float4 *s_nu, float n0, const float2 (&n2)[C / 2],
                                           const float2 (&d2)[C / 2], float2 (&a2)[C / 2])
 {
 #pragma unroll(CLASS <= 2 ? 2 : 1)
     for (int i = i0; i < i1; ++i) {
         const float4 e = s_nu[i];
-        const float2 nk = make_float2(e.x, e.y), lf = make_float2(e.z, e.w);
+        const float2 nk = make_float2(e.x, e.y), lf = f2(fmaf(e.x, n0, e.z));
         const float2 nk1 = __fmul2_rn(nk, f2((float)taylor_coeff(0)));  // class 1
 #pragma unroll
         for (int m = 0; m < C / 2; ++m) {

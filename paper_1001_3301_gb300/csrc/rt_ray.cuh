@@ -6,14 +6,21 @@
 // so rays shorter than 32 C cells keep every lane busy); lane l of a segment owns
 // the cells [l C, (l+1) C) of its ray, so the radial constants of a lane never
 // change and the ray's fields are read straight from HBM in 16-byte vectors (no
-// staging, no block barrier in the ray loop). Per ray:
-//   - dN = [T <= t_sub] rho dr per cell, and its exclusive prefix N_in along the
-//     ray (Eq. 19, tau = 0 at the inner radius): compensated lane sums, then a
-//     compensated warp scan;
-//   - the bins optically thin along all the warp's rays as one power series in the
-//     column (thin_series), the others by the per-bin loop of rt_device.cuh
-//     (Eqs. 17, 20, 31-32), into one accumulator per cell, with the warp's bin
-//     classes chosen from its largest and smallest column;
+// staging, no block barrier in the ray loop). While it traces one warp-slot, the
+// warp asks L2 for the fields of its next one (a bulk prefetch: nothing to wait
+// for). Per ray:
+//   - dN = [T <= t_sub] rho dr per cell, and its exclusive prefix along the ray
+//     (Eq. 19, tau = 0 at the inner radius) in one compensated pass: each lane keeps
+//     the column u from its own first cell, and a compensated warp scan of the lane
+//     sums gives the column N0 in front of the lane, so N_in = N0 + u;
+//   - every exponent is taken about the lane's N0: e^{-kappa N_in} =
+//     e^{-kappa N0} e^{-kappa u};
+//   - the bins optically thin along all the warp's rays (one power series in the
+//     column for the lot, whose rows the set-up builds) and the bins thin within
+//     every lane's own cells (expanded about N0 per lane) are summed as one series
+//     in u per lane (lane_series); the others go bin by bin (rt_device.cuh: Eqs.
+//     17, 20, 31-32) with the warp's bin classes from its largest and smallest
+//     column; all into one accumulator per cell;
 //   - escaping power sum_i F_i/F_max e^{-kappa_i N_total} (Eqs. 33-35), the lanes
 //     sharing the bins outside the thin series (that part from the series row);
 //   - q_abs = Gq acc and a_rad = q/(rho c) = Ga0 acc / dN (Sect. 5; the rho -> 0
@@ -26,12 +33,14 @@
 namespace rt {
 namespace {
 
-// Radial constants of every lane's cells, stored [j][lane] so that the lanes of a
-// warp read consecutive words (lane l's cell j is radial index (l mod G) C + j; a
-// [k] layout would put all 32 lanes on one shared-memory bank).
+// Radial constants of every lane's cells, stored [j / 2][lane] as pairs of
+// consecutive cells (lane l's cell j is radial index (l mod G) C + j), so that the
+// lanes of a warp read consecutive words and every read yields the packed pair the
+// f32x2 arithmetic works on: dr as (dr_j, dr_j+1), (Gq_j, Gq_j+1, Ga0_j, Ga0_j+1).
 template <int C>
 struct RayShared {
-    float dr[C][32], gq[C][32], ga[C][32];
+    float2 dr[C / 2][32];
+    float4 gqa[C / 2][32];
 };
 
 // dynamic shared memory of the bin tables: kappa, (nk, nk, lf, lf) and the series
@@ -51,13 +60,127 @@ __device__ __forceinline__ void ray_tables(const TraceArgs &p, int G, RayShared<
         s_nu[i] = make_float4(e.nk, e.nk, e.lf, e.lf);
         fill_moments(s_mom, i, e.nk);
     }
-    for (int i = tid; i < 32 * C; i += W * 32) {
-        const int l = i / C, j = i % C, k = (l % G) * C + j;
-        const float4 g = (k < p.nr) ? __ldg(&p.rtab[k]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        rs.dr[j][l] = g.x;
-        rs.gq[j][l] = g.y;
-        rs.ga[j][l] = g.z;
+    for (int i = tid; i < 16 * C; i += W * 32) {
+        const int l = i / (C / 2), m = i % (C / 2), k = (l % G) * C + 2 * m;
+        const float4 g0 = (k < p.nr) ? __ldg(&p.rtab[k]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        const float4 g1 = (k + 1 < p.nr) ? __ldg(&p.rtab[k + 1]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        rs.dr[m][l] = make_float2(g0.x, g1.x);
+        rs.gqa[m][l] = make_float4(g0.y, g1.y, g0.z, g1.z);
     }
+}
+
+// Ask L2 for `bytes` bytes from p (16-byte aligned, a multiple of 16): a hint with
+// no completion to wait for.
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// One lane's series in v = s2 u: Q(v) = sum_{k=1..K} F_k v^k. A cell with column u
+// in front of it (from the lane's first cell) and dN in it absorbs
+// Q(s2 (u + dN)) - Q(s2 u) = s2 dN sum_k F_k h_{k-1}(a, c), a = s2 (u + dN), c = s2 u,
+// evaluated by the paired Horner recurrence of thin_series (no a - c cancellation).
+template <int C>
+__device__ __forceinline__ void lane_series(const float (&F)[kThinTerms + 1], float s2, const float2 (&u2)[C / 2],
+                                            const float2 (&d2)[C / 2], float2 (&a2)[C / 2])
+{
+    const float2 s22 = f2(s2);
+    float2 Fk[kThinTerms + 1];
+#pragma unroll
+    for (int k = 1; k <= kThinTerms; ++k) Fk[k] = f2(F[k]);
+#pragma unroll
+    for (int m = 0; m < C / 2; ++m) {
+        const float2 cc = __fmul2_rn(s22, u2[m]);
+        const float2 aa = __ffma2_rn(s22, d2[m], cc);
+        float2 dd = Fk[kThinTerms];
+        float2 pc = __ffma2_rn(dd, cc, Fk[kThinTerms - 1]);
+#pragma unroll
+        for (int k = kThinTerms - 2; k >= 1; --k) {
+            dd = __ffma2_rn(dd, aa, pc);
+            pc = __ffma2_rn(pc, cc, Fk[k]);
+        }
+        dd = __ffma2_rn(dd, aa, pc);
+        a2[m] = __ffma2_rn(__fmul2_rn(d2[m], dd), s22, a2[m]);
+    }
+}
+
+// The coefficients F_1..F_K of a lane's series (lane_series) and its scale s2:
+//   - the bins i < bt, thin along all the warp's rays: their set-up row holds
+//     P(x) = sum_k C_k x^k with x = s N (s = kappa_{bt-1}), so that a cell absorbs
+//     P(s N_out) - P(s N_in). Shifted to the lane's column N0 (Taylor shift,
+//     synthetic division: E_k = P^(k)(x0) / k!, x0 = s N0 <= kThinX) and rescaled to
+//     v = s2 u: F_k += E_k (s / s2)^k.
+//   - the bins bt <= i < bt2, thin within every lane's own cells (kappa_i u <=
+//     kThinX for every u of the lane): expanded about N0,
+//     sum_i g_i (1 - e^{-kappa_i u}) = sum_k T_k v^k, g_i = F_i/F_max e^{-kappa_i N0},
+//     T_k = (-1)^{k+1} / k! sum_i g_i (kappa_i / s2)^k, s2 = kappa_{bt2-1}.
+// Every power sum of the tier has one sign (no cancellation); the shifted row
+// alternates with |x0| <= kThinX (precision loss below e^{2 kThinX}). Both parts
+// are truncated after K terms with |v| <= kThinX: the first omitted term is below
+// kThinX^K / K! of the leading one.
+__device__ __forceinline__ float lane_coefficients(const float *thin_row, int bt, int bt2, const float4 *s_nu,
+                                                   float n0, float (&F)[kThinTerms + 1])
+{
+    constexpr int K = kThinTerms;
+#pragma unroll
+    for (int k = 0; k <= K; ++k) F[k] = 0.0f;
+    // s2 in the units of -nk (the ratio of two bins' nk is the ratio of their kappa);
+    // without tier bins the row's own s
+    const float nks2 = s_nu[bt2 - 1].x;
+    const float s2 = (bt2 > bt || bt == 0) ? -nks2 * (float)kLn2 : __ldg(thin_row);
+    if (bt > 0) {
+        const float s = __ldg(thin_row);
+        float c[K + 1];
+        c[0] = 0.0f;
+#pragma unroll
+        for (int k = 1; k <= K; ++k) c[k] = __ldg(thin_row + k);
+        const float x0 = s * n0;
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+#pragma unroll
+            for (int j = K - 1; j >= (i > 1 ? i : 1); --j) c[j] = fmaf(x0, c[j + 1], c[j]);
+        if (bt2 > bt) {
+            const float rho = s / s2;
+            float pk = rho;
+#pragma unroll
+            for (int k = 1; k <= K; ++k) {
+                F[k] = c[k] * pk;
+                pk *= rho;
+            }
+        } else {
+#pragma unroll
+            for (int k = 1; k <= K; ++k) F[k] = c[k];
+        }
+    }
+    if (bt2 > bt) {
+        const float inv = 1.0f / nks2;
+        float2 m[K + 1];
+#pragma unroll
+        for (int k = 1; k <= K; ++k) m[k] = f2(0.0f);
+        const float2 n02 = f2(n0);
+        for (int i = bt; i < bt2; i += 2) {  // warp-uniform; bins in pairs
+            const float4 e0 = s_nu[i];
+            const float4 e1 = s_nu[i + 1 < bt2 ? i + 1 : i];
+            const float2 nk = make_float2(e0.x, e1.x);
+            float2 g = ex2_approx2(__ffma2_rn(nk, n02, make_float2(e0.z, e1.z)));
+            if (i + 1 >= bt2) g.y = 0.0f;
+            const float2 r = __fmul2_rn(nk, f2(inv));
+            float2 pw = g;
+#pragma unroll
+            for (int k = 1; k <= K; ++k) {
+                pw = __fmul2_rn(pw, r);
+                m[k] = __fadd2_rn(m[k], pw);
+            }
+        }
+        float fact = 1.0f;
+#pragma unroll
+        for (int k = 1; k <= K; ++k) {
+            fact *= (float)k;
+            const float t = (m[k].x + m[k].y) / fact;
+            F[k] += (k & 1) ? t : -t;
+        }
+    }
+    return s2;
 }
 
 // Warp-slots wr = wr_begin, wr_begin + step, ... (< wr_end) of grid p, R = 32 / G rays
@@ -83,60 +206,85 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
     const bool vec = (nr % V == 0) &&
                      ((reinterpret_cast<size_t>(p.rho) | reinterpret_cast<size_t>(p.tdust) |
                        reinterpret_cast<size_t>(p.q) | reinterpret_cast<size_t>(p.a)) % (4 * V) == 0);
+    // a warp-slot's fields are R consecutive rays: one contiguous run per field
+    const bool pf = (nr % 4 == 0) &&
+                    ((reinterpret_cast<size_t>(p.rho) | reinterpret_cast<size_t>(p.tdust)) % 16 == 0);
+    const int na = p.n_active;
+    const float2 tiny2 = f2(FLT_MIN);
 
     for (unsigned wr = wr_begin; wr < wr_end; wr += step) {
         const unsigned ray = wr * R + seg;
         const bool live = ray < p.nrays;  // the last warp may hold fewer than R rays
         const int nv = live ? nv_ray : 0;
         const size_t base = (size_t)(live ? ray : 0u) * nr + c0;
-        float rho[C], td[C];
+
+        // the fields, straight from HBM (or from L2, where the prefetch got there first)
+        float2 rho2[C / 2], td2[C / 2];
         if (vec && nv == C) {
 #pragma unroll
             for (int j = 0; j < C; j += V) {
                 if constexpr (V == 4) {
                     const float4 r4 = __ldg(reinterpret_cast<const float4 *>(p.rho + base + j));
                     const float4 t4 = __ldg(reinterpret_cast<const float4 *>(p.tdust + base + j));
-                    rho[j] = r4.x; rho[j + 1] = r4.y; rho[j + 2] = r4.z; rho[j + 3] = r4.w;
-                    td[j] = t4.x; td[j + 1] = t4.y; td[j + 2] = t4.z; td[j + 3] = t4.w;
+                    rho2[j / 2] = make_float2(r4.x, r4.y);
+                    rho2[j / 2 + 1] = make_float2(r4.z, r4.w);
+                    td2[j / 2] = make_float2(t4.x, t4.y);
+                    td2[j / 2 + 1] = make_float2(t4.z, t4.w);
                 } else {
-                    const float2 r2 = __ldg(reinterpret_cast<const float2 *>(p.rho + base + j));
-                    const float2 t2 = __ldg(reinterpret_cast<const float2 *>(p.tdust + base + j));
-                    rho[j] = r2.x; rho[j + 1] = r2.y;
-                    td[j] = t2.x; td[j + 1] = t2.y;
+                    rho2[j / 2] = __ldg(reinterpret_cast<const float2 *>(p.rho + base + j));
+                    td2[j / 2] = __ldg(reinterpret_cast<const float2 *>(p.tdust + base + j));
                 }
             }
         } else {
             // cells past the ray's end: no density, no dust (their column is 0 with any t_sub)
 #pragma unroll
-            for (int j = 0; j < C; ++j) {
-                rho[j] = 0.0f;
-                td[j] = INFINITY;
-                if (j < nv) {
-                    rho[j] = __ldg(p.rho + base + j);
-                    td[j] = __ldg(p.tdust + base + j);
-                }
+            for (int j = 0; j < C; j += 2) {
+                rho2[j / 2] = make_float2(j < nv ? __ldg(p.rho + base + j) : 0.0f,
+                                          j + 1 < nv ? __ldg(p.rho + base + j + 1) : 0.0f);
+                td2[j / 2] = make_float2(j < nv ? __ldg(p.tdust + base + j) : INFINITY,
+                                         j + 1 < nv ? __ldg(p.tdust + base + j + 1) : INFINITY);
+            }
+        }
+        // the fields of this warp's next slot, on their way to L2
+        if (pf && lane == 0 && wr + step < wr_end) {
+            const unsigned r0 = (wr + step) * R;
+            if (r0 < p.nrays) {
+                const unsigned nrs = p.nrays - r0 < (unsigned)R ? p.nrays - r0 : (unsigned)R;
+                const unsigned bytes = nrs * (unsigned)nr * 4u;
+                prefetch_l2(p.rho + (size_t)r0 * nr, bytes);
+                prefetch_l2(p.tdust + (size_t)r0 * nr, bytes);
             }
         }
 
-        // column density of the dust in each cell, and invalid-input flags
-        Cells<float, C> D, N, acc;
-        unsigned zero_m = 0;
-        bool bad = false;
+        // column density of the dust in each cell, its compensated prefix u from the
+        // lane's first cell, and the invalid-input and no-column flags
+        // (a cell without dust gets the column -0, one with dust but no density +0: the
+        // sign tells the two apart where the force needs it, and -0 adds nothing)
+        float2 D[C / 2], U[C / 2], acc[C / 2];
+        unsigned rho_bits = 0u;
+        bool td_nan = false, zc = false;
         Sum lsum;
         lsum.zero();
 #pragma unroll
-        for (int j = 0; j < C; ++j) {
-            const bool dust = td[j] <= p.t_sub;
-            const float d = dust ? rho[j] * rs.dr[j][lane] : 0.0f;
-            D.set(j, d);
-            bad |= !(rho[j] >= 0.0f && rho[j] <= FLT_MAX) || (td[j] != td[j]);
-            if (dust && d == 0.0f) zero_m |= 1u << j;
-            lsum.add(d);
+        for (int m = 0; m < C / 2; ++m) {
+            const float2 dr = rs.dr[m][lane];
+            const bool d0 = td2[m].x <= p.t_sub, d1 = td2[m].y <= p.t_sub;
+            // rho must be finite and >= 0 (-0 counts as 0): the bits of rho + 0 stay
+            // below those of +Inf; t_dust must not be NaN
+            const float2 rz = __fadd2_rn(rho2[m], f2(0.0f));
+            rho_bits = max(rho_bits, max(__float_as_uint(rz.x), __float_as_uint(rz.y)));
+            td_nan |= (td2[m].x != td2[m].x) || (td2[m].y != td2[m].y);
+            D[m] = __fmul2_rn(rz, make_float2(d0 ? dr.x : -0.0f, d1 ? dr.y : -0.0f));
+            zc |= (__float_as_uint(D[m].x) == 0u) || (__float_as_uint(D[m].y) == 0u);
+            acc[m] = f2(0.0f);
+            U[m].x = lsum.value();
+            lsum.add(D[m].x);
+            U[m].y = lsum.value();
+            lsum.add(D[m].y);
         }
-        zero_m &= nv >= 32 ? 0xffffffffu : (1u << nv) - 1u;  // cells of the ray only
-        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicMax(p.bad_input, p.seq);
+        if (__any_sync(0xffffffffu, rho_bits >= 0x7f800000u || td_nan) && lane == 0) atomicMax(p.bad_input, p.seq);
 
-        // exclusive prefix along the ray: scan of the lane sums within the segment
+        // column in front of each lane: compensated scan of the lane sums within the segment
         Sum inc = lsum;
 #pragma unroll
         for (int d = 1; d < G; d <<= 1) {
@@ -145,55 +293,49 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
         }
         Sum pre = inc.shfl_up(1, G);
         if (ll == 0) pre.zero();
-#pragma unroll
-        for (int j = 0; j < C; ++j) {
-            N.set(j, pre.value());
-            pre.add(D.get(j));
-            acc.set(j, 0.0f);
-        }
-        const float ntot = __shfl_sync(0xffffffffu, pre.value(), G - 1, G);
+        const float n0 = pre.value();
+        const float ntot = __shfl_sync(0xffffffffu, inc.value(), G - 1, G);
 
-        const int na = p.n_active;
-        // bins thin along all the warp's rays: one series for the lot, the rest bin by bin
+        // bins thin along all the warp's rays (bt of them) and, after those, bins thin
+        // within every lane's cells (up to bt2): one series per lane; the rest bin by bin
         float nmax = ntot;
         for (int o = G; o < 32; o <<= 1) nmax = fmaxf(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+        float cmax = lsum.value();
+        for (int o = 16; o > 0; o >>= 1) cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
         const int bt = thin_count(s_nu, na, lane, nmax);
+        int bt2 = bt;
+        if (bt < na) {
+            const int bc = thin_count(s_nu, na, lane, cmax);
+            // with no row to shift, a few tier bins do not pay for the series
+            if (bc > bt && (bt > 0 || bc >= 4)) bt2 = bc;
+        }
         const float *thin_row = p.kap + kKapTable + bt * kThinStride;
-        if (bt > 0) thin_series<C>(thin_row, N.v, D.v, acc.v);
-        if (bt < na) {  // warp-uniform
+        if (bt2 > 0) {
+            float F[kThinTerms + 1];
+            const float s2 = lane_coefficients(thin_row, bt, bt2, s_nu, n0, F);
+            lane_series<C>(F, s2, U, D, acc);
+        }
+        if (bt2 < na) {  // warp-uniform
             // the warp's largest and smallest non-zero column decide each bin's class
             float dmax = 0.0f, dmin = INFINITY;
 #pragma unroll
-            for (int j = 0; j < C; ++j) {
-                dmax = fmaxf(dmax, D.get(j));
-                if (D.get(j) > 0.0f) dmin = fminf(dmin, D.get(j));
+            for (int m = 0; m < C / 2; ++m) {
+                dmax = fmaxf(dmax, fmaxf(D[m].x, D[m].y));
+                dmin = fminf(dmin, fminf(D[m].x > 0.0f ? D[m].x : INFINITY, D[m].y > 0.0f ? D[m].y : INFINITY));
             }
             for (int o = 16; o > 0; o >>= 1) {
                 dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
                 dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
             }
-            const BinClasses bc = classify_bins(s_nu, na, lane, dmax, dmin, bt);
-            const int t1 = max(bc.b1, bt), t2 = max(bc.b2, bt), t3 = max(bc.b3, bt), t5 = max(bc.b5, bt);
-            const int tb = max(bc.bb, bt);
-            moment_range<1, C>(bt, t1, s_nu, s_mom, N.v, D.v, acc.v);
-            moment_range<2, C>(t1, t2, s_nu, s_mom, N.v, D.v, acc.v);
-            bin_range<3, C>(t2, t3, s_nu, N.v, D.v, acc.v);
-            bin_range<5, C>(t3, t5, s_nu, N.v, D.v, acc.v);
-            bin_range<6, C>(t5, tb, s_nu, N.v, D.v, acc.v);
-            bin_range<7, C>(tb, na, s_nu, N.v, D.v, acc.v);
-        }
-
-        // cells with dust but no column: the rho -> 0 force limit sum_i kappa_i g_i
-        if (__any_sync(0xffffffffu, zero_m != 0u)) {
-#pragma unroll
-            for (int j = 0; j < C; ++j) {
-                if (__any_sync(0xffffffffu, (zero_m >> j) & 1u)) {
-                    float s = 0.0f;
-                    for (int i = 0; i < p.nnu_pad; ++i)
-                        s = fmaf(s_kap[i], ex2_approx(fmaf(s_nu[i].x, N.get(j), s_nu[i].z)), s);
-                    if ((zero_m >> j) & 1u) D.set(j, s);
-                }
-            }
+            const BinClasses bc = classify_bins(s_nu, na, lane, dmax, dmin, bt2);
+            const int t1 = max(bc.b1, bt2), t2 = max(bc.b2, bt2), t3 = max(bc.b3, bt2), t5 = max(bc.b5, bt2);
+            const int tb = max(bc.bb, bt2);
+            moment_range<1, C>(bt2, t1, s_nu, s_mom, n0, U, D, acc);
+            moment_range<2, C>(t1, t2, s_nu, s_mom, n0, U, D, acc);
+            bin_range<3, C>(t2, t3, s_nu, n0, U, D, acc);
+            bin_range<5, C>(t3, t5, s_nu, n0, U, D, acc);
+            bin_range<6, C>(t5, tb, s_nu, n0, U, D, acc);
+            bin_range<7, C>(tb, na, s_nu, n0, U, D, acc);
         }
 
         // escaping power of the ray, the lanes of its segment sharing the bins
@@ -208,36 +350,57 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
             }
         }
 
-        // outputs and the lane's absorbed power
-        // (a cell with no column, past the ray or without dust or density, absorbed 0)
-        float qv[C], av[C];
-        float lane_abs = 0.0f;
+        // outputs and the lane's absorbed power: q = Gq acc, a = Ga0 acc / dN (a cell
+        // with no column, past the ray or without dust or density, absorbed 0)
+        float2 lane_abs2 = f2(0.0f);
+        float2 qv[C / 2];
 #pragma unroll
-        for (int j = 0; j < C; ++j) {
-            const float aj = acc.get(j), dj = D.get(j);
-            const bool zc = (zero_m >> j) & 1u;
-            qv[j] = rs.gq[j][lane] * aj;
-            av[j] = rs.ga[j][lane] * (zc ? dj : (dj > 0.0f ? __fdividef(aj, dj) : 0.0f));
-            lane_abs += aj;
+        for (int m = 0; m < C / 2; ++m) {
+            const float4 g = rs.gqa[m][lane];
+            qv[m] = __fmul2_rn(make_float2(g.x, g.y), acc[m]);
+            lane_abs2 = __fadd2_rn(lane_abs2, acc[m]);
+            const float2 dd = make_float2(fmaxf(D[m].x, tiny2.x), fmaxf(D[m].y, tiny2.y));
+            acc[m] = __fmul2_rn(make_float2(g.z, g.w), __fmul2_rn(acc[m], make_float2(rcp_approx(dd.x), rcp_approx(dd.y))));
         }
-        eabs.add(lane_abs * w);
+        // cells with dust but no column: the rho -> 0 force limit Ga0 sum_i kappa_i g_i
+        if (__any_sync(0xffffffffu, zc)) {
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                const float dj = (j & 1) ? D[j / 2].y : D[j / 2].x;
+                const bool zj = zc && __float_as_uint(dj) == 0u;
+                if (__any_sync(0xffffffffu, zj)) {
+                    const float uj = (j & 1) ? U[j / 2].y : U[j / 2].x;
+                    float s = 0.0f;
+                    for (int i = 0; i < na; ++i)
+                        s = fmaf(s_kap[i], ex2_approx(fmaf(s_nu[i].x, uj, fmaf(s_nu[i].x, n0, s_nu[i].z))), s);
+                    if (zj) {
+                        const float4 g = rs.gqa[j / 2][lane];
+                        if (j & 1) acc[j / 2].y = g.w * s;
+                        else acc[j / 2].x = g.z * s;
+                    }
+                }
+            }
+        }
+        eabs.add((lane_abs2.x + lane_abs2.y) * w);
         if (vec && nv == C) {
 #pragma unroll
             for (int j = 0; j < C; j += V) {
                 if constexpr (V == 4) {
-                    *reinterpret_cast<float4 *>(p.q + base + j) = make_float4(qv[j], qv[j + 1], qv[j + 2], qv[j + 3]);
-                    *reinterpret_cast<float4 *>(p.a + base + j) = make_float4(av[j], av[j + 1], av[j + 2], av[j + 3]);
+                    *reinterpret_cast<float4 *>(p.q + base + j) =
+                        make_float4(qv[j / 2].x, qv[j / 2].y, qv[j / 2 + 1].x, qv[j / 2 + 1].y);
+                    *reinterpret_cast<float4 *>(p.a + base + j) =
+                        make_float4(acc[j / 2].x, acc[j / 2].y, acc[j / 2 + 1].x, acc[j / 2 + 1].y);
                 } else {
-                    *reinterpret_cast<float2 *>(p.q + base + j) = make_float2(qv[j], qv[j + 1]);
-                    *reinterpret_cast<float2 *>(p.a + base + j) = make_float2(av[j], av[j + 1]);
+                    *reinterpret_cast<float2 *>(p.q + base + j) = qv[j / 2];
+                    *reinterpret_cast<float2 *>(p.a + base + j) = acc[j / 2];
                 }
             }
         } else {
 #pragma unroll
             for (int j = 0; j < C; ++j) {
                 if (j < nv) {
-                    p.q[base + j] = qv[j];
-                    p.a[base + j] = av[j];
+                    p.q[base + j] = (j & 1) ? qv[j / 2].y : qv[j / 2].x;
+                    p.a[base + j] = (j & 1) ? acc[j / 2].y : acc[j / 2].x;
                 }
             }
         }

@@ -268,12 +268,12 @@ __device__ __forceinline__ void trace_tile_range(const TraceArgs &p, unsigned t_
             }
             const int na = p.n_active;
             const BinClasses bc = classify_bins(s_nu, na, lane, dmax, dmin);
-            moment_range<1, C>(0, bc.b1, s_nu, s_mom, N.v, D.v, acc.v);
-            moment_range<2, C>(bc.b1, bc.b2, s_nu, s_mom, N.v, D.v, acc.v);
-            bin_range<3, C>(bc.b2, bc.b3, s_nu, N.v, D.v, acc.v);
-            bin_range<5, C>(bc.b3, bc.b5, s_nu, N.v, D.v, acc.v);
-            bin_range<6, C>(bc.b5, bc.bb, s_nu, N.v, D.v, acc.v);
-            bin_range<7, C>(bc.bb, na, s_nu, N.v, D.v, acc.v);
+            moment_range<1, C>(0, bc.b1, s_nu, s_mom, 0.0f, N.v, D.v, acc.v);
+            moment_range<2, C>(bc.b1, bc.b2, s_nu, s_mom, 0.0f, N.v, D.v, acc.v);
+            bin_range<3, C>(bc.b2, bc.b3, s_nu, 0.0f, N.v, D.v, acc.v);
+            bin_range<5, C>(bc.b3, bc.b5, s_nu, 0.0f, N.v, D.v, acc.v);
+            bin_range<6, C>(bc.b5, bc.bb, s_nu, 0.0f, N.v, D.v, acc.v);
+            bin_range<7, C>(bc.bb, na, s_nu, 0.0f, N.v, D.v, acc.v);
         }
 
         // rho == 0 cells with dust: the force limit sum_i kappa_i g_i (rare; per

@@ -10,31 +10,44 @@ import bench
 import synth
 
 
-def _brute(w, shape):
-    """Per warp of R = 32 / G rays: bins with kappa_i N_max > THIN_X, times the
-    warp's rays' cells; every (cell, bin) for the tile kernel."""
+def _brute_warps(w, shape):
+    """Per warp of R = 32 / G rays (G lanes of C cells per ray): its cells, the bins
+    its thin series takes (kappa_i N_max <= THIN_X, N_max the largest ray total) and
+    the end of its tier (kappa_i c_max <= THIN_X, c_max the largest column of one
+    lane's C cells; used if it adds bins and a thin row exists or it adds >= 4)."""
     g = w.grid
-    kap = w.kappa[w.kappa > 0]
-    if shape[0] != 1:
-        return g.ncells * len(kap)
+    kap = sorted(w.kappa[w.kappa > 0])
     c = shape[1]
     lanes = 8 if 8 * c >= g.nr else (16 if 16 * c >= g.nr else 32)
     r = 32 // lanes
     rho = w.rho32().astype(np.float64).reshape(-1, g.nr)
     td = w.tdust32().reshape(-1, g.nr)
     dr = np.diff(g.r_if)
-    total = 0
+    col = lambda j, k: rho[j, k] * dr[k] if td[j, k] <= w.t_sub else 0.0
+    out = []
     nrays = rho.shape[0]
     for first in range(0, nrays, r):
         rays = range(first, min(first + r, nrays))
-        nmax = max(sum(rho[j, k] * dr[k] for k in range(g.nr) if td[j, k] <= w.t_sub) for j in rays)
-        exact = sum(1 for kk in kap if kk * nmax > bench.THIN_X)
-        total += exact * len(rays) * g.nr
-    return total
+        nmax = max(sum(col(j, k) for k in range(g.nr)) for j in rays)
+        cmax = max(sum(col(j, k) for k in range(l * c, min((l + 1) * c, g.nr)))
+                   for j in rays for l in range(lanes))
+        bt = sum(1 for kk in kap if kk * nmax <= bench.THIN_X)
+        bc = sum(1 for kk in kap if kk * cmax <= bench.THIN_X)
+        bt2 = bc if (bc > bt and (bt > 0 or bc >= 4)) else bt
+        out.append((len(rays) * g.nr, bt, bt2, len(kap)))
+    return out
+
+
+def _brute(w, shape):
+    """One exponential per (cell, bin) beyond the tier, one per (lane, bin) of the
+    tier; every (cell, bin) for the tile kernel."""
+    if shape[0] != 1:
+        return w.grid.ncells * int(np.count_nonzero(w.kappa > 0))
+    return sum((na - bt2) * cells + 32 * (bt2 - bt) for cells, bt, bt2, na in _brute_warps(w, shape))
 
 
 @pytest.mark.parametrize("tau,shape", [(10.0, (1, 8, 4, 6)), (100.0, (1, 4, 4, 8)), (1.0, (1, 16, 4, 3)),
-                                       (10.0, (0, 8, 4, 6))])
+                                       (1e3, (1, 2, 4, 8)), (10.0, (0, 8, 4, 6))])
 def test_exact_exp_ops_matches_brute_force(tau, shape):
     w = synth.disk3d(40, 6, 5, n_nu=16, tau550=tau, seed=4)   # 30 rays: a partial last warp
     assert bench.exact_exp_ops(w, shape) == _brute(w, shape)
@@ -52,26 +65,12 @@ def test_exact_exp_ops_limits():
 
 
 def _brute_fma(w, shape):
-    """Series FMAs per cell in every warp that leaves some bin in the series, plus
+    """Series FMAs per cell in every warp that sums some bin in the series, plus
     EXACT_FMA_PER_PAIR per (cell, bin) traced bin by bin."""
-    g = w.grid
-    kap = w.kappa[w.kappa > 0]
-    exact = _brute(w, shape)
     if shape[0] != 1:
-        return bench.EXACT_FMA_PER_PAIR * exact
-    c = shape[1]
-    lanes = 8 if 8 * c >= g.nr else (16 if 16 * c >= g.nr else 32)
-    r = 32 // lanes
-    rho = w.rho32().astype(np.float64).reshape(-1, g.nr)
-    td = w.tdust32().reshape(-1, g.nr)
-    dr = np.diff(g.r_if)
-    cells = 0
-    for first in range(0, rho.shape[0], r):
-        rays = range(first, min(first + r, rho.shape[0]))
-        nmax = max(sum(rho[j, k] * dr[k] for k in range(g.nr) if td[j, k] <= w.t_sub) for j in rays)
-        if any(kk * nmax <= bench.THIN_X for kk in kap):
-            cells += len(rays) * g.nr
-    return bench.SERIES_FMA_PER_CELL * cells + bench.EXACT_FMA_PER_PAIR * exact
+        return bench.EXACT_FMA_PER_PAIR * _brute(w, shape)
+    return sum(bench.SERIES_FMA_PER_CELL * cells * (bt2 > 0) + bench.EXACT_FMA_PER_PAIR * (na - bt2) * cells
+               for cells, bt, bt2, na in _brute_warps(w, shape))
 
 
 @pytest.mark.parametrize("tau,shape", [(10.0, (1, 8, 4, 6)), (1e4, (1, 4, 4, 8)), (0.3, (0, 8, 4, 6))])
