@@ -71,11 +71,11 @@ FLD_SETUP_MG_B, FLD_PASS_MG_B, FLD_ITER_MG_B = 98, 100, 100
 EXP_PER_CELL_NU = 1
 # bins with kappa_i N_max <= THIN_X (N_max the largest total column of the rays one
 # warp traces) enter the tracer's power series instead (no exponential per cell)
-THIN_X = 0.5
+THIN_X = 1.0
 # FMA-pipe operations of the power series per cell (paired Horner form of
-# kThinTerms = 8 terms: 2 K + 1), and per (cell, bin) traced bin by bin at the least
+# kThinTerms = 10 terms: 2 K + 1), and per (cell, bin) traced bin by bin at the least
 # (the exponent's FMA and the accumulation)
-SERIES_FMA_PER_CELL = 17
+SERIES_FMA_PER_CELL = 21
 EXACT_FMA_PER_PAIR = 2
 # algorithmic bytes per cell of the tracer: rho, T_dust in, q_abs, a_rad out (FP32)
 TRACE_BYTES_PER_CELL = 16
@@ -225,31 +225,41 @@ def traffic_from_profile(path: str, src_hash: str):
 
 
 def _warp_partition(w, shape):
-    """Per warp of the warp-per-ray kernel (R = 32 / G rays of nr cells, G lanes of C
-    cells each): the cells it traces, the bins its thin series takes (bt: kappa_i N_max
-    <= THIN_X, N_max the largest total column of its rays) and the end of its tier
-    (bt2: kappa_i c_max <= THIN_X, c_max the largest column of one lane's C cells; the
-    tier is used when it adds bins and either a thin row exists or it adds >= 4)."""
+    """Per warp of the warp-per-ray kernel: the cells it traces, the bins its thin
+    series takes (bt: kappa_i N_max <= THIN_X, N_max the largest total column of its
+    rays) and the end of its tier (bt2: kappa_i c_max <= THIN_X, c_max the largest
+    column of one lane's C cells; the tier is used when it adds bins and either a thin
+    row exists or it adds >= 4). A warp holds R = 32 / G rays of G lanes of C cells
+    where 32 C cells hold a ray; for C <= 8 and rays of up to 64 C cells, two warps
+    share a ray (each 32 C of its cells, N_max the ray's total)."""
     nr, c = w.grid.nr, shape[1]
-    g = 8 if 8 * c >= nr else (16 if 16 * c >= nr else 32)   # lanes per ray
-    r = 32 // g                                               # rays per warp
     dust = w.tdust32() <= w.t_sub
     col = (np.where(dust, w.rho32().astype(np.float64), 0.0) * np.diff(w.grid.r_if)).reshape(-1, nr)
-    nrays = col.shape[0]
-    pad = (-nrays) % r
-    colp = np.concatenate([col, np.zeros((pad, nr))]).reshape(-1, r, nr)
-    nmax = colp.sum(axis=2).max(axis=1)
-    chunks = np.zeros((colp.shape[0], r, g * c))
-    chunks[:, :, :nr] = colp
-    cmax = chunks.reshape(colp.shape[0], r, g, c).sum(axis=3).max(axis=(1, 2))
     kap = np.sort(w.kappa[w.kappa > 0])
+    if 32 * c < nr:   # two warps per ray
+        half = np.zeros((col.shape[0], 2, 32 * c))
+        half.reshape(col.shape[0], -1)[:, :nr] = col
+        nmax = np.repeat(col.sum(axis=1), 2)
+        cmax = half.reshape(col.shape[0], 2, 32, c).sum(axis=3).max(axis=2).reshape(-1)
+        cells = np.array([min(32 * c, nr), nr - min(32 * c, nr)] * col.shape[0])
+    else:
+        g = 8 if 8 * c >= nr else (16 if 16 * c >= nr else 32)   # lanes per ray
+        r = 32 // g                                               # rays per warp
+        nrays = col.shape[0]
+        pad = (-nrays) % r
+        colp = np.concatenate([col, np.zeros((pad, nr))]).reshape(-1, r, nr)
+        nmax = colp.sum(axis=2).max(axis=1)
+        chunks = np.zeros((colp.shape[0], r, g * c))
+        chunks[:, :, :nr] = colp
+        cmax = chunks.reshape(colp.shape[0], r, g, c).sum(axis=3).max(axis=(1, 2))
+        rays = np.full(len(nmax), r)
+        rays[-1] = r - pad
+        cells = rays * nr
     bt = np.searchsorted(kap, THIN_X / np.maximum(nmax, 1e-300), side="right")
     bc = np.searchsorted(kap, THIN_X / np.maximum(cmax, 1e-300), side="right")
     use = (bc > bt) & ((bt > 0) | (bc >= 4))
     bt2 = np.where(use, bc, bt)
-    rays = np.full(len(nmax), r)
-    rays[-1] = r - pad
-    return rays * nr, bt, bt2, len(kap)
+    return cells, bt, bt2, len(kap)
 
 
 def exact_exp_ops(w, shape):

@@ -61,6 +61,11 @@ struct rt_ctx {
     double *kappa_t_d = nullptr;
     float *tg32 = nullptr;
     float2 *kt2 = nullptr;
+    // a table that separates, kappa_i(T) = kappa_i b(T): the one-column tracer with the
+    // column weight b(T) (grid padded with +Inf; (b_j, slope to the next point))
+    bool tw_sep = false;
+    float *tw_t_d = nullptr;
+    float2 *tw_b_d = nullptr;
     int *order_d = nullptr;
     unsigned long long fingerprint = 0;
     // learned surrogate (rt_surrogate.cu), created by rt_surrogate_train / _load
@@ -122,16 +127,29 @@ bool increasing(const double *a, int n)
     return true;
 }
 
-// shape choice cache across contexts: (precision, nr, nrays, nnu_pad) -> shape
+// shape choice cache across contexts: (precision, nr, nrays, nnu_pad, table kind) -> shape
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, long long, int>, Shape> g_tune_cache;
+std::map<std::tuple<int, int, long long, int, int>, Shape> g_tune_cache;
 
 long long total_tiles(const rt_ctx *c, Shape s);
+
+// A separable kappa(nu, T) table goes through the one-column ray kernel with the
+// column weight b(T) where that kernel holds the rays (FP32 modes); other
+// temperature-dependent tables through the per-bin kernel of rt_tdep.cu.
+bool use_tw(const rt_ctx *c)
+{
+    if (c->n_t <= 0 || !c->tw_sep || c->precision == RT_FP64) return false;
+    Shape s[16];
+    return rt::ray_shapes_tw(c->precision, c->nr, s, 16) > 0;
+}
+
+int table_kind(const rt_ctx *c) { return c->n_t <= 0 ? RT_TABLE_NU : (use_tw(c) ? RT_TABLE_NU_T_SEPARABLE : RT_TABLE_NU_T); }
 
 // every compiled shape that applies to this context: tile shapes, then ray shapes
 int all_shapes(const rt_ctx *c, Shape *out, int max_out)
 {
-    if (c->n_t > 0) return rt::tdep_shapes(c->nr, out, max_out);
+    if (c->n_t > 0) return use_tw(c) ? rt::ray_shapes_tw(c->precision, c->nr, out, max_out)
+                                     : rt::tdep_shapes(c->nr, out, max_out);
     int n = rt::trace_shapes(c->precision, out, max_out);
     if (c->precision != RT_FP64) n += rt::ray_shapes(c->precision, c->nr, out + n, max_out - n);
     return n;
@@ -139,7 +157,8 @@ int all_shapes(const rt_ctx *c, Shape *out, int max_out)
 
 Shape default_shape(const rt_ctx *c)
 {
-    if (c->n_t > 0) {  // temperature-dependent table: the fewest cells per lane that hold a ray
+    const bool tw = use_tw(c);
+    if (c->n_t > 0 && !tw) {  // temperature-dependent table: the fewest cells per lane that hold a ray
         Shape ts[16];
         const int n = rt::tdep_shapes(c->nr, ts, 16);
         int bi = -1;
@@ -151,7 +170,7 @@ Shape default_shape(const rt_ctx *c)
     }
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune_cache.find(std::make_tuple(c->precision, c->nr, c->nrays, c->sc_h.nnu_pad));
+        auto it = g_tune_cache.find(std::make_tuple(c->precision, c->nr, c->nrays, c->sc_h.nnu_pad, table_kind(c)));
         if (it != g_tune_cache.end()) return it->second;
     }
     // Prefer the warp-per-ray kernel with the fewest cells per lane when the rays
@@ -159,10 +178,10 @@ Shape default_shape(const rt_ctx *c)
     // that still gives every SM several tiles.
     if (c->precision != RT_FP64) {
         Shape rs[32];
-        const int nrs = rt::ray_shapes(c->precision, c->nr, rs, 32);
+        const int nrs = tw ? rt::ray_shapes_tw(c->precision, c->nr, rs, 32) : rt::ray_shapes(c->precision, c->nr, rs, 32);
         int bi = -1;
         for (int i = 0; i < nrs; ++i)
-            if (4 * c->nr >= 3 * rt::ray_lanes(rs[i].cells_per_lane, c->nr) * rs[i].cells_per_lane &&
+            if (4 * c->nr >= 3 * rt::ray_cells_held(rs[i].cells_per_lane, c->nr) &&
                 (bi < 0 || rs[i].cells_per_lane < rs[bi].cells_per_lane))
                 bi = i;
         if (bi >= 0) return rs[bi];
@@ -250,7 +269,7 @@ long long total_tiles(const rt_ctx *c, Shape s)
     long long tiles = 0;
     for (long long r0 = 0; r0 < c->nrays; r0 += cr) {
         const long long nr_c = (c->nrays - r0 < cr) ? c->nrays - r0 : cr;
-        tiles += (s.kind == rt::kKindRay) ? (nr_c + s.warps - 1) / s.warps
+        tiles += (s.kind == rt::kKindRay) ? (nr_c * rt::ray_warps_per_ray(s.cells_per_lane, c->nr) + s.warps - 1) / s.warps
                                           : (nr_c * (c->nr + 1) + T - 1) / T;
     }
     return tiles;
@@ -275,6 +294,10 @@ int trace_range(rt_ctx *c, const float *rho, const float *td, float *q, float *a
     args.nnu_pad = c->sc_h.nnu_pad;
     args.n_active = c->sc_h.n_active;
     args.t_sub = (float)c->t_sub;
+    const bool tw = use_tw(c);
+    args.tw_t = tw ? c->tw_t_d : nullptr;
+    args.tw_b = tw ? c->tw_b_d : nullptr;
+    args.n_tw = tw ? c->n_t : 0;
     const long long T = rt::trace_tile_cells(s), cr = chunk_rays(c);
     for (long long r0 = r_begin; r0 < r_end; r0 += cr) {
         const long long nr_c = (r_end - r0 < cr) ? r_end - r0 : cr;
@@ -290,8 +313,8 @@ int trace_range(rt_ctx *c, const float *rho, const float *td, float *q, float *a
         args.nrays = (unsigned)nr_c;
         const long long nt = (nr_c * (c->nr + 1) + T - 1) / T;
         unsigned grid = 0;
-        cudaError_t e = c->n_t > 0 ? rt::launch_tdep(s, args, c->kt2, c->tg32, c->n_t, stream, &grid)
-                                   : rt::launch_trace(c->precision, s, args, (unsigned)nt, stream, &grid);
+        cudaError_t e = (c->n_t > 0 && !tw) ? rt::launch_tdep(s, args, c->kt2, c->tg32, c->n_t, stream, &grid)
+                                            : rt::launch_trace(c->precision, s, args, (unsigned)nt, stream, &grid);
         if (e != cudaSuccess) return cuda_fail(c, "trace kernel launch", e);
         *npart += grid;
     }
@@ -305,7 +328,8 @@ long long range_tiles(const rt_ctx *c, Shape s, long long r_begin, long long r_e
     long long tiles = 0;
     for (long long r0 = r_begin; r0 < r_end; r0 += cr) {
         const long long nr_c = (r_end - r0 < cr) ? r_end - r0 : cr;
-        tiles += (s.kind == rt::kKindRay) ? (nr_c + s.warps - 1) / s.warps : (nr_c * (c->nr + 1) + T - 1) / T;
+        tiles += (s.kind == rt::kKindRay) ? (nr_c * rt::ray_warps_per_ray(s.cells_per_lane, c->nr) + s.warps - 1) / s.warps
+                                          : (nr_c * (c->nr + 1) + T - 1) / T;
     }
     return tiles;
 }
@@ -353,7 +377,7 @@ void free_all(rt_ctx *c)
     void *ptrs[] = {c->r_if, c->theta_if, c->phi_if, c->rtab, c->rtab64, c->domega, c->domega32, c->nu_mid,
                     c->kappa, c->f_bin, c->nu_tab, c->kap, c->nu64, c->sc, c->partials, c->bad,
                     c->energy_d, c->h_rho, c->h_t, c->h_q, c->h_a, c->temp_lkp, c->kappa_t_d,
-                    c->tg32, c->kt2, c->order_d};
+                    c->tg32, c->kt2, c->order_d, c->tw_t_d, c->tw_b_d};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->energy_h) cudaFreeHost(c->energy_h);
@@ -539,6 +563,7 @@ int rt_set_opacity_table(rt_ctx *ctx, int n_nu, const double *nu_mid, const doub
     ctx->t_sub = t_sub;
     ctx->kappa_bf16 = kappa_bf16 ? 1 : 0;
     ctx->n_t = 0;
+    ctx->tw_sep = false;
     ctx->tgrid_h.clear();
     ctx->kappa_t_h.clear();
     ctx->nu_h.assign(nu_mid, nu_mid + n_nu);
@@ -586,6 +611,45 @@ int rt_set_opacity_table_t(rt_ctx *ctx, int n_nu, const double *nu_mid, int n_t,
     for (int i = 0; i < n_nu; ++i)
         for (int j = 0; j < n_t; ++j) kmax[i] = std::max(kmax[i], kappa_t[(size_t)i * n_t + j]);
     std::vector<float> tg(t_grid, t_grid + n_t);
+    // Does the table separate, kappa_i(T_j) = kmax_i b_j for every entry (to 1e-12)? Then
+    // every bin's optical depth is kmax_i times one column weighted by b(T), linear in T
+    // between the grid points like the rows themselves.
+    int iref = 0;
+    for (int i = 1; i < n_nu; ++i)
+        if (kmax[i] > kmax[iref]) iref = i;
+    std::vector<double> bj(n_t, 0.0);
+    if (kmax[iref] > 0.0)
+        for (int j = 0; j < n_t; ++j) bj[j] = kappa_t[(size_t)iref * n_t + j] / kmax[iref];
+    bool sep = true;
+    for (int i = 0; i < n_nu && sep; ++i)
+        for (int j = 0; j < n_t; ++j) {
+            const double have = kappa_t[(size_t)i * n_t + j], want = kmax[i] * bj[j];
+            if (std::fabs(have - want) > 1e-12 * std::max(std::fabs(have), std::fabs(want))) {
+                sep = false;
+                break;
+            }
+        }
+    if (sep) {
+        float tw_t[rt::kMaxTdepPoints];
+        float2 tw_b[rt::kMaxTdepPoints];
+        for (int j = 0; j < rt::kMaxTdepPoints; ++j) {
+            const int jj = j < n_t ? j : n_t - 1;
+            tw_t[j] = j < n_t ? (float)t_grid[j] : INFINITY;
+            const double slope = jj + 1 < n_t ? (bj[jj + 1] - bj[jj]) / (t_grid[jj + 1] - t_grid[jj]) : 0.0;
+            tw_b[j] = make_float2((float)bj[jj], (float)slope);
+        }
+        if (!ctx->tw_t_d) {
+            bool ok = dalloc(&ctx->tw_t_d, rt::kMaxTdepPoints) == cudaSuccess &&
+                      dalloc(&ctx->tw_b_d, rt::kMaxTdepPoints) == cudaSuccess;
+            if (!ok) {
+                cudaGetLastError();
+                return fail(ctx, RT_ERR_NO_MEMORY, "cannot allocate the column-weight table");
+            }
+        }
+        RT_CK(ctx, cudaMemcpyAsync(ctx->tw_t_d, tw_t, sizeof(tw_t), cudaMemcpyHostToDevice, ctx->stream));
+        RT_CK(ctx, cudaMemcpyAsync(ctx->tw_b_d, tw_b, sizeof(tw_b), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    ctx->tw_sep = sep;
     RT_CK(ctx, cudaMemcpyAsync(ctx->nu_mid, nu_mid, sizeof(double) * n_nu, cudaMemcpyHostToDevice, ctx->stream));
     RT_CK(ctx, cudaMemcpyAsync(ctx->kappa, kmax.data(), sizeof(double) * n_nu, cudaMemcpyHostToDevice, ctx->stream));
     RT_CK(ctx, cudaMemcpyAsync(ctx->kappa_t_d, kappa_t, sizeof(double) * n_nu * n_t, cudaMemcpyHostToDevice,
@@ -755,6 +819,14 @@ int rt_energy_last(rt_ctx *ctx, rt_energy *out)
     return read_energy(ctx, out);
 }
 
+int rt_opacity_table_kind(const rt_ctx *ctx, int *kind)
+{
+    if (!ctx || !kind) return RT_ERR_INVALID_ARG;
+    if (!ctx->configured) return RT_ERR_NOT_CONFIGURED;
+    *kind = table_kind(ctx);
+    return RT_OK;
+}
+
 int rt_energy_reduce(rt_ctx *ctx)
 {
     if (!ctx) return RT_ERR_INVALID_ARG;
@@ -853,7 +925,7 @@ int rt_autotune(rt_ctx *ctx, const float *rho, const float *t_dust, float *q_abs
     ctx->shape_forced = true;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[std::make_tuple(ctx->precision, ctx->nr, ctx->nrays, ctx->sc_h.nnu_pad)] = best;
+        g_tune_cache[std::make_tuple(ctx->precision, ctx->nr, ctx->nrays, ctx->sc_h.nnu_pad, table_kind(ctx))] = best;
     }
     return RT_OK;
 }

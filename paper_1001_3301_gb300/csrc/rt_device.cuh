@@ -158,6 +158,14 @@ __host__ __device__ constexpr double taylor_coeff(int k)
     return c;
 }
 
+// 1 / k! (a compile-time constant for constant k)
+__host__ __device__ constexpr double inv_factorial(int k)
+{
+    double f = 1.0;
+    for (int i = 2; i <= k; ++i) f *= i;
+    return 1.0 / f;
+}
+
 // Largest x = kappa dN for which n terms keep the first omitted term x^n/(n+1)!
 // below 5e-7 of the value; the last class ends where the MUFU form takes over.
 constexpr double kTrunc = 5e-7;
@@ -329,6 +337,27 @@ __device__ __forceinline__ int thin_count(const float4 *s_nu, int n_active, int 
         bt += __popc(__ballot_sync(0xffffffffu, ak * nmax <= kThinY));
     }
     return bt;
+}
+
+// thin_count for two columns at once (one pass over the bins)
+__device__ __forceinline__ void thin_counts(const float4 *s_nu, int n_active, int lane, float n1, float n2, int &b1,
+                                            int &b2)
+{
+    b1 = b2 = 0;
+    for (int c0 = 0; c0 < n_active; c0 += 32) {
+        const int i = c0 + lane;
+        const float ak = (i < n_active) ? -s_nu[i].x : INFINITY;
+        b1 += __popc(__ballot_sync(0xffffffffu, ak * n1 <= kThinY));
+        b2 += __popc(__ballot_sync(0xffffffffu, ak * n2 <= kThinY));
+    }
+}
+
+// the larger of a and b, NaN if either is NaN (PTX max.NaN)
+__device__ __forceinline__ float max_nan(float a, float b)
+{
+    float r;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
 }
 
 // The bins i < b of a thin prefix (Eqs. 17, 19 and 31-32 summed over them) as one

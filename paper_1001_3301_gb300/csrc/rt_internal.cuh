@@ -37,13 +37,15 @@ struct alignas(8) NuEntry {
 // it: row b = 1..n_active holds s_b = kappa_{b-1} (column units) and then
 // C_k(b) = (-1)^{k+1} / k! sum_{i<b} w_i (kappa_i / s_b)^k for k = 1..kThinTerms,
 // then S_0(b) = sum_{i<b} w_i; w_i = F_i / F_max, bins in the kappa-sorted order.
-// With x = kThinX the first omitted term is below x^kThinTerms / kThinTerms! = 1e-7
-// of the leading one.
-constexpr int kThinTerms = 8;
+// With x = kThinX the first omitted term is below x^kThinTerms / kThinTerms! =
+// 2.8e-7 of the leading one; the alternating sum loses at most a factor
+// e^{2 kThinX} = 7.4 of FP32 precision.
+constexpr int kThinTerms = 10;
 constexpr int kThinStride = 12;                                       // floats per row (>= kThinTerms + 2)
 constexpr int kKapTable = RT_MAX_NU + kNuPad;                         // floats of the kappa table
 constexpr int kKapBuffer = kKapTable + (RT_MAX_NU + 1) * kThinStride;  // with the series rows
-constexpr float kThinX = 0.5f;
+constexpr float kThinX = 1.0f;
+static_assert(kThinStride >= kThinTerms + 2, "a series row holds s, C_1..C_K and S_0");
 
 // Scalars of one configured grid, resident in device memory.
 struct DevScalars {
@@ -81,6 +83,9 @@ struct alignas(32) RadRow64 {
     double x, y, z, w;
 };
 
+// Most temperature points of a temperature-dependent opacity table
+constexpr int kMaxTdepPoints = 32;
+
 // Largest flattened length one launch of the tracer covers; longer grids are
 // split into ray chunks by the host.
 constexpr long long kMaxLaunchCells = (1LL << 31) - (1LL << 16);
@@ -109,6 +114,13 @@ struct TraceArgs {
     int nnu_pad;
     int n_active;             // bins with kappa > 0, sorted by kappa ascending
     float t_sub;
+    // A temperature-dependent table that separates, kappa_i(T) = kappa_i b(T) (kappa_i
+    // the bin's largest tabulated value): the column of a cell is weighted by b(T),
+    // linear between the points of the temperature grid and held beyond its ends.
+    // n_tw = 0: no weight (a table of kappa(nu) only).
+    const float *tw_t;        // [kMaxTdepPoints] grid (K), padded with +Inf
+    const float2 *tw_b;       // [kMaxTdepPoints] (b_j, (b_{j+1} - b_j) / (T_{j+1} - T_j)); slope 0 from the last point
+    int n_tw;
 };
 
 // Launch shapes of the fused tracer that are compiled in.
@@ -124,10 +136,22 @@ struct Shape {
 // Lanes per ray of the warp-per-ray kernel with C cells per lane: the fewest of 8,
 // 16 and 32 that hold the ray (a warp then traces 32 / G rays at a time).
 inline int ray_lanes(int c, int nr) { return 8 * c >= nr ? 8 : (16 * c >= nr ? 16 : 32); }
+// Warps per ray of the warp-per-ray kernel: 1 where 32 C cells hold the ray, 2 where
+// 64 C do (for C <= 8: two warps of a CTA share a ray, exchanging their column sums
+// in shared memory), 0 where the kernel does not apply.
+inline int ray_warps_per_ray(int c, int nr) { return 32 * c >= nr ? 1 : ((c <= 8 && 64 * c >= nr) ? 2 : 0); }
+// Cells of one ray that the lanes tracing it hold (G C, or 32 P C with P warps).
+inline int ray_cells_held(int c, int nr)
+{
+    const int p = ray_warps_per_ray(c, nr);
+    return p > 1 ? 32 * p * c : ray_lanes(c, nr) * c;
+}
 
 // Host-side launchers (rt_trace.cu, rt_ray.cu)
 int trace_shapes(int precision, Shape *out, int max_out);      // tile kernel
 int ray_shapes(int precision, int nr, Shape *out, int max_out);  // ray kernel, 32 C >= nr
+// ray-kernel shapes compiled with the column weight of a separable kappa(nu, T) table
+int ray_shapes_tw(int precision, int nr, Shape *out, int max_out);
 long long trace_tile_cells(Shape s);
 cudaError_t launch_ray_shape(int precision, Shape s, const TraceArgs &args, cudaStream_t stream,
                              unsigned *grid_out, unsigned max_grid = 0);
@@ -138,7 +162,6 @@ cudaError_t launch_trace(int precision, Shape s, const TraceArgs &args, unsigned
                          cudaStream_t stream, unsigned *grid_out, unsigned max_grid = 0);
 
 // Tracer with temperature-dependent opacity tables (rt_tdep.cu)
-constexpr int kMaxTdepPoints = 32;
 int tdep_shapes(int nr, Shape *out, int max_out);
 cudaError_t launch_tdep(Shape s, const TraceArgs &args, const float2 *kt2, const float *tg, int n_t,
                         cudaStream_t stream, unsigned *grid_out);

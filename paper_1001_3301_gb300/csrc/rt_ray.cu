@@ -1,32 +1,35 @@
 // Warp-per-ray form of the frequency-dependent tracer (Kuiper et al. 2010,
-// Sect. 2.2-2.3, 3.3.4), for grids whose rays fill most of 32 * C cells: the body
-// of rt_ray.cuh over all rays of one grid, then the CTA's energy partial.
-// Persistent: the grid holds (SMs x resident CTAs) CTAs that stride over the rays.
+// Sect. 2.2-2.3, 3.3.4), for grids whose rays fill most of 32 P C cells (P = 1 or 2
+// warps per ray): the body of rt_ray.cuh over all rays of one grid, then the CTA's
+// energy partial. Persistent: the grid holds (SMs x resident CTAs) CTAs that stride
+// over the rays.
 #include "rt_ray.cuh"
 
 namespace rt {
 namespace {
 
-template <int C, int W, int MODE, int MINB, int G>
+template <int C, int W, int MODE, int MINB, int G, int P, bool TW>
 __global__ void __launch_bounds__(W * 32, MINB) k_ray(const TraceArgs p)
 {
     using ESum = KahanSum;
     constexpr int R = 32 / G;  // rays per warp
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    __shared__ RayShared<C> rs;
+    __shared__ RayShared<C, P> rs;
     extern __shared__ __align__(16) unsigned char smem[];
     float *s_kap = reinterpret_cast<float *>(smem);
     float4 *s_nu = reinterpret_cast<float4 *>(s_kap + p.nnu_pad);
     float4 *s_mom = s_nu + p.nnu_pad;
     __shared__ ESum s_red[W][2];
-    ray_tables<C, W>(p, G, rs, s_kap, s_nu, s_mom);
+    ray_tables<C, W, P>(p, G, rs, s_kap, s_nu, s_mom);
     __syncthreads();
 
     ESum eabs, eesc;
     eabs.zero();
     eesc.zero();
     const unsigned slots = (p.nrays + R - 1) / R;
-    ray_slots<C, W, MODE, G>(p, blockIdx.x * W + warp, slots, gridDim.x * W, rs, s_kap, s_nu, s_mom, eabs, eesc);
+    constexpr int WG = W / P;  // ray groups per CTA
+    ray_slots<C, W, MODE, G, P, TW>(p, blockIdx.x * WG + warp / P, slots, gridDim.x * WG, rs, s_kap, s_nu, s_mom,
+                                    eabs, eesc);
 
     for (int o = 16; o > 0; o >>= 1) {
         eabs.add(eabs.shfl_xor(o));
@@ -41,12 +44,12 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray(const TraceArgs p)
     }
 }
 
-template <int C, int W, int MODE, int MINB, int G>
+template <int C, int W, int MODE, int MINB, int G, int P, bool TW>
 cudaError_t launch_ray_g(const TraceArgs &a, cudaStream_t stream, unsigned *grid_out, unsigned max_grid)
 {
     constexpr int R = 32 / G;
     const size_t smem = ray_bin_smem(a.nnu_pad) + 16;
-    auto kern = k_ray<C, W, MODE, MINB, G>;
+    auto kern = k_ray<C, W, MODE, MINB, G, P, TW>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -58,7 +61,7 @@ cudaError_t launch_ray_g(const TraceArgs &a, cudaStream_t stream, unsigned *grid
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     unsigned grid = (unsigned)nsm * (unsigned)per_sm;
-    const unsigned need = (a.nrays + W * R - 1) / (W * R);
+    const unsigned need = (a.nrays * P + W * R - 1) / (W * R);
     if (grid > need) grid = need;
     if (max_grid > 0 && grid > max_grid) grid = max_grid;
     if (grid < 1) grid = 1;
@@ -67,13 +70,19 @@ cudaError_t launch_ray_g(const TraceArgs &a, cudaStream_t stream, unsigned *grid
     return cudaGetLastError();
 }
 
-// The fewest lanes per ray that still hold the ray: 8, 16 or 32 (G C >= nr).
-template <int C, int W, int MODE, int MINB>
+// The fewest lanes per ray that still hold the ray: 8, 16 or 32 (G C >= nr), else two
+// warps per ray (ray_warps_per_ray).
+template <int C, int W, int MODE, int MINB, bool TW = false>
 cudaError_t launch_ray(const TraceArgs &a, unsigned, cudaStream_t stream, unsigned *grid_out, unsigned max_grid)
 {
-    if (8 * C >= a.nr) return launch_ray_g<C, W, MODE, MINB, 8>(a, stream, grid_out, max_grid);
-    if (16 * C >= a.nr) return launch_ray_g<C, W, MODE, MINB, 16>(a, stream, grid_out, max_grid);
-    return launch_ray_g<C, W, MODE, MINB, 32>(a, stream, grid_out, max_grid);
+    if ((a.n_tw > 0) != TW) return cudaErrorInvalidValue;
+    if (8 * C >= a.nr) return launch_ray_g<C, W, MODE, MINB, 8, 1, TW>(a, stream, grid_out, max_grid);
+    if (16 * C >= a.nr) return launch_ray_g<C, W, MODE, MINB, 16, 1, TW>(a, stream, grid_out, max_grid);
+    if (32 * C >= a.nr) return launch_ray_g<C, W, MODE, MINB, 32, 1, TW>(a, stream, grid_out, max_grid);
+    if constexpr (C <= 8) {
+        if (64 * C >= a.nr) return launch_ray_g<C, W, MODE, MINB, 32, 2, TW>(a, stream, grid_out, max_grid);
+    }
+    return cudaErrorInvalidValue;
 }
 
 struct RayEntry {
@@ -88,6 +97,13 @@ const RayEntry kRayShapes[] = {
     RT_RAY(RT_FP32_KAHAN, 16, 4, 3), RT_RAY(RT_FP32_KAHAN, 16, 4, 4), RT_RAY(RT_FP32_PLAIN, 4, 4, 8),
     RT_RAY(RT_FP32_PLAIN, 8, 4, 6),  RT_RAY(RT_FP32_PLAIN, 16, 4, 4),
 };
+// shapes compiled with the column weight of a separable kappa(nu, T) table
+#define RT_RAYW(P, C, W, MB) {P, C, W, MB, &launch_ray<C, W, P, MB, true>}
+const RayEntry kRayShapesTW[] = {
+    RT_RAYW(RT_FP32_KAHAN, 4, 4, 8),  RT_RAYW(RT_FP32_KAHAN, 8, 4, 6), RT_RAYW(RT_FP32_KAHAN, 16, 4, 4),
+    RT_RAYW(RT_FP32_PLAIN, 8, 4, 6),  RT_RAYW(RT_FP32_PLAIN, 16, 4, 4),
+};
+#undef RT_RAYW
 #undef RT_RAY
 
 }  // namespace
@@ -96,7 +112,16 @@ int ray_shapes(int precision, int nr, Shape *out, int max_out)
 {
     int n = 0;
     for (const RayEntry &s : kRayShapes)
-        if (s.precision == precision && 32 * s.c >= nr && n < max_out)
+        if (s.precision == precision && ray_warps_per_ray(s.c, nr) > 0 && n < max_out)
+            out[n++] = Shape{kKindRay, s.c, s.w, s.minb};
+    return n;
+}
+
+int ray_shapes_tw(int precision, int nr, Shape *out, int max_out)
+{
+    int n = 0;
+    for (const RayEntry &s : kRayShapesTW)
+        if (s.precision == precision && ray_warps_per_ray(s.c, nr) > 0 && n < max_out)
             out[n++] = Shape{kKindRay, s.c, s.w, s.minb};
     return n;
 }
@@ -104,10 +129,15 @@ int ray_shapes(int precision, int nr, Shape *out, int max_out)
 cudaError_t launch_ray_shape(int precision, Shape s, const TraceArgs &args, cudaStream_t stream,
                              unsigned *grid_out, unsigned max_grid)
 {
-    for (const RayEntry &e : kRayShapes)
+    const bool tw = args.n_tw > 0;
+    const RayEntry *tab = tw ? kRayShapesTW : kRayShapes;
+    const int ntab = tw ? (int)(sizeof(kRayShapesTW) / sizeof(RayEntry)) : (int)(sizeof(kRayShapes) / sizeof(RayEntry));
+    for (int k = 0; k < ntab; ++k) {
+        const RayEntry &e = tab[k];
         if (e.precision == precision && e.c == s.cells_per_lane && e.w == s.warps &&
-            (s.min_blocks == 0 || e.minb == s.min_blocks) && 32 * e.c >= args.nr)
+            (s.min_blocks == 0 || e.minb == s.min_blocks) && ray_warps_per_ray(e.c, args.nr) > 0)
             return e.fn(args, 0, stream, grid_out, max_grid);
+    }
     return cudaErrorInvalidValue;
 }
 

@@ -3,8 +3,9 @@
 // multi-grid batch (rt_batch.cu).
 //
 // A segment of G lanes traces one radial ray (a warp holds 32 / G rays at a time,
-// so rays shorter than 32 C cells keep every lane busy); lane l of a segment owns
-// the cells [l C, (l+1) C) of its ray, so the radial constants of a lane never
+// so rays shorter than 32 C cells keep every lane busy), or P = 2 warps of a CTA
+// trace one ray together (64 C cells: fewer cells per lane, fewer registers, more
+// warps per SM); lane l of a segment owns the cells [l C, (l+1) C) of its ray, so the radial constants of a lane never
 // change and the ray's fields are read straight from HBM in 16-byte vectors (no
 // staging, no block barrier in the ray loop). While it traces one warp-slot, the
 // warp asks L2 for the fields of its next one (a bulk prefetch: nothing to wait
@@ -37,21 +38,21 @@ namespace {
 // consecutive cells (lane l's cell j is radial index (l mod G) C + j), so that the
 // lanes of a warp read consecutive words and every read yields the packed pair the
 // f32x2 arithmetic works on: dr as (dr_j, dr_j+1), (Gq_j, Gq_j+1, Ga0_j, Ga0_j+1).
-template <int C>
+template <int C, int P = 1>
 struct RayShared {
-    float2 dr[C / 2][32];
-    float4 gqa[C / 2][32];
+    float2 dr[P][C / 2][32];
+    float4 gqa[P][C / 2][32];
 };
 
 // dynamic shared memory of the bin tables: kappa, (nk, nk, lf, lf) and the series
 // moments' constants (two float4 per bin)
 __host__ __device__ constexpr size_t ray_bin_smem(int nnu_pad) { return (size_t)nnu_pad * (4 + 16 + 32); }
 
-// The tables of grid p for G lanes per ray (call from every thread of the CTA,
-// then __syncthreads()).
-template <int C, int W>
-__device__ __forceinline__ void ray_tables(const TraceArgs &p, int G, RayShared<C> &rs, float *s_kap, float4 *s_nu,
-                                           float4 *s_mom)
+// The tables of grid p for G lanes per ray, or P warps per ray (call from every
+// thread of the CTA, then __syncthreads()).
+template <int C, int W, int P = 1>
+__device__ __forceinline__ void ray_tables(const TraceArgs &p, int G, RayShared<C, P> &rs, float *s_kap,
+                                           float4 *s_nu, float4 *s_mom)
 {
     const int tid = threadIdx.x;
     for (int i = tid; i < p.nnu_pad; i += W * 32) {
@@ -60,12 +61,13 @@ __device__ __forceinline__ void ray_tables(const TraceArgs &p, int G, RayShared<
         s_nu[i] = make_float4(e.nk, e.nk, e.lf, e.lf);
         fill_moments(s_mom, i, e.nk);
     }
-    for (int i = tid; i < 16 * C; i += W * 32) {
-        const int l = i / (C / 2), m = i % (C / 2), k = (l % G) * C + 2 * m;
+    for (int i = tid; i < P * 16 * C; i += W * 32) {
+        const int h = i / (16 * C), l = (i / (C / 2)) % 32, m = i % (C / 2);
+        const int k = (P > 1 ? h * 32 + l : l % G) * C + 2 * m;
         const float4 g0 = (k < p.nr) ? __ldg(&p.rtab[k]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         const float4 g1 = (k + 1 < p.nr) ? __ldg(&p.rtab[k + 1]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        rs.dr[m][l] = make_float2(g0.x, g1.x);
-        rs.gqa[m][l] = make_float4(g0.y, g1.y, g0.z, g1.z);
+        rs.dr[h][m][l] = make_float2(g0.x, g1.x);
+        rs.gqa[h][m][l] = make_float4(g0.y, g1.y, g0.z, g1.z);
     }
 }
 
@@ -172,33 +174,72 @@ __device__ __forceinline__ float lane_coefficients(const float *thin_row, int bt
                 m[k] = __fadd2_rn(m[k], pw);
             }
         }
-        float fact = 1.0f;
 #pragma unroll
         for (int k = 1; k <= K; ++k) {
-            fact *= (float)k;
-            const float t = (m[k].x + m[k].y) / fact;
+            const float t = (m[k].x + m[k].y) * (float)inv_factorial(k);
             F[k] += (k & 1) ? t : -t;
         }
     }
     return s2;
 }
 
+// Column weight b(T) of a separable kappa(nu, T) table (TraceArgs::tw_t, tw_b): T
+// clamped to the grid, its interval found by a five-step binary search over the
+// 32-entry grid (padded with +Inf), then linear in T. t_lo, t_hi: the grid's ends.
+__device__ __forceinline__ float tw_weight(const float *tg, const float2 *tb, float t_lo, float t_hi, float t)
+{
+    t = fminf(fmaxf(t, t_lo), t_hi);
+    int j = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1)
+        if (tg[j + step] <= t) j += step;
+    const float2 e = tb[j];
+    return fmaf(t - tg[j], e.y, e.x);
+}
+
+// Bar.sync on a named barrier of n threads (the P warps of one group).
+__device__ __forceinline__ void group_sync(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
 // Warp-slots wr = wr_begin, wr_begin + step, ... (< wr_end) of grid p, R = 32 / G rays
-// each; the lanes' energy sums are added to eabs / eesc.
-template <int C, int W, int MODE, int G>
+// each (or, with P > 1, one ray per group of P consecutive warps, which all walk the
+// same slots); the lanes' energy sums are added to eabs / eesc. TW: the table is a
+// separable kappa(nu, T) (TraceArgs::n_tw > 0) and each cell's column carries the
+// weight b(T).
+template <int C, int W, int MODE, int G, int P = 1, bool TW = false>
 __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin, unsigned wr_end, unsigned step,
-                                          const RayShared<C> &rs, const float *s_kap, const float4 *s_nu,
+                                          const RayShared<C, P> &rs, const float *s_kap, const float4 *s_nu,
                                           const float4 *s_mom, KahanSum &eabs, KahanSum &eesc)
 {
     static_assert(MODE != RT_FP64, "the FP64 mode uses the tile kernel");
     static_assert(C % 2 == 0, "cells per lane must be even");
     static_assert(G == 8 || G == 16 || G == 32, "lanes per ray");
+    static_assert(P == 1 || (G == 32 && W % P == 0 && P == 2), "warps per ray");
     using Sum = ColSum<MODE>;
     constexpr int V = (C % 4 == 0) ? 4 : 2;  // vector width of the field loads
     constexpr int R = 32 / G;                // rays per warp
 
     const int lane = threadIdx.x & 31;
-    const int seg = lane / G, ll = lane % G;  // ray slot of the lane, lane within the ray
+    const int half = P > 1 ? (int)(threadIdx.x >> 5) % P : 0;  // warp within its group
+    const int group = (int)(threadIdx.x >> 5) / P;
+    // lane totals of the group's warps, double buffered by slot parity
+    __shared__ Sum s_grp[P > 1 ? W / P : 1][2][P];
+    // separable table: each warp's copy of the weight table, and its cells' weights
+    __shared__ float s_twt[TW ? W : 1][kMaxTdepPoints];
+    __shared__ float2 s_twb[TW ? W : 1][kMaxTdepPoints];
+    __shared__ float2 s_bw[TW ? W : 1][C / 2][32];
+    const int wid = TW ? (int)(threadIdx.x >> 5) : 0;
+    float tw_lo = 0.0f, tw_hi = 0.0f;
+    if constexpr (TW) {
+        s_twt[wid][lane] = __ldg(p.tw_t + lane);
+        s_twb[wid][lane] = __ldg(p.tw_b + lane);
+        tw_lo = __ldg(p.tw_t);
+        tw_hi = __ldg(p.tw_t + p.n_tw - 1);
+        __syncwarp();
+    }
+    const int seg = lane / G, ll = half * 32 + lane % G;  // ray slot of the lane, lane within the ray
     const int nr = p.nr;
     const int c0 = ll * C;
     const int nv_ray = nr - c0 < 0 ? 0 : (nr - c0 > C ? C : nr - c0);  // valid cells of this lane
@@ -245,8 +286,9 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
                                          j + 1 < nv ? __ldg(p.tdust + base + j + 1) : INFINITY);
             }
         }
-        // the fields of this warp's next slot, on their way to L2
-        if (pf && lane == 0 && wr + step < wr_end) {
+        // the fields of this warp's next slot, on their way to L2 (with P > 1 the group's
+        // first warp asks for the whole ray)
+        if (pf && lane == 0 && half == 0 && wr + step < wr_end) {
             const unsigned r0 = (wr + step) * R;
             if (r0 < p.nrays) {
                 const unsigned nrs = p.nrays - r0 < (unsigned)R ? p.nrays - r0 : (unsigned)R;
@@ -261,40 +303,75 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
         // (a cell without dust gets the column -0, one with dust but no density +0: the
         // sign tells the two apart where the force needs it, and -0 adds nothing)
         float2 D[C / 2], U[C / 2], acc[C / 2];
-        unsigned rho_bits = 0u;
-        bool td_nan = false, zc = false;
+        unsigned rho_bits = 0u, d_min = 0xffffffffu;
+        float td_max = 0.0f;  // NaN as soon as one t_dust is NaN
         Sum lsum;
         lsum.zero();
 #pragma unroll
         for (int m = 0; m < C / 2; ++m) {
-            const float2 dr = rs.dr[m][lane];
+            const float2 dr = rs.dr[half][m][lane];
             const bool d0 = td2[m].x <= p.t_sub, d1 = td2[m].y <= p.t_sub;
             // rho must be finite and >= 0 (-0 counts as 0): the bits of rho + 0 stay
             // below those of +Inf; t_dust must not be NaN
             const float2 rz = __fadd2_rn(rho2[m], f2(0.0f));
             rho_bits = max(rho_bits, max(__float_as_uint(rz.x), __float_as_uint(rz.y)));
-            td_nan |= (td2[m].x != td2[m].x) || (td2[m].y != td2[m].y);
-            D[m] = __fmul2_rn(rz, make_float2(d0 ? dr.x : -0.0f, d1 ? dr.y : -0.0f));
-            zc |= (__float_as_uint(D[m].x) == 0u) || (__float_as_uint(D[m].y) == 0u);
+            td_max = max_nan(td_max, max_nan(td2[m].x, td2[m].y));
+            float2 mw = make_float2(d0 ? dr.x : -0.0f, d1 ? dr.y : -0.0f);
+            if constexpr (TW) {
+                // kappa_i(T) = kappa_i b(T): the weight enters the column (0 without dust)
+                const float2 bw = make_float2(d0 ? tw_weight(s_twt[wid], s_twb[wid], tw_lo, tw_hi, td2[m].x) : 0.0f,
+                                              d1 ? tw_weight(s_twt[wid], s_twb[wid], tw_lo, tw_hi, td2[m].y) : 0.0f);
+                s_bw[wid][m][lane] = bw;
+                mw = make_float2(d0 ? mw.x * bw.x : -0.0f, d1 ? mw.y * bw.y : -0.0f);
+            }
+            D[m] = __fmul2_rn(rz, mw);
+            // +0 (dust, no column) has the smallest bits of all columns a valid input gives
+            d_min = min(d_min, min(__float_as_uint(D[m].x), __float_as_uint(D[m].y)));
             acc[m] = f2(0.0f);
             U[m].x = lsum.value();
             lsum.add(D[m].x);
             U[m].y = lsum.value();
             lsum.add(D[m].y);
         }
-        if (__any_sync(0xffffffffu, rho_bits >= 0x7f800000u || td_nan) && lane == 0) atomicMax(p.bad_input, p.seq);
+        const bool zc = d_min == 0u;
+        if (__any_sync(0xffffffffu, rho_bits >= 0x7f800000u || td_max != td_max) && lane == 0)
+            atomicMax(p.bad_input, p.seq);
 
         // column in front of each lane: compensated scan of the lane sums within the segment
         Sum inc = lsum;
 #pragma unroll
         for (int d = 1; d < G; d <<= 1) {
             const Sum o = inc.shfl_up(d, G);
-            if (ll >= d) inc.add(o);
+            if ((ll % G) >= d) inc.add(o);
         }
         Sum pre = inc.shfl_up(1, G);
-        if (ll == 0) pre.zero();
-        const float n0 = pre.value();
-        const float ntot = __shfl_sync(0xffffffffu, inc.value(), G - 1, G);
+        if ((ll % G) == 0) pre.zero();
+        float n0, ntot;
+        if constexpr (P > 1) {
+            // the group's warps exchange their totals: the warps before this one give its
+            // offset, all of them the ray's total
+            const int par = (int)(((wr - wr_begin) / step) & 1u);
+            Sum wt;
+            wt.hi = __shfl_sync(0xffffffffu, inc.hi, 31);
+            if constexpr (MODE == RT_FP32_KAHAN) wt.lo = __shfl_sync(0xffffffffu, inc.lo, 31);
+            if (lane == 0) s_grp[group][par][half] = wt;
+            group_sync(1 + group, 32 * P);
+            Sum off, tot;
+            off.zero();
+            tot.zero();
+#pragma unroll
+            for (int h = 0; h < P; ++h) {
+                const Sum t = s_grp[group][par][h];
+                if (h < half) off.add(t);
+                tot.add(t);
+            }
+            off.add(pre);
+            n0 = off.value();
+            ntot = tot.value();
+        } else {
+            n0 = pre.value();
+            ntot = __shfl_sync(0xffffffffu, inc.value(), G - 1, G);
+        }
 
         // bins thin along all the warp's rays (bt of them) and, after those, bins thin
         // within every lane's cells (up to bt2): one series per lane; the rest bin by bin
@@ -302,13 +379,10 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
         for (int o = G; o < 32; o <<= 1) nmax = fmaxf(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
         float cmax = lsum.value();
         for (int o = 16; o > 0; o >>= 1) cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
-        const int bt = thin_count(s_nu, na, lane, nmax);
-        int bt2 = bt;
-        if (bt < na) {
-            const int bc = thin_count(s_nu, na, lane, cmax);
-            // with no row to shift, a few tier bins do not pay for the series
-            if (bc > bt && (bt > 0 || bc >= 4)) bt2 = bc;
-        }
+        int bt, bc;
+        thin_counts(s_nu, na, lane, nmax, cmax, bt, bc);
+        // with no row to shift, a few tier bins do not pay for the series
+        const int bt2 = (bc > bt && (bt > 0 || bc >= 4)) ? bc : bt;
         const float *thin_row = p.kap + kKapTable + bt * kThinStride;
         if (bt2 > 0) {
             float F[kThinTerms + 1];
@@ -338,14 +412,15 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
             bin_range<7, C>(tb, na, s_nu, n0, U, D, acc);
         }
 
-        // escaping power of the ray, the lanes of its segment sharing the bins
+        // escaping power of the ray, the lanes of its segment (all P warps of a group)
+        // sharing the bins
         const float w = live ? __ldg(p.domega32 + ray) : 0.0f;
         {
             float s = 0.0f;
-            for (int i = bt + ll; i < na; i += G) s += ex2_approx(fmaf(s_nu[i].x, ntot, s_nu[i].z));
+            for (int i = bt + ll; i < na; i += G * P) s += ex2_approx(fmaf(s_nu[i].x, ntot, s_nu[i].z));
             for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (ll == 0) {
-                if (bt > 0) s += thin_escape(thin_row, ntot);
+            if ((ll % G) == 0) {
+                if (bt > 0 && half == 0) s += thin_escape(thin_row, ntot);
                 eesc.add(s * w);
             }
         }
@@ -356,11 +431,12 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
         float2 qv[C / 2];
 #pragma unroll
         for (int m = 0; m < C / 2; ++m) {
-            const float4 g = rs.gqa[m][lane];
+            const float4 g = rs.gqa[half][m][lane];
             qv[m] = __fmul2_rn(make_float2(g.x, g.y), acc[m]);
             lane_abs2 = __fadd2_rn(lane_abs2, acc[m]);
             const float2 dd = make_float2(fmaxf(D[m].x, tiny2.x), fmaxf(D[m].y, tiny2.y));
             acc[m] = __fmul2_rn(make_float2(g.z, g.w), __fmul2_rn(acc[m], make_float2(rcp_approx(dd.x), rcp_approx(dd.y))));
+            if constexpr (TW) acc[m] = __fmul2_rn(acc[m], s_bw[wid][m][lane]);  // per mass: dN b / (rho dr)
         }
         // cells with dust but no column: the rho -> 0 force limit Ga0 sum_i kappa_i g_i
         if (__any_sync(0xffffffffu, zc)) {
@@ -374,7 +450,11 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
                     for (int i = 0; i < na; ++i)
                         s = fmaf(s_kap[i], ex2_approx(fmaf(s_nu[i].x, uj, fmaf(s_nu[i].x, n0, s_nu[i].z))), s);
                     if (zj) {
-                        const float4 g = rs.gqa[j / 2][lane];
+                        const float4 g = rs.gqa[half][j / 2][lane];
+                        if constexpr (TW) {  // kappa_i(T) = kappa_i b(T)
+                            const float2 bw = s_bw[wid][j / 2][lane];
+                            s *= (j & 1) ? bw.y : bw.x;
+                        }
                         if (j & 1) acc[j / 2].y = g.w * s;
                         else acc[j / 2].x = g.z * s;
                     }

@@ -98,7 +98,7 @@ int fail(int status, const std::string &msg)
     return status;
 }
 
-// Warp-per-ray kernel when the rays fill 3/4 of 32 C cells, else an 8-cell tile.
+// Warp-per-ray kernel when the rays fill 3/4 of the cells its lanes hold, else an 8-cell tile.
 rt::Shape pick_shape(int precision, int nr)
 {
     rt::Shape s[32];
@@ -106,7 +106,7 @@ rt::Shape pick_shape(int precision, int nr)
         const int n = rt::ray_shapes(precision, nr, s, 32);
         int bi = -1;
         for (int i = 0; i < n; ++i)
-            if (4 * nr >= 3 * rt::ray_lanes(s[i].cells_per_lane, nr) * s[i].cells_per_lane &&
+            if (4 * nr >= 3 * rt::ray_cells_held(s[i].cells_per_lane, nr) &&
                 (bi < 0 || s[i].cells_per_lane < s[bi].cells_per_lane))
                 bi = i;
         if (bi >= 0) return s[bi];
@@ -211,6 +211,9 @@ extern "C" int rt_irradiate_static(const rt_grid_desc *g, double t_star, double 
     args.nnu_pad = sc.nnu_pad;
     args.n_active = sc.n_active;
     args.t_sub = (float)t_sub;
+    args.tw_t = nullptr;
+    args.tw_b = nullptr;
+    args.n_tw = 0;
     const long long T = rt::trace_tile_cells(shape);
     const unsigned ntiles = (unsigned)((nrays * (g->nr + 1) + T - 1) / T);
     unsigned grid = 0;

@@ -18,14 +18,25 @@ def _brute_warps(w, shape):
     g = w.grid
     kap = sorted(w.kappa[w.kappa > 0])
     c = shape[1]
-    lanes = 8 if 8 * c >= g.nr else (16 if 16 * c >= g.nr else 32)
-    r = 32 // lanes
     rho = w.rho32().astype(np.float64).reshape(-1, g.nr)
     td = w.tdust32().reshape(-1, g.nr)
     dr = np.diff(g.r_if)
     col = lambda j, k: rho[j, k] * dr[k] if td[j, k] <= w.t_sub else 0.0
     out = []
     nrays = rho.shape[0]
+    if 32 * c < g.nr:   # two warps per ray, each 32 c of its cells
+        for j in range(nrays):
+            nmax = sum(col(j, k) for k in range(g.nr))
+            for h in range(2):
+                k0, k1 = 32 * c * h, min(32 * c * (h + 1), g.nr)
+                cmax = max(sum(col(j, k) for k in range(a, min(a + c, k1))) for a in range(k0, k0 + 32 * c, c))
+                bt = sum(1 for kk in kap if kk * nmax <= bench.THIN_X)
+                bc = sum(1 for kk in kap if kk * cmax <= bench.THIN_X)
+                bt2 = bc if (bc > bt and (bt > 0 or bc >= 4)) else bt
+                out.append((k1 - k0, bt, bt2, len(kap)))
+        return out
+    lanes = 8 if 8 * c >= g.nr else (16 if 16 * c >= g.nr else 32)
+    r = 32 // lanes
     for first in range(0, nrays, r):
         rays = range(first, min(first + r, nrays))
         nmax = max(sum(col(j, k) for k in range(g.nr)) for j in rays)
@@ -51,6 +62,15 @@ def _brute(w, shape):
 def test_exact_exp_ops_matches_brute_force(tau, shape):
     w = synth.disk3d(40, 6, 5, n_nu=16, tau550=tau, seed=4)   # 30 rays: a partial last warp
     assert bench.exact_exp_ops(w, shape) == _brute(w, shape)
+
+
+@pytest.mark.parametrize("tau", [1.0, 100.0])
+def test_exact_exp_ops_two_warps_per_ray(tau):
+    """Rays of 80 cells with 2 cells per lane: two warps share each ray."""
+    w = synth.disk3d(80, 4, 3, n_nu=16, tau550=tau, seed=5)
+    shape = (1, 2, 4, 8)
+    assert bench.exact_exp_ops(w, shape) == _brute(w, shape)
+    assert bench.series_fma_ops(w, shape) == _brute_fma(w, shape)
 
 
 def test_exact_exp_ops_limits():
