@@ -116,7 +116,12 @@ int rt_set_opacity_table(rt_ctx *ctx, int n_nu, const double *nu_mid, const doub
  * (K, 2 <= n_t <= 32); a cell's kappa of bin i is row i linear in T between the
  * bracketing grid points (the end values beyond the grid), zero where
  * T_dust > t_sub. The optical depth of every bin is then its own scan along the
- * ray (Eq. 19), traced by a separate warp-per-ray kernel (nr <= 1024). The
+ * ray (Eq. 19), traced by a separate warp-per-ray kernel (nr <= 1024). A table
+ * whose rows are one spectral shape times one temperature factor,
+ * kappa_i(T_j) = kappa_i b_j for every entry to 1e-12 (one dust species whose
+ * abundance depends on T), keeps the single column of the temperature-independent
+ * tracer instead, each cell's column weighted by b(T) (FP32 precisions, rays up to
+ * 512 cells; rt_opacity_table_kind reports which). The
  * temperature-independent entry rt_set_opacity_table switches back. Not
  * available to the multi-grid batch or the learned surrogate (their calls fail
  * with RT_ERR_INVALID_ARG); rt_planck_mean_opacity / rt_dust_temperature use
@@ -129,6 +134,16 @@ int rt_set_opacity_table_t(rt_ctx *ctx, int n_nu, const double *nu_mid, int n_t,
  * Bin fluxes F_i = pi * int B_nu(T_s) dnu over each bin (sum_i F_i = sigma T_s^4) are
  * computed on the device in FP64. Errors: RT_ERR_INVALID_ARG, RT_ERR_CUDA. */
 int rt_set_star(rt_ctx *ctx, double t_star, double r_star);
+
+/* rt_opacity_table_kind -- how the configured table is traced: RT_TABLE_NU (kappa per
+ * bin, one column for every bin), RT_TABLE_NU_T_SEPARABLE (a temperature-dependent
+ * table that separates: the same single column, weighted per cell by b(T)),
+ * RT_TABLE_NU_T (one scan per bin). Errors: RT_ERR_INVALID_ARG,
+ * RT_ERR_NOT_CONFIGURED. */
+#define RT_TABLE_NU             0
+#define RT_TABLE_NU_T_SEPARABLE 1
+#define RT_TABLE_NU_T           2
+int rt_opacity_table_kind(const rt_ctx *ctx, int *kind);
 
 /* rt_irradiate -- trace every ray of the grid (Eqs. 17-20, 27-36).
  *   rho       device [nphi][ntheta][nr] gas density (g cm^-3), >= 0 and finite.

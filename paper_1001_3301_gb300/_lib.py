@@ -27,6 +27,9 @@ RT_FP32_KAHAN = 0
 RT_FP32_PLAIN = 1
 RT_FP64 = 2
 RT_MAX_NU = 128
+RT_TABLE_NU = 0
+RT_TABLE_NU_T_SEPARABLE = 1
+RT_TABLE_NU_T = 2
 RT_BATCH_MAX = 256
 
 PRECISIONS = {"fp32_kahan": RT_FP32_KAHAN, "fp32_plain": RT_FP32_PLAIN, "fp64": RT_FP64}
@@ -89,6 +92,7 @@ SIGNATURES = {
     "rt_host_wait": (_I, [_P]),
     "rt_energy_last": (_I, [_P, ctypes.POINTER(RtEnergy)]),
     "rt_energy_reduce": (_I, [_P]),
+    "rt_opacity_table_kind": (_I, [_P, ctypes.POINTER(_I)]),
     "rt_get_bins": (_I, [_P, _DP]),
     "rt_set_tuning": (_I, [_P, _I, _I, _I, _I]),
     "rt_get_tuning": (_I, [_P] + [ctypes.POINTER(_I)] * 4),

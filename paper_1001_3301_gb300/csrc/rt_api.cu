@@ -65,7 +65,7 @@ struct rt_ctx {
     // column weight b(T) (grid padded with +Inf; (b_j, slope to the next point))
     bool tw_sep = false;
     float *tw_t_d = nullptr;
-    float2 *tw_b_d = nullptr;
+    float4 *tw_b_d = nullptr;
     int *order_d = nullptr;
     unsigned long long fingerprint = 0;
     // learned surrogate (rt_surrogate.cu), created by rt_surrogate_train / _load
@@ -631,12 +631,17 @@ int rt_set_opacity_table_t(rt_ctx *ctx, int n_nu, const double *nu_mid, int n_t,
         }
     if (sep) {
         float tw_t[rt::kMaxTdepPoints];
-        float2 tw_b[rt::kMaxTdepPoints];
+        float4 tw_b[rt::kMaxTdepPoints];
         for (int j = 0; j < rt::kMaxTdepPoints; ++j) {
-            const int jj = j < n_t ? j : n_t - 1;
             tw_t[j] = j < n_t ? (float)t_grid[j] : INFINITY;
-            const double slope = jj + 1 < n_t ? (bj[jj + 1] - bj[jj]) / (t_grid[jj + 1] - t_grid[jj]) : 0.0;
-            tw_b[j] = make_float2((float)bj[jj], (float)slope);
+            if (j + 1 < n_t) {
+                const double idt = 1.0 / ((double)(float)t_grid[j + 1] - (double)(float)t_grid[j]);
+                tw_b[j] = make_float4((float)t_grid[j], (float)t_grid[j + 1], (float)(bj[j] * idt),
+                                      (float)(bj[j + 1] * idt));
+            } else {  // the last point holds: b_last (T_last + 1 - T) + b_last (T - T_last)
+                const float tl = (float)t_grid[n_t - 1], bl = (float)bj[n_t - 1];
+                tw_b[j] = make_float4(tl, tl + 1.0f, bl, bl);
+            }
         }
         if (!ctx->tw_t_d) {
             bool ok = dalloc(&ctx->tw_t_d, rt::kMaxTdepPoints) == cudaSuccess &&

@@ -119,7 +119,8 @@ struct TraceArgs {
     // linear between the points of the temperature grid and held beyond its ends.
     // n_tw = 0: no weight (a table of kappa(nu) only).
     const float *tw_t;        // [kMaxTdepPoints] grid (K), padded with +Inf
-    const float2 *tw_b;       // [kMaxTdepPoints] (b_j, (b_{j+1} - b_j) / (T_{j+1} - T_j)); slope 0 from the last point
+    const float4 *tw_b;       // [kMaxTdepPoints] (T_j, T_{j+1}, b_j / dT, b_{j+1} / dT) per interval;
+                              // (T_last, T_last + 1, b_last, b_last) from the last point on
     int n_tw;
 };
 

@@ -185,16 +185,18 @@ __device__ __forceinline__ float lane_coefficients(const float *thin_row, int bt
 
 // Column weight b(T) of a separable kappa(nu, T) table (TraceArgs::tw_t, tw_b): T
 // clamped to the grid, its interval found by a five-step binary search over the
-// 32-entry grid (padded with +Inf), then linear in T. t_lo, t_hi: the grid's ends.
-__device__ __forceinline__ float tw_weight(const float *tg, const float2 *tb, float t_lo, float t_hi, float t)
+// 32-entry grid (padded with +Inf), then linear in T as
+// (b_j (T_{j+1} - T) + b_{j+1} (T - T_j)) / dT: two non-negative terms, so no
+// cancellation where b falls towards zero. t_lo, t_hi: the grid's ends.
+__device__ __forceinline__ float tw_weight(const float *tg, const float4 *tb, float t_lo, float t_hi, float t)
 {
     t = fminf(fmaxf(t, t_lo), t_hi);
     int j = 0;
 #pragma unroll
     for (int step = 16; step > 0; step >>= 1)
         if (tg[j + step] <= t) j += step;
-    const float2 e = tb[j];
-    return fmaf(t - tg[j], e.y, e.x);
+    const float4 e = tb[j];
+    return fmaf(e.z, e.y - t, e.w * (t - e.x));
 }
 
 // Bar.sync on a named barrier of n threads (the P warps of one group).
@@ -228,7 +230,7 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
     __shared__ Sum s_grp[P > 1 ? W / P : 1][2][P];
     // separable table: each warp's copy of the weight table, and its cells' weights
     __shared__ float s_twt[TW ? W : 1][kMaxTdepPoints];
-    __shared__ float2 s_twb[TW ? W : 1][kMaxTdepPoints];
+    __shared__ float4 s_twb[TW ? W : 1][kMaxTdepPoints];
     __shared__ float2 s_bw[TW ? W : 1][C / 2][32];
     const int wid = TW ? (int)(threadIdx.x >> 5) : 0;
     float tw_lo = 0.0f, tw_hi = 0.0f;

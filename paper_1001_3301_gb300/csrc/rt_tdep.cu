@@ -33,7 +33,8 @@ struct TdepTab {
 // different table rows, so the interpolation itself stays scalar).
 template <int CLASS, int C>
 __device__ __forceinline__ void tdep_range(int i0, int i1, const float *s_lf, const float2 *s_kt, int n_t,
-                                           const int (&jt)[C], const float (&wt)[C], const float2 (&d2)[C / 2],
+                                           const int (&jt)[C], const float (&wt)[C], const float (&wb)[C],
+                                           const float2 (&d2)[C / 2],
                                            float2 (&a2)[C / 2], float2 (&a02)[C / 2], bool any_zero, int lane,
                                            float &esc)
 {
@@ -42,8 +43,10 @@ __device__ __forceinline__ void tdep_range(int i0, int i1, const float *s_lf, co
         const float lf = s_lf[i];
         const float2 *row = s_kt + i * n_t;
         auto kappa2 = [&](int m) {  // the two cells' kappa of this bin
+            // kappa_j (T_{j+1} - T) / dT + kappa_{j+1} (T - T_j) / dT: two non-negative
+            // terms, no cancellation where the row falls towards zero
             const float2 k0 = row[jt[2 * m]], k1 = row[jt[2 * m + 1]];
-            return make_float2(fmaf(wt[2 * m], k0.y - k0.x, k0.x), fmaf(wt[2 * m + 1], k1.y - k1.x, k1.x));
+            return make_float2(fmaf(k0.y, wt[2 * m], k0.x * wb[2 * m]), fmaf(k1.y, wt[2 * m + 1], k1.x * wb[2 * m + 1]));
         };
         float2 dt2[C / 2];
         float2 ls2 = f2(0.0f);  // the lane's sum, at most C terms in two halves (plain FP32)
@@ -97,7 +100,7 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray_tdep(const TraceArgs p, co
     const int nv = nr - c0 < 0 ? 0 : (nr - c0 > C ? C : nr - c0);
 
     __shared__ float s_dr[C][32], s_gq[C][32], s_ga[C][32];
-    __shared__ float s_tg[32];
+    __shared__ float s_tg[32], s_idt[32];  // grid, 1 / (T_{j+1} - T_j)
     __shared__ KahanSum s_red[W][2];
     extern __shared__ __align__(16) unsigned char smem[];
     float4 *s_nu = reinterpret_cast<float4 *>(smem);                 // [nnu_pad] (nk_max, ., lf, .)
@@ -111,7 +114,10 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray_tdep(const TraceArgs p, co
         s_lf[i] = e.lf;
     }
     for (int i = tid; i < p.nnu_pad * t.n_t; i += W * 32) s_kt[i] = t.kt2[i];
-    for (int i = tid; i < t.n_t; i += W * 32) s_tg[i] = t.tg[i];
+    for (int i = tid; i < t.n_t; i += W * 32) {
+        s_tg[i] = t.tg[i];
+        s_idt[i] = i + 1 < t.n_t ? 1.0f / (t.tg[i + 1] - t.tg[i]) : 0.0f;
+    }
     for (int i = tid; i < 32 * C; i += W * 32) {
         const int l = i / C, j = i % C, k = l * C + j;
         const float4 g = (k < nr) ? __ldg(&p.rtab[k]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -128,7 +134,7 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray_tdep(const TraceArgs p, co
     for (unsigned ray = blockIdx.x * W + warp; ray < p.nrays; ray += gridDim.x * W) {
         const size_t base = (size_t)ray * nr + c0;
         Cells<float, C> d, acc, acc0;
-        float wt[C];
+        float wt[C], wb[C];  // the weights of the upper and the lower point
         int jt[C];
         unsigned zero_m = 0;
         bool bad = false;
@@ -152,9 +158,9 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray_tdep(const TraceArgs p, co
             int lo = 0;
             for (int s = 16; s > 0; s >>= 1)
                 if (lo + s < nt - 1 && s_tg[lo + s] <= td) lo += s;
-            const float w = (td - s_tg[lo]) / (s_tg[lo + 1] - s_tg[lo]);
             jt[j] = lo;
-            wt[j] = fminf(fmaxf(w, 0.0f), 1.0f);
+            wt[j] = fminf(fmaxf((td - s_tg[lo]) * s_idt[lo], 0.0f), 1.0f);
+            wb[j] = fminf(fmaxf((s_tg[lo + 1] - td) * s_idt[lo], 0.0f), 1.0f);
         }
         if (__any_sync(0xffffffffu, bad) && lane == 0) atomicMax(p.bad_input, p.seq);
         for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
@@ -163,11 +169,11 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray_tdep(const TraceArgs p, co
         const int na = p.n_active;
         const BinClasses bc = classify_bins(s_nu, na, lane, dmax, 0.0f);
         float esc = 0.0f;
-        tdep_range<1, C>(0, bc.b1, s_lf, s_kt, nt, jt, wt, d.v, acc.v, acc0.v, any_zero, lane, esc);
-        tdep_range<2, C>(bc.b1, bc.b2, s_lf, s_kt, nt, jt, wt, d.v, acc.v, acc0.v, any_zero, lane, esc);
-        tdep_range<3, C>(bc.b2, bc.b3, s_lf, s_kt, nt, jt, wt, d.v, acc.v, acc0.v, any_zero, lane, esc);
-        tdep_range<5, C>(bc.b3, bc.b5, s_lf, s_kt, nt, jt, wt, d.v, acc.v, acc0.v, any_zero, lane, esc);
-        tdep_range<6, C>(bc.b5, na, s_lf, s_kt, nt, jt, wt, d.v, acc.v, acc0.v, any_zero, lane, esc);
+        tdep_range<1, C>(0, bc.b1, s_lf, s_kt, nt, jt, wt, wb, d.v, acc.v, acc0.v, any_zero, lane, esc);
+        tdep_range<2, C>(bc.b1, bc.b2, s_lf, s_kt, nt, jt, wt, wb, d.v, acc.v, acc0.v, any_zero, lane, esc);
+        tdep_range<3, C>(bc.b2, bc.b3, s_lf, s_kt, nt, jt, wt, wb, d.v, acc.v, acc0.v, any_zero, lane, esc);
+        tdep_range<5, C>(bc.b3, bc.b5, s_lf, s_kt, nt, jt, wt, wb, d.v, acc.v, acc0.v, any_zero, lane, esc);
+        tdep_range<6, C>(bc.b5, na, s_lf, s_kt, nt, jt, wt, wb, d.v, acc.v, acc0.v, any_zero, lane, esc);
 
         const float w = __ldg(p.domega32 + ray);
         if (lane == 31) eesc.add(esc * w);

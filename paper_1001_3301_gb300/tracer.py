@@ -140,6 +140,12 @@ class Tracer:
         check(lib.rt_energy_last(self._ctx, ctypes.byref(e)), self._ctx)
         return Energy(e)
 
+    def table_kind(self) -> int:
+        """RT_TABLE_NU, RT_TABLE_NU_T_SEPARABLE or RT_TABLE_NU_T: how the table is traced."""
+        k = ctypes.c_int()
+        check(lib.rt_opacity_table_kind(self._ctx, ctypes.byref(k)), self._ctx)
+        return k.value
+
     def energy_reduce(self):
         """Enqueue the FP64 energy reduction of the last trace (device only, no sync)."""
         check(lib.rt_energy_reduce(self._ctx), self._ctx)

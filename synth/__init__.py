@@ -175,6 +175,24 @@ def kappa_synth_t(nu: np.ndarray, tg: np.ndarray) -> np.ndarray:
     return np.outer(kappa_synth(nu), s)
 
 
+# a second species with its own spectral shape: water-ice bands at 3.1 and 45 micron
+# (Gaussians in log10 nu, 0.08 dex wide, 40 and 20 cm^2/g) present below ~150 K
+_ICE_BANDS = ((C_CM_S / 3.1e-4, 40.0), (C_CM_S / 45e-4, 20.0))
+
+
+def kappa_synth_t2(nu: np.ndarray, tg: np.ndarray) -> np.ndarray:
+    """A kappa(nu, T) [n_nu][n_t] that does not separate into kappa(nu) b(T): the
+    table of kappa_synth_t plus ice bands whose carrier evaporates near 150 K (the
+    same logistic step), two spectral shapes with different temperature factors."""
+    nu = np.asarray(nu, dtype=np.float64)
+    step = 1.0 / (1.0 + np.exp(-(np.asarray(tg, dtype=np.float64) - 150.0) / 15.0))
+    lg = np.log10(nu)
+    ice = np.zeros_like(nu)
+    for centre, amp in _ICE_BANDS:
+        ice = ice + amp * np.exp(-0.5 * ((lg - math.log10(centre)) / 0.08) ** 2)
+    return kappa_synth_t(nu, tg) + np.outer(ice, 1.0 - step)
+
+
 def rho0_for_tau550(tau550: float, kappa550: float | None = None) -> float:
     """Midplane normalisation: tau550 = int_{r_min}^{r_max} rho0 (r_d/r) kappa dr
     along z = 0, i.e. rho0 = tau550 / (kappa550 r_d ln(r_max/r_min))."""

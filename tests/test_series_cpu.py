@@ -143,3 +143,20 @@ def test_lane_series_matches_the_bin_sum(seed):
         # the first omitted term is below X^K / K! of the leading one, and the value
         # below the leading term by at most e^{-X}
         np.testing.assert_allclose(series[m], exact[m], rtol=math.exp(X_MAX) * X_MAX ** K_TERMS / math.factorial(K_TERMS))
+
+
+def test_mixed_class_fraction_bound():
+    """The absorbed fraction of the mixed class (rt_device.cuh): the smaller of the
+    5-term series of 1 - e^{-x} and 1 - e^{-x} (1 + d) + 2^-22, with |d| up to the
+    hardware exp2 error 2^-22.7 (either sign), stays within 1.6e-6 of 1 - e^{-x} for
+    every x, and is the series itself below x = 1/8; the series is an upper bound."""
+    x = np.geomspace(1e-9, 90.0, 200001)
+    om = -np.expm1(-x)
+    t5 = x - x ** 2 / 2 + x ** 3 / 6 - x ** 4 / 24 + x ** 5 / 120
+    assert np.all(t5 >= om * (1 - 1e-15))
+    for d in (-2.0 ** -22.7, 0.0, 2.0 ** -22.7):
+        big = 1.0 - np.exp(-x) * (1 + d) + 2.0 ** -22
+        v = np.minimum(t5, big)
+        assert np.max(np.abs(v / om - 1)) < 1.6e-6
+        small = x < 0.125
+        assert np.all(v[small] == t5[small])

@@ -1,5 +1,7 @@
-"""The tracer with temperature-dependent opacity tables (per-bin scans of Eq. 19 with
-every cell's own kappa) against the FP64 oracle."""
+"""The tracer with temperature-dependent opacity tables against the FP64 oracle: a
+table that separates, kappa_i(T) = kappa_i b(T) (the one-column tracer with each
+cell's column weighted by b(T)), and one that does not (per-bin scans of Eq. 19 with
+every cell's own kappa)."""
 from __future__ import annotations
 
 import numpy as np
@@ -26,12 +28,14 @@ def _oracle(w, tg, kt):
                                  w.rho32().astype(np.float64), w.tdust32().astype(np.float64), nthreads=8)
 
 
-def _run(w, tg, kt, shape=None):
+def _run(w, tg, kt, shape=None, precision="fp32_kahan", kind=None):
     import torch
     from paper_1001_3301_gb300 import Tracer
-    tr = Tracer.from_grid(w.grid)
+    tr = Tracer.from_grid(w.grid, precision)
     tr.set_opacity_table_t(w.nu, tg, kt, w.t_sub)
     tr.set_star(w.t_star, w.r_star)
+    if kind is not None:
+        assert tr.table_kind() == kind
     if shape is not None:
         tr.set_tuning(*shape)
     r = torch.from_numpy(w.rho32()).cuda()
@@ -42,35 +46,76 @@ def _run(w, tg, kt, shape=None):
     return out
 
 
+TABLES = {"separable": synth.kappa_synth_t, "two-species": synth.kappa_synth_t2}
+
+
+def _tg(n):
+    """The synthetic temperature grid as float32 values: the form the device holds
+    (like the float32 fields, both sides see the same points)."""
+    return synth.t_grid(n).astype(np.float32).astype(np.float64)
+
+
+def _kind(table, nr, precision="fp32_kahan", n_nu=2):
+    """The path the library takes: the one-column tracer with the column weight where
+    the table separates (a one-bin table always does) and the rays fit its shapes."""
+    from paper_1001_3301_gb300._lib import RT_TABLE_NU_T, RT_TABLE_NU_T_SEPARABLE
+    sep = table == "separable" or n_nu == 1
+    return RT_TABLE_NU_T_SEPARABLE if (sep and nr <= 512 and precision != "fp64") else RT_TABLE_NU_T
+
+
+@pytest.mark.parametrize("table", sorted(TABLES))
 @pytest.mark.parametrize("tau", [0.1, 1.0, 100.0])
-def test_disk_against_oracle(torch, tau):
+def test_disk_against_oracle(torch, tau, table):
     w = synth.disk3d(96, 24, 8, n_nu=79, tau550=tau, seed=11)
-    tg = synth.t_grid(24)
-    kt = synth.kappa_synth_t(w.nu, tg)
+    tg = _tg(24)
+    kt = TABLES[table](w.nu, tg)
     orc = _oracle(w, tg, kt)
-    q, a, e, _ = _run(w, tg, kt)
-    _parity.assert_parity(w, q, a, e, orc, label=f"tdep tau {tau}")
+    q, a, e, _ = _run(w, tg, kt, kind=_kind(table, w.grid.nr))
+    _parity.assert_parity(w, q, a, e, orc, label=f"tdep {table} tau {tau}")
 
 
+@pytest.mark.parametrize("table", sorted(TABLES))
 @pytest.mark.parametrize("dims", [(1, 1, 1, 1), (7, 3, 2, 5), (33, 5, 3, 17), (65, 4, 2, 40), (200, 3, 2, 79),
-                                  (513, 2, 2, 32), (1024, 2, 1, 16)],
+                                  (300, 3, 2, 24), (513, 2, 2, 32), (1024, 2, 1, 16)],
                          ids=lambda d: "x".join(map(str, d)))
-def test_ragged_all_shapes(torch, dims):
+def test_ragged_all_shapes(torch, dims, table):
     nr, nth, nph, nnu = dims
     w = synth.disk3d(nr, nth, nph, n_nu=nnu, tau550=10.0, seed=nr + nth)
-    tg = synth.t_grid(9)
-    kt = synth.kappa_synth_t(w.nu, tg)
+    tg = _tg(9)
+    kt = TABLES[table](w.nu, tg)
     orc = _oracle(w, tg, kt)
-    _, _, _, shapes = _run(w, tg, kt)
+    _, _, _, shapes = _run(w, tg, kt, kind=_kind(table, nr, n_nu=nnu))
     assert shapes and all(s[0] == 1 for s in shapes)
     for shape in shapes:
         q, a, e, _ = _run(w, tg, kt, shape=shape)
-        _parity.assert_parity(w, q, a, e, orc, label=f"tdep {dims} {shape}")
+        _parity.assert_parity(w, q, a, e, orc, label=f"tdep {table} {dims} {shape}")
+
+
+def test_separable_weight_edges(torch):
+    """A separable table whose temperature factor is zero above 1000 K (dust that
+    stays but stops absorbing: the column weight 0, the force 0) and temperatures
+    beyond both ends of its grid (the end values hold); every precision mode, the
+    FP64 one through the per-bin kernel."""
+    w = synth.disk3d(128, 12, 4, n_nu=32, tau550=30.0, seed=9)
+    tg = np.array([40.0, 100.0, 300.0, 600.0, 1000.0, 1200.0])
+    b = np.array([0.6, 1.0, 0.8, 0.5, 0.0, 0.0])
+    kt = np.outer(w.kappa, b)
+    td = w.tdust32().copy()
+    td.reshape(-1)[::7] = 15.0                    # below the grid
+    orc = oracle.irradiate_tdep(w.grid.r_if, w.grid.theta_if, w.grid.phi_if, w.t_star, w.r_star, w.nu, tg, kt,
+                                w.t_sub, w.rho32().astype(np.float64), td.astype(np.float64), nthreads=8)
+    ww = synth.Workload(w.name, w.grid, w.nu, w.kappa, w.rho, td, tau550=w.tau550)
+    # (an FP64 context takes the per-bin kernel, whose arithmetic is FP32: the same 1e-5)
+    for precision, rtol in (("fp32_kahan", 1e-5), ("fp32_plain", 1e-5), ("fp64", 1e-5)):
+        q, a, e, _ = _run(ww, tg, kt, precision=precision, kind=_kind("separable", 128, precision))
+        _parity.assert_parity(ww, q, a, e, orc, rtol_q=rtol, rtol_a=rtol, label=f"edges {precision}")
+        hot = (td > 1000.0) & (td <= w.t_sub)
+        assert hot.any() and np.all(q[hot] == 0.0) and np.all(a[hot] == 0.0)
 
 
 def test_constant_table_matches_plain_tracer(torch):
     w = synth.disk3d(64, 16, 4, n_nu=32, tau550=10.0, seed=2)
-    tg = synth.t_grid(4)
+    tg = _tg(4)
     kt = np.repeat(w.kappa[:, None], 4, axis=1)
     q, a, e, _ = _run(w, tg, kt)
     q0, a0, e0 = _parity.run_gpu(w)
@@ -82,7 +127,7 @@ def test_constant_table_matches_plain_tracer(torch):
 def test_planck_mean_uses_kappa_of_t(torch):
     from paper_1001_3301_gb300 import Tracer
     w = synth.disk2d(16, 8, 40)
-    tg = synth.t_grid(12)
+    tg = _tg(12)
     kt = synth.kappa_synth_t(w.nu, tg)
     tr = Tracer.from_grid(w.grid)
     tr.set_opacity_table_t(w.nu, tg, kt, w.t_sub)
@@ -98,7 +143,7 @@ def test_planck_mean_uses_kappa_of_t(torch):
 def test_unsupported_paths_refuse(torch):
     from paper_1001_3301_gb300 import Batch, RtError, Tracer
     w = synth.disk3d(16, 4, 2, n_nu=8, tau550=1.0, seed=1)
-    tg = synth.t_grid(4)
+    tg = _tg(4)
     tr = Tracer.from_grid(w.grid)
     tr.set_opacity_table_t(w.nu, tg, synth.kappa_synth_t(w.nu, tg), w.t_sub)
     tr.set_star(w.t_star, w.r_star)
