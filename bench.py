@@ -45,6 +45,8 @@ NNU = 79
 # the 256 x 128 x 256 grid of the steps after the tracer (dust temperature, kappa(nu, T)
 # tracer, flux-limited diffusion) and of the secondary tracer object
 NR, NTH, NPH = 256, 128, 256
+# rt_opacity_table_kind values
+TABLE_KINDS = ("nu", "nu_t_separable", "nu_t", "nu_t_rank2")
 
 
 def workload_name(spec, taus):
@@ -123,6 +125,8 @@ def parse():
                    help="skip the learned-surrogate leg of the default line")
     p.add_argument("--surrogate", action="store_true",
                    help="print only the learned-surrogate leg (train, then time against the exact tracer)")
+    p.add_argument("--lut", action="store_true",
+                   help="print only the lookup-table comparator (against the exact tracer on the 512x256x512 grids)")
     p.add_argument("--sur-grid", default="512x256x512", help="grid the surrogate is timed on")
     p.add_argument("--sur-train-grid", default="256x128x128", help="geometry of the training fields")
     p.add_argument("--sur-steps", type=int, default=60000, help="Adam steps of the surrogate training")
@@ -699,8 +703,8 @@ def run_ours(args, rank, world, local):
 
     # the tracer with temperature-dependent tables (24 temperatures) on the tau = 1 grid:
     # the synthetic table (one species whose abundance depends on T: it separates, the
-    # one-column tracer with a per-cell column weight) and a two-species table (per-bin
-    # scans)
+    # one-column tracer with a per-cell column weight), a two-species table (rank two:
+    # two columns per ray) and a three-species one (per-bin scans)
     tdep = None
     if rank == 0 and c2:
         from paper_1001_3301_gb300 import Tracer
@@ -710,7 +714,8 @@ def run_ours(args, rank, world, local):
         qt, at = torch.empty_like(ri), torch.empty_like(ri)
         units = w1.grid.ncells * len(w1.nu)
         tdep = {"workload": f"disk3d {NR}x{NTH}x{NPH}, {NNU} bins x 24 temperatures, tau550 = {w1.tau550:g}"}
-        for name, table in (("separable", synth.kappa_synth_t), ("two_species", synth.kappa_synth_t2)):
+        for name, table in (("separable", synth.kappa_synth_t), ("two_species", synth.kappa_synth_t2),
+                            ("three_species", synth.kappa_synth_t3)):
             trt = Tracer.from_grid(w1.grid)
             trt.set_opacity_table_t(w1.nu, tg, table(w1.nu, tg), w1.t_sub)
             trt.set_star(w1.t_star, w1.r_star)
@@ -727,7 +732,7 @@ def run_ours(args, rank, world, local):
             t_ms = e0.elapsed_time(e1) / args.steps
             ach = EXP_PER_CELL_NU * units / (t_ms * 1e-3) / 1e9
             _, _, et = trt.irradiate(ri, ti, qt, at, energy=True)
-            tdep[name] = {"table_kind": ["nu", "nu_t_separable", "nu_t"][trt.table_kind()], "ms": t_ms,
+            tdep[name] = {"table_kind": TABLE_KINDS[trt.table_kind()], "ms": t_ms,
                           "cell_nu_per_s": units / (t_ms * 1e-3),
                           "roofline": {"bound": "alu", "unit": "Gop/s (MUFU ex2, one per cell-nu)", "achieved": ach,
                                        "peak": ex2_peak, "frac": ach / ex2_peak},
@@ -750,6 +755,7 @@ def run_ours(args, rank, world, local):
     sur = None
     if rank == 0 and world == 1 and not args.no_surrogate:
         sur = run_surrogate(args, local)
+        sur["lut_comparator"] = run_lut(args, local)
 
     if rank == 0:
         line = {
@@ -896,6 +902,67 @@ def run_surrogate(args, local):
                      "tensor_mac_per_cell": 36864, "umma_mac_per_sm_clk": rates["umma_n128_mac"]},
         "clocks": clocks,
     }
+
+
+def run_lut(args, local):
+    """The lookup-table comparator (rt_lut_build, rt_irradiate_lut) against the exact
+    tracer on the 512 x 256 x 512 grids at tau550 = 1 and 100: time per launch, the
+    warp-slots that fell back to the per-bin sum, and the largest relative error of q_abs
+    and a_rad against the exact tracer in the cells that absorb more than 1e-12 L*."""
+    import torch
+    from paper_1001_3301_gb300 import Tracer
+    torch.cuda.set_device(local)
+    spec = WORKLOADS["c3"]
+    out = {"err_tol": SUR_TOL}
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    for tau in spec["taus"]:
+        w = synth.disk3d(spec["nr"], spec["ntheta"], spec["nphi"], n_nu=spec["n_nu"], tau550=tau, seed=spec["seed"])
+        g = w.grid
+        tr = Tracer.from_grid(g)
+        tr.set_opacity_table(w.nu, w.kappa, w.t_sub)
+        tr.set_star(w.t_star, w.r_star)
+        rho = torch.from_numpy(w.rho32()).cuda()
+        td = torch.from_numpy(w.tdust32()).cuda()
+        q_ex, a_ex = torch.empty_like(rho), torch.empty_like(rho)
+        q_l, a_l = torch.empty_like(rho), torch.empty_like(rho)
+        shape = tr.autotune(rho, td, q_ex, a_ex, reps=2)
+        t0 = time.perf_counter()
+        tr.lut_build(SUR_TOL)
+        t_build = time.perf_counter() - t0
+        _, _, e_ex = tr.irradiate(rho, td, q_ex, a_ex, energy=True)
+        _, _, e_l, fb = tr.irradiate_lut(rho, td, q_l, a_l, energy=True, stats=True)
+        dom = torch.from_numpy(np.outer(np.diff(g.phi_if), np.cos(g.theta_if[:-1]) - np.cos(g.theta_if[1:]))).cuda()
+        d3 = torch.from_numpy((g.r_if[1:] ** 3 - g.r_if[:-1] ** 3) / 3.0).cuda()
+        mask = (q_ex.double() * dom[:, :, None] * d3[None, None, :]) > 1e-12 * e_ex.l_star
+        rq = ((q_l.double() - q_ex.double()).abs() / q_ex.double().clamp_min(1e-300))[mask]
+        ra = ((a_l.double() - a_ex.double()).abs() / a_ex.double().abs().clamp_min(1e-300))[mask]
+        t_ex = timed(lambda: tr.irradiate(rho, td, q_ex, a_ex), args.sur_reps)
+        t_l = timed(lambda: tr.irradiate_lut(rho, td, q_l, a_l), args.sur_reps)
+        slots = g.ntheta * g.nphi // max(1, 32 // (8 if 8 * shape[1] >= g.nr else (16 if 16 * shape[1] >= g.nr else 32)))
+        out[f"tau{tau:g}"] = {
+            "exact_ms": t_ex, "lut_ms": t_l, "speedup_vs_exact": t_ex / t_l,
+            "lut_cell_nu_per_s": g.ncells * len(w.nu) / (t_l * 1e-3),
+            "fallback_warp_slots": fb, "fallback_frac": fb / max(slots, 1),
+            "max_rel_err_q_vs_exact": float(rq.max()), "max_rel_err_a_vs_exact": float(ra.max()),
+            "cells_over_tol": int((rq > SUR_TOL).sum()), "judged_cells": int(mask.sum()),
+            "e_abs_rel_diff": abs(e_l.e_abs - e_ex.e_abs) / e_ex.l_star, "build_s": t_build,
+            "launch_shape": list(shape)}
+        tr.close()
+        del rho, td, q_ex, a_ex, q_l, a_l, mask, rq, ra
+        torch.cuda.empty_cache()
+    return out
 
 
 def bf16_round(x):
@@ -1095,6 +1162,10 @@ def main():
     if args.surrogate:
         if rank == 0:
             print(json.dumps({"mode": "surrogate", **run_surrogate(args, local)}), flush=True)
+        return
+    if args.lut:
+        if rank == 0:
+            print(json.dumps({"mode": "lut_comparator", **run_lut(args, local)}), flush=True)
         return
     if args.fld:
         if rank == 0:

@@ -121,7 +121,11 @@ int rt_set_opacity_table(rt_ctx *ctx, int n_nu, const double *nu_mid, const doub
  * kappa_i(T_j) = kappa_i b_j for every entry to 1e-12 (one dust species whose
  * abundance depends on T), keeps the single column of the temperature-independent
  * tracer instead, each cell's column weighted by b(T) (FP32 precisions, rays up to
- * 512 cells; rt_opacity_table_kind reports which). The
+ * 512 cells). A table of rank two with non-negative factors, every entry a
+ * non-negative combination of two of the table's own columns to 1e-10 of itself
+ * (two species whose abundances depend on T), is traced with two columns per ray
+ * (kappa_i(T) = A_i1 b_1(T) + A_i2 b_2(T); FP32 precisions, nr <= 1024).
+ * rt_opacity_table_kind reports which kernel serves the table. The
  * temperature-independent entry rt_set_opacity_table switches back. Not
  * available to the multi-grid batch or the learned surrogate (their calls fail
  * with RT_ERR_INVALID_ARG); rt_planck_mean_opacity / rt_dust_temperature use
@@ -138,11 +142,12 @@ int rt_set_star(rt_ctx *ctx, double t_star, double r_star);
 /* rt_opacity_table_kind -- how the configured table is traced: RT_TABLE_NU (kappa per
  * bin, one column for every bin), RT_TABLE_NU_T_SEPARABLE (a temperature-dependent
  * table that separates: the same single column, weighted per cell by b(T)),
- * RT_TABLE_NU_T (one scan per bin). Errors: RT_ERR_INVALID_ARG,
- * RT_ERR_NOT_CONFIGURED. */
+ * RT_TABLE_NU_T_RANK2 (a table of rank two: two columns per ray), RT_TABLE_NU_T
+ * (one scan per bin). Errors: RT_ERR_INVALID_ARG, RT_ERR_NOT_CONFIGURED. */
 #define RT_TABLE_NU             0
 #define RT_TABLE_NU_T_SEPARABLE 1
 #define RT_TABLE_NU_T           2
+#define RT_TABLE_NU_T_RANK2     3
 int rt_opacity_table_kind(const rt_ctx *ctx, int *kind);
 
 /* rt_irradiate -- trace every ray of the grid (Eqs. 17-20, 27-36).
@@ -299,6 +304,35 @@ const char *rt_batch_last_error(const rt_batch *b);
 
 /* rt_batch_destroy -- wait for the batch's stream, free the batch (NULL ignored). */
 void rt_batch_destroy(rt_batch *b);
+
+/* ---- lookup-table comparator (no counterpart in the paper) ----------------- */
+
+/* rt_lut_build -- build the context's lookup table for the per-bin sum (a
+ * non-learned comparator of the learned surrogate). With kappa depending on the
+ * frequency only, the power a cell absorbs over all bins, sum_i F_i e^{-kappa_i N_in}
+ * (1 - e^{-kappa_i dN}) (Eqs. 17, 28-32, 36 summed over the bins of Sect. 2.3), is a
+ * function of the column in front of the cell and of its own column. The table holds
+ * log2 of that sum per unit kappa_ref dN on a grid of s = log2(kappa_ref N_in +
+ * 2^-20) in [-20, 8] and d = log2(kappa_ref dN + 2^-30) in [-30, 8], steps 1/32
+ * (897 x 1217 pairs of floats, 8.7 MB of device memory the context owns), computed in FP64
+ * from the tracer's bin table; kappa_ref is the flux-weighted mean opacity. Each grid
+ * square whose bilinear interpolation is off by more than err_tol / 2 at its centre
+ * or an edge midpoint is flagged. Rebuild after rt_set_star / rt_set_opacity_table.
+ * Only for temperature-independent tables in the FP32 precisions. Synchronises.
+ * Errors: RT_ERR_NOT_CONFIGURED, RT_ERR_INVALID_ARG, RT_ERR_NO_MEMORY, RT_ERR_CUDA. */
+int rt_lut_build(rt_ctx *ctx, float err_tol);
+
+/* rt_irradiate_lut -- rt_irradiate with the per-bin sum of every cell taken from the
+ * lookup table (bilinear in log2; rays of at most 512 cells). A warp of rays that
+ * holds a cell in a flagged square or off the table computes the per-bin sum
+ * instead. The escaping power and the rho -> 0 force limit stay exact. The result is
+ * within about err_tol of rt_irradiate per cell (not within the tracer's 1e-5), and
+ * so is the energy. fallback_slots, if not NULL, receives the number of warp-slots
+ * that took the per-bin sum (the call then synchronises). Arguments and errors as
+ * rt_irradiate, plus RT_ERR_NOT_CONFIGURED (no table for the current configuration)
+ * and RT_ERR_INVALID_ARG (rays longer than 512 cells). */
+int rt_irradiate_lut(rt_ctx *ctx, const float *rho, const float *t_dust, float *q_abs, float *a_rad,
+                     rt_energy *energy, unsigned *fallback_slots);
 
 /* ---- allocation-free form (no counterpart in the paper) -------------------- */
 

@@ -30,6 +30,7 @@ RT_MAX_NU = 128
 RT_TABLE_NU = 0
 RT_TABLE_NU_T_SEPARABLE = 1
 RT_TABLE_NU_T = 2
+RT_TABLE_NU_T_RANK2 = 3
 RT_BATCH_MAX = 256
 
 PRECISIONS = {"fp32_kahan": RT_FP32_KAHAN, "fp32_plain": RT_FP32_PLAIN, "fp64": RT_FP64}
@@ -93,6 +94,8 @@ SIGNATURES = {
     "rt_energy_last": (_I, [_P, ctypes.POINTER(RtEnergy)]),
     "rt_energy_reduce": (_I, [_P]),
     "rt_opacity_table_kind": (_I, [_P, ctypes.POINTER(_I)]),
+    "rt_lut_build": (_I, [_P, ctypes.c_float]),
+    "rt_irradiate_lut": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(RtEnergy), ctypes.POINTER(ctypes.c_uint)]),
     "rt_get_bins": (_I, [_P, _DP]),
     "rt_set_tuning": (_I, [_P, _I, _I, _I, _I]),
     "rt_get_tuning": (_I, [_P] + [ctypes.POINTER(_I)] * 4),

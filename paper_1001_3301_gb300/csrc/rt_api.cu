@@ -66,6 +66,20 @@ struct rt_ctx {
     bool tw_sep = false;
     float *tw_t_d = nullptr;
     float4 *tw_b_d = nullptr;
+    // a table of rank two, kappa_i(T_j) = A_i1 B_1j + A_i2 B_2j with A, B >= 0: the
+    // two-column kernel of rt_tdep2.cu (A in FP64 per bin, sorted (A, nk) per bin, and
+    // (B_1j, B_1,j+1, B_2j, B_2,j+1) per interval)
+    bool r2 = false;
+    double *fac_a_d = nullptr;
+    float4 *r2_ab = nullptr, *r2_bw = nullptr;
+    // lookup-table comparator (rt_lut.cu): table, reference opacity, tolerance and the
+    // table fingerprint it was built for; per-call count of warp-slots that fell back
+    float2 *lut = nullptr;
+    unsigned *lut_count = nullptr;
+    double lut_kref = 0.0;
+    float lut_tol = -1.0f;
+    unsigned long long lut_fp = 0;
+    bool lut_on = false;  // rt_irradiate_lut is tracing
     int *order_d = nullptr;
     unsigned long long fingerprint = 0;
     // learned surrogate (rt_surrogate.cu), created by rt_surrogate_train / _load
@@ -143,13 +157,27 @@ bool use_tw(const rt_ctx *c)
     return rt::ray_shapes_tw(c->precision, c->nr, s, 16) > 0;
 }
 
-int table_kind(const rt_ctx *c) { return c->n_t <= 0 ? RT_TABLE_NU : (use_tw(c) ? RT_TABLE_NU_T_SEPARABLE : RT_TABLE_NU_T); }
+// A table of rank two goes through the two-column kernel of rt_tdep2.cu (FP32 modes).
+bool use_r2(const rt_ctx *c)
+{
+    if (c->n_t <= 0 || !c->r2 || use_tw(c) || c->precision == RT_FP64) return false;
+    Shape s[16];
+    return rt::tdep2_shapes(c->nr, s, 16) > 0;
+}
+
+int table_kind(const rt_ctx *c)
+{
+    if (c->n_t <= 0) return RT_TABLE_NU;
+    if (use_tw(c)) return RT_TABLE_NU_T_SEPARABLE;
+    return use_r2(c) ? RT_TABLE_NU_T_RANK2 : RT_TABLE_NU_T;
+}
 
 // every compiled shape that applies to this context: tile shapes, then ray shapes
 int all_shapes(const rt_ctx *c, Shape *out, int max_out)
 {
     if (c->n_t > 0) return use_tw(c) ? rt::ray_shapes_tw(c->precision, c->nr, out, max_out)
-                                     : rt::tdep_shapes(c->nr, out, max_out);
+                                     : use_r2(c) ? rt::tdep2_shapes(c->nr, out, max_out)
+                                                 : rt::tdep_shapes(c->nr, out, max_out);
     int n = rt::trace_shapes(c->precision, out, max_out);
     if (c->precision != RT_FP64) n += rt::ray_shapes(c->precision, c->nr, out + n, max_out - n);
     return n;
@@ -160,7 +188,7 @@ Shape default_shape(const rt_ctx *c)
     const bool tw = use_tw(c);
     if (c->n_t > 0 && !tw) {  // temperature-dependent table: the fewest cells per lane that hold a ray
         Shape ts[16];
-        const int n = rt::tdep_shapes(c->nr, ts, 16);
+        const int n = use_r2(c) ? rt::tdep2_shapes(c->nr, ts, 16) : rt::tdep_shapes(c->nr, ts, 16);
         int bi = -1;
         for (int i = 0; i < n; ++i)
             if (bi < 0 || ts[i].cells_per_lane < ts[bi].cells_per_lane ||
@@ -225,6 +253,11 @@ int finalize(rt_ctx *c)
         e = rt::launch_build_tdep(c->sc_h.n_active, c->sc_h.nnu_pad, c->n_t, c->kappa_t_d, c->order_d, c->kt2,
                                   c->stream);
         if (e != cudaSuccess) return cuda_fail(c, "build temperature table", e);
+        if (c->r2) {
+            e = rt::launch_build_rank2(c->sc_h.n_active, c->sc_h.nnu_pad, c->fac_a_d, c->order_d, c->r2_ab,
+                                       c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, "build rank-two table", e);
+        }
         RT_CK(c, cudaStreamSynchronize(c->stream));
     }
     if (!c->shape_forced) c->shape = default_shape(c);
@@ -295,6 +328,9 @@ int trace_range(rt_ctx *c, const float *rho, const float *td, float *q, float *a
     args.n_active = c->sc_h.n_active;
     args.t_sub = (float)c->t_sub;
     const bool tw = use_tw(c);
+    args.lut = c->lut_on ? c->lut : nullptr;
+    args.lut_kref = (float)c->lut_kref;
+    args.lut_fallback = c->lut_on ? c->lut_count : nullptr;
     args.tw_t = tw ? c->tw_t_d : nullptr;
     args.tw_b = tw ? c->tw_b_d : nullptr;
     args.n_tw = tw ? c->n_t : 0;
@@ -313,8 +349,12 @@ int trace_range(rt_ctx *c, const float *rho, const float *td, float *q, float *a
         args.nrays = (unsigned)nr_c;
         const long long nt = (nr_c * (c->nr + 1) + T - 1) / T;
         unsigned grid = 0;
-        cudaError_t e = (c->n_t > 0 && !tw) ? rt::launch_tdep(s, args, c->kt2, c->tg32, c->n_t, stream, &grid)
-                                            : rt::launch_trace(c->precision, s, args, (unsigned)nt, stream, &grid);
+        cudaError_t e;
+        if (c->n_t > 0 && !tw)
+            e = use_r2(c) ? rt::launch_tdep2(s, args, c->r2_ab, c->r2_bw, c->tg32, c->n_t, stream, &grid)
+                          : rt::launch_tdep(s, args, c->kt2, c->tg32, c->n_t, stream, &grid);
+        else
+            e = rt::launch_trace(c->precision, s, args, (unsigned)nt, stream, &grid);
         if (e != cudaSuccess) return cuda_fail(c, "trace kernel launch", e);
         *npart += grid;
     }
@@ -377,7 +417,8 @@ void free_all(rt_ctx *c)
     void *ptrs[] = {c->r_if, c->theta_if, c->phi_if, c->rtab, c->rtab64, c->domega, c->domega32, c->nu_mid,
                     c->kappa, c->f_bin, c->nu_tab, c->kap, c->nu64, c->sc, c->partials, c->bad,
                     c->energy_d, c->h_rho, c->h_t, c->h_q, c->h_a, c->temp_lkp, c->kappa_t_d,
-                    c->tg32, c->kt2, c->order_d, c->tw_t_d, c->tw_b_d};
+                    c->tg32, c->kt2, c->order_d, c->tw_t_d, c->tw_b_d, c->fac_a_d, c->r2_ab, c->r2_bw,
+                    c->lut, c->lut_count};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->energy_h) cudaFreeHost(c->energy_h);
@@ -564,6 +605,7 @@ int rt_set_opacity_table(rt_ctx *ctx, int n_nu, const double *nu_mid, const doub
     ctx->kappa_bf16 = kappa_bf16 ? 1 : 0;
     ctx->n_t = 0;
     ctx->tw_sep = false;
+    ctx->r2 = false;
     ctx->tgrid_h.clear();
     ctx->kappa_t_h.clear();
     ctx->nu_h.assign(nu_mid, nu_mid + n_nu);
@@ -580,6 +622,86 @@ int rt_set_opacity_table(rt_ctx *ctx, int n_nu, const double *nu_mid, const doub
     ctx->have_table = true;
     return finalize(ctx);
 }
+
+namespace {
+
+// Is the table [n_nu][n_t] of rank two with non-negative factors? In the plane of its
+// columns every column is a non-negative vector, so all of them lie in the cone of the
+// two columns with the smallest and the largest angle, and each column is a
+// non-negative combination of those two:
+//   kappa[i][j] = a[i][0] b[0][j] + a[i][1] b[1][j],  a = the two columns.
+// The plane: u along the longest column, v along the largest residual orthogonal to
+// it. Accepted when every entry is reproduced to 1e-10 of itself (FP64).
+bool rank_two(const double *kappa, int n_nu, int n_t, std::vector<double> &a, std::vector<double> &b)
+{
+    auto col = [&](int i, int j) { return kappa[(size_t)i * n_t + j]; };
+    std::vector<double> nrm(n_t, 0.0);
+    int j1 = 0;
+    for (int j = 0; j < n_t; ++j) {
+        for (int i = 0; i < n_nu; ++i) nrm[j] += col(i, j) * col(i, j);
+        nrm[j] = std::sqrt(nrm[j]);
+        if (nrm[j] > nrm[j1]) j1 = j;
+    }
+    if (!(nrm[j1] > 0.0)) return false;
+    std::vector<double> u(n_nu), v(n_nu, 0.0);
+    for (int i = 0; i < n_nu; ++i) u[i] = col(i, j1) / nrm[j1];
+    auto dot = [&](const std::vector<double> &w, int j) {
+        double d = 0.0;
+        for (int i = 0; i < n_nu; ++i) d += w[i] * col(i, j);
+        return d;
+    };
+    int j2 = -1;
+    double rmax = 0.0;
+    for (int j = 0; j < n_t; ++j) {
+        const double pu = dot(u, j);
+        double r = 0.0;
+        for (int i = 0; i < n_nu; ++i) r += (col(i, j) - pu * u[i]) * (col(i, j) - pu * u[i]);
+        if (r > rmax) { rmax = r; j2 = j; }
+    }
+    if (j2 < 0 || !(std::sqrt(rmax) > 1e-12 * nrm[j1])) return false;  // one direction: not rank two
+    const double pu2 = dot(u, j2);
+    double vn = 0.0;
+    for (int i = 0; i < n_nu; ++i) {
+        v[i] = col(i, j2) - pu2 * u[i];
+        vn += v[i] * v[i];
+    }
+    vn = std::sqrt(vn);
+    for (int i = 0; i < n_nu; ++i) v[i] /= vn;
+    std::vector<double> pu(n_t), pv(n_t);
+    int jlo = -1, jhi = -1;
+    double tlo = 0.0, thi = 0.0;
+    for (int j = 0; j < n_t; ++j) {
+        pu[j] = dot(u, j);
+        pv[j] = dot(v, j);
+        if (!(nrm[j] > 0.0)) continue;
+        const double th = std::atan2(pv[j], pu[j]);
+        if (jlo < 0 || th < tlo) { jlo = j; tlo = th; }
+        if (jhi < 0 || th > thi) { jhi = j; thi = th; }
+    }
+    const double det = pu[jlo] * pv[jhi] - pu[jhi] * pv[jlo];
+    if (jlo == jhi || !(det != 0.0)) return false;
+    a.assign((size_t)2 * n_nu, 0.0);
+    b.assign((size_t)2 * n_t, 0.0);
+    for (int i = 0; i < n_nu; ++i) {
+        a[2 * i] = col(i, jlo);
+        a[2 * i + 1] = col(i, jhi);
+    }
+    for (int j = 0; j < n_t; ++j) {
+        // (pu, pv)_j = x (pu, pv)_lo + y (pu, pv)_hi; rounding may leave a tiny negative
+        const double x = (pu[j] * pv[jhi] - pu[jhi] * pv[j]) / det;
+        const double y = (pu[jlo] * pv[j] - pu[j] * pv[jlo]) / det;
+        b[j] = std::max(x, 0.0);
+        b[n_t + j] = std::max(y, 0.0);
+    }
+    for (int i = 0; i < n_nu; ++i)
+        for (int j = 0; j < n_t; ++j) {
+            const double have = col(i, j), want = a[2 * i] * b[j] + a[2 * i + 1] * b[n_t + j];
+            if (std::fabs(have - want) > 1e-10 * std::max(std::fabs(have), std::fabs(want))) return false;
+        }
+    return true;
+}
+
+}  // namespace
 
 int rt_set_opacity_table_t(rt_ctx *ctx, int n_nu, const double *nu_mid, int n_t, const double *t_grid,
                            const double *kappa_t, double t_sub)
@@ -655,6 +777,29 @@ int rt_set_opacity_table_t(rt_ctx *ctx, int n_nu, const double *nu_mid, int n_t,
         RT_CK(ctx, cudaMemcpyAsync(ctx->tw_b_d, tw_b, sizeof(tw_b), cudaMemcpyHostToDevice, ctx->stream));
     }
     ctx->tw_sep = sep;
+    // not separable: is it of rank two?
+    std::vector<double> fa, fb;
+    const bool r2 = !sep && rank_two(kappa_t, n_nu, n_t, fa, fb);
+    if (r2) {
+        float4 bw[rt::kMaxTdepPoints];
+        for (int j = 0; j < rt::kMaxTdepPoints; ++j) {
+            const int j0 = j < n_t ? j : n_t - 1, j1 = j + 1 < n_t ? j + 1 : n_t - 1;
+            bw[j] = make_float4((float)fb[j0], (float)fb[j1], (float)fb[n_t + j0], (float)fb[n_t + j1]);
+        }
+        if (!ctx->fac_a_d) {
+            bool ok = dalloc(&ctx->fac_a_d, (size_t)2 * RT_MAX_NU) == cudaSuccess &&
+                      dalloc(&ctx->r2_ab, (size_t)RT_MAX_NU + rt::kNuPad) == cudaSuccess &&
+                      dalloc(&ctx->r2_bw, rt::kMaxTdepPoints) == cudaSuccess;
+            if (!ok) {
+                cudaGetLastError();
+                return fail(ctx, RT_ERR_NO_MEMORY, "cannot allocate the rank-two table");
+            }
+        }
+        RT_CK(ctx, cudaMemcpyAsync(ctx->fac_a_d, fa.data(), sizeof(double) * fa.size(), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+        RT_CK(ctx, cudaMemcpyAsync(ctx->r2_bw, bw, sizeof(bw), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    ctx->r2 = r2;
     RT_CK(ctx, cudaMemcpyAsync(ctx->nu_mid, nu_mid, sizeof(double) * n_nu, cudaMemcpyHostToDevice, ctx->stream));
     RT_CK(ctx, cudaMemcpyAsync(ctx->kappa, kmax.data(), sizeof(double) * n_nu, cudaMemcpyHostToDevice, ctx->stream));
     RT_CK(ctx, cudaMemcpyAsync(ctx->kappa_t_d, kappa_t, sizeof(double) * n_nu * n_t, cudaMemcpyHostToDevice,
@@ -822,6 +967,78 @@ int rt_energy_last(rt_ctx *ctx, rt_energy *out)
     if (!ctx->traced) return fail(ctx, RT_ERR_NOT_CONFIGURED, "nothing traced yet");
     RT_CK(ctx, cudaSetDevice(ctx->dev));
     return read_energy(ctx, out);
+}
+
+int rt_lut_build(rt_ctx *ctx, float err_tol)
+{
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (!ctx->configured) return fail(ctx, RT_ERR_NOT_CONFIGURED, "call rt_set_star and rt_set_opacity_table first");
+    if (ctx->n_t > 0) return fail(ctx, RT_ERR_INVALID_ARG, "the lookup table needs an opacity table kappa(nu)");
+    if (ctx->precision == RT_FP64) return fail(ctx, RT_ERR_INVALID_ARG, "the lookup table is for the FP32 precisions");
+    if (!(err_tol > 0.0f) || !(err_tol < 1.0f)) return fail(ctx, RT_ERR_INVALID_ARG, "err_tol must be in (0, 1)");
+    RT_CK(ctx, cudaSetDevice(ctx->dev));
+    const int na = ctx->sc_h.n_active;
+    if (na < 1) return fail(ctx, RT_ERR_INVALID_ARG, "the table has no bin with kappa > 0");
+    // kappa_ref = sum_i w_i kappa_i / sum_i w_i from the tracer's own bin table
+    std::vector<NuEntry> nu(na);
+    RT_CK(ctx, cudaMemcpyAsync(nu.data(), ctx->nu_tab, sizeof(NuEntry) * na, cudaMemcpyDeviceToHost, ctx->stream));
+    RT_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    double sw = 0.0, swk = 0.0;
+    for (const NuEntry &e : nu) {
+        const double w = exp2((double)e.lf);
+        sw += w;
+        swk += w * -(double)e.nk * rt::kLn2;
+    }
+    if (!(sw > 0.0) || !(swk > 0.0)) return fail(ctx, RT_ERR_INVALID_ARG, "no stellar flux in the absorbing bins");
+    const size_t n = (size_t)rt::kLutNs * rt::kLutNd;
+    if (!ctx->lut) {
+        bool ok = dalloc(&ctx->lut, n) == cudaSuccess && dalloc(&ctx->lut_count, 1) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            return fail(ctx, RT_ERR_NO_MEMORY, "cannot allocate the lookup table");
+        }
+    }
+    float *raw = nullptr;
+    if (dalloc(&raw, n) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, RT_ERR_NO_MEMORY, "cannot allocate the lookup table's scratch");
+    }
+    ctx->lut_kref = swk / sw;
+    cudaError_t e = rt::launch_build_lut(ctx->nu_tab, ctx->sc, ctx->lut_kref, raw, ctx->lut, err_tol, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(raw);
+    if (e != cudaSuccess) return cuda_fail(ctx, "lookup table", e);
+    ctx->lut_tol = err_tol;
+    ctx->lut_fp = ctx->fingerprint;
+    return RT_OK;
+}
+
+int rt_irradiate_lut(rt_ctx *ctx, const float *rho, const float *t_dust, float *q_abs, float *a_rad,
+                     rt_energy *energy, unsigned *fallback_slots)
+{
+    int st = check_call(ctx, rho, t_dust, q_abs, a_rad);
+    if (st != RT_OK) return st;
+    if (!ctx->lut || ctx->lut_fp != ctx->fingerprint || ctx->n_t > 0)
+        return fail(ctx, RT_ERR_NOT_CONFIGURED, "build the lookup table for this opacity table and star first");
+    Shape cand[16];
+    const int nc = rt::ray_shapes_lut(ctx->precision, ctx->nr, cand, 16);
+    if (nc < 1) return fail(ctx, RT_ERR_INVALID_ARG, "the lookup table needs rays of at most 512 cells");
+    Shape s = cand[0];
+    for (int i = 0; i < nc; ++i)  // the context's own shape where it is compiled with the table
+        if (cand[i].cells_per_lane == ctx->shape.cells_per_lane && cand[i].warps == ctx->shape.warps &&
+            cand[i].min_blocks == ctx->shape.min_blocks && ctx->shape.kind == rt::kKindRay)
+            s = cand[i];
+    if (fallback_slots) RT_CK(ctx, cudaMemsetAsync(ctx->lut_count, 0, sizeof(unsigned), ctx->stream));
+    ctx->lut_on = true;
+    st = trace(ctx, rho, t_dust, q_abs, a_rad, s);
+    ctx->lut_on = false;
+    if (st != RT_OK) return st;
+    if (fallback_slots) {
+        RT_CK(ctx, cudaMemcpyAsync(fallback_slots, ctx->lut_count, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+        RT_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    if (!energy) return RT_OK;
+    return read_energy(ctx, energy);
 }
 
 int rt_opacity_table_kind(const rt_ctx *ctx, int *kind)

@@ -86,6 +86,14 @@ struct alignas(32) RadRow64 {
 // Most temperature points of a temperature-dependent opacity table
 constexpr int kMaxTdepPoints = 32;
 
+// The lookup-table comparator's grid: s = log2(kappa_ref N_in + 2^-20) in [-20, 8],
+// d = log2(kappa_ref dN + 2^-30) in [-30, 8], both in steps of 1/32 (rt_lut.cu).
+constexpr int kLutNs = 897;
+constexpr int kLutNd = 1217;
+constexpr float kLutS0 = -20.0f;
+constexpr float kLutD0 = -30.0f;
+constexpr float kLutInvH = 32.0f;
+
 // Largest flattened length one launch of the tracer covers; longer grids are
 // split into ray chunks by the host.
 constexpr long long kMaxLaunchCells = (1LL << 31) - (1LL << 16);
@@ -118,6 +126,14 @@ struct TraceArgs {
     // the bin's largest tabulated value): the column of a cell is weighted by b(T),
     // linear between the points of the temperature grid and held beyond its ends.
     // n_tw = 0: no weight (a table of kappa(nu) only).
+    // Lookup-table comparator (rt_lut.cu): when lut is set, log2 G of every cell comes
+    // from the bilinear table instead of the per-bin sum; a warp-slot holding a cell in
+    // a flagged square (or off the table) takes the per-bin sum (one count per such
+    // slot into lut_fallback, if set).
+    const float2 *lut;        // [kLutNd][kLutNs] (log2 G at (s_i, d_j), at (s_{i+1}, d_j)); the lowest
+                              // mantissa bit of .x: square (i, j) flagged
+    float lut_kref;           // the reference opacity of the table's optical depths
+    unsigned *lut_fallback;
     const float *tw_t;        // [kMaxTdepPoints] grid (K), padded with +Inf
     const float4 *tw_b;       // [kMaxTdepPoints] (T_j, T_{j+1}, b_j / dT, b_{j+1} / dT) per interval;
                               // (T_last, T_last + 1, b_last, b_last) from the last point on
@@ -153,6 +169,8 @@ int trace_shapes(int precision, Shape *out, int max_out);      // tile kernel
 int ray_shapes(int precision, int nr, Shape *out, int max_out);  // ray kernel, 32 C >= nr
 // ray-kernel shapes compiled with the column weight of a separable kappa(nu, T) table
 int ray_shapes_tw(int precision, int nr, Shape *out, int max_out);
+// ray-kernel shapes compiled with the lookup-table comparator
+int ray_shapes_lut(int precision, int nr, Shape *out, int max_out);
 long long trace_tile_cells(Shape s);
 cudaError_t launch_ray_shape(int precision, Shape s, const TraceArgs &args, cudaStream_t stream,
                              unsigned *grid_out, unsigned max_grid = 0);
@@ -162,12 +180,23 @@ cudaError_t launch_ray_shape(int precision, Shape s, const TraceArgs &args, cuda
 cudaError_t launch_trace(int precision, Shape s, const TraceArgs &args, unsigned ntiles,
                          cudaStream_t stream, unsigned *grid_out, unsigned max_grid = 0);
 
+// Lookup-table comparator (rt_lut.cu): builds the [kLutNd][kLutNs] table of log2 G
+// pairs with square flags for the tolerance tol (raw: kLutNs * kLutNd floats of scratch)
+cudaError_t launch_build_lut(const NuEntry *nu, const DevScalars *sc, double kref, float *raw, float2 *tab, double tol,
+                             cudaStream_t st);
+
 // Tracer with temperature-dependent opacity tables (rt_tdep.cu)
 int tdep_shapes(int nr, Shape *out, int max_out);
 cudaError_t launch_tdep(Shape s, const TraceArgs &args, const float2 *kt2, const float *tg, int n_t,
                         cudaStream_t stream, unsigned *grid_out);
 cudaError_t launch_build_tdep(int n_active, int nnu_pad, int n_t, const double *kappa_t, const int *order,
                               float2 *kt2, cudaStream_t stream);
+// Tracer for kappa(nu, T) tables of rank two: two columns per ray (rt_tdep2.cu)
+int tdep2_shapes(int nr, Shape *out, int max_out);
+cudaError_t launch_tdep2(Shape s, const TraceArgs &args, const float4 *ab, const float4 *bw, const float *tg, int n_t,
+                         cudaStream_t stream, unsigned *grid_out);
+cudaError_t launch_build_rank2(int n_active, int nnu_pad, const double *fac_a, const int *order, float4 *ab,
+                               cudaStream_t stream);
 
 // A configured context's device tables, for the batch launcher (rt_api.cu).
 struct CtxView {

@@ -8,7 +8,7 @@
 namespace rt {
 namespace {
 
-template <int C, int W, int MODE, int MINB, int G, int P, bool TW>
+template <int C, int W, int MODE, int MINB, int G, int P, bool TW, bool LUT>
 __global__ void __launch_bounds__(W * 32, MINB) k_ray(const TraceArgs p)
 {
     using ESum = KahanSum;
@@ -28,8 +28,8 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray(const TraceArgs p)
     eesc.zero();
     const unsigned slots = (p.nrays + R - 1) / R;
     constexpr int WG = W / P;  // ray groups per CTA
-    ray_slots<C, W, MODE, G, P, TW>(p, blockIdx.x * WG + warp / P, slots, gridDim.x * WG, rs, s_kap, s_nu, s_mom,
-                                    eabs, eesc);
+    ray_slots<C, W, MODE, G, P, TW, LUT>(p, blockIdx.x * WG + warp / P, slots, gridDim.x * WG, rs, s_kap, s_nu,
+                                         s_mom, eabs, eesc);
 
     for (int o = 16; o > 0; o >>= 1) {
         eabs.add(eabs.shfl_xor(o));
@@ -44,12 +44,12 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray(const TraceArgs p)
     }
 }
 
-template <int C, int W, int MODE, int MINB, int G, int P, bool TW>
+template <int C, int W, int MODE, int MINB, int G, int P, bool TW, bool LUT>
 cudaError_t launch_ray_g(const TraceArgs &a, cudaStream_t stream, unsigned *grid_out, unsigned max_grid)
 {
     constexpr int R = 32 / G;
     const size_t smem = ray_bin_smem(a.nnu_pad) + 16;
-    auto kern = k_ray<C, W, MODE, MINB, G, P, TW>;
+    auto kern = k_ray<C, W, MODE, MINB, G, P, TW, LUT>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -72,15 +72,15 @@ cudaError_t launch_ray_g(const TraceArgs &a, cudaStream_t stream, unsigned *grid
 
 // The fewest lanes per ray that still hold the ray: 8, 16 or 32 (G C >= nr), else two
 // warps per ray (ray_warps_per_ray).
-template <int C, int W, int MODE, int MINB, bool TW = false>
+template <int C, int W, int MODE, int MINB, bool TW = false, bool LUT = false>
 cudaError_t launch_ray(const TraceArgs &a, unsigned, cudaStream_t stream, unsigned *grid_out, unsigned max_grid)
 {
-    if ((a.n_tw > 0) != TW) return cudaErrorInvalidValue;
-    if (8 * C >= a.nr) return launch_ray_g<C, W, MODE, MINB, 8, 1, TW>(a, stream, grid_out, max_grid);
-    if (16 * C >= a.nr) return launch_ray_g<C, W, MODE, MINB, 16, 1, TW>(a, stream, grid_out, max_grid);
-    if (32 * C >= a.nr) return launch_ray_g<C, W, MODE, MINB, 32, 1, TW>(a, stream, grid_out, max_grid);
+    if ((a.n_tw > 0) != TW || (a.lut != nullptr) != LUT) return cudaErrorInvalidValue;
+    if (8 * C >= a.nr) return launch_ray_g<C, W, MODE, MINB, 8, 1, TW, LUT>(a, stream, grid_out, max_grid);
+    if (16 * C >= a.nr) return launch_ray_g<C, W, MODE, MINB, 16, 1, TW, LUT>(a, stream, grid_out, max_grid);
+    if (32 * C >= a.nr) return launch_ray_g<C, W, MODE, MINB, 32, 1, TW, LUT>(a, stream, grid_out, max_grid);
     if constexpr (C <= 8) {
-        if (64 * C >= a.nr) return launch_ray_g<C, W, MODE, MINB, 32, 2, TW>(a, stream, grid_out, max_grid);
+        if (64 * C >= a.nr) return launch_ray_g<C, W, MODE, MINB, 32, 2, TW, LUT>(a, stream, grid_out, max_grid);
     }
     return cudaErrorInvalidValue;
 }
@@ -104,6 +104,13 @@ const RayEntry kRayShapesTW[] = {
     RT_RAYW(RT_FP32_PLAIN, 8, 4, 6),  RT_RAYW(RT_FP32_PLAIN, 16, 4, 4),
 };
 #undef RT_RAYW
+// shapes compiled with the lookup-table comparator
+#define RT_RAYL(P, C, W, MB) {P, C, W, MB, &launch_ray<C, W, P, MB, false, true>}
+const RayEntry kRayShapesLUT[] = {
+    RT_RAYL(RT_FP32_KAHAN, 4, 4, 8), RT_RAYL(RT_FP32_KAHAN, 8, 4, 6), RT_RAYL(RT_FP32_KAHAN, 16, 4, 4),
+    RT_RAYL(RT_FP32_PLAIN, 8, 4, 6), RT_RAYL(RT_FP32_PLAIN, 16, 4, 4),
+};
+#undef RT_RAYL
 #undef RT_RAY
 
 }  // namespace
@@ -126,12 +133,23 @@ int ray_shapes_tw(int precision, int nr, Shape *out, int max_out)
     return n;
 }
 
+int ray_shapes_lut(int precision, int nr, Shape *out, int max_out)
+{
+    int n = 0;
+    for (const RayEntry &s : kRayShapesLUT)
+        if (s.precision == precision && ray_warps_per_ray(s.c, nr) > 0 && n < max_out)
+            out[n++] = Shape{kKindRay, s.c, s.w, s.minb};
+    return n;
+}
+
 cudaError_t launch_ray_shape(int precision, Shape s, const TraceArgs &args, cudaStream_t stream,
                              unsigned *grid_out, unsigned max_grid)
 {
-    const bool tw = args.n_tw > 0;
-    const RayEntry *tab = tw ? kRayShapesTW : kRayShapes;
-    const int ntab = tw ? (int)(sizeof(kRayShapesTW) / sizeof(RayEntry)) : (int)(sizeof(kRayShapes) / sizeof(RayEntry));
+    const bool tw = args.n_tw > 0, lut = args.lut != nullptr;
+    const RayEntry *tab = lut ? kRayShapesLUT : (tw ? kRayShapesTW : kRayShapes);
+    const int ntab = lut  ? (int)(sizeof(kRayShapesLUT) / sizeof(RayEntry))
+                     : tw ? (int)(sizeof(kRayShapesTW) / sizeof(RayEntry))
+                          : (int)(sizeof(kRayShapes) / sizeof(RayEntry));
     for (int k = 0; k < ntab; ++k) {
         const RayEntry &e = tab[k];
         if (e.precision == precision && e.c == s.cells_per_lane && e.w == s.warps &&

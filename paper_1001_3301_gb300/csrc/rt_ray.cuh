@@ -71,6 +71,14 @@ __device__ __forceinline__ void ray_tables(const TraceArgs &p, int G, RayShared<
     }
 }
 
+// the hardware log2 (absolute error near 2^-22)
+__device__ __forceinline__ float ex_lg2(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Ask L2 for `bytes` bytes from p (16-byte aligned, a multiple of 16): a hint with
 // no completion to wait for.
 __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
@@ -209,8 +217,9 @@ __device__ __forceinline__ void group_sync(int id, int n)
 // each (or, with P > 1, one ray per group of P consecutive warps, which all walk the
 // same slots); the lanes' energy sums are added to eabs / eesc. TW: the table is a
 // separable kappa(nu, T) (TraceArgs::n_tw > 0) and each cell's column carries the
-// weight b(T).
-template <int C, int W, int MODE, int G, int P = 1, bool TW = false>
+// weight b(T). LUT: the absorbed power of the cells comes from the lookup table of
+// TraceArgs::lut (the per-bin sum only in warp-slots that hold a flagged cell).
+template <int C, int W, int MODE, int G, int P = 1, bool TW = false, bool LUT = false>
 __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin, unsigned wr_end, unsigned step,
                                           const RayShared<C, P> &rs, const float *s_kap, const float4 *s_nu,
                                           const float4 *s_mom, KahanSum &eabs, KahanSum &eesc)
@@ -386,12 +395,48 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
         // with no row to shift, a few tier bins do not pay for the series
         const int bt2 = (bc > bt && (bt > 0 || bc >= 4)) ? bc : bt;
         const float *thin_row = p.kap + kKapTable + bt * kThinStride;
-        if (bt2 > 0) {
+        bool per_bin = true;
+        if constexpr (LUT) {
+            // acc = G kappa_ref dN with log2 G bilinear in (s, d); per_bin where a cell's
+            // square is flagged or the cell lies off the table (warp-uniform)
+            bool flagged = false;
+            const float kr = p.lut_kref;
+#pragma unroll
+            for (int m = 0; m < C / 2; ++m) {
+                float g2[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float dn = h ? D[m].y : D[m].x, uu = h ? U[m].y : U[m].x;
+                    const float fs = (ex_lg2(fmaf(kr, n0 + uu, 0x1p-20f)) - kLutS0) * kLutInvH;
+                    const float fd = (ex_lg2(fmaf(kr, dn, 0x1p-30f)) - kLutD0) * kLutInvH;
+                    flagged |= !(fs >= 0.0f && fs < (float)(kLutNs - 1) && fd >= 0.0f && fd < (float)(kLutNd - 1));
+                    // clamped into the table (NaN to 0), so every read stays inside it
+                    const float fsc = fminf(fmaxf(fs, 0.0f), (float)(kLutNs - 1));
+                    const float fdc = fminf(fmaxf(fd, 0.0f), (float)(kLutNd - 1));
+                    const int i = min((int)fsc, kLutNs - 2), j = min((int)fdc, kLutNd - 2);
+                    const float ts = fsc - (float)i, tdd = fdc - (float)j;
+                    // (s_i, s_{i+1}) at d_j and at d_{j+1}: two 8-byte reads, s the fast index
+                    const float2 *row = p.lut + (size_t)j * kLutNs + i;
+                    const float2 a = __ldg(row), b = __ldg(row + kLutNs);
+                    flagged |= (__float_as_uint(a.x) & 1u) != 0u;
+                    const float v0 = fmaf(tdd, b.x - a.x, a.x), v1 = fmaf(tdd, b.y - a.y, a.y);
+                    g2[h] = ex2_approx(fmaf(ts, v1 - v0, v0));
+                }
+                acc[m] = __fmul2_rn(__fmul2_rn(make_float2(g2[0], g2[1]), f2(kr)), D[m]);
+            }
+            per_bin = __any_sync(0xffffffffu, flagged);
+            if (per_bin) {
+                if (lane == 0 && p.lut_fallback) atomicAdd(p.lut_fallback, 1u);
+#pragma unroll
+                for (int m = 0; m < C / 2; ++m) acc[m] = f2(0.0f);
+            }
+        }
+        if (per_bin && bt2 > 0) {
             float F[kThinTerms + 1];
             const float s2 = lane_coefficients(thin_row, bt, bt2, s_nu, n0, F);
             lane_series<C>(F, s2, U, D, acc);
         }
-        if (bt2 < na) {  // warp-uniform
+        if (per_bin && bt2 < na) {  // warp-uniform
             // the warp's largest and smallest non-zero column decide each bin's class
             float dmax = 0.0f, dmin = INFINITY;
 #pragma unroll

@@ -211,6 +211,9 @@ extern "C" int rt_irradiate_static(const rt_grid_desc *g, double t_star, double 
     args.nnu_pad = sc.nnu_pad;
     args.n_active = sc.n_active;
     args.t_sub = (float)t_sub;
+    args.lut = nullptr;
+    args.lut_kref = 0.0f;
+    args.lut_fallback = nullptr;
     args.tw_t = nullptr;
     args.tw_b = nullptr;
     args.n_tw = 0;

@@ -140,8 +140,31 @@ class Tracer:
         check(lib.rt_energy_last(self._ctx, ctypes.byref(e)), self._ctx)
         return Energy(e)
 
+    def lut_build(self, err_tol: float = 1e-3):
+        """Build the lookup-table comparator of the per-bin sum (rt_lut_build)."""
+        check(lib.rt_lut_build(self._ctx, float(err_tol)), self._ctx)
+
+    def irradiate_lut(self, rho, t_dust, q_abs=None, a_rad=None, energy: bool = False, stats: bool = False):
+        """Trace with the per-bin sum from the lookup table. Returns (q_abs, a_rad,
+        Energy or None, warp-slots that fell back to the per-bin sum or None)."""
+        import torch
+        self._check_field(rho, "rho")
+        self._check_field(t_dust, "t_dust")
+        if q_abs is None:
+            q_abs = torch.empty(self.shape, dtype=torch.float32, device=rho.device)
+        if a_rad is None:
+            a_rad = torch.empty(self.shape, dtype=torch.float32, device=rho.device)
+        self._check_field(q_abs, "q_abs")
+        self._check_field(a_rad, "a_rad")
+        e = RtEnergy()
+        fb = ctypes.c_uint()
+        check(lib.rt_irradiate_lut(self._ctx, rho.data_ptr(), t_dust.data_ptr(), q_abs.data_ptr(), a_rad.data_ptr(),
+                                   ctypes.byref(e) if energy else None, ctypes.byref(fb) if stats else None),
+              self._ctx)
+        return q_abs, a_rad, (Energy(e) if energy else None), (fb.value if stats else None)
+
     def table_kind(self) -> int:
-        """RT_TABLE_NU, RT_TABLE_NU_T_SEPARABLE or RT_TABLE_NU_T: how the table is traced."""
+        """RT_TABLE_NU, RT_TABLE_NU_T_SEPARABLE, RT_TABLE_NU_T_RANK2 or RT_TABLE_NU_T: how the table is traced."""
         k = ctypes.c_int()
         check(lib.rt_opacity_table_kind(self._ctx, ctypes.byref(k)), self._ctx)
         return k.value

@@ -193,6 +193,23 @@ def kappa_synth_t2(nu: np.ndarray, tg: np.ndarray) -> np.ndarray:
     return kappa_synth_t(nu, tg) + np.outer(ice, 1.0 - step)
 
 
+# a third species: CO2-ice bands at 4.27 and 15.2 micron (0.06 dex wide, 25 and 12
+# cm^2/g) whose carrier evaporates near 70 K
+_CO2_BANDS = ((C_CM_S / 4.27e-4, 25.0), (C_CM_S / 15.2e-4, 12.0))
+
+
+def kappa_synth_t3(nu: np.ndarray, tg: np.ndarray) -> np.ndarray:
+    """A kappa(nu, T) [n_nu][n_t] of rank three: the table of kappa_synth_t2 plus
+    CO2-ice bands present below ~70 K (logistic step, 8 K wide)."""
+    nu = np.asarray(nu, dtype=np.float64)
+    step = 1.0 / (1.0 + np.exp(-(np.asarray(tg, dtype=np.float64) - 70.0) / 8.0))
+    lg = np.log10(nu)
+    co2 = np.zeros_like(nu)
+    for centre, amp in _CO2_BANDS:
+        co2 = co2 + amp * np.exp(-0.5 * ((lg - math.log10(centre)) / 0.06) ** 2)
+    return kappa_synth_t2(nu, tg) + np.outer(co2, 1.0 - step)
+
+
 def rho0_for_tau550(tau550: float, kappa550: float | None = None) -> float:
     """Midplane normalisation: tau550 = int_{r_min}^{r_max} rho0 (r_d/r) kappa dr
     along z = 0, i.e. rho0 = tau550 / (kappa550 r_d ln(r_max/r_min))."""

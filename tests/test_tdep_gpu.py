@@ -1,7 +1,7 @@
 """The tracer with temperature-dependent opacity tables against the FP64 oracle: a
 table that separates, kappa_i(T) = kappa_i b(T) (the one-column tracer with each
-cell's column weighted by b(T)), and one that does not (per-bin scans of Eq. 19 with
-every cell's own kappa)."""
+cell's column weighted by b(T)), a two-species table of rank two (two columns per
+ray) and a three-species one (per-bin scans of Eq. 19 with every cell's own kappa)."""
 from __future__ import annotations
 
 import numpy as np
@@ -46,7 +46,8 @@ def _run(w, tg, kt, shape=None, precision="fp32_kahan", kind=None):
     return out
 
 
-TABLES = {"separable": synth.kappa_synth_t, "two-species": synth.kappa_synth_t2}
+TABLES = {"separable": synth.kappa_synth_t, "two-species": synth.kappa_synth_t2,
+          "three-species": synth.kappa_synth_t3}
 
 
 def _tg(n):
@@ -55,12 +56,62 @@ def _tg(n):
     return synth.t_grid(n).astype(np.float32).astype(np.float64)
 
 
-def _kind(table, nr, precision="fp32_kahan", n_nu=2):
+def _separates(kt):
+    """kappa_i(T_j) = kmax_i b_j to 1e-12 of every entry, b the row of the largest kmax."""
+    kmax = kt.max(axis=1)
+    iref = int(np.argmax(kmax))
+    if kmax[iref] == 0.0:
+        return True
+    want = np.outer(kmax, kt[iref] / kmax[iref])
+    return bool(np.all(np.abs(kt - want) <= 1e-12 * np.maximum(np.abs(kt), np.abs(want))))
+
+
+def _rank_two(kt):
+    """Every column a non-negative combination of the two columns of extreme angle in
+    the plane of the columns, to 1e-10 of every entry."""
+    n = np.linalg.norm(kt, axis=0)
+    j1 = int(np.argmax(n))
+    if n[j1] == 0.0:
+        return False
+    u = kt[:, j1] / n[j1]
+    pu = u @ kt
+    r = kt - np.outer(u, pu)
+    rn = np.linalg.norm(r, axis=0)
+    j2 = int(np.argmax(rn))
+    if not rn[j2] > 1e-12 * n[j1]:
+        return False
+    pv = (r[:, j2] / rn[j2]) @ kt
+    th = np.where(n > 0, np.arctan2(pv, pu), np.nan)
+    lo, hi = int(np.nanargmin(th)), int(np.nanargmax(th))
+    det = pu[lo] * pv[hi] - pu[hi] * pv[lo]
+    if lo == hi or det == 0.0:
+        return False
+    x = np.maximum((pu * pv[hi] - pu[hi] * pv) / det, 0.0)
+    y = np.maximum((pu[lo] * pv - pu * pv[lo]) / det, 0.0)
+    want = np.outer(kt[:, lo], x) + np.outer(kt[:, hi], y)
+    return bool(np.all(np.abs(kt - want) <= 1e-10 * np.maximum(np.abs(kt), np.abs(want))))
+
+
+def _kind(kt, nr, precision="fp32_kahan"):
     """The path the library takes: the one-column tracer with the column weight where
-    the table separates (a one-bin table always does) and the rays fit its shapes."""
-    from paper_1001_3301_gb300._lib import RT_TABLE_NU_T, RT_TABLE_NU_T_SEPARABLE
-    sep = table == "separable" or n_nu == 1
-    return RT_TABLE_NU_T_SEPARABLE if (sep and nr <= 512 and precision != "fp64") else RT_TABLE_NU_T
+    the table separates and the rays fit its shapes, else the two-column kernel where
+    the table is of rank two, else the per-bin scans (FP32 arithmetic in every path)."""
+    from paper_1001_3301_gb300._lib import RT_TABLE_NU_T, RT_TABLE_NU_T_RANK2, RT_TABLE_NU_T_SEPARABLE
+    if precision == "fp64":
+        return RT_TABLE_NU_T
+    if _separates(kt):
+        return RT_TABLE_NU_T_SEPARABLE if nr <= 512 else RT_TABLE_NU_T
+    return RT_TABLE_NU_T_RANK2 if _rank_two(kt) else RT_TABLE_NU_T
+
+
+def test_synthetic_tables_take_their_kernels():
+    """The three synthetic tables on the bench's 79 bins: one per path."""
+    from paper_1001_3301_gb300._lib import RT_TABLE_NU_T, RT_TABLE_NU_T_RANK2, RT_TABLE_NU_T_SEPARABLE
+    nu = synth.disk3d(8, 2, 2, n_nu=79, tau550=1.0, seed=1).nu
+    tg = _tg(24)
+    assert _kind(synth.kappa_synth_t(nu, tg), 256) == RT_TABLE_NU_T_SEPARABLE
+    assert _kind(synth.kappa_synth_t2(nu, tg), 256) == RT_TABLE_NU_T_RANK2
+    assert _kind(synth.kappa_synth_t3(nu, tg), 256) == RT_TABLE_NU_T
 
 
 @pytest.mark.parametrize("table", sorted(TABLES))
@@ -70,7 +121,7 @@ def test_disk_against_oracle(torch, tau, table):
     tg = _tg(24)
     kt = TABLES[table](w.nu, tg)
     orc = _oracle(w, tg, kt)
-    q, a, e, _ = _run(w, tg, kt, kind=_kind(table, w.grid.nr))
+    q, a, e, _ = _run(w, tg, kt, kind=_kind(kt, w.grid.nr))
     _parity.assert_parity(w, q, a, e, orc, label=f"tdep {table} tau {tau}")
 
 
@@ -84,7 +135,7 @@ def test_ragged_all_shapes(torch, dims, table):
     tg = _tg(9)
     kt = TABLES[table](w.nu, tg)
     orc = _oracle(w, tg, kt)
-    _, _, _, shapes = _run(w, tg, kt, kind=_kind(table, nr, n_nu=nnu))
+    _, _, _, shapes = _run(w, tg, kt, kind=_kind(kt, nr))
     assert shapes and all(s[0] == 1 for s in shapes)
     for shape in shapes:
         q, a, e, _ = _run(w, tg, kt, shape=shape)
@@ -107,10 +158,40 @@ def test_separable_weight_edges(torch):
     ww = synth.Workload(w.name, w.grid, w.nu, w.kappa, w.rho, td, tau550=w.tau550)
     # (an FP64 context takes the per-bin kernel, whose arithmetic is FP32: the same 1e-5)
     for precision, rtol in (("fp32_kahan", 1e-5), ("fp32_plain", 1e-5), ("fp64", 1e-5)):
-        q, a, e, _ = _run(ww, tg, kt, precision=precision, kind=_kind("separable", 128, precision))
+        q, a, e, _ = _run(ww, tg, kt, precision=precision, kind=_kind(kt, 128, precision))
         _parity.assert_parity(ww, q, a, e, orc, rtol_q=rtol, rtol_a=rtol, label=f"edges {precision}")
         hot = (td > 1000.0) & (td <= w.t_sub)
         assert hot.any() and np.all(q[hot] == 0.0) and np.all(a[hot] == 0.0)
+
+
+def test_rank_two_edges(torch):
+    """The two-species table through the two-column kernel with zero-density dust cells
+    (the rho -> 0 limit of a_rad, kappa_i(T) from both columns), cells hotter than the
+    sublimation temperature, temperatures beyond both ends of the grid, and a species
+    whose weight is zero above 400 K; both FP32 scans."""
+    w = synth.disk3d(160, 12, 4, n_nu=48, tau550=30.0, seed=5)
+    tg = np.array([12.0, 60.0, 140.0, 160.0, 400.0, 900.0])
+    kt = synth.kappa_synth_t2(w.nu, tg)
+    kt[:, 4:] = np.outer(synth.kappa_synth(w.nu), [0.7, 0.7])   # the ice gone, silicate at 0.7
+    rho = w.rho32().copy()
+    td = w.tdust32().copy()
+    rho.reshape(-1)[::11] = 0.0                   # zero density, dust present
+    td.reshape(-1)[::7] = 5.0                     # below the grid
+    td.reshape(-1)[3::13] = 1200.0                # above the grid, below t_sub
+    assert (td > w.t_sub).any()
+    orc = oracle.irradiate_tdep(w.grid.r_if, w.grid.theta_if, w.grid.phi_if, w.t_star, w.r_star, w.nu, tg, kt,
+                                w.t_sub, rho.astype(np.float64), td.astype(np.float64), nthreads=8)
+    ww = synth.Workload(w.name, w.grid, w.nu, w.kappa, rho, td, tau550=w.tau550)
+    from paper_1001_3301_gb300._lib import RT_TABLE_NU_T_RANK2
+    assert _kind(kt, 160) == RT_TABLE_NU_T_RANK2
+    for precision in ("fp32_kahan", "fp32_plain"):
+        q, a, e, shapes = _run(ww, tg, kt, precision=precision, kind=RT_TABLE_NU_T_RANK2)
+        _parity.assert_parity(ww, q, a, e, orc, label=f"rank two edges {precision}")
+        zc = (rho == 0.0) & (td <= w.t_sub)
+        assert zc.any() and np.all(q[zc] == 0.0) and np.all(a[zc] >= 0.0) and (a[zc] > 0.0).any()
+        for shape in shapes:
+            q, a, e, _ = _run(ww, tg, kt, shape=shape, precision=precision)
+            _parity.assert_parity(ww, q, a, e, orc, label=f"rank two edges {precision} {shape}")
 
 
 def test_constant_table_matches_plain_tracer(torch):
