@@ -13,8 +13,9 @@
 // 4 y + ln a = ln(E_R + a_rad e^{-L(y)}), y = ln T, L = ln kappa_P, by Newton's
 // method in FP32 (the derivative 4 + w L'(y), 0 <= w <= 1, is positive wherever
 // the mean grows slower than T^4). Where E_R = 0 the equation is
-// 4 y + L(y) = ln a_rad - ln a: a cell reads y from the tabulated inverse of the left
-// side (built once per table) and polishes it with a Newton step.
+// 4 y + L(y) = ln a_rad - ln a: a cell reads T itself from the tabulated inverse of the
+// left side (built once per table, each interval checked against the FP64 root) and
+// takes Newton steps only in the intervals where that check failed.
 #include <math.h>
 
 #include <string>
@@ -26,11 +27,17 @@
 namespace rt {
 
 constexpr int kTempNodes = 1024;
-// the context's table buffer: lkp [kTempNodes], inv [kTempNodes + 2], then (16-byte
-// aligned) the cubic coefficients of both, [kTempNodes - 1] float4 each
-constexpr int kTempCoefLkp = ((2 * kTempNodes + 2 + 3) / 4) * 4;
+// The inverse table of T (E_R = 0) sits on the grid v = lg2 a_rad with spacing 2^-e:
+// node i at v = (v_org + i) 2^-e, v_org an integer, at most kTempInvNodes nodes.
+constexpr int kTempInvNodes = 2048;
+// the context's table buffer: lkp [kTempNodes]; 8 constants (X(y_lo), X(y_hi), 2^e,
+// v_org, the node count of the inverse table); then (16-byte aligned) the cubic
+// coefficients of lkp [kTempNodes - 1] and of the inverse table [kTempInvNodes - 1],
+// float4 each
+constexpr int kTempConsts = kTempNodes;
+constexpr int kTempCoefLkp = kTempConsts + 8;
 constexpr int kTempCoefInv = kTempCoefLkp + 4 * (kTempNodes - 1);
-constexpr int kTempTableFloats = kTempCoefInv + 4 * (kTempNodes - 1);
+constexpr int kTempTableFloats = kTempCoefInv + 4 * (kTempInvNodes - 1);
 constexpr double kTempLnLo = 0.0;                    // ln 1 K
 constexpr double kTempLnHi = 11.512925464970229;     // ln 1e5 K
 
@@ -61,45 +68,89 @@ __global__ void k_planck_mean(int n_nodes, const double *t_nodes, int n_nu, cons
     }
 }
 
-// The inverse of X(y) = 4 y + L(y) (y = ln T, L = ln kappa_P by the interpolation the
-// cells use, held constant outside the table) on kTempNodes uniform points of X between
-// X(y_lo) and X(y_hi): with E_R = 0, Eq. 16 reads X(y) = ln a_rad - ln a, so a cell's ln T
-// is this table at its X, polished by a Newton step. One CTA; bisection in FP64.
-// inv[n] = y, inv[n + 0..1] after the table: X(y_lo), X(y_hi).
-__device__ double interp_d(const float *s, double y, double y0, double inv_dy)
+// ln kappa_P by the interpolation the cells use (cubic Hermite with Catmull-Rom
+// tangents on the node table s, constant outside it), and its derivative, in FP64
+__device__ double interp_d(const float *s, double y, double y0, double inv_dy, double *deriv = nullptr)
 {
     double u = (y - y0) * inv_dy;
-    if (!(u > 0.0)) return s[0];
-    if (u >= (double)(kTempNodes - 1)) return s[kTempNodes - 1];
+    if (!(u > 0.0) || u >= (double)(kTempNodes - 1)) {
+        if (deriv) *deriv = 0.0;
+        return !(u > 0.0) ? s[0] : s[kTempNodes - 1];
+    }
     const int k = min((int)u, kTempNodes - 2);
     const double t = u - (double)k;
     const double p0 = s[k], p1 = s[k + 1];
     const double m0 = 0.5 * (p1 - s[k > 0 ? k - 1 : 0]) * (k > 0 ? 1.0 : 2.0);
     const double m1 = 0.5 * (s[k + 2 < kTempNodes ? k + 2 : kTempNodes - 1] - p0) * (k + 2 < kTempNodes ? 1.0 : 2.0);
     const double t2 = t * t, t3 = t2 * t;
+    if (deriv)
+        *deriv = ((6.0 * t2 - 6.0 * t) * p0 + (3.0 * t2 - 4.0 * t + 1.0) * m0 + (-6.0 * t2 + 6.0 * t) * p1 +
+                  (3.0 * t2 - 2.0 * t) * m1) * inv_dy;
     return (2.0 * t3 - 3.0 * t2 + 1.0) * p0 + (t3 - 2.0 * t2 + t) * m0 + (-2.0 * t3 + 3.0 * t2) * p1 + (t3 - t2) * m1;
 }
 
-__global__ void __launch_bounds__(1024) k_inverse_table(const float *lkp, float *inv, double y0, double y1)
+// the root y of 4 y + L(y) = x (bisection in [y0, y1], FP64); outside the table L is
+// constant and the root is (x - L_end) / 4
+__device__ double inverse_root(const float *s, double x, double y0, double y1, double inv_dy)
+{
+    const double x_lo = 4.0 * y0 + s[0], x_hi = 4.0 * y1 + s[kTempNodes - 1];
+    if (x <= x_lo) return 0.25 * (x - s[0]);
+    if (x >= x_hi) return 0.25 * (x - s[kTempNodes - 1]);
+    double lo = y0, hi = y1;
+    for (int it = 0; it < 64; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (4.0 * mid + interp_d(s, mid, y0, inv_dy) < x) lo = mid;
+        else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// The inverse of X(y) = 4 y + L(y) (y = ln T): with E_R = 0, Eq. 16 reads
+// X(y) = ln a_rad - ln a. The nodes are uniform in v = lg2 a_rad (spacing 2^-e, node i
+// at v = (v_org + i) 2^-e, X = v ln 2 - ln a), so a cell finds its interval and its
+// offset t in it from lg2 a_rad with exact arithmetic. Per interval the cubic Hermite
+// of T = e^y in t in [0, 1] with the exact slopes dT/dX = T / (4 + L'(y)), as
+// coefficients (c0, c1, c2, c3) like k_hermite_coeffs. Each interval is checked at 8
+// points against the FP64 root, evaluated the way a cell does (FP32 FMAs); where the
+// cubic is off by more than 4e-7 of T the lowest bit of c3 is set, and the cells
+// there polish ln T with Newton steps. One CTA.
+__global__ void __launch_bounds__(1024) k_inverse_table(const float *lkp, float *consts, float4 *c, double y0,
+                                                        double y1, double ln_a, int e, int v_org, int n_inv)
 {
     __shared__ float s[kTempNodes];
+    __shared__ double s_y[kTempInvNodes], s_m[kTempInvNodes];
     for (int i = threadIdx.x; i < kTempNodes; i += blockDim.x) s[i] = lkp[i];
     __syncthreads();
     const double inv_dy = (kTempNodes - 1) / (y1 - y0);
-    const double x_lo = 4.0 * y0 + s[0], x_hi = 4.0 * y1 + s[kTempNodes - 1];
-    for (int i = threadIdx.x; i < kTempNodes; i += blockDim.x) {
-        const double x = x_lo + (x_hi - x_lo) * i / (kTempNodes - 1);
-        double lo = y0, hi = y1;
-        for (int it = 0; it < 64; ++it) {
-            const double mid = 0.5 * (lo + hi);
-            if (4.0 * mid + interp_d(s, mid, y0, inv_dy) < x) lo = mid;
-            else hi = mid;
+    const double hv = ldexp(1.0, -e), hx = hv * kLn2;
+    auto node_x = [&](double i) { return (v_org + i) * hv * kLn2 - ln_a; };
+    for (int i = threadIdx.x; i < n_inv; i += blockDim.x) {
+        const double y = inverse_root(s, node_x(i), y0, y1, inv_dy);
+        double dl = 0.0;
+        interp_d(s, y, y0, inv_dy, &dl);
+        s_y[i] = y;
+        s_m[i] = hx * exp(y) / fmax(4.0 + dl, 0.5);  // dT/dt
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_inv - 1; k += blockDim.x) {
+        const double p0 = exp(s_y[k]), p1 = exp(s_y[k + 1]), m0 = s_m[k], m1 = s_m[k + 1];
+        const float c0 = (float)p0, c1 = (float)m0, c2 = (float)(3.0 * (p1 - p0) - 2.0 * m0 - m1);
+        const float c3 = __uint_as_float(__float_as_uint((float)(2.0 * (p0 - p1) + m0 + m1)) & ~1u);
+        bool bad = false;
+        for (int j = 0; j < 8; ++j) {
+            const float t = (j + 0.5f) * 0.125f;
+            const float tc = fmaf(fmaf(fmaf(c3, t, c2), t, c1), t, c0);
+            const double te = exp(inverse_root(s, node_x(k + (double)t), y0, y1, inv_dy));
+            bad |= !(fabs((double)tc / te - 1.0) <= 4e-7);
         }
-        inv[i] = (float)(0.5 * (lo + hi));
+        c[k] = make_float4(c0, c1, c2, __uint_as_float(__float_as_uint(c3) | (bad ? 1u : 0u)));
     }
     if (threadIdx.x == 0) {
-        inv[kTempNodes] = (float)x_lo;
-        inv[kTempNodes + 1] = (float)x_hi;
+        consts[0] = (float)(4.0 * y0 + s[0]);
+        consts[1] = (float)(4.0 * y1 + s[kTempNodes - 1]);
+        consts[2] = (float)ldexp(1.0, e);
+        consts[3] = (float)v_org;
+        consts[4] = (float)n_inv;
     }
 }
 
@@ -124,9 +175,9 @@ struct TempArgs {
     const float *e_rad;   // may be null (E_R = 0)
     float *t_out;
     const float *lkp;     // [kTempNodes] ln kappa_P on the uniform ln T grid
-    const float *inv;     // [kTempNodes + 2] ln T on the uniform grid of 4 ln T + ln kappa_P
+    const float *consts;  // X(y_lo), X(y_hi), 2^e, v_org, node count of the inverse table
     const float4 *c_lkp;  // [kTempNodes - 1] cubic coefficients of lkp per interval
-    const float4 *c_inv;  // [kTempNodes - 1] the same of inv
+    const float4 *c_inv;  // [n_inv - 1] cubic coefficients of T on the v = lg2 a_rad grid
     int vec;              // a_rad, e_rad (if any) and t_out are 16-byte aligned
     long long n;
     float y0, inv_dy;     // grid origin and 1 / spacing
@@ -170,17 +221,21 @@ __device__ __forceinline__ float exp_ex2(float y)
     return fmaf(r, lo * 0.69314718055994530942f, r);
 }
 
-// ln x for x > 0 from the hardware log2 (absolute error ~2^-22 in log2 x)
-__device__ __forceinline__ float log_lg2(float x)
+// the hardware log2 (absolute error ~2^-22)
+__device__ __forceinline__ float lg2_approx(float x)
 {
     float r;
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r * 0.69314718055994530942f;
+    return r;
 }
+
+// ln x for x > 0 from the hardware log2
+__device__ __forceinline__ float log_lg2(float x) { return lg2_approx(x) * 0.69314718055994530942f; }
 
 // The table ends and the inverse table's grid, read once per thread.
 struct TempConsts {
-    float l_lo, l_hi, i_lo, i_hi, x_lo, x_hi, inv_dx;
+    float l_lo, l_hi, v_scale, v_org, u_max;
+    int k_max;
 };
 
 // T of one cell (Eq. 16): a T^4 = E_R + a_rad / kappa_P(T); 0 where both sources vanish.
@@ -191,27 +246,33 @@ __device__ __forceinline__ float cell_temperature(const TempArgs &p, const TempC
     if (!(ar > 0.0f) && !(er > 0.0f)) return 0.0f;
     float L, dL, y;
     if (!(er > 0.0f)) {
-        // X(y) = 4 y + L(y) = ln a_rad - ln a: the inverse table, then Newton steps until one
-        // is below 2e-6 (quadratic convergence: normally the step from the table and one
-        // more that confirms it)
-        const float x = log_lg2(ar) - p.ln_a;
-        if (x <= k.x_lo) {
-            y = 0.25f * (x - k.l_lo);
-        } else if (x >= k.x_hi) {
-            y = 0.25f * (x - k.l_hi);
-        } else {
-            float yi, dyi;
-            interp_c(p.c_inv, k.i_lo, k.i_hi, x, k.x_lo, k.inv_dx, yi, dyi);
-            y = yi;
+        // X(y) = 4 y + L(y) = ln a_rad - ln a: T from the inverse table at v = lg2 a_rad.
+        // The interval index from u = v 2^e - v_org, the offset in it from one FMA with
+        // the exact integer v_org + k (so t keeps the full precision of v).
+        const float lg = lg2_approx(ar);
+        const float u = fmaf(lg, k.v_scale, -k.v_org);
+        if (u > 0.0f && u < k.u_max) {
+            const int kk = min((int)u, k.k_max);
+            const float t = fmaf(lg, k.v_scale, -(k.v_org + (float)kk));
+            const float4 q = __ldg(p.c_inv + kk);
+            const float tc = fmaf(fmaf(fmaf(q.w, t, q.z), t, q.y), t, q.x);
+            if (!(__float_as_uint(q.w) & 1u)) return tc;
+            // an interval whose cubic failed its check: Newton steps on ln T from it,
+            // until one is below 2e-6 (quadratic convergence: the root to FP32)
+            const float x = fmaf(lg, 0.69314718055994530942f, -p.ln_a);
+            y = log_lg2(tc);
+            for (int it = 0; it < 24; ++it) {
+                interp_c(p.c_lkp, k.l_lo, k.l_hi, y, p.y0, p.inv_dy, L, dL);
+                float dy = -__fdividef(4.0f * y + L - x, fmaxf(4.0f + dL, 0.5f));  // the step, not the root
+                dy = fminf(fmaxf(dy, -2.0f), 2.0f);
+                y += dy;
+                if (fabsf(dy) < 2e-6f) break;
+            }
+            return exp_ex2(y);
         }
-        for (int it = 0; it < 24; ++it) {
-            interp_c(p.c_lkp, k.l_lo, k.l_hi, y, p.y0, p.inv_dy, L, dL);
-            float dy = -__fdividef(4.0f * y + L - x, fmaxf(4.0f + dL, 0.5f));  // the step, not the root: fast divide
-            dy = fminf(fmaxf(dy, -2.0f), 2.0f);
-            y += dy;
-            if (fabsf(dy) < 2e-6f) break;
-        }
-        return exp_ex2(y);
+        // beyond the table kappa_P is held constant: the root in closed form
+        const float x = fmaf(lg, 0.69314718055994530942f, -p.ln_a);
+        return exp_ex2(0.25f * (x - (u > 0.0f ? k.l_hi : k.l_lo)));
     }
     // Newton on F(y) = 4 y + ln a - ln(E_R + a_rad e^{-L}) from 300 K's opacity; it
     // converges quadratically: once a step is below 1e-5 the next one reaches the FP32
@@ -241,17 +302,23 @@ __global__ void __launch_bounds__(256) k_dust_temperature(const TempArgs p)
     TempConsts k;
     k.l_lo = __ldg(p.lkp);
     k.l_hi = __ldg(p.lkp + kTempNodes - 1);
-    k.i_lo = __ldg(p.inv);
-    k.i_hi = __ldg(p.inv + kTempNodes - 1);
-    k.x_lo = __ldg(p.inv + kTempNodes);
-    k.x_hi = __ldg(p.inv + kTempNodes + 1);
-    k.inv_dx = (float)(kTempNodes - 1) / (k.x_hi - k.x_lo);
+    k.v_scale = __ldg(p.consts + 2);
+    k.v_org = __ldg(p.consts + 3);
+    k.k_max = (int)__ldg(p.consts + 4) - 2;
+    k.u_max = (float)(k.k_max + 1);
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long n4 = p.vec ? p.n / 4 : 0;
+    // the next quad's inputs are loaded while the current one is solved
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 an = tid < n4 ? __ldg(reinterpret_cast<const float4 *>(p.a_rad) + tid) : zero4;
+    float4 en = (tid < n4 && p.e_rad) ? __ldg(reinterpret_cast<const float4 *>(p.e_rad) + tid) : zero4;
     for (long long v = tid; v < n4; v += stride) {
-        const float4 a4 = __ldg(reinterpret_cast<const float4 *>(p.a_rad) + v);
-        const float4 e4 = p.e_rad ? __ldg(reinterpret_cast<const float4 *>(p.e_rad) + v) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 a4 = an, e4 = en;
+        if (v + stride < n4) {
+            an = __ldg(reinterpret_cast<const float4 *>(p.a_rad) + v + stride);
+            if (p.e_rad) en = __ldg(reinterpret_cast<const float4 *>(p.e_rad) + v + stride);
+        }
         float4 t4;
         t4.x = cell_temperature(p, k, a4.x, e4.x);
         t4.y = cell_temperature(p, k, a4.y, e4.y);
@@ -331,6 +398,8 @@ int rt_dust_temperature(rt_ctx *ctx, const float *a_rad, const float *e_rad, flo
     if (!in.configured) return ctx_fail(ctx, RT_ERR_NOT_CONFIGURED, "call rt_set_star and rt_set_opacity_table first");
     if (!a_rad || !t_dust) return ctx_fail(ctx, RT_ERR_INVALID_ARG, "a_rad and t_dust must be non-NULL");
     if (cudaSetDevice(in.dev) != cudaSuccess) return ctx_fail(ctx, RT_ERR_CUDA, "cudaSetDevice");
+    const double sigma = 2.0 * pow(kPi, 5) * pow(kKB, 4) / (15.0 * kH * kH * kH * kC * kC);
+    const double ln_a = log(4.0 * sigma / kC);
     float *&lkp = ctx_temp_table(ctx);
     unsigned long long &fp = ctx_temp_fingerprint(ctx);
     if (!lkp || fp != in.table_fingerprint) {
@@ -345,26 +414,41 @@ int rt_dust_temperature(rt_ctx *ctx, const float *a_rad, const float *e_rad, flo
         std::string err;
         const int rc = planck_means(in, tn, nullptr, lkp, in.stream, err);
         if (rc != RT_OK) return ctx_fail(ctx, rc, err);
-        k_inverse_table<<<1, 1024, 0, in.stream>>>(lkp, lkp + kTempNodes, kTempLnLo, kTempLnHi);
+        // the inverse table's grid in v = lg2 a_rad: the finest spacing 2^-e whose nodes
+        // (whole steps from v_org) cover X(y_lo)..X(y_hi) within kTempInvNodes
+        float ends[2];
+        if (cudaMemcpyAsync(&ends[0], lkp, sizeof(float), cudaMemcpyDeviceToHost, in.stream) != cudaSuccess ||
+            cudaMemcpyAsync(&ends[1], lkp + kTempNodes - 1, sizeof(float), cudaMemcpyDeviceToHost, in.stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(in.stream) != cudaSuccess)
+            return ctx_fail(ctx, RT_ERR_CUDA, "Planck-mean table ends");
+        const double v_lo = (4.0 * kTempLnLo + ends[0] + ln_a) / kLn2, v_hi = (4.0 * kTempLnHi + ends[1] + ln_a) / kLn2;
+        int e = 6, v_org = 0, n_inv = 0;
+        for (; e >= 0; --e) {
+            v_org = (int)floor(ldexp(v_lo, e));
+            n_inv = (int)ceil(ldexp(v_hi, e)) - v_org + 1;
+            if (n_inv <= kTempInvNodes) break;
+        }
+        if (e < 0 || n_inv < 2) return ctx_fail(ctx, RT_ERR_INVALID_ARG, "Planck mean outside the tabulated range");
+        k_inverse_table<<<1, 1024, 0, in.stream>>>(lkp, lkp + kTempConsts, reinterpret_cast<float4 *>(lkp + kTempCoefInv),
+                                                   kTempLnLo, kTempLnHi, ln_a, e, v_org, n_inv);
         k_hermite_coeffs<<<4, 256, 0, in.stream>>>(lkp, reinterpret_cast<float4 *>(lkp + kTempCoefLkp));
-        k_hermite_coeffs<<<4, 256, 0, in.stream>>>(lkp + kTempNodes, reinterpret_cast<float4 *>(lkp + kTempCoefInv));
         if (cudaGetLastError() != cudaSuccess) return ctx_fail(ctx, RT_ERR_CUDA, "inverse temperature table");
         fp = in.table_fingerprint;
     }
-    const double sigma = 2.0 * pow(kPi, 5) * pow(kKB, 4) / (15.0 * kH * kH * kH * kC * kC);
     TempArgs p;
     p.a_rad = a_rad;
     p.e_rad = e_rad;
     p.t_out = t_dust;
     p.lkp = lkp;
-    p.inv = lkp + kTempNodes;
+    p.consts = lkp + kTempConsts;
     p.c_lkp = reinterpret_cast<const float4 *>(lkp + kTempCoefLkp);
     p.c_inv = reinterpret_cast<const float4 *>(lkp + kTempCoefInv);
     p.vec = ((reinterpret_cast<size_t>(a_rad) | reinterpret_cast<size_t>(e_rad) | reinterpret_cast<size_t>(t_dust)) % 16) == 0;
     p.n = in.ncells;
     p.y0 = (float)kTempLnLo;
     p.inv_dy = (float)((kTempNodes - 1) / (kTempLnHi - kTempLnLo));
-    p.ln_a = (float)log(4.0 * sigma / kC);
+    p.ln_a = (float)ln_a;
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, in.dev);
     long long blocks = (in.ncells / 4 + 255) / 256;

@@ -67,6 +67,30 @@ def test_dust_temperature_matches_oracle(torch, tau):
     tr.close()
 
 
+@pytest.mark.parametrize("table", ["disk", "step"])
+def test_dust_temperature_whole_range(torch, table):
+    """E_R = 0 over the whole range of a_rad: temperatures from 0.3 K to 3e5 K (beyond
+    both ends of the tabulated mean, and densely around them, where the inverse table
+    bends), for the disk's opacities and for a table that steps by 1e3 at 30 micron
+    (a steep Planck mean). Every cell against the oracle's FP64 bisection."""
+    w = synth.disk3d(40, 25, 20, n_nu=79, tau550=1.0, seed=1)   # 20,000 cells, one per temperature
+    kappa = w.kappa if table == "disk" else np.where(w.nu > synth.C_CM_S / 30e-4, 1e3, 1.0)
+    tr = _tracer(w, kappa=kappa)
+    a_const = 4 * 5.670374419e-5 / 2.99792458e10
+    rng = np.random.default_rng(11)
+    t_want = np.concatenate([10 ** rng.uniform(np.log10(0.3), np.log10(3e5), 16_000),
+                             10 ** rng.uniform(-0.05, 0.05, 2_000), 1e5 * 10 ** rng.uniform(-0.05, 0.05, 2_000)])
+    kp = np.array([oracle.planck_mean(min(max(t, 1.0), 1e5), w.nu, kappa) for t in np.geomspace(0.3, 3e5, 64)])
+    kp_i = np.exp(np.interp(np.log(t_want), np.log(np.geomspace(0.3, 3e5, 64)), np.log(kp)))
+    a = (a_const * t_want ** 4 * kp_i).astype(np.float32).reshape(w.grid.shape)  # about those temperatures
+    assert np.all(a > 0)
+    got = tr.dust_temperature(torch.from_numpy(a).cuda()).double().cpu().numpy()
+    ref = oracle.dust_temperature(a.astype(np.float64), None, w.nu, kappa)
+    rel = np.abs(got / ref - 1)
+    assert rel.max() < RTOL_T, (rel.max(), ref[np.argmax(rel)])
+    tr.close()
+
+
 def test_zero_source_gives_zero(torch):
     w = synth.disk2d(16, 8, 16)
     tr = _tracer(w)
