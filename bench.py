@@ -47,6 +47,8 @@ NNU = 79
 NR, NTH, NPH = 256, 128, 256
 # rt_opacity_table_kind values
 TABLE_KINDS = ("nu", "nu_t_separable", "nu_t", "nu_t_rank2")
+# tracer kernels (RT_KERNEL_*)
+KERNEL_KINDS = ("tile", "ray", "ray_chunked")
 
 
 def workload_name(spec, taus):
@@ -84,7 +86,7 @@ TRACE_BYTES_PER_CELL = 16
 # the roofline fraction the tracer is meant to reach on its binding floor
 ROOFLINE_TARGET = 0.6
 PROFILE_DIR = os.path.join(ROOT, "profiles")
-KERNEL_SOURCES = ("rt_ray.cu", "rt_ray.cuh", "rt_device.cuh", "rt_internal.cuh")
+KERNEL_SOURCES = ("rt_ray.cu", "rt_ray_mc.cu", "rt_ray.cuh", "rt_device.cuh", "rt_internal.cuh")
 
 
 def parse():
@@ -235,12 +237,35 @@ def _warp_partition(w, shape):
     column of one lane's C cells; the tier is used when it adds bins and either a thin
     row exists or it adds >= 4). A warp holds R = 32 / G rays of G lanes of C cells
     where 32 C cells hold a ray; for C <= 8 and rays of up to 64 C cells, two warps
-    share a ray (each 32 C of its cells, N_max the ray's total)."""
+    share a ray (each 32 C of its cells, N_max the ray's total). The chunked kernel
+    (kind 2) counts per warp and chunk: 4 rays of 8 lanes, N_max the largest column at
+    the chunk's end, and its last live bin (na: kappa_i N <= 127 ln 2 at the smallest
+    column in front of a lane; the bins after it underflow and are skipped). Returns
+    cells, bt, bt2 and na per unit (na a single value but for the chunked kernel)."""
     nr, c = w.grid.nr, shape[1]
     dust = w.tdust32() <= w.t_sub
     col = (np.where(dust, w.rho32().astype(np.float64), 0.0) * np.diff(w.grid.r_if)).reshape(-1, nr)
     kap = np.sort(w.kappa[w.kappa > 0])
-    if 32 * c < nr:   # two warps per ray
+    na = np.full(1, len(kap))
+    if shape[0] == 2:   # chunked: 4 rays of 8 lanes per warp, chunks of 8 C cells
+        L = 8 * c
+        nch = -(-nr // L)
+        nrays = col.shape[0]
+        nw = -(-nrays // 4)
+        colp = np.zeros((nw * 4, nch * L))
+        colp[:nrays, :nr] = col
+        valid = np.zeros((nw * 4, nch * L), dtype=bool)
+        valid[:nrays, :nr] = True
+        lane = colp.reshape(nw, 4, nch * 8, c).sum(axis=3)           # lane sums, chunks and lanes in ray order
+        end = np.cumsum(lane, axis=2)
+        start = (end - lane).reshape(nw, 4, nch, 8)
+        end = end.reshape(nw, 4, nch, 8)
+        nmax = end[..., 7].max(axis=1).reshape(-1)
+        cmax = lane.reshape(nw, 4, nch, 8).max(axis=(1, 3)).reshape(-1)
+        n0min = start.min(axis=(1, 3)).reshape(-1)
+        cells = valid.reshape(nw, 4, nch, L).sum(axis=(1, 3)).reshape(-1)
+        na = np.searchsorted(kap, 127.0 * np.log(2.0) / np.maximum(n0min, 1e-300), side="right")
+    elif 32 * c < nr:   # two warps per ray
         half = np.zeros((col.shape[0], 2, 32 * c))
         half.reshape(col.shape[0], -1)[:, :nr] = col
         nmax = np.repeat(col.sum(axis=1), 2)
@@ -263,7 +288,7 @@ def _warp_partition(w, shape):
     bc = np.searchsorted(kap, THIN_X / np.maximum(cmax, 1e-300), side="right")
     use = (bc > bt) & ((bt > 0) | (bc >= 4))
     bt2 = np.where(use, bc, bt)
-    return cells, bt, bt2, len(kap)
+    return cells, bt, bt2, na
 
 
 def exact_exp_ops(w, shape):
@@ -271,20 +296,20 @@ def exact_exp_ops(w, shape):
     one per (cell, bin) beyond the warp's tier (bt2), one per (lane, bin) of the tier
     (the tier's bins are expanded about each lane's first column), none for the thin
     series. The tile kernel traces every (cell, bin) bin by bin."""
-    if shape[0] != 1:
+    if shape[0] not in (1, 2):
         return w.grid.ncells * int(np.count_nonzero(w.kappa > 0))
     cells, bt, bt2, na = _warp_partition(w, shape)
-    return int(np.sum((na - bt2) * cells) + 32 * np.sum(bt2 - bt))
+    return int(np.sum(np.maximum(na - bt2, 0) * cells) + 32 * np.sum(bt2 - bt))
 
 
 def series_fma_ops(w, shape):
     """FMA-pipe operations of one tracer launch on grid w that its arithmetic needs at
     the least: the power series (SERIES_FMA_PER_CELL per cell) in every warp that
     sums some bin in it, and EXACT_FMA_PER_PAIR per (cell, bin) traced bin by bin."""
-    if shape[0] != 1:
+    if shape[0] not in (1, 2):
         return EXACT_FMA_PER_PAIR * exact_exp_ops(w, shape)
     cells, bt, bt2, na = _warp_partition(w, shape)
-    return int(SERIES_FMA_PER_CELL * np.sum(cells[bt2 > 0]) + EXACT_FMA_PER_PAIR * np.sum((na - bt2) * cells))
+    return int(SERIES_FMA_PER_CELL * np.sum(cells[bt2 > 0]) + EXACT_FMA_PER_PAIR * np.sum(np.maximum(na - bt2, 0) * cells))
 
 
 def roofline_summary(grids, hbm_peak_gbs, ex2_peak_gops, ffma_peak_gops, ex2_basis, ffma_basis):
@@ -609,7 +634,7 @@ def run_ours(args, rank, world, local):
     roofline = tracer_roofline(prim, launch_ms, ex2_peak, ffma_peak, hbm, ex2_basis, ffma_basis)
     kinds = {s[0] for s in prim_shapes}
     roofline.update({"traffic": traffic_from_profile(profile_summary_path(spec), src_hash),
-                     "kernel": "k_ray" if kinds == {1} else ("k_trace" if kinds == {0} else "k_ray/k_trace"),
+                     "kernel": "k_ray" if kinds <= {1, 2} else ("k_trace" if kinds == {0} else "k_ray/k_trace"),
                      "ffma_per_sm_clk": ffma_clk, "ex2_per_sm_clk": ex2_clk, "kernel_source_sha256": src_hash})
 
     # end to end through the host-buffer entry point (pinned host memory)
@@ -767,7 +792,7 @@ def run_ours(args, rank, world, local):
                        "grids_per_step": len(ws), "cells_per_step": sum(w.grid.ncells for w in ws),
                        "nu_bins": spec["n_nu"],
                        "step": "per grid: rt_irradiate (tracer kernel) + rt_energy_reduce (FP64 energy reduction)",
-                       "launch_shapes": [{"kernel": ["tile", "ray"][sh[0]], "cells_per_lane": sh[1], "warps": sh[2],
+                       "launch_shapes": [{"kernel": KERNEL_KINDS[sh[0]], "cells_per_lane": sh[1], "warps": sh[2],
                                           "min_blocks_per_sm": sh[3]} for sh in prim_shapes],
                        "l2": f"no flush: inputs+outputs {16 * sum(w.grid.ncells for w in ws) / 1e6:.0f} MB per step "
                              f"exceed the 129 MB L2",

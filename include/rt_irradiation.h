@@ -216,13 +216,17 @@ int rt_get_bins(rt_ctx *ctx, double *f_bin);
 /* Tracer kernels. RT_KERNEL_TILE: the flattened ray array in tiles of
  * 32 * warps * cells_per_lane cells, any nr (rays straddle threads and tiles).
  * RT_KERNEL_RAY: one warp per ray, each lane cells_per_lane consecutive cells of
- * it; only for nr <= 32 * cells_per_lane. Neither applies to the FP64 mode's
- * ray kernel, which does not exist (FP64 always uses tiles). */
-#define RT_KERNEL_TILE 0
-#define RT_KERNEL_RAY  1
+ * it; only for nr <= 32 * cells_per_lane. RT_KERNEL_RAY_CHUNKED: 8 lanes per ray
+ * (4 rays per warp) walk each ray outward in chunks of 8 * cells_per_lane cells,
+ * the column carried from chunk to chunk; for 8 * cells_per_lane < nr <= 4096,
+ * the plain (temperature-independent) table and the FP32 modes. The FP64 mode
+ * always uses tiles. */
+#define RT_KERNEL_TILE        0
+#define RT_KERNEL_RAY         1
+#define RT_KERNEL_RAY_CHUNKED 2
 
 /* rt_set_tuning -- force the tracer kernel and its launch shape: kind
- * (RT_KERNEL_TILE or RT_KERNEL_RAY), cells_per_lane, warps_per_block and
+ * (RT_KERNEL_TILE, RT_KERNEL_RAY or RT_KERNEL_RAY_CHUNKED), cells_per_lane, warps_per_block and
  * min_blocks_per_sm (the resident CTAs per SM the registers are capped for; 0 =
  * the first compiled variant). cells_per_lane = warps_per_block = 0 restores
  * automatic choice. Shapes that are not compiled in or do not fit the grid return

@@ -22,6 +22,7 @@ RT_ERR_NO_MEMORY = -6
 
 RT_KERNEL_TILE = 0
 RT_KERNEL_RAY = 1
+RT_KERNEL_RAY_CHUNKED = 2
 
 RT_FP32_KAHAN = 0
 RT_FP32_PLAIN = 1

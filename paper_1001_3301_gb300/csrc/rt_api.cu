@@ -179,7 +179,10 @@ int all_shapes(const rt_ctx *c, Shape *out, int max_out)
                                      : use_r2(c) ? rt::tdep2_shapes(c->nr, out, max_out)
                                                  : rt::tdep_shapes(c->nr, out, max_out);
     int n = rt::trace_shapes(c->precision, out, max_out);
-    if (c->precision != RT_FP64) n += rt::ray_shapes(c->precision, c->nr, out + n, max_out - n);
+    if (c->precision != RT_FP64) {
+        n += rt::ray_shapes(c->precision, c->nr, out + n, max_out - n);
+        n += rt::ray_shapes_mc(c->precision, c->nr, out + n, max_out - n);
+    }
     return n;
 }
 
@@ -296,14 +299,23 @@ int ensure_partials(rt_ctx *c, long long ntiles)
 // kMaxLaunchCells flattened cells (32-bit indexing inside the kernel).
 long long chunk_rays(const rt_ctx *c) { return rt::kMaxLaunchCells / (c->nr + 1); }
 
+// an upper bound of the CTAs of one launch of shape s over nr_c rays
+long long launch_ctas(const rt_ctx *c, Shape s, long long nr_c)
+{
+    if (s.kind == rt::kKindRay)
+        return (nr_c * rt::ray_warps_per_ray(s.cells_per_lane, c->nr) + s.warps - 1) / s.warps;
+    if (s.kind == rt::kKindRayChunked) return (nr_c + 4LL * s.warps - 1) / (4LL * s.warps);
+    const long long T = rt::trace_tile_cells(s);
+    return (nr_c * (c->nr + 1) + T - 1) / T;
+}
+
 long long total_tiles(const rt_ctx *c, Shape s)
 {
-    const long long T = rt::trace_tile_cells(s), cr = chunk_rays(c);
+    const long long cr = chunk_rays(c);
     long long tiles = 0;
     for (long long r0 = 0; r0 < c->nrays; r0 += cr) {
         const long long nr_c = (c->nrays - r0 < cr) ? c->nrays - r0 : cr;
-        tiles += (s.kind == rt::kKindRay) ? (nr_c * rt::ray_warps_per_ray(s.cells_per_lane, c->nr) + s.warps - 1) / s.warps
-                                          : (nr_c * (c->nr + 1) + T - 1) / T;
+        tiles += launch_ctas(c, s, nr_c);
     }
     return tiles;
 }
@@ -364,12 +376,11 @@ int trace_range(rt_ctx *c, const float *rho, const float *td, float *q, float *a
 // tiles (an upper bound of the CTAs) of the launches over rays [r_begin, r_end)
 long long range_tiles(const rt_ctx *c, Shape s, long long r_begin, long long r_end)
 {
-    const long long T = rt::trace_tile_cells(s), cr = chunk_rays(c);
+    const long long cr = chunk_rays(c);
     long long tiles = 0;
     for (long long r0 = r_begin; r0 < r_end; r0 += cr) {
         const long long nr_c = (r_end - r0 < cr) ? r_end - r0 : cr;
-        tiles += (s.kind == rt::kKindRay) ? (nr_c * rt::ray_warps_per_ray(s.cells_per_lane, c->nr) + s.warps - 1) / s.warps
-                                          : (nr_c * (c->nr + 1) + T - 1) / T;
+        tiles += launch_ctas(c, s, nr_c);
     }
     return tiles;
 }

@@ -143,6 +143,8 @@ struct TraceArgs {
 // Launch shapes of the fused tracer that are compiled in.
 constexpr int kKindTile = RT_KERNEL_TILE;  // flattened tiles, any nr (rt_trace.cu)
 constexpr int kKindRay = RT_KERNEL_RAY;    // one warp per ray, nr <= 32 C (rt_ray.cu)
+constexpr int kKindRayChunked = RT_KERNEL_RAY_CHUNKED;  // 8 lanes per ray, chunks of 8 C cells (rt_ray.cu)
+constexpr int kMaxChunkedNr = 4096;                     // longest ray of the chunked form
 struct Shape {
     int kind;
     int cells_per_lane;
@@ -171,6 +173,10 @@ int ray_shapes(int precision, int nr, Shape *out, int max_out);  // ray kernel, 
 int ray_shapes_tw(int precision, int nr, Shape *out, int max_out);
 // ray-kernel shapes compiled with the lookup-table comparator
 int ray_shapes_lut(int precision, int nr, Shape *out, int max_out);
+// shapes of the chunked ray kernel (8 C < nr <= kMaxChunkedNr), rt_ray_mc.cu
+int ray_shapes_mc(int precision, int nr, Shape *out, int max_out);
+cudaError_t launch_ray_mc_shape(int precision, Shape s, const TraceArgs &args, cudaStream_t stream,
+                                unsigned *grid_out, unsigned max_grid);
 long long trace_tile_cells(Shape s);
 cudaError_t launch_ray_shape(int precision, Shape s, const TraceArgs &args, cudaStream_t stream,
                              unsigned *grid_out, unsigned max_grid = 0);

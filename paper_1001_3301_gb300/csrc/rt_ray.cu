@@ -8,68 +8,6 @@
 namespace rt {
 namespace {
 
-template <int C, int W, int MODE, int MINB, int G, int P, bool TW, bool LUT>
-__global__ void __launch_bounds__(W * 32, MINB) k_ray(const TraceArgs p)
-{
-    using ESum = KahanSum;
-    constexpr int R = 32 / G;  // rays per warp
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    __shared__ RayShared<C, P> rs;
-    extern __shared__ __align__(16) unsigned char smem[];
-    float *s_kap = reinterpret_cast<float *>(smem);
-    float4 *s_nu = reinterpret_cast<float4 *>(s_kap + p.nnu_pad);
-    float4 *s_mom = s_nu + p.nnu_pad;
-    __shared__ ESum s_red[W][2];
-    ray_tables<C, W, P>(p, G, rs, s_kap, s_nu, s_mom);
-    __syncthreads();
-
-    ESum eabs, eesc;
-    eabs.zero();
-    eesc.zero();
-    const unsigned slots = (p.nrays + R - 1) / R;
-    constexpr int WG = W / P;  // ray groups per CTA
-    ray_slots<C, W, MODE, G, P, TW, LUT>(p, blockIdx.x * WG + warp / P, slots, gridDim.x * WG, rs, s_kap, s_nu,
-                                         s_mom, eabs, eesc);
-
-    for (int o = 16; o > 0; o >>= 1) {
-        eabs.add(eabs.shfl_xor(o));
-        eesc.add(eesc.shfl_xor(o));
-    }
-    if (lane == 0) { s_red[warp][0] = eabs; s_red[warp][1] = eesc; }
-    __syncthreads();
-    if (tid == 0) {
-        ESum sa = s_red[0][0], se = s_red[0][1];
-        for (int w2 = 1; w2 < W; ++w2) { sa.add(s_red[w2][0]); se.add(s_red[w2][1]); }
-        p.partials[blockIdx.x] = make_double2(to_double(sa), to_double(se));
-    }
-}
-
-template <int C, int W, int MODE, int MINB, int G, int P, bool TW, bool LUT>
-cudaError_t launch_ray_g(const TraceArgs &a, cudaStream_t stream, unsigned *grid_out, unsigned max_grid)
-{
-    constexpr int R = 32 / G;
-    const size_t smem = ray_bin_smem(a.nnu_pad) + 16;
-    auto kern = k_ray<C, W, MODE, MINB, G, P, TW, LUT>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    int dev = 0, nsm = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W * 32, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    unsigned grid = (unsigned)nsm * (unsigned)per_sm;
-    const unsigned need = (a.nrays * P + W * R - 1) / (W * R);
-    if (grid > need) grid = need;
-    if (max_grid > 0 && grid > max_grid) grid = max_grid;
-    if (grid < 1) grid = 1;
-    kern<<<grid, W * 32, smem, stream>>>(a);
-    *grid_out = grid;
-    return cudaGetLastError();
-}
-
 // The fewest lanes per ray that still hold the ray: 8, 16 or 32 (G C >= nr), else two
 // warps per ray (ray_warps_per_ray).
 template <int C, int W, int MODE, int MINB, bool TW = false, bool LUT = false>
@@ -145,6 +83,7 @@ int ray_shapes_lut(int precision, int nr, Shape *out, int max_out)
 cudaError_t launch_ray_shape(int precision, Shape s, const TraceArgs &args, cudaStream_t stream,
                              unsigned *grid_out, unsigned max_grid)
 {
+    if (s.kind == kKindRayChunked) return launch_ray_mc_shape(precision, s, args, stream, grid_out, max_grid);
     const bool tw = args.n_tw > 0, lut = args.lut != nullptr;
     const RayEntry *tab = lut ? kRayShapesLUT : (tw ? kRayShapesTW : kRayShapes);
     const int ntab = lut  ? (int)(sizeof(kRayShapesLUT) / sizeof(RayEntry))

@@ -27,6 +27,13 @@
 //   - q_abs = Gq acc and a_rad = q/(rho c) = Ga0 acc / dN (Sect. 5; the rho -> 0
 //     limit where dN = 0 with dust), stored as 16-byte vectors;
 //   - energy sums per lane.
+// Chunked form (MC): a segment of G lanes holds G C cells of its ray at a time and
+// walks the ray outward chunk by chunk, the column in front of the chunk carried
+// (compensated) from one chunk to the next. Every per-warp decision (thin series,
+// tier, bin classes) is then taken over the cells of one chunk of R neighbouring
+// rays, a narrow range of radii, and the bins whose attenuation underflows in every
+// cell of the chunk (kappa_i N_in >= 127 / log2 e at the smallest N_in of the warp:
+// 2^{-127} and below flush to zero) are skipped, which changes no bit of the result.
 #pragma once
 
 #include "rt_device.cuh"
@@ -47,6 +54,8 @@ struct RayShared {
 // dynamic shared memory of the bin tables: kappa, (nk, nk, lf, lf) and the series
 // moments' constants (two float4 per bin)
 __host__ __device__ constexpr size_t ray_bin_smem(int nnu_pad) { return (size_t)nnu_pad * (4 + 16 + 32); }
+// chunked form: the pairs of radial constants of all chunks (chunks x C/2 x G)
+__host__ __device__ constexpr int ray_chunk_pairs(int c, int g, int nr) { return (nr + g * c - 1) / (g * c) * (c / 2) * g; }
 
 // The tables of grid p for G lanes per ray, or P warps per ray (call from every
 // thread of the CTA, then __syncthreads()).
@@ -213,18 +222,53 @@ __device__ __forceinline__ void group_sync(int id, int n)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
+// Bins (sorted by kappa) whose attenuation over a column n stays at or above 2^-127:
+// (-nk_i) n <= 127, a prefix of the sorted bins (warp-uniform count).
+__device__ __forceinline__ int live_count(const float4 *s_nu, int n_active, int lane, float n)
+{
+    int b = 0;
+    for (int c0 = 0; c0 < n_active; c0 += 32) {
+        const int i = c0 + lane;
+        const float ak = (i < n_active) ? -s_nu[i].x : INFINITY;
+        b += __popc(__ballot_sync(0xffffffffu, ak * n <= 127.0f));
+    }
+    return b;
+}
+
+// The radial constants of every chunk for the chunked form (G lanes of C cells per
+// chunk): s_dr[(ch C/2 + m) G + l] = (dr, dr) of cells (ch G + l) C + 2m, +1, and
+// s_gqa the (Gq, Gq, Ga0, Ga0) pairs. Call from every thread of the CTA, then
+// __syncthreads().
+template <int C, int W, int G>
+__device__ __forceinline__ void ray_tables_mc(const TraceArgs &p, float2 *s_dr, float4 *s_gqa)
+{
+    const int nch = (p.nr + G * C - 1) / (G * C);
+    for (int i = threadIdx.x; i < nch * (C / 2) * G; i += W * 32) {
+        const int l = i % G, m = (i / G) % (C / 2), ch = i / (G * (C / 2));
+        const int k = (ch * G + l) * C + 2 * m;
+        const float4 g0 = (k < p.nr) ? __ldg(&p.rtab[k]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        const float4 g1 = (k + 1 < p.nr) ? __ldg(&p.rtab[k + 1]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        s_dr[i] = make_float2(g0.x, g1.x);
+        s_gqa[i] = make_float4(g0.y, g1.y, g0.z, g1.z);
+    }
+}
+
 // Warp-slots wr = wr_begin, wr_begin + step, ... (< wr_end) of grid p, R = 32 / G rays
 // each (or, with P > 1, one ray per group of P consecutive warps, which all walk the
 // same slots); the lanes' energy sums are added to eabs / eesc. TW: the table is a
 // separable kappa(nu, T) (TraceArgs::n_tw > 0) and each cell's column carries the
 // weight b(T). LUT: the absorbed power of the cells comes from the lookup table of
 // TraceArgs::lut (the per-bin sum only in warp-slots that hold a flagged cell).
-template <int C, int W, int MODE, int G, int P = 1, bool TW = false, bool LUT = false>
+// MC: the chunked form; s_dr_mc / s_gqa_mc hold the radial constants of every chunk,
+// [chunk][j / 2][lane in the segment] (ray_tables_mc).
+template <int C, int W, int MODE, int G, int P = 1, bool TW = false, bool LUT = false, bool MC = false>
 __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin, unsigned wr_end, unsigned step,
                                           const RayShared<C, P> &rs, const float *s_kap, const float4 *s_nu,
-                                          const float4 *s_mom, KahanSum &eabs, KahanSum &eesc)
+                                          const float4 *s_mom, KahanSum &eabs, KahanSum &eesc,
+                                          const float2 *s_dr_mc = nullptr, const float4 *s_gqa_mc = nullptr)
 {
     static_assert(MODE != RT_FP64, "the FP64 mode uses the tile kernel");
+    static_assert(!MC || (P == 1 && !TW && !LUT), "chunks: one warp per segment, the plain table");
     static_assert(C % 2 == 0, "cells per lane must be even");
     static_assert(G == 8 || G == 16 || G == 32, "lanes per ray");
     static_assert(P == 1 || (G == 32 && W % P == 0 && P == 2), "warps per ray");
@@ -252,8 +296,7 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
     }
     const int seg = lane / G, ll = half * 32 + lane % G;  // ray slot of the lane, lane within the ray
     const int nr = p.nr;
-    const int c0 = ll * C;
-    const int nv_ray = nr - c0 < 0 ? 0 : (nr - c0 > C ? C : nr - c0);  // valid cells of this lane
+    const int nch = MC ? (nr + G * C - 1) / (G * C) : 1;  // chunks per ray
     // vector access needs every lane start and the field bases 4V-byte aligned
     const bool vec = (nr % V == 0) &&
                      ((reinterpret_cast<size_t>(p.rho) | reinterpret_cast<size_t>(p.tdust) |
@@ -267,7 +310,12 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
     for (unsigned wr = wr_begin; wr < wr_end; wr += step) {
         const unsigned ray = wr * R + seg;
         const bool live = ray < p.nrays;  // the last warp may hold fewer than R rays
-        const int nv = live ? nv_ray : 0;
+        const float w = live ? __ldg(p.domega32 + ray) : 0.0f;
+        Sum carry;  // chunked form: the ray's column in front of the chunk
+        carry.zero();
+        for (int ch = 0; ch < nch; ++ch) {
+        const int c0 = (ch * G + ll) * C;  // the lane's first cell in the ray
+        const int nv = !live ? 0 : (nr - c0 < 0 ? 0 : (nr - c0 > C ? C : nr - c0));  // its valid cells
         const size_t base = (size_t)(live ? ray : 0u) * nr + c0;
 
         // the fields, straight from HBM (or from L2, where the prefetch got there first)
@@ -299,7 +347,7 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
         }
         // the fields of this warp's next slot, on their way to L2 (with P > 1 the group's
         // first warp asks for the whole ray)
-        if (pf && lane == 0 && half == 0 && wr + step < wr_end) {
+        if (pf && lane == 0 && half == 0 && ch == 0 && wr + step < wr_end) {
             const unsigned r0 = (wr + step) * R;
             if (r0 < p.nrays) {
                 const unsigned nrs = p.nrays - r0 < (unsigned)R ? p.nrays - r0 : (unsigned)R;
@@ -320,7 +368,7 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
         lsum.zero();
 #pragma unroll
         for (int m = 0; m < C / 2; ++m) {
-            const float2 dr = rs.dr[half][m][lane];
+            const float2 dr = MC ? s_dr_mc[(ch * (C / 2) + m) * G + ll] : rs.dr[half][m][lane];
             const bool d0 = td2[m].x <= p.t_sub, d1 = td2[m].y <= p.t_sub;
             // rho must be finite and >= 0 (-0 counts as 0): the bits of rho + 0 stay
             // below those of +Inf; t_dust must not be NaN
@@ -379,6 +427,17 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
             off.add(pre);
             n0 = off.value();
             ntot = tot.value();
+        } else if constexpr (MC) {
+            // the chunk's offset: the carried column plus the segment's exclusive prefix;
+            // then the carry moves past the chunk (ntot: the column at its end)
+            Sum off = carry;
+            off.add(pre);
+            n0 = off.value();
+            Sum st;
+            st.hi = __shfl_sync(0xffffffffu, inc.hi, G - 1, G);
+            if constexpr (MODE == RT_FP32_KAHAN) st.lo = __shfl_sync(0xffffffffu, inc.lo, G - 1, G);
+            carry.add(st);
+            ntot = carry.value();
         } else {
             n0 = pre.value();
             ntot = __shfl_sync(0xffffffffu, inc.value(), G - 1, G);
@@ -392,6 +451,14 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
         for (int o = 16; o > 0; o >>= 1) cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
         int bt, bc;
         thin_counts(s_nu, na, lane, nmax, cmax, bt, bc);
+        // chunked form: the bins from na_live on underflow in every cell of the chunk
+        // (e^{-kappa N_in} <= 2^{-127} at the warp's smallest column in front of a lane)
+        int na_live = na;
+        if constexpr (MC) {
+            float n0min = n0;
+            for (int o = 16; o > 0; o >>= 1) n0min = fminf(n0min, __shfl_xor_sync(0xffffffffu, n0min, o));
+            na_live = live_count(s_nu, na, lane, n0min);
+        }
         // with no row to shift, a few tier bins do not pay for the series
         const int bt2 = (bc > bt && (bt > 0 || bc >= 4)) ? bc : bt;
         const float *thin_row = p.kap + kKapTable + bt * kThinStride;
@@ -436,7 +503,7 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
             const float s2 = lane_coefficients(thin_row, bt, bt2, s_nu, n0, F);
             lane_series<C>(F, s2, U, D, acc);
         }
-        if (per_bin && bt2 < na) {  // warp-uniform
+        if (per_bin && bt2 < na_live) {  // warp-uniform
             // the warp's largest and smallest non-zero column decide each bin's class
             float dmax = 0.0f, dmin = INFINITY;
 #pragma unroll
@@ -448,7 +515,7 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
                 dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
                 dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
             }
-            const BinClasses bc = classify_bins(s_nu, na, lane, dmax, dmin, bt2);
+            const BinClasses bc = classify_bins(s_nu, na_live, lane, dmax, dmin, bt2);
             const int t1 = max(bc.b1, bt2), t2 = max(bc.b2, bt2), t3 = max(bc.b3, bt2), t5 = max(bc.b5, bt2);
             const int tb = max(bc.bb, bt2);
             moment_range<1, C>(bt2, t1, s_nu, s_mom, n0, U, D, acc);
@@ -456,13 +523,12 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
             bin_range<3, C>(t2, t3, s_nu, n0, U, D, acc);
             bin_range<5, C>(t3, t5, s_nu, n0, U, D, acc);
             bin_range<6, C>(t5, tb, s_nu, n0, U, D, acc);
-            bin_range<7, C>(tb, na, s_nu, n0, U, D, acc);
+            bin_range<7, C>(tb, na_live, s_nu, n0, U, D, acc);
         }
 
         // escaping power of the ray, the lanes of its segment (all P warps of a group)
-        // sharing the bins
-        const float w = live ? __ldg(p.domega32 + ray) : 0.0f;
-        {
+        // sharing the bins (chunked form: after its last chunk)
+        if (!MC || ch == nch - 1) {
             float s = 0.0f;
             for (int i = bt + ll; i < na; i += G * P) s += ex2_approx(fmaf(s_nu[i].x, ntot, s_nu[i].z));
             for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -478,7 +544,7 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
         float2 qv[C / 2];
 #pragma unroll
         for (int m = 0; m < C / 2; ++m) {
-            const float4 g = rs.gqa[half][m][lane];
+            const float4 g = MC ? s_gqa_mc[(ch * (C / 2) + m) * G + ll] : rs.gqa[half][m][lane];
             qv[m] = __fmul2_rn(make_float2(g.x, g.y), acc[m]);
             lane_abs2 = __fadd2_rn(lane_abs2, acc[m]);
             const float2 dd = make_float2(fmaxf(D[m].x, tiny2.x), fmaxf(D[m].y, tiny2.y));
@@ -497,7 +563,7 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
                     for (int i = 0; i < na; ++i)
                         s = fmaf(s_kap[i], ex2_approx(fmaf(s_nu[i].x, uj, fmaf(s_nu[i].x, n0, s_nu[i].z))), s);
                     if (zj) {
-                        const float4 g = rs.gqa[half][j / 2][lane];
+                        const float4 g = MC ? s_gqa_mc[(ch * (C / 2) + j / 2) * G + ll] : rs.gqa[half][j / 2][lane];
                         if constexpr (TW) {  // kappa_i(T) = kappa_i b(T)
                             const float2 bw = s_bw[wid][j / 2][lane];
                             s *= (j & 1) ? bw.y : bw.x;
@@ -531,7 +597,77 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
                 }
             }
         }
+        }  // chunks
     }
+}
+
+
+// The kernel over all rays of one grid (persistent CTAs striding over the warp-slots),
+// then the CTA's energy partial.
+template <int C, int W, int MODE, int MINB, int G, int P, bool TW, bool LUT, bool MC>
+__global__ void __launch_bounds__(W * 32, MINB) k_ray(const TraceArgs p)
+{
+    using ESum = KahanSum;
+    constexpr int R = 32 / G;  // rays per warp
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ RayShared<C, P> rs;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *s_kap = reinterpret_cast<float *>(smem);
+    float4 *s_nu = reinterpret_cast<float4 *>(s_kap + p.nnu_pad);
+    float4 *s_mom = s_nu + p.nnu_pad;
+    // chunked form: the radial constants of every chunk after the bin tables
+    float2 *s_dr_mc = reinterpret_cast<float2 *>(s_mom + 2 * p.nnu_pad);
+    float4 *s_gqa_mc = reinterpret_cast<float4 *>(s_dr_mc + (MC ? ray_chunk_pairs(C, G, p.nr) : 0));
+    __shared__ ESum s_red[W][2];
+    ray_tables<C, W, P>(p, G, rs, s_kap, s_nu, s_mom);
+    if constexpr (MC) ray_tables_mc<C, W, G>(p, s_dr_mc, s_gqa_mc);
+    __syncthreads();
+
+    ESum eabs, eesc;
+    eabs.zero();
+    eesc.zero();
+    const unsigned slots = (p.nrays + R - 1) / R;
+    constexpr int WG = W / P;  // ray groups per CTA
+    ray_slots<C, W, MODE, G, P, TW, LUT, MC>(p, blockIdx.x * WG + warp / P, slots, gridDim.x * WG, rs, s_kap, s_nu,
+                                             s_mom, eabs, eesc, s_dr_mc, s_gqa_mc);
+
+    for (int o = 16; o > 0; o >>= 1) {
+        eabs.add(eabs.shfl_xor(o));
+        eesc.add(eesc.shfl_xor(o));
+    }
+    if (lane == 0) { s_red[warp][0] = eabs; s_red[warp][1] = eesc; }
+    __syncthreads();
+    if (tid == 0) {
+        ESum sa = s_red[0][0], se = s_red[0][1];
+        for (int w2 = 1; w2 < W; ++w2) { sa.add(s_red[w2][0]); se.add(s_red[w2][1]); }
+        p.partials[blockIdx.x] = make_double2(to_double(sa), to_double(se));
+    }
+}
+
+template <int C, int W, int MODE, int MINB, int G, int P, bool TW, bool LUT, bool MC = false>
+cudaError_t launch_ray_g(const TraceArgs &a, cudaStream_t stream, unsigned *grid_out, unsigned max_grid)
+{
+    constexpr int R = 32 / G;
+    const size_t smem = ray_bin_smem(a.nnu_pad) + 16 + (MC ? (size_t)ray_chunk_pairs(C, G, a.nr) * (8 + 16) : 0);
+    auto kern = k_ray<C, W, MODE, MINB, G, P, TW, LUT, MC>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    unsigned grid = (unsigned)nsm * (unsigned)per_sm;
+    const unsigned need = (a.nrays * P + W * R - 1) / (W * R);
+    if (grid > need) grid = need;
+    if (max_grid > 0 && grid > max_grid) grid = max_grid;
+    if (grid < 1) grid = 1;
+    kern<<<grid, W * 32, smem, stream>>>(a);
+    *grid_out = grid;
+    return cudaGetLastError();
 }
 
 }  // namespace

@@ -119,7 +119,8 @@ long long trace_tile_cells(Shape s) { return 32LL * s.warps * s.cells_per_lane; 
 cudaError_t launch_trace(int precision, Shape s, const TraceArgs &args, unsigned ntiles,
                          cudaStream_t stream, unsigned *grid_out, unsigned max_grid)
 {
-    if (s.kind == kKindRay) return launch_ray_shape(precision, s, args, stream, grid_out, max_grid);
+    if (s.kind == kKindRay || s.kind == kKindRayChunked)
+        return launch_ray_shape(precision, s, args, stream, grid_out, max_grid);
     const ShapeEntry *e = find_shape(precision, s.cells_per_lane, s.warps, s.min_blocks);
     if (!e) return cudaErrorInvalidValue;
     return e->fn(args, ntiles, stream, grid_out, max_grid);

@@ -24,6 +24,24 @@ def _brute_warps(w, shape):
     col = lambda j, k: rho[j, k] * dr[k] if td[j, k] <= w.t_sub else 0.0
     out = []
     nrays = rho.shape[0]
+    if shape[0] == 2:   # chunked: 4 rays of 8 lanes per warp, chunks of 8 c cells
+        L = 8 * c
+        for first in range(0, nrays, 4):
+            slots = range(first, first + 4)          # ray slots past the last ray hold nothing
+            for k0 in range(0, g.nr, L):
+                def lane_start(j, l):
+                    return sum(col(j, k) for k in range(min(k0 + l * c, g.nr))) if j < nrays else 0.0
+                nmax = max(lane_start(j, 8) for j in slots)
+                cmax = max(sum(col(j, k) for k in range(k0 + l * c, min(k0 + (l + 1) * c, g.nr))) if j < nrays else 0.0
+                           for j in slots for l in range(8))
+                n0min = min(lane_start(j, l) for j in slots for l in range(8))
+                bt = sum(1 for kk in kap if kk * nmax <= bench.THIN_X)
+                bc = sum(1 for kk in kap if kk * cmax <= bench.THIN_X)
+                bt2 = bc if (bc > bt and (bt > 0 or bc >= 4)) else bt
+                na = sum(1 for kk in kap if kk * n0min <= 127.0 * np.log(2.0))
+                cells = sum(1 for j in slots if j < nrays for k in range(k0, min(k0 + L, g.nr)))
+                out.append((cells, bt, bt2, na))
+        return out
     if 32 * c < g.nr:   # two warps per ray, each 32 c of its cells
         for j in range(nrays):
             nmax = sum(col(j, k) for k in range(g.nr))
@@ -52,9 +70,9 @@ def _brute_warps(w, shape):
 def _brute(w, shape):
     """One exponential per (cell, bin) beyond the tier, one per (lane, bin) of the
     tier; every (cell, bin) for the tile kernel."""
-    if shape[0] != 1:
+    if shape[0] not in (1, 2):
         return w.grid.ncells * int(np.count_nonzero(w.kappa > 0))
-    return sum((na - bt2) * cells + 32 * (bt2 - bt) for cells, bt, bt2, na in _brute_warps(w, shape))
+    return sum(max(na - bt2, 0) * cells + 32 * (bt2 - bt) for cells, bt, bt2, na in _brute_warps(w, shape))
 
 
 @pytest.mark.parametrize("tau,shape", [(10.0, (1, 8, 4, 6)), (100.0, (1, 4, 4, 8)), (1.0, (1, 16, 4, 3)),
@@ -73,6 +91,15 @@ def test_exact_exp_ops_two_warps_per_ray(tau):
     assert bench.series_fma_ops(w, shape) == _brute_fma(w, shape)
 
 
+@pytest.mark.parametrize("tau,shape", [(10.0, (2, 8, 4, 6)), (1e3, (2, 4, 4, 8)), (1e5, (2, 2, 4, 8))])
+def test_chunked_ops_match_brute_force(tau, shape):
+    """The chunked kernel: 150-cell rays in chunks of 8 c cells (a ragged last chunk),
+    30 rays (a partial last warp), thick enough for bins to underflow."""
+    w = synth.disk3d(150, 6, 5, n_nu=16, tau550=tau, seed=6)
+    assert bench.exact_exp_ops(w, shape) == _brute(w, shape)
+    assert bench.series_fma_ops(w, shape) == _brute_fma(w, shape)
+
+
 def test_exact_exp_ops_limits():
     """No dust column: the series takes every bin; a column far above 1/kappa_min:
     no bin is thin."""
@@ -87,9 +114,9 @@ def test_exact_exp_ops_limits():
 def _brute_fma(w, shape):
     """Series FMAs per cell in every warp that sums some bin in the series, plus
     EXACT_FMA_PER_PAIR per (cell, bin) traced bin by bin."""
-    if shape[0] != 1:
+    if shape[0] not in (1, 2):
         return bench.EXACT_FMA_PER_PAIR * _brute(w, shape)
-    return sum(bench.SERIES_FMA_PER_CELL * cells * (bt2 > 0) + bench.EXACT_FMA_PER_PAIR * (na - bt2) * cells
+    return sum(bench.SERIES_FMA_PER_CELL * cells * (bt2 > 0) + bench.EXACT_FMA_PER_PAIR * max(na - bt2, 0) * cells
                for cells, bt, bt2, na in _brute_warps(w, shape))
 
 

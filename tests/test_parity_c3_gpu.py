@@ -60,13 +60,14 @@ def _trace(w, precision="fp32_kahan", shape=None, autotune=False, kappa_bf16=Fal
 
 def test_c3_kahan_every_ray_shape_and_autotuned(c3):
     """Compensated FP32 (the bench's mode): the autotuned shape and every compiled
-    warp-per-ray shape, each over all 67 M cells, energies of the whole grid."""
+    warp-per-ray shape, one-chunk and chunked, each over all 67 M cells, energies of
+    the whole grid."""
     w, orc = c3
     (q, a, e), used, shapes = _trace(w, autotune=True)
     st = _parity.assert_parity(w, q, a, e, orc, label=f"autotuned {used}")
     assert st["n_mask"] > 10_000_000
     for s in shapes:
-        if s[0] != 1 or tuple(s) == tuple(used):
+        if s[0] not in (1, 2) or tuple(s) == tuple(used):
             continue
         (q, a, e), _, _ = _trace(w, shape=s)
         _parity.assert_parity(w, q, a, e, orc, label=f"{s}")

@@ -97,12 +97,14 @@ def _thin_counts(w, x=0.5):
     return np.searchsorted(kap, x / np.maximum(ntot, 1e-300), side="right"), len(kap)
 
 
-@pytest.mark.parametrize("tau", [1e-4, 1e3])
+@pytest.mark.parametrize("tau", [1e-4, 1e3, 1e5])
 def test_thin_series_extremes(tau):
     """The power series over the bins optically thin along whole rays: at
     tau550 = 1e-4 every bin of every ray goes through it; at 1e3 the midplane rays
-    keep only the far-infrared bins in it and trace the rest bin by bin. Both
-    segment widths (32 and 16 lanes per ray, one and two rays per warp)."""
+    keep only the far-infrared bins in it and trace the rest bin by bin; at 1e5 the
+    outer chunks of the chunked kernel skip the bins that underflow there. Both
+    segment widths of the one-chunk kernel (32 and 16 lanes per ray, one and two
+    rays per warp) and the chunked kernel (chunks of 64 and 128 cells)."""
     w = _w3(256, 24, 4, 79, tau=tau, seed=5)
     bt, na = _thin_counts(w)
     if tau < 1:
@@ -110,19 +112,20 @@ def test_thin_series_extremes(tau):
     else:
         assert bt.min() < na // 2 and bt.max() > 0
     orc = _parity.oracle_for(w)
-    for shape in [(1, 8, 4, 6), (1, 16, 4, 3)]:
+    for shape in [(1, 8, 4, 6), (1, 16, 4, 3), (2, 8, 4, 6), (2, 16, 4, 3)]:
         q, a, e = _parity.run_gpu(w, "fp32_kahan", shape=shape)
         _parity.assert_parity(w, q, a, e, orc, label=f"tau={tau} {shape}")
 
 
 # --------------------------------------------------------------------------
-# deep rays: 2048 and 4096 cells at tau550 = 100, longer than any warp-per-ray
-# shape holds, so every ray spans many tiles and the column crosses tiles and CTAs
-# through the FP64 carry of the tile kernel
+# deep rays: 2048 and 4096 cells at tau550 = 100, longer than any one-chunk
+# warp-per-ray shape holds: in the tile kernel every ray spans many tiles and the
+# column crosses tiles and CTAs through its FP64 carry; the chunked kernel walks
+# each ray in 16 to 64 chunks with the compensated carry
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("nr", [2048, 4096])
 @pytest.mark.parametrize("precision,rtol", [("fp32_kahan", 1e-5), ("fp64", 3e-7)])
-def test_deep_rays_tile_kernel(nr, precision, rtol):
+def test_deep_rays(nr, precision, rtol):
     from paper_1001_3301_gb300 import Tracer
     # 7 polar cells (one centred on the midplane) x 64 azimuths: 448 rays, more tiles
     # than the persistent grid has CTAs, so CTAs also hand the column from tile to tile
@@ -130,7 +133,8 @@ def test_deep_rays_tile_kernel(nr, precision, rtol):
     orc = oracle.irradiate_workload(w, nthreads=oracle.max_threads())
     with Tracer.from_grid(w.grid, precision) as tr:
         shapes = tr.tunings()
-    assert shapes and all(s[0] == 0 for s in shapes)  # no warp-per-ray shape holds these rays
+    assert shapes and all(s[0] in (0, 2) for s in shapes)  # no one-chunk shape holds these rays
+    assert any(s[0] == 2 for s in shapes) == (precision != "fp64")
     for shape in shapes:
         q, a, e = _parity.run_gpu(w, precision, shape=shape)
         _parity.assert_parity(w, q, a, e, orc, rtol_q=rtol, rtol_a=rtol,
