@@ -346,8 +346,21 @@ __device__ __forceinline__ void ray_slots(const TraceArgs &p, unsigned wr_begin,
             }
         }
         // the fields of this warp's next slot, on their way to L2 (with P > 1 the group's
-        // first warp asks for the whole ray)
-        if (pf && lane == 0 && half == 0 && ch == 0 && wr + step < wr_end) {
+        // first warp asks for the whole ray); in the chunked form each segment's first
+        // lane asks for its ray's next chunk (the first chunk of its next ray after the
+        // last), the same distance ahead as one slot of the one-chunk form
+        if constexpr (MC) {
+            if (pf && lane % G == 0) {
+                const bool last = ch + 1 == nch;
+                const unsigned rn = last ? (wr + step) * R + seg : ray;
+                const int k0 = last ? 0 : (ch + 1) * G * C;
+                if ((!last || wr + step < wr_end) && rn < p.nrays) {
+                    const unsigned bytes = (unsigned)min(G * C, nr - k0) * 4u;
+                    prefetch_l2(p.rho + (size_t)rn * nr + k0, bytes);
+                    prefetch_l2(p.tdust + (size_t)rn * nr + k0, bytes);
+                }
+            }
+        } else if (pf && lane == 0 && half == 0 && wr + step < wr_end) {
             const unsigned r0 = (wr + step) * R;
             if (r0 < p.nrays) {
                 const unsigned nrs = p.nrays - r0 < (unsigned)R ? p.nrays - r0 : (unsigned)R;
