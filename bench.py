@@ -464,6 +464,36 @@ def run_cpu_table(args, local):
 REF_STEP_S = 1.0
 
 
+def time_dust_temperature(st, steps, stream, hbm, i_med):
+    """rt_dust_temperature (E_R = 0) on every grid of a tracer set, fed by its a_rad:
+    CUDA events over `steps` passes over the grids (their 8 bytes per cell exceed L2
+    together), the mean time per grid against the measured copy bandwidth."""
+    import torch
+    t_out = [torch.empty(w.grid.shape, dtype=torch.float32, device="cuda") for w in st["ws"]]
+    for _ in range(3):
+        for i, tr in enumerate(st["tracers"]):
+            tr.dust_temperature(st["a"][i], None, t_out[i])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        for i, tr in enumerate(st["tracers"]):
+            tr.dust_temperature(st["a"][i], None, t_out[i])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_ms = e0.elapsed_time(e1) / (steps * len(st["ws"]))
+    g = st["ws"][0].grid
+    ncell = g.ncells
+    out = {"workload": f"disk3d {g.nr}x{g.ntheta}x{g.nphi}, a_rad of the tracer, "
+                       f"tau550 in {{{','.join(f'{w.tau550:g}' for w in st['ws'])}}}",
+           "ms_per_grid": t_ms, "cells_per_s": ncell / (t_ms * 1e-3),
+           "achieved_gbs": 8.0 * ncell / (t_ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm,
+           "frac_of_hbm": 8.0 * ncell / (t_ms * 1e-3) / 1e9 / hbm,
+           "median_t_k": float(t_out[i_med].median())}
+    del t_out
+    return out
+
+
 def run_reference(args, rank, world):
     """The FP64 oracle on the host cores, on the GPU arm's workload: per step an evenly
     spaced sample of rays of every grid of the step, as many as fill about REF_STEP_S
@@ -670,6 +700,11 @@ def run_ours(args, rank, world, local):
                "entry_point": "rt_irradiate_host_async + rt_host_wait (pinned host buffers)"}
         del h_rho, h_td, h_q, h_a
 
+    # the dust-temperature update on the primary grids (their a_rad from the last step)
+    temp_c3 = None
+    if rank == 0 and args.workload == "c3":
+        temp_c3 = time_dust_temperature(prim, args.steps, stream, hbm, 0)
+
     # the other workload's tracer step (rank 0), and the 256 x 128 x 256 tau = 1 grid
     # that the steps after the tracer run on
     sec = None
@@ -700,31 +735,15 @@ def run_ours(args, rank, world, local):
         i1 = next((i for i, w in enumerate(c2["ws"]) if w.tau550 == 1.0), 0)
 
     # the dust-temperature update (Eq. 16) on the 256 x 128 x 256 grids, fed by their
-    # a_rad (timed on its own, 8 bytes per cell against HBM)
+    # a_rad (timed on its own, 8 bytes per cell against HBM); beside it the same on the
+    # 512 x 256 x 512 grids (measured before they were freed)
     temp = None
     if rank == 0 and c2:
         for i, tr in enumerate(c2["tracers"]):
             tr.irradiate(c2["rho"][i], c2["td"][i], c2["q"][i], c2["a"][i])
-        t_out = [torch.empty(w.grid.shape, dtype=torch.float32, device="cuda") for w in c2["ws"]]
-        for i, tr in enumerate(c2["tracers"]):
-            tr.dust_temperature(c2["a"][i], None, t_out[i])
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            for i, tr in enumerate(c2["tracers"]):
-                tr.dust_temperature(c2["a"][i], None, t_out[i])
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t_ms = e0.elapsed_time(e1) / (args.steps * len(c2["ws"]))
-        ncell = c2["ws"][0].grid.ncells
-        temp = {"workload": f"disk3d {NR}x{NTH}x{NPH}, a_rad of the tracer, "
-                            f"tau550 in {{{','.join(f'{w.tau550:g}' for w in c2['ws'])}}}",
-                "ms_per_grid": t_ms, "cells_per_s": ncell / (t_ms * 1e-3),
-                "achieved_gbs": 8.0 * ncell / (t_ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm,
-                "frac_of_hbm": 8.0 * ncell / (t_ms * 1e-3) / 1e9 / hbm,
-                "median_t_k": float(t_out[i1].median())}
-        del t_out
+        temp = time_dust_temperature(c2, args.steps, stream, hbm, i1)
+        if temp_c3 is not None:
+            temp["on_512x256x512"] = temp_c3
 
     # the tracer with temperature-dependent tables (24 temperatures) on the tau = 1 grid:
     # the synthetic table (one species whose abundance depends on T: it separates, the
