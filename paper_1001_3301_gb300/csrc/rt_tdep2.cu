@@ -27,13 +27,39 @@ struct Rank2Tab {
 
 // Bins [i0, i1) of one class for the lane's cells. Zero-density dust cells carry
 // (b_1, b_2) in place of their (zero) column steps, so y = -kappa_i(T) log2 e there:
-// their a_rad limit sums g kappa_i = -g y ln 2 (a02, rare).
-template <int CLASS, int C>
+// their a_rad limit sums g kappa_i = -g y ln 2 (a02; ZERO: the warp holds such a cell).
+// Class 1 (one Taylor term, 1 - 2^y = p0 y) in the moment form: with y = k1 d1 + k2 d2,
+// sum_i g_i p0 y_i = p0 (d1 sum_i g_i k1_i + d2 sum_i g_i k2_i), two FMAs per (cell, bin).
+template <int CLASS, int C, bool ZERO>
 __device__ __forceinline__ void rank2_range(int i0, int i1, const float *s_lf, const float4 *s_ab,
                                             const float2 (&n1)[C / 2], const float2 (&n2)[C / 2],
                                             const float2 (&d1)[C / 2], const float2 (&d2)[C / 2],
-                                            float2 (&a2)[C / 2], float2 (&a02)[C / 2], bool any_zero)
+                                            float2 (&a2)[C / 2], float2 (&a02)[C / 2])
 {
+    if constexpr (CLASS == 1) {
+        if (i0 >= i1) return;  // warp-uniform
+        float2 m1[C / 2], m2[C / 2];
+#pragma unroll
+        for (int m = 0; m < C / 2; ++m) m1[m] = m2[m] = f2(0.0f);
+#pragma unroll 2
+        for (int i = i0; i < i1; ++i) {
+            const float4 e = s_ab[i];
+            const float2 k1 = f2(e.x), k2 = f2(e.y), lf = f2(s_lf[i]);
+#pragma unroll
+            for (int m = 0; m < C / 2; ++m) {
+                const float2 g = ex2_approx2(__ffma2_rn(k1, n1[m], __ffma2_rn(k2, n2[m], lf)));
+                m1[m] = __ffma2_rn(g, k1, m1[m]);
+                m2[m] = __ffma2_rn(g, k2, m2[m]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < C / 2; ++m) {
+            const float2 gy = __ffma2_rn(d1[m], m1[m], __fmul2_rn(d2[m], m2[m]));  // sum_i g_i y_i
+            a2[m] = __ffma2_rn(f2((float)taylor_coeff(0)), gy, a2[m]);
+            if constexpr (ZERO) a02[m] = __fadd2_rn(a02[m], gy);
+        }
+        return;
+    }
 #pragma unroll(CLASS <= 2 ? 2 : 1)
     for (int i = i0; i < i1; ++i) {
         const float4 e = s_ab[i];
@@ -43,9 +69,7 @@ __device__ __forceinline__ void rank2_range(int i0, int i1, const float *s_lf, c
             const float2 g = ex2_approx2(__ffma2_rn(k1, n1[m], __ffma2_rn(k2, n2[m], lf)));
             const float2 y = __ffma2_rn(k1, d1[m], __fmul2_rn(k2, d2[m]));  // -dtau log2 e
             float2 om;                                                       // 1 - 2^y
-            if constexpr (CLASS == 1) {
-                om = __fmul2_rn(f2((float)taylor_coeff(0)), y);
-            } else if constexpr (CLASS <= 5) {
+            if constexpr (CLASS <= 5) {
                 om = taylor_fraction<CLASS>(y);
             } else {
                 // the smaller of the 5-term series and 1 - ex2(y) + 2^-22, as in bin_range
@@ -54,9 +78,23 @@ __device__ __forceinline__ void rank2_range(int i0, int i1, const float *s_lf, c
                 om = make_float2(fminf(small.x, big.x), fminf(small.y, big.y));
             }
             a2[m] = __ffma2_rn(g, om, a2[m]);
-            if (any_zero) a02[m] = __ffma2_rn(g, y, a02[m]);
+            if constexpr (ZERO) a02[m] = __ffma2_rn(g, y, a02[m]);
         }
     }
+}
+
+// every class range of one warp
+template <int C, bool ZERO>
+__device__ __forceinline__ void rank2_ranges(const BinClasses &bc, int na, const float *s_lf, const float4 *s_ab,
+                                             const float2 (&n1)[C / 2], const float2 (&n2)[C / 2],
+                                             const float2 (&d1)[C / 2], const float2 (&d2)[C / 2],
+                                             float2 (&a2)[C / 2], float2 (&a02)[C / 2])
+{
+    rank2_range<1, C, ZERO>(0, bc.b1, s_lf, s_ab, n1, n2, d1, d2, a2, a02);
+    rank2_range<2, C, ZERO>(bc.b1, bc.b2, s_lf, s_ab, n1, n2, d1, d2, a2, a02);
+    rank2_range<3, C, ZERO>(bc.b2, bc.b3, s_lf, s_ab, n1, n2, d1, d2, a2, a02);
+    rank2_range<5, C, ZERO>(bc.b3, bc.b5, s_lf, s_ab, n1, n2, d1, d2, a2, a02);
+    rank2_range<6, C, ZERO>(bc.b5, na, s_lf, s_ab, n1, n2, d1, d2, a2, a02);
 }
 
 template <int C, int W, int MINB>
@@ -202,11 +240,8 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray_tdep2(const TraceArgs p, c
         }
 
         const BinClasses bc = classify_bins(s_nu, na, lane, dmax, 0.0f);
-        rank2_range<1, C>(0, bc.b1, s_lf, s_ab, n1, n2, d1, d2, acc, acc0, any_zero);
-        rank2_range<2, C>(bc.b1, bc.b2, s_lf, s_ab, n1, n2, d1, d2, acc, acc0, any_zero);
-        rank2_range<3, C>(bc.b2, bc.b3, s_lf, s_ab, n1, n2, d1, d2, acc, acc0, any_zero);
-        rank2_range<5, C>(bc.b3, bc.b5, s_lf, s_ab, n1, n2, d1, d2, acc, acc0, any_zero);
-        rank2_range<6, C>(bc.b5, na, s_lf, s_ab, n1, n2, d1, d2, acc, acc0, any_zero);
+        if (any_zero) rank2_ranges<C, true>(bc, na, s_lf, s_ab, n1, n2, d1, d2, acc, acc0);
+        else rank2_ranges<C, false>(bc, na, s_lf, s_ab, n1, n2, d1, d2, acc, acc0);
 
         // the flux leaving the ray, bins spread over the lanes (Eq. 33)
         float esc = 0.0f;
