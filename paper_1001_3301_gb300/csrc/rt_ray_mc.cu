@@ -22,6 +22,7 @@ struct ChunkEntry {
 #define RT_RAYC(P, C, W, MB) {P, C, W, MB, &launch_ray_mc<C, W, P, MB>}
 const ChunkEntry kRayShapesMC[] = {
     RT_RAYC(RT_FP32_KAHAN, 8, 4, 6),  RT_RAYC(RT_FP32_KAHAN, 16, 4, 3), RT_RAYC(RT_FP32_KAHAN, 16, 4, 4),
+    RT_RAYC(RT_FP32_KAHAN, 16, 4, 5),
     RT_RAYC(RT_FP32_PLAIN, 8, 4, 6),  RT_RAYC(RT_FP32_PLAIN, 16, 4, 4),
 };
 #undef RT_RAYC
