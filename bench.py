@@ -46,7 +46,7 @@ NNU = 79
 # tracer, flux-limited diffusion) and of the secondary tracer object
 NR, NTH, NPH = 256, 128, 256
 # rt_opacity_table_kind values
-TABLE_KINDS = ("nu", "nu_t_separable", "nu_t", "nu_t_rank2")
+TABLE_KINDS = ("nu", "nu_t_separable", "nu_t", "nu_t_rank2", "nu_t_low_rank")
 # tracer kernels (RT_KERNEL_*)
 KERNEL_KINDS = ("tile", "ray", "ray_chunked")
 
@@ -747,8 +747,8 @@ def run_ours(args, rank, world, local):
 
     # the tracer with temperature-dependent tables (24 temperatures) on the tau = 1 grid:
     # the synthetic table (one species whose abundance depends on T: it separates, the
-    # one-column tracer with a per-cell column weight), a two-species table (rank two:
-    # two columns per ray) and a three-species one (per-bin scans)
+    # one-column tracer with a per-cell column weight), two- to four-species tables (rank
+    # two to four: that many columns per ray) and a full-rank one (per-bin scans)
     tdep = None
     if rank == 0 and c2:
         from paper_1001_3301_gb300 import Tracer
@@ -759,7 +759,8 @@ def run_ours(args, rank, world, local):
         units = w1.grid.ncells * len(w1.nu)
         tdep = {"workload": f"disk3d {NR}x{NTH}x{NPH}, {NNU} bins x 24 temperatures, tau550 = {w1.tau550:g}"}
         for name, table in (("separable", synth.kappa_synth_t), ("two_species", synth.kappa_synth_t2),
-                            ("three_species", synth.kappa_synth_t3)):
+                            ("three_species", synth.kappa_synth_t3), ("four_species", synth.kappa_synth_t4),
+                            ("full_rank", synth.kappa_synth_t_full)):
             trt = Tracer.from_grid(w1.grid)
             trt.set_opacity_table_t(w1.nu, tg, table(w1.nu, tg), w1.t_sub)
             trt.set_star(w1.t_star, w1.r_star)

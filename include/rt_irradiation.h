@@ -124,7 +124,10 @@ int rt_set_opacity_table(rt_ctx *ctx, int n_nu, const double *nu_mid, const doub
  * 512 cells). A table of rank two with non-negative factors, every entry a
  * non-negative combination of two of the table's own columns to 1e-10 of itself
  * (two species whose abundances depend on T), is traced with two columns per ray
- * (kappa_i(T) = A_i1 b_1(T) + A_i2 b_2(T); FP32 precisions, nr <= 1024).
+ * (kappa_i(T) = A_i1 b_1(T) + A_i2 b_2(T); FP32 precisions, nr <= 1024). A table of
+ * rank three or four (three or four species), whose leading singular vectors reproduce
+ * every entry to 1e-10 of its row's largest value, is traced the same way with that
+ * many columns (factors of either sign).
  * rt_opacity_table_kind reports which kernel serves the table. The
  * temperature-independent entry rt_set_opacity_table switches back. Not
  * available to the multi-grid batch or the learned surrogate (their calls fail
@@ -142,12 +145,14 @@ int rt_set_star(rt_ctx *ctx, double t_star, double r_star);
 /* rt_opacity_table_kind -- how the configured table is traced: RT_TABLE_NU (kappa per
  * bin, one column for every bin), RT_TABLE_NU_T_SEPARABLE (a temperature-dependent
  * table that separates: the same single column, weighted per cell by b(T)),
- * RT_TABLE_NU_T_RANK2 (a table of rank two: two columns per ray), RT_TABLE_NU_T
+ * RT_TABLE_NU_T_RANK2 (a table of rank two: two columns per ray),
+ * RT_TABLE_NU_T_LOW_RANK (rank three or four: that many columns per ray), RT_TABLE_NU_T
  * (one scan per bin). Errors: RT_ERR_INVALID_ARG, RT_ERR_NOT_CONFIGURED. */
 #define RT_TABLE_NU             0
 #define RT_TABLE_NU_T_SEPARABLE 1
 #define RT_TABLE_NU_T           2
 #define RT_TABLE_NU_T_RANK2     3
+#define RT_TABLE_NU_T_LOW_RANK  4
 int rt_opacity_table_kind(const rt_ctx *ctx, int *kind);
 
 /* rt_irradiate -- trace every ray of the grid (Eqs. 17-20, 27-36).

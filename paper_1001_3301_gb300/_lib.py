@@ -32,6 +32,7 @@ RT_TABLE_NU = 0
 RT_TABLE_NU_T_SEPARABLE = 1
 RT_TABLE_NU_T = 2
 RT_TABLE_NU_T_RANK2 = 3
+RT_TABLE_NU_T_LOW_RANK = 4
 RT_BATCH_MAX = 256
 
 PRECISIONS = {"fp32_kahan": RT_FP32_KAHAN, "fp32_plain": RT_FP32_PLAIN, "fp64": RT_FP64}

@@ -66,10 +66,10 @@ struct rt_ctx {
     bool tw_sep = false;
     float *tw_t_d = nullptr;
     float4 *tw_b_d = nullptr;
-    // a table of rank two, kappa_i(T_j) = A_i1 B_1j + A_i2 B_2j with A, B >= 0: the
-    // two-column kernel of rt_tdep2.cu (A in FP64 per bin, sorted (A, nk) per bin, and
-    // (B_1j, B_1,j+1, B_2j, B_2,j+1) per interval)
-    bool r2 = false;
+    // a table of low rank rk (2-4), kappa_i(T_j) = sum_r A_ir B_rj: the rk-column kernel
+    // of rt_tdep2.cu (A in FP64 per bin, 4 wide; the sorted -A log2 e per bin; B per
+    // grid point); 0: none found
+    int rk = 0;
     double *fac_a_d = nullptr;
     float4 *r2_ab = nullptr, *r2_bw = nullptr;
     // lookup-table comparator (rt_lut.cu): table, reference opacity, tolerance and the
@@ -157,26 +157,27 @@ bool use_tw(const rt_ctx *c)
     return rt::ray_shapes_tw(c->precision, c->nr, s, 16) > 0;
 }
 
-// A table of rank two goes through the two-column kernel of rt_tdep2.cu (FP32 modes).
+// A table of low rank goes through the rk-column kernel of rt_tdep2.cu (FP32 modes).
 bool use_r2(const rt_ctx *c)
 {
-    if (c->n_t <= 0 || !c->r2 || use_tw(c) || c->precision == RT_FP64) return false;
+    if (c->n_t <= 0 || c->rk < 2 || use_tw(c) || c->precision == RT_FP64) return false;
     Shape s[16];
-    return rt::tdep2_shapes(c->nr, s, 16) > 0;
+    return rt::tdep2_shapes(c->rk, c->nr, s, 16) > 0;
 }
 
 int table_kind(const rt_ctx *c)
 {
     if (c->n_t <= 0) return RT_TABLE_NU;
     if (use_tw(c)) return RT_TABLE_NU_T_SEPARABLE;
-    return use_r2(c) ? RT_TABLE_NU_T_RANK2 : RT_TABLE_NU_T;
+    if (!use_r2(c)) return RT_TABLE_NU_T;
+    return c->rk == 2 ? RT_TABLE_NU_T_RANK2 : RT_TABLE_NU_T_LOW_RANK;
 }
 
 // every compiled shape that applies to this context: tile shapes, then ray shapes
 int all_shapes(const rt_ctx *c, Shape *out, int max_out)
 {
     if (c->n_t > 0) return use_tw(c) ? rt::ray_shapes_tw(c->precision, c->nr, out, max_out)
-                                     : use_r2(c) ? rt::tdep2_shapes(c->nr, out, max_out)
+                                     : use_r2(c) ? rt::tdep2_shapes(c->rk, c->nr, out, max_out)
                                                  : rt::tdep_shapes(c->nr, out, max_out);
     int n = rt::trace_shapes(c->precision, out, max_out);
     if (c->precision != RT_FP64) {
@@ -191,7 +192,7 @@ Shape default_shape(const rt_ctx *c)
     const bool tw = use_tw(c);
     if (c->n_t > 0 && !tw) {  // temperature-dependent table: the fewest cells per lane that hold a ray
         Shape ts[16];
-        const int n = use_r2(c) ? rt::tdep2_shapes(c->nr, ts, 16) : rt::tdep_shapes(c->nr, ts, 16);
+        const int n = use_r2(c) ? rt::tdep2_shapes(c->rk, c->nr, ts, 16) : rt::tdep_shapes(c->nr, ts, 16);
         int bi = -1;
         for (int i = 0; i < n; ++i)
             if (bi < 0 || ts[i].cells_per_lane < ts[bi].cells_per_lane ||
@@ -256,7 +257,7 @@ int finalize(rt_ctx *c)
         e = rt::launch_build_tdep(c->sc_h.n_active, c->sc_h.nnu_pad, c->n_t, c->kappa_t_d, c->order_d, c->kt2,
                                   c->stream);
         if (e != cudaSuccess) return cuda_fail(c, "build temperature table", e);
-        if (c->r2) {
+        if (c->rk >= 2) {
             e = rt::launch_build_rank2(c->sc_h.n_active, c->sc_h.nnu_pad, c->fac_a_d, c->order_d, c->r2_ab,
                                        c->stream);
             if (e != cudaSuccess) return cuda_fail(c, "build rank-two table", e);
@@ -363,7 +364,7 @@ int trace_range(rt_ctx *c, const float *rho, const float *td, float *q, float *a
         unsigned grid = 0;
         cudaError_t e;
         if (c->n_t > 0 && !tw)
-            e = use_r2(c) ? rt::launch_tdep2(s, args, c->r2_ab, c->r2_bw, c->tg32, c->n_t, stream, &grid)
+            e = use_r2(c) ? rt::launch_tdep2(c->rk, s, args, c->r2_ab, c->r2_bw, c->tg32, c->n_t, stream, &grid)
                           : rt::launch_tdep(s, args, c->kt2, c->tg32, c->n_t, stream, &grid);
         else
             e = rt::launch_trace(c->precision, s, args, (unsigned)nt, stream, &grid);
@@ -616,7 +617,7 @@ int rt_set_opacity_table(rt_ctx *ctx, int n_nu, const double *nu_mid, const doub
     ctx->kappa_bf16 = kappa_bf16 ? 1 : 0;
     ctx->n_t = 0;
     ctx->tw_sep = false;
-    ctx->r2 = false;
+    ctx->rk = 0;
     ctx->tgrid_h.clear();
     ctx->kappa_t_h.clear();
     ctx->nu_h.assign(nu_mid, nu_mid + n_nu);
@@ -712,6 +713,75 @@ bool rank_two(const double *kappa, int n_nu, int n_t, std::vector<double> &a, st
     return true;
 }
 
+// Is the table [n_nu][n_t] of rank R (3 or 4)? Its leading R right singular vectors v_r
+// (one-sided Jacobi on the columns of K, FP64, which keeps the small singular values'
+// vectors accurate) give B = V^T and A = K V, so that
+//   kappa[i][j] = sum_r a[i][r] b[r][j]  (a: [n_nu][4], b: [4][n_t], unused rows 0).
+// The first vector of a non-negative table is non-negative; the others carry either
+// sign. Accepted when every entry is reproduced to 1e-10 of its row's largest.
+bool low_rank(const double *kappa, int n_nu, int n_t, int R, std::vector<double> &a, std::vector<double> &b)
+{
+    if (R > n_t) return false;
+    std::vector<double> u(kappa, kappa + (size_t)n_nu * n_t), v((size_t)n_t * n_t, 0.0);
+    for (int p = 0; p < n_t; ++p) v[(size_t)p * n_t + p] = 1.0;
+    auto U = [&](int i, int p) -> double & { return u[(size_t)i * n_t + p]; };
+    auto V = [&](int k, int p) -> double & { return v[(size_t)k * n_t + p]; };
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        bool rotated = false;
+        for (int p = 0; p < n_t; ++p)
+            for (int q = p + 1; q < n_t; ++q) {
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int i = 0; i < n_nu; ++i) {
+                    al += U(i, p) * U(i, p);
+                    be += U(i, q) * U(i, q);
+                    ga += U(i, p) * U(i, q);
+                }
+                if (!(std::fabs(ga) > 1e-15 * std::sqrt(al * be))) continue;
+                rotated = true;
+                const double ze = (be - al) / (2.0 * ga);
+                const double t = (ze >= 0.0 ? 1.0 : -1.0) / (std::fabs(ze) + std::sqrt(1.0 + ze * ze));
+                const double c = 1.0 / std::sqrt(1.0 + t * t), sn = c * t;
+                for (int i = 0; i < n_nu; ++i) {
+                    const double up = U(i, p), uq = U(i, q);
+                    U(i, p) = c * up - sn * uq;
+                    U(i, q) = sn * up + c * uq;
+                }
+                for (int k = 0; k < n_t; ++k) {
+                    const double vp = V(k, p), vq = V(k, q);
+                    V(k, p) = c * vp - sn * vq;
+                    V(k, q) = sn * vp + c * vq;
+                }
+            }
+        if (!rotated) break;
+    }
+    std::vector<double> sig(n_t, 0.0);
+    for (int p = 0; p < n_t; ++p)
+        for (int i = 0; i < n_nu; ++i) sig[p] += U(i, p) * U(i, p);
+    std::vector<int> idx(n_t);
+    for (int p = 0; p < n_t; ++p) idx[p] = p;
+    std::sort(idx.begin(), idx.end(), [&](int x, int y) { return sig[x] > sig[y]; });
+    a.assign((size_t)4 * n_nu, 0.0);
+    b.assign((size_t)4 * n_t, 0.0);
+    for (int r = 0; r < R; ++r) {
+        const int e = idx[r];
+        double sum = 0.0;
+        for (int k = 0; k < n_t; ++k) sum += V(k, e);
+        const double sg = sum < 0.0 ? -1.0 : 1.0;
+        for (int k = 0; k < n_t; ++k) b[(size_t)r * n_t + k] = sg * V(k, e);
+        for (int i = 0; i < n_nu; ++i) a[(size_t)4 * i + r] = sg * U(i, e);  // (K V)_ie
+    }
+    for (int i = 0; i < n_nu; ++i) {
+        double rowmax = 0.0;
+        for (int j = 0; j < n_t; ++j) rowmax = std::max(rowmax, std::fabs(kappa[(size_t)i * n_t + j]));
+        for (int j = 0; j < n_t; ++j) {
+            double want = 0.0;
+            for (int r = 0; r < R; ++r) want += a[(size_t)4 * i + r] * b[(size_t)r * n_t + j];
+            if (!(std::fabs(kappa[(size_t)i * n_t + j] - want) <= 1e-10 * rowmax)) return false;
+        }
+    }
+    return true;
+}
+
 }  // namespace
 
 int rt_set_opacity_table_t(rt_ctx *ctx, int n_nu, const double *nu_mid, int n_t, const double *t_grid,
@@ -788,29 +858,46 @@ int rt_set_opacity_table_t(rt_ctx *ctx, int n_nu, const double *nu_mid, int n_t,
         RT_CK(ctx, cudaMemcpyAsync(ctx->tw_b_d, tw_b, sizeof(tw_b), cudaMemcpyHostToDevice, ctx->stream));
     }
     ctx->tw_sep = sep;
-    // not separable: is it of rank two?
-    std::vector<double> fa, fb;
-    const bool r2 = !sep && rank_two(kappa_t, n_nu, n_t, fa, fb);
-    if (r2) {
+    // not separable: is it of rank two (with non-negative factors), else of rank 3 or 4?
+    std::vector<double> fa, fb, f4(4 * (size_t)n_nu, 0.0), b4(4 * (size_t)n_t, 0.0);
+    int rk = 0;
+    if (!sep) {
+        if (rank_two(kappa_t, n_nu, n_t, fa, fb)) {
+            rk = 2;
+            for (int i = 0; i < n_nu; ++i) {
+                f4[4 * (size_t)i] = fa[2 * (size_t)i];
+                f4[4 * (size_t)i + 1] = fa[2 * (size_t)i + 1];
+            }
+            for (int j = 0; j < n_t; ++j) {
+                b4[j] = fb[j];
+                b4[(size_t)n_t + j] = fb[(size_t)n_t + j];
+            }
+        } else {
+            for (int R = 3; R <= 4 && rk == 0; ++R)
+                if (low_rank(kappa_t, n_nu, n_t, R, f4, b4)) rk = R;
+        }
+    }
+    if (rk >= 2) {
         float4 bw[rt::kMaxTdepPoints];
         for (int j = 0; j < rt::kMaxTdepPoints; ++j) {
-            const int j0 = j < n_t ? j : n_t - 1, j1 = j + 1 < n_t ? j + 1 : n_t - 1;
-            bw[j] = make_float4((float)fb[j0], (float)fb[j1], (float)fb[n_t + j0], (float)fb[n_t + j1]);
+            const int jj = j < n_t ? j : n_t - 1;
+            bw[j] = make_float4((float)b4[jj], (float)b4[(size_t)n_t + jj], (float)b4[2 * (size_t)n_t + jj],
+                                (float)b4[3 * (size_t)n_t + jj]);
         }
         if (!ctx->fac_a_d) {
-            bool ok = dalloc(&ctx->fac_a_d, (size_t)2 * RT_MAX_NU) == cudaSuccess &&
+            bool ok = dalloc(&ctx->fac_a_d, (size_t)4 * RT_MAX_NU) == cudaSuccess &&
                       dalloc(&ctx->r2_ab, (size_t)RT_MAX_NU + rt::kNuPad) == cudaSuccess &&
                       dalloc(&ctx->r2_bw, rt::kMaxTdepPoints) == cudaSuccess;
             if (!ok) {
                 cudaGetLastError();
-                return fail(ctx, RT_ERR_NO_MEMORY, "cannot allocate the rank-two table");
+                return fail(ctx, RT_ERR_NO_MEMORY, "cannot allocate the low-rank table");
             }
         }
-        RT_CK(ctx, cudaMemcpyAsync(ctx->fac_a_d, fa.data(), sizeof(double) * fa.size(), cudaMemcpyHostToDevice,
+        RT_CK(ctx, cudaMemcpyAsync(ctx->fac_a_d, f4.data(), sizeof(double) * 4 * n_nu, cudaMemcpyHostToDevice,
                                    ctx->stream));
         RT_CK(ctx, cudaMemcpyAsync(ctx->r2_bw, bw, sizeof(bw), cudaMemcpyHostToDevice, ctx->stream));
     }
-    ctx->r2 = r2;
+    ctx->rk = rk;
     RT_CK(ctx, cudaMemcpyAsync(ctx->nu_mid, nu_mid, sizeof(double) * n_nu, cudaMemcpyHostToDevice, ctx->stream));
     RT_CK(ctx, cudaMemcpyAsync(ctx->kappa, kmax.data(), sizeof(double) * n_nu, cudaMemcpyHostToDevice, ctx->stream));
     RT_CK(ctx, cudaMemcpyAsync(ctx->kappa_t_d, kappa_t, sizeof(double) * n_nu * n_t, cudaMemcpyHostToDevice,

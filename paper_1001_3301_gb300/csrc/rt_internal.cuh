@@ -197,11 +197,11 @@ cudaError_t launch_tdep(Shape s, const TraceArgs &args, const float2 *kt2, const
                         cudaStream_t stream, unsigned *grid_out);
 cudaError_t launch_build_tdep(int n_active, int nnu_pad, int n_t, const double *kappa_t, const int *order,
                               float2 *kt2, cudaStream_t stream);
-// Tracer for kappa(nu, T) tables of rank two: two columns per ray (rt_tdep2.cu)
-int tdep2_shapes(int nr, Shape *out, int max_out);
-cudaError_t launch_tdep2(Shape s, const TraceArgs &args, const float4 *ab, const float4 *bw, const float *tg, int n_t,
-                         cudaStream_t stream, unsigned *grid_out);
-cudaError_t launch_build_rank2(int n_active, int nnu_pad, const double *fac_a, const int *order, float4 *ab,
+// Tracer for kappa(nu, T) tables of rank 2-4: that many columns per ray (rt_tdep2.cu)
+int tdep2_shapes(int rank, int nr, Shape *out, int max_out);
+cudaError_t launch_tdep2(int rank, Shape s, const TraceArgs &args, const float4 *kr, const float4 *bw, const float *tg,
+                         int n_t, cudaStream_t stream, unsigned *grid_out);
+cudaError_t launch_build_rank2(int n_active, int nnu_pad, const double *fac_a, const int *order, float4 *kr,
                                cudaStream_t stream);
 
 // A configured context's device tables, for the batch launcher (rt_api.cu).

@@ -164,7 +164,7 @@ class Tracer:
         return q_abs, a_rad, (Energy(e) if energy else None), (fb.value if stats else None)
 
     def table_kind(self) -> int:
-        """RT_TABLE_NU, RT_TABLE_NU_T_SEPARABLE, RT_TABLE_NU_T_RANK2 or RT_TABLE_NU_T: how the table is traced."""
+        """RT_TABLE_NU, RT_TABLE_NU_T_SEPARABLE, RT_TABLE_NU_T_RANK2, RT_TABLE_NU_T_LOW_RANK or RT_TABLE_NU_T: how the table is traced."""
         k = ctypes.c_int()
         check(lib.rt_opacity_table_kind(self._ctx, ctypes.byref(k)), self._ctx)
         return k.value

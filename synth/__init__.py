@@ -210,6 +210,30 @@ def kappa_synth_t3(nu: np.ndarray, tg: np.ndarray) -> np.ndarray:
     return kappa_synth_t2(nu, tg) + np.outer(co2, 1.0 - step)
 
 
+# a fourth species: CO-ice band at 4.67 micron (0.05 dex wide, 30 cm^2/g) whose carrier
+# evaporates near 25 K
+_CO_BANDS = ((C_CM_S / 4.67e-4, 30.0),)
+
+
+def kappa_synth_t4(nu: np.ndarray, tg: np.ndarray) -> np.ndarray:
+    """A kappa(nu, T) [n_nu][n_t] of rank four: the table of kappa_synth_t3 plus a
+    CO-ice band present below ~25 K (logistic step, 3 K wide)."""
+    nu = np.asarray(nu, dtype=np.float64)
+    step = 1.0 / (1.0 + np.exp(-(np.asarray(tg, dtype=np.float64) - 25.0) / 3.0))
+    lg = np.log10(nu)
+    co = np.zeros_like(nu)
+    for centre, amp in _CO_BANDS:
+        co = co + amp * np.exp(-0.5 * ((lg - math.log10(centre)) / 0.05) ** 2)
+    return kappa_synth_t3(nu, tg) + np.outer(co, 1.0 - step)
+
+
+def kappa_synth_t_full(nu: np.ndarray, tg: np.ndarray, seed: int = 0) -> np.ndarray:
+    """A kappa(nu, T) [n_nu][n_t] with no low-rank structure: kappa_synth(nu) times an
+    independent factor in [0.5, 1.5) per entry (full rank)."""
+    rng = np.random.default_rng(seed)
+    return kappa_synth(np.asarray(nu, dtype=np.float64))[:, None] * (0.5 + rng.random((len(nu), len(tg))))
+
+
 def rho0_for_tau550(tau550: float, kappa550: float | None = None) -> float:
     """Midplane normalisation: tau550 = int_{r_min}^{r_max} rho0 (r_d/r) kappa dr
     along z = 0, i.e. rho0 = tau550 / (kappa550 r_d ln(r_max/r_min))."""

@@ -1,7 +1,8 @@
 """The tracer with temperature-dependent opacity tables against the FP64 oracle: a
 table that separates, kappa_i(T) = kappa_i b(T) (the one-column tracer with each
-cell's column weighted by b(T)), a two-species table of rank two (two columns per
-ray) and a three-species one (per-bin scans of Eq. 19 with every cell's own kappa)."""
+cell's column weighted by b(T)), two-, three- and four-species tables of rank two to
+four (that many columns per ray) and a full-rank table (per-bin scans of Eq. 19 with
+every cell's own kappa)."""
 from __future__ import annotations
 
 import numpy as np
@@ -47,7 +48,8 @@ def _run(w, tg, kt, shape=None, precision="fp32_kahan", kind=None):
 
 
 TABLES = {"separable": synth.kappa_synth_t, "two-species": synth.kappa_synth_t2,
-          "three-species": synth.kappa_synth_t3}
+          "three-species": synth.kappa_synth_t3, "four-species": synth.kappa_synth_t4,
+          "full-rank": synth.kappa_synth_t_full}
 
 
 def _tg(n):
@@ -92,26 +94,45 @@ def _rank_two(kt):
     return bool(np.all(np.abs(kt - want) <= 1e-10 * np.maximum(np.abs(kt), np.abs(want))))
 
 
+def _low_rank(kt, r):
+    """The leading r right singular vectors reproduce every entry to 1e-10 of its row's
+    largest value."""
+    if r > kt.shape[1]:
+        return False
+    vr = np.linalg.svd(kt, full_matrices=False)[2][:r].T
+    want = (kt @ vr) @ vr.T
+    rowmax = np.abs(kt).max(axis=1, keepdims=True)
+    return bool(np.all(np.abs(kt - want) <= 1e-10 * rowmax))
+
+
 def _kind(kt, nr, precision="fp32_kahan"):
     """The path the library takes: the one-column tracer with the column weight where
     the table separates and the rays fit its shapes, else the two-column kernel where
-    the table is of rank two, else the per-bin scans (FP32 arithmetic in every path)."""
-    from paper_1001_3301_gb300._lib import RT_TABLE_NU_T, RT_TABLE_NU_T_RANK2, RT_TABLE_NU_T_SEPARABLE
+    the table is of rank two with non-negative factors, else the three- or four-column
+    kernel where it is of rank three or four, else the per-bin scans (FP32 arithmetic
+    in every path)."""
+    from paper_1001_3301_gb300._lib import (RT_TABLE_NU_T, RT_TABLE_NU_T_LOW_RANK, RT_TABLE_NU_T_RANK2,
+                                            RT_TABLE_NU_T_SEPARABLE)
     if precision == "fp64":
         return RT_TABLE_NU_T
     if _separates(kt):
         return RT_TABLE_NU_T_SEPARABLE if nr <= 512 else RT_TABLE_NU_T
-    return RT_TABLE_NU_T_RANK2 if _rank_two(kt) else RT_TABLE_NU_T
+    if _rank_two(kt):
+        return RT_TABLE_NU_T_RANK2
+    return RT_TABLE_NU_T_LOW_RANK if (_low_rank(kt, 3) or _low_rank(kt, 4)) else RT_TABLE_NU_T
 
 
 def test_synthetic_tables_take_their_kernels():
-    """The three synthetic tables on the bench's 79 bins: one per path."""
-    from paper_1001_3301_gb300._lib import RT_TABLE_NU_T, RT_TABLE_NU_T_RANK2, RT_TABLE_NU_T_SEPARABLE
+    """The synthetic tables on the bench's 79 bins: one per path."""
+    from paper_1001_3301_gb300._lib import (RT_TABLE_NU_T, RT_TABLE_NU_T_LOW_RANK, RT_TABLE_NU_T_RANK2,
+                                            RT_TABLE_NU_T_SEPARABLE)
     nu = synth.disk3d(8, 2, 2, n_nu=79, tau550=1.0, seed=1).nu
     tg = _tg(24)
     assert _kind(synth.kappa_synth_t(nu, tg), 256) == RT_TABLE_NU_T_SEPARABLE
     assert _kind(synth.kappa_synth_t2(nu, tg), 256) == RT_TABLE_NU_T_RANK2
-    assert _kind(synth.kappa_synth_t3(nu, tg), 256) == RT_TABLE_NU_T
+    assert _kind(synth.kappa_synth_t3(nu, tg), 256) == RT_TABLE_NU_T_LOW_RANK
+    assert _kind(synth.kappa_synth_t4(nu, tg), 256) == RT_TABLE_NU_T_LOW_RANK
+    assert _kind(synth.kappa_synth_t_full(nu, tg), 256) == RT_TABLE_NU_T
 
 
 @pytest.mark.parametrize("table", sorted(TABLES))
@@ -164,15 +185,17 @@ def test_separable_weight_edges(torch):
         assert hot.any() and np.all(q[hot] == 0.0) and np.all(a[hot] == 0.0)
 
 
-def test_rank_two_edges(torch):
-    """The two-species table through the two-column kernel with zero-density dust cells
-    (the rho -> 0 limit of a_rad, kappa_i(T) from both columns), cells hotter than the
-    sublimation temperature, temperatures beyond both ends of the grid, and a species
-    whose weight is zero above 400 K; both FP32 scans."""
+@pytest.mark.parametrize("table", ["two-species", "four-species"])
+def test_low_rank_edges(torch, table):
+    """The two- and four-species tables through the two- and four-column kernels with
+    zero-density dust cells (the rho -> 0 limit of a_rad, kappa_i(T) from every column),
+    cells hotter than the sublimation temperature, temperatures beyond both ends of the
+    grid, and species whose weight is zero above 400 K; both FP32 scans."""
+    from paper_1001_3301_gb300._lib import RT_TABLE_NU_T_LOW_RANK
     w = synth.disk3d(160, 12, 4, n_nu=48, tau550=30.0, seed=5)
-    tg = np.array([12.0, 60.0, 140.0, 160.0, 400.0, 900.0])
-    kt = synth.kappa_synth_t2(w.nu, tg)
-    kt[:, 4:] = np.outer(synth.kappa_synth(w.nu), [0.7, 0.7])   # the ice gone, silicate at 0.7
+    tg = np.array([12.0, 20.0, 60.0, 140.0, 160.0, 400.0, 900.0])
+    kt = TABLES[table](w.nu, tg)
+    kt[:, 5:] = np.outer(synth.kappa_synth(w.nu), [0.7, 0.7])   # the ices gone, silicate at 0.7
     rho = w.rho32().copy()
     td = w.tdust32().copy()
     rho.reshape(-1)[::11] = 0.0                   # zero density, dust present
@@ -183,15 +206,16 @@ def test_rank_two_edges(torch):
                                 w.t_sub, rho.astype(np.float64), td.astype(np.float64), nthreads=8)
     ww = synth.Workload(w.name, w.grid, w.nu, w.kappa, rho, td, tau550=w.tau550)
     from paper_1001_3301_gb300._lib import RT_TABLE_NU_T_RANK2
-    assert _kind(kt, 160) == RT_TABLE_NU_T_RANK2
+    kind = RT_TABLE_NU_T_RANK2 if table == "two-species" else RT_TABLE_NU_T_LOW_RANK
+    assert _kind(kt, 160) == kind
     for precision in ("fp32_kahan", "fp32_plain"):
-        q, a, e, shapes = _run(ww, tg, kt, precision=precision, kind=RT_TABLE_NU_T_RANK2)
-        _parity.assert_parity(ww, q, a, e, orc, label=f"rank two edges {precision}")
+        q, a, e, shapes = _run(ww, tg, kt, precision=precision, kind=kind)
+        _parity.assert_parity(ww, q, a, e, orc, label=f"{table} edges {precision}")
         zc = (rho == 0.0) & (td <= w.t_sub)
         assert zc.any() and np.all(q[zc] == 0.0) and np.all(a[zc] >= 0.0) and (a[zc] > 0.0).any()
         for shape in shapes:
             q, a, e, _ = _run(ww, tg, kt, shape=shape, precision=precision)
-            _parity.assert_parity(ww, q, a, e, orc, label=f"rank two edges {precision} {shape}")
+            _parity.assert_parity(ww, q, a, e, orc, label=f"{table} edges {precision} {shape}")
 
 
 def test_constant_table_matches_plain_tracer(torch):
