@@ -742,8 +742,8 @@ def run_ours(args, rank, world, local):
         for i, tr in enumerate(c2["tracers"]):
             tr.irradiate(c2["rho"][i], c2["td"][i], c2["q"][i], c2["a"][i])
         temp = time_dust_temperature(c2, args.steps, stream, hbm, i1)
-        if temp_c3 is not None:
-            temp["on_512x256x512"] = temp_c3
+    if temp_c3 is not None:
+        temp = dict(temp or {}, on_512x256x512=temp_c3)
 
     # the tracer with temperature-dependent tables (24 temperatures) on the tau = 1 grid:
     # the synthetic table (one species whose abundance depends on T: it separates, the
