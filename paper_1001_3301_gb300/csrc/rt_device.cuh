@@ -320,13 +320,14 @@ __device__ __forceinline__ BinClasses classify_bins(const float4 *s_nu, int n_ac
     BinClasses c{start, start, start, start, start};
     for (int c0 = start; c0 < n_active; c0 += 32) {
         const int i = c0 + lane;
-        const float ak = (i < n_active) ? -s_nu[i].x : INFINITY;
+        const bool in = i < n_active;  // bins past n_active never count, whatever the columns' sign
+        const float ak = in ? -s_nu[i].x : 0.0f;
         const float ym = ak * dmax, yn = ak * dmin;
-        c.b1 += __popc(__ballot_sync(0xffffffffu, ym < kYT1));
-        c.b2 += __popc(__ballot_sync(0xffffffffu, ym < kYT2));
-        c.b3 += __popc(__ballot_sync(0xffffffffu, ym < kYT3));
-        c.b5 += __popc(__ballot_sync(0xffffffffu, ym < kYSplit));
-        c.bb += __popc(__ballot_sync(0xffffffffu, yn < kYSplit));
+        c.b1 += __popc(__ballot_sync(0xffffffffu, in && ym < kYT1));
+        c.b2 += __popc(__ballot_sync(0xffffffffu, in && ym < kYT2));
+        c.b3 += __popc(__ballot_sync(0xffffffffu, in && ym < kYT3));
+        c.b5 += __popc(__ballot_sync(0xffffffffu, in && ym < kYSplit));
+        c.bb += __popc(__ballot_sync(0xffffffffu, in && yn < kYSplit));
     }
     c.bb = c.bb > c.b5 ? c.bb : c.b5;
     return c;
@@ -341,8 +342,9 @@ __device__ __forceinline__ int thin_count(const float4 *s_nu, int n_active, int 
     int bt = 0;
     for (int c0 = 0; c0 < n_active; c0 += 32) {
         const int i = c0 + lane;
-        const float ak = (i < n_active) ? -s_nu[i].x : INFINITY;
-        bt += __popc(__ballot_sync(0xffffffffu, ak * nmax <= kThinY));
+        const bool in = i < n_active;  // bins past n_active never count, whatever the column's sign
+        const float ak = in ? -s_nu[i].x : 0.0f;
+        bt += __popc(__ballot_sync(0xffffffffu, in && ak * nmax <= kThinY));
     }
     return bt;
 }
@@ -354,9 +356,10 @@ __device__ __forceinline__ void thin_counts(const float4 *s_nu, int n_active, in
     b1 = b2 = 0;
     for (int c0 = 0; c0 < n_active; c0 += 32) {
         const int i = c0 + lane;
-        const float ak = (i < n_active) ? -s_nu[i].x : INFINITY;
-        b1 += __popc(__ballot_sync(0xffffffffu, ak * n1 <= kThinY));
-        b2 += __popc(__ballot_sync(0xffffffffu, ak * n2 <= kThinY));
+        const bool in = i < n_active;
+        const float ak = in ? -s_nu[i].x : 0.0f;
+        b1 += __popc(__ballot_sync(0xffffffffu, in && ak * n1 <= kThinY));
+        b2 += __popc(__ballot_sync(0xffffffffu, in && ak * n2 <= kThinY));
     }
 }
 

@@ -240,6 +240,21 @@ def test_density_floor_zeros():
     _parity.assert_parity(w, q, a, e, orc)
 
 
+def test_density_floor_zeros_every_shape():
+    """The same limit on 200-cell rays in every compiled shape, the chunked ones
+    included (the zero-density cells of a chunk take the limit from the chunk's own
+    column in front of them)."""
+    from paper_1001_3301_gb300 import Tracer
+    w = synth.disk2d(200, 32, 16, tau550=100.0)
+    assert (w.rho32() == 0).any()
+    orc = _parity.oracle_for(w)
+    shapes = shapes_of(Tracer.from_grid(w.grid))
+    assert any(s[0] == 2 for s in shapes)
+    for shape in shapes:
+        q, a, e = _parity.run_gpu(w, "fp32_kahan", shape=shape)
+        _parity.assert_parity(w, q, a, e, orc, label=f"{shape}")
+
+
 def test_bf16_table():
     """kappa rounded to bfloat16 on the device equals the oracle run on the
     bfloat16-rounded table."""
@@ -313,6 +328,35 @@ def test_nonfinite_input_is_flagged():
     with pytest.raises(RtError):
         tr.irradiate(rho, t2, energy=True)
     tr.irradiate(rho, td, energy=True)  # clean again: the flag is per call
+    tr.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 8, 4, 6), (2, 8, 4, 6), (0, 8, 4, 6)])
+def test_nonfinite_input_is_flagged_in_every_kernel(shape):
+    """A bad density or temperature deep in the last chunk of a 200-cell ray is flagged
+    by the one-chunk, the chunked and the tile kernel alike."""
+    import torch
+    from paper_1001_3301_gb300 import Tracer
+    from paper_1001_3301_gb300._lib import RT_ERR_NONFINITE_INPUT, RtError
+    w = _w3(200, 4, 2, 8, tau=1.0)
+    tr = Tracer.from_grid(w.grid)
+    tr.set_opacity_table(w.nu, w.kappa, w.t_sub)
+    tr.set_star(w.t_star, w.r_star)
+    tr.set_tuning(*shape)
+    rho = torch.from_numpy(w.rho32()).cuda()
+    td = torch.from_numpy(w.tdust32()).cuda()
+    tr.irradiate(rho, td, energy=True)
+    for bad in (float("nan"), -1.0, float("inf")):
+        r2 = rho.clone()
+        r2.view(-1)[3 * 200 + 195] = bad
+        with pytest.raises(RtError) as ei:
+            tr.irradiate(r2, td, energy=True)
+        assert ei.value.status == RT_ERR_NONFINITE_INPUT
+    t2 = td.clone()
+    t2.view(-1)[5 * 200 + 199] = float("nan")
+    with pytest.raises(RtError):
+        tr.irradiate(rho, t2, energy=True)
+    tr.irradiate(rho, td, energy=True)
     tr.close()
 
 
