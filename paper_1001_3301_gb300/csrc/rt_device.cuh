@@ -317,17 +317,17 @@ __device__ __forceinline__ BinClasses classify_bins(const float4 *s_nu, int n_ac
                                                      float dmax, float dmin, int from = 0)
 {
     const int start = from & ~31;
+    // dmax >= 0 and dmin >= 0 at every caller, so padding lanes (ak = inf) never count
     BinClasses c{start, start, start, start, start};
     for (int c0 = start; c0 < n_active; c0 += 32) {
         const int i = c0 + lane;
-        const bool in = i < n_active;  // bins past n_active never count, whatever the columns' sign
-        const float ak = in ? -s_nu[i].x : 0.0f;
+        const float ak = (i < n_active) ? -s_nu[i].x : INFINITY;
         const float ym = ak * dmax, yn = ak * dmin;
-        c.b1 += __popc(__ballot_sync(0xffffffffu, in && ym < kYT1));
-        c.b2 += __popc(__ballot_sync(0xffffffffu, in && ym < kYT2));
-        c.b3 += __popc(__ballot_sync(0xffffffffu, in && ym < kYT3));
-        c.b5 += __popc(__ballot_sync(0xffffffffu, in && ym < kYSplit));
-        c.bb += __popc(__ballot_sync(0xffffffffu, in && yn < kYSplit));
+        c.b1 += __popc(__ballot_sync(0xffffffffu, ym < kYT1));
+        c.b2 += __popc(__ballot_sync(0xffffffffu, ym < kYT2));
+        c.b3 += __popc(__ballot_sync(0xffffffffu, ym < kYT3));
+        c.b5 += __popc(__ballot_sync(0xffffffffu, ym < kYSplit));
+        c.bb += __popc(__ballot_sync(0xffffffffu, yn < kYSplit));
     }
     c.bb = c.bb > c.b5 ? c.bb : c.b5;
     return c;
@@ -339,12 +339,15 @@ __device__ __forceinline__ BinClasses classify_bins(const float4 *s_nu, int n_ac
 constexpr float kThinY = (float)(kThinX * kLog2e);  // the bound in the units of -nk
 __device__ __forceinline__ int thin_count(const float4 *s_nu, int n_active, int lane, float nmax)
 {
+    // Padding lanes carry ak = inf and must never count: with a column of at least 0,
+    // inf * n is inf or NaN. A negative or NaN column (invalid input, flagged) is taken
+    // as 0 so that the count stays within n_active.
+    nmax = fmaxf(nmax, 0.0f);
     int bt = 0;
     for (int c0 = 0; c0 < n_active; c0 += 32) {
         const int i = c0 + lane;
-        const bool in = i < n_active;  // bins past n_active never count, whatever the column's sign
-        const float ak = in ? -s_nu[i].x : 0.0f;
-        bt += __popc(__ballot_sync(0xffffffffu, in && ak * nmax <= kThinY));
+        const float ak = (i < n_active) ? -s_nu[i].x : INFINITY;
+        bt += __popc(__ballot_sync(0xffffffffu, ak * nmax <= kThinY));
     }
     return bt;
 }
@@ -353,13 +356,14 @@ __device__ __forceinline__ int thin_count(const float4 *s_nu, int n_active, int 
 __device__ __forceinline__ void thin_counts(const float4 *s_nu, int n_active, int lane, float n1, float n2, int &b1,
                                             int &b2)
 {
+    n1 = fmaxf(n1, 0.0f);  // as in thin_count
+    n2 = fmaxf(n2, 0.0f);
     b1 = b2 = 0;
     for (int c0 = 0; c0 < n_active; c0 += 32) {
         const int i = c0 + lane;
-        const bool in = i < n_active;
-        const float ak = in ? -s_nu[i].x : 0.0f;
-        b1 += __popc(__ballot_sync(0xffffffffu, in && ak * n1 <= kThinY));
-        b2 += __popc(__ballot_sync(0xffffffffu, in && ak * n2 <= kThinY));
+        const float ak = (i < n_active) ? -s_nu[i].x : INFINITY;
+        b1 += __popc(__ballot_sync(0xffffffffu, ak * n1 <= kThinY));
+        b2 += __popc(__ballot_sync(0xffffffffu, ak * n2 <= kThinY));
     }
 }
 

@@ -226,12 +226,12 @@ __device__ __forceinline__ void group_sync(int id, int n)
 // (-nk_i) n <= 127, a prefix of the sorted bins (warp-uniform count).
 __device__ __forceinline__ int live_count(const float4 *s_nu, int n_active, int lane, float n)
 {
+    n = fmaxf(n, 0.0f);  // as in thin_count: padding lanes (ak = inf) never count
     int b = 0;
     for (int c0 = 0; c0 < n_active; c0 += 32) {
         const int i = c0 + lane;
-        const bool in = i < n_active;  // bins past n_active never count, whatever the column's sign
-        const float ak = in ? -s_nu[i].x : 0.0f;
-        b += __popc(__ballot_sync(0xffffffffu, in && ak * n <= 127.0f));
+        const float ak = (i < n_active) ? -s_nu[i].x : INFINITY;
+        b += __popc(__ballot_sync(0xffffffffu, ak * n <= 127.0f));
     }
     return b;
 }
