@@ -239,13 +239,15 @@ struct TempConsts {
 };
 
 // T of one cell (Eq. 16): a T^4 = E_R + a_rad / kappa_P(T); 0 where both sources vanish.
+// ER: an E_R field is given (without one, E_R = 0 and every cell takes the table)
+template <bool ER>
 __device__ __forceinline__ float cell_temperature(const TempArgs &p, const TempConsts &k, float ar, float er)
 {
     ar = fmaxf(ar, 0.0f);
-    er = fmaxf(er, 0.0f);
-    if (!(ar > 0.0f) && !(er > 0.0f)) return 0.0f;
+    if constexpr (ER) er = fmaxf(er, 0.0f);
+    if (!(ar > 0.0f) && (!ER || !(er > 0.0f))) return 0.0f;
     float L, dL, y;
-    if (!(er > 0.0f)) {
+    if (!ER || !(er > 0.0f)) {
         // X(y) = 4 y + L(y) = ln a_rad - ln a: T from the inverse table at v = lg2 a_rad.
         // The interval index from u = v 2^e - v_org, the offset in it from one FMA with
         // the exact integer v_org + k (so t keeps the full precision of v).
@@ -296,7 +298,9 @@ __device__ __forceinline__ float cell_temperature(const TempArgs &p, const TempC
 }
 
 // Four cells per thread and iteration, moved as 16-byte vectors where the fields allow
-// (p.vec): one load in flight per thread would leave HBM latency-bound.
+// (p.vec): one load in flight per thread would leave HBM latency-bound. ER: p.e_rad is
+// given (a separate instance, so the common E_R = 0 call carries none of its tests).
+template <bool ER>
 __global__ void __launch_bounds__(256) k_dust_temperature(const TempArgs p)
 {
     TempConsts k;
@@ -309,25 +313,39 @@ __global__ void __launch_bounds__(256) k_dust_temperature(const TempArgs p)
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long n4 = p.vec ? p.n / 4 : 0;
-    // the next quad's inputs are loaded while the current one is solved
+    // D quads in flight per thread: slot d holds the inputs of quad v + d stride, and is
+    // refilled with quad v + (d + D) stride before quad v + d stride is solved (one with
+    // an E_R field: its Newton solve needs the registers)
+    constexpr int D = ER ? 1 : 2;
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 an = tid < n4 ? __ldg(reinterpret_cast<const float4 *>(p.a_rad) + tid) : zero4;
-    float4 en = (tid < n4 && p.e_rad) ? __ldg(reinterpret_cast<const float4 *>(p.e_rad) + tid) : zero4;
-    for (long long v = tid; v < n4; v += stride) {
-        const float4 a4 = an, e4 = en;
-        if (v + stride < n4) {
-            an = __ldg(reinterpret_cast<const float4 *>(p.a_rad) + v + stride);
-            if (p.e_rad) en = __ldg(reinterpret_cast<const float4 *>(p.e_rad) + v + stride);
+    float4 an[D], en[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const long long v = tid + d * stride;
+        an[d] = v < n4 ? __ldg(reinterpret_cast<const float4 *>(p.a_rad) + v) : zero4;
+        en[d] = (ER && v < n4) ? __ldg(reinterpret_cast<const float4 *>(p.e_rad) + v) : zero4;
+    }
+    for (long long v0 = tid; v0 < n4; v0 += D * stride) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const long long v = v0 + d * stride;
+            if (v >= n4) break;
+            const float4 a4 = an[d], e4 = en[d];
+            const long long vn = v + D * stride;
+            if (vn < n4) {
+                an[d] = __ldg(reinterpret_cast<const float4 *>(p.a_rad) + vn);
+                if constexpr (ER) en[d] = __ldg(reinterpret_cast<const float4 *>(p.e_rad) + vn);
+            }
+            float4 t4;
+            t4.x = cell_temperature<ER>(p, k, a4.x, e4.x);
+            t4.y = cell_temperature<ER>(p, k, a4.y, e4.y);
+            t4.z = cell_temperature<ER>(p, k, a4.z, e4.z);
+            t4.w = cell_temperature<ER>(p, k, a4.w, e4.w);
+            reinterpret_cast<float4 *>(p.t_out)[v] = t4;
         }
-        float4 t4;
-        t4.x = cell_temperature(p, k, a4.x, e4.x);
-        t4.y = cell_temperature(p, k, a4.y, e4.y);
-        t4.z = cell_temperature(p, k, a4.z, e4.z);
-        t4.w = cell_temperature(p, k, a4.w, e4.w);
-        reinterpret_cast<float4 *>(p.t_out)[v] = t4;
     }
     for (long long c = 4 * n4 + tid; c < p.n; c += stride)
-        p.t_out[c] = cell_temperature(p, k, p.a_rad[c], p.e_rad ? p.e_rad[c] : 0.0f);
+        p.t_out[c] = cell_temperature<ER>(p, k, p.a_rad[c], ER ? p.e_rad[c] : 0.0f);
 }
 
 }  // namespace
@@ -454,7 +472,8 @@ int rt_dust_temperature(rt_ctx *ctx, const float *a_rad, const float *e_rad, flo
     long long blocks = (in.ncells / 4 + 255) / 256;
     if (blocks > 8LL * nsm) blocks = 8LL * nsm;
     if (blocks < 1) blocks = 1;
-    k_dust_temperature<<<(unsigned)blocks, 256, 0, in.stream>>>(p);
+    if (e_rad) k_dust_temperature<true><<<(unsigned)blocks, 256, 0, in.stream>>>(p);
+    else k_dust_temperature<false><<<(unsigned)blocks, 256, 0, in.stream>>>(p);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return ctx_fail(ctx, RT_ERR_CUDA, std::string("temperature kernel: ") + cudaGetErrorString(e));
     return RT_OK;
