@@ -7,22 +7,24 @@
 // then the attenuated flux (Eq. 17) and the absorbed fraction of the cell
 // (Eqs. 31-32, 36) per (cell, bin) as in the per-bin loop of rt_device.cuh.
 //
-// One warp per ray, lane l owns cells [l C, (l+1) C). Per bin: every cell's kappa
-// from the table (one 8-byte shared-memory read of the bracketing pair), the lane's
-// sum (C terms, plain FP32), a compensated warp scan of the lane sums, then a second
-// pass over the lane's cells carrying the exclusive prefix (no per-cell prefix is
-// stored). The per-cell arithmetic runs on pairs of cells in f32x2 registers.
+// One warp per ray, lane l owns cells [l C, (l+1) C). The bins go in pairs (2p, 2p + 1),
+// one f32x2 register per cell holding both: every cell's two kappa from the table (one
+// 16-byte shared-memory read of both rows' bracketing points), the lane's two sums (C
+// terms, plain FP32), one compensated warp scan of both (packed: half the scan
+// instructions per bin), then a second pass over the lane's cells carrying the
+// exclusive prefix (no per-cell prefix is stored).
 // The bins are ordered by their largest tabulated kappa; the Taylor classes of the
 // absorbed fraction (1, 2, 3, 5 terms) come from that largest kappa and the warp's
 // largest column, the remaining bins take the per-cell select between the 5-term
-// series and 1 - ex2 (kappa's smallest value need not follow the same order).
+// series and 1 - ex2 (kappa's smallest value need not follow the same order). A pair
+// takes the class of its upper bin, which holds for the lower one too.
 #include "rt_device.cuh"
 
 namespace rt {
 namespace {
 
 struct TdepTab {
-    const float2 *kt2;  // [nnu_pad][n_t] (kappa_j, kappa_{j+1}) of every sorted bin
+    const float2 *kt2;  // [nnu_pad][n_t] (kappa_j, kappa_{j+1}) of every sorted bin (global)
     const float *tg;    // [n_t] temperature grid (K)
     int n_t;
 };
@@ -91,7 +93,88 @@ __device__ __forceinline__ void tdep_range(int i0, int i1, const float *s_lf, co
     }
 }
 
-template <int C, int W, int MINB>
+// Bin pairs [p0, p1) of one class: scan, attenuation, absorption for the lane's cells,
+// one cell per f32x2 register pair holding the pair's two bins (packed FMA/ADD/MUL on the
+// opacity, the column, the exponent, the absorbed fraction). s_kt4[p n_t + j] =
+// (kappa_2p(T_j), kappa_2p+1(T_j), kappa_2p(T_j+1), kappa_2p+1(T_j+1)).
+template <int CLASS, int C>
+__device__ __forceinline__ void tdep_pairs(int p0, int p1, const float *s_lf, const float4 *s_kt4, int n_t,
+                                           const int (&jt)[C], const float (&wt)[C], const float (&wb)[C],
+                                           const Cells<float, C> &dc, Cells<float, C> &ac, Cells<float, C> &ac0,
+                                           bool any_zero, int lane, float &esc)
+{
+    const float2 nl2e = f2(-(float)kLog2e);
+    for (int pp = p0; pp < p1; ++pp) {
+        const float2 lf2 = make_float2(s_lf[2 * pp], s_lf[2 * pp + 1]);
+        const float4 *row = s_kt4 + pp * n_t;
+        auto kappa2 = [&](int j) {  // the pair's kappa in cell j
+            // kappa_j (T_{j+1} - T) / dT + kappa_{j+1} (T - T_j) / dT: two non-negative
+            // terms, no cancellation where the row falls towards zero
+            const float4 k = row[jt[j]];
+            return __ffma2_rn(make_float2(k.z, k.w), f2(wt[j]), __fmul2_rn(make_float2(k.x, k.y), f2(wb[j])));
+        };
+        float2 dt2[C];
+        float2 ls2 = f2(0.0f);  // the lane's two sums, C terms each (plain FP32)
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            dt2[j] = __fmul2_rn(kappa2(j), f2(dc.get(j)));
+            ls2 = __fadd2_rn(ls2, dt2[j]);
+        }
+        // compensated warp scan of both bins' lane sums (the ray-long sums): a Kahan pair
+        // per bin, the two bins side by side
+        float2 ih = ls2, il = f2(0.0f);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float2 vh = make_float2(__shfl_up_sync(0xffffffffu, ih.x, o), __shfl_up_sync(0xffffffffu, ih.y, o));
+            const float2 vl = make_float2(__shfl_up_sync(0xffffffffu, il.x, o), __shfl_up_sync(0xffffffffu, il.y, o));
+            if (lane >= o) {
+                // two_sum(vh, ih) exactly, then the low parts
+                const float2 sm = __fadd2_rn(vh, ih);
+                const float2 bb = __fadd2_rn(sm, __fmul2_rn(vh, f2(-1.0f)));
+                const float2 ea = __fadd2_rn(vh, __fmul2_rn(__fadd2_rn(sm, __fmul2_rn(bb, f2(-1.0f))), f2(-1.0f)));
+                const float2 eb = __fadd2_rn(ih, __fmul2_rn(bb, f2(-1.0f)));
+                il = __fadd2_rn(__fadd2_rn(il, vl), __fadd2_rn(ea, eb));
+                ih = sm;
+            }
+        }
+        // exclusive prefix: the inclusive one of the lane before
+        float2 bhi = make_float2(__shfl_up_sync(0xffffffffu, ih.x, 1), __shfl_up_sync(0xffffffffu, ih.y, 1));
+        float2 blo = make_float2(__shfl_up_sync(0xffffffffu, il.x, 1), __shfl_up_sync(0xffffffffu, il.y, 1));
+        if (lane == 0) bhi = blo = f2(0.0f);
+        if (lane == 31) {
+            const float2 tot = __fadd2_rn(ih, il);
+            const float2 ee = ex2_approx2(__ffma2_rn(nl2e, tot, lf2));
+            esc += ee.x + ee.y;
+        }
+        // the lane's exclusive prefix: the warp offset (hi + lo) plus a plain partial sum
+        float2 part = f2(0.0f);
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            const float2 tau = __fadd2_rn(bhi, __fadd2_rn(blo, part));
+            const float2 g = ex2_approx2(__ffma2_rn(nl2e, tau, lf2));
+            const float2 y = __fmul2_rn(nl2e, dt2[j]);  // -dtau log2(e)
+            float2 om;                                  // 1 - 2^y
+            if constexpr (CLASS <= 5) {
+                om = taylor_fraction<CLASS>(y);
+            } else {
+                const float2 big = __ffma2_rn(ex2_approx2(y), f2(-1.0f), f2(1.0f));
+                const float2 small = taylor_fraction<5>(y);
+                om = make_float2(y.x > -kYSplit ? small.x : big.x, y.y > -kYSplit ? small.y : big.y);
+            }
+            ac.set(j, fmaf(g.y, om.y, fmaf(g.x, om.x, ac.get(j))));
+            if (any_zero) {  // (rare: the kappa read again, not kept)
+                const float2 k2 = kappa2(j);
+                ac0.set(j, fmaf(g.y, k2.y, fmaf(g.x, k2.x, ac0.get(j))));
+            }
+            part = __fadd2_rn(part, dt2[j]);
+        }
+    }
+}
+
+// PAIRS: the bins in pairs (tdep_pairs; 2C more registers for both bins' column
+// increments), else one at a time (tdep_range), for the shapes whose register cap the
+// pair form overflows
+template <int C, int W, int MINB, bool PAIRS>
 __global__ void __launch_bounds__(W * 32, MINB) k_ray_tdep(const TraceArgs p, const TdepTab t)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -105,15 +188,25 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray_tdep(const TraceArgs p, co
     extern __shared__ __align__(16) unsigned char smem[];
     float4 *s_nu = reinterpret_cast<float4 *>(smem);                 // [nnu_pad] (nk_max, ., lf, .)
     float *s_lf = reinterpret_cast<float *>(s_nu + p.nnu_pad);        // [nnu_pad]
-    float2 *s_kt = reinterpret_cast<float2 *>(s_lf + p.nnu_pad + 2);  // [nnu_pad][n_t], 8-byte aligned
-    s_kt = reinterpret_cast<float2 *>((reinterpret_cast<size_t>(s_kt) + 7) & ~size_t(7));
+    // [nnu_pad][n_t] rows of (kappa_j, kappa_j+1), or [nnu_pad / 2][n_t] bin-pair rows of
+    // both bins' (kappa_j, kappa_j+1) (the same bytes); 16-byte aligned
+    float4 *s_kt4 = reinterpret_cast<float4 *>((reinterpret_cast<size_t>(s_lf + p.nnu_pad) + 15) & ~size_t(15));
+    float2 *s_kt = reinterpret_cast<float2 *>(s_kt4);
 
     for (int i = tid; i < p.nnu_pad; i += W * 32) {
         const NuEntry e = p.nu[i];
         s_nu[i] = make_float4(e.nk, e.nk, e.lf, e.lf);
         s_lf[i] = e.lf;
     }
-    for (int i = tid; i < p.nnu_pad * t.n_t; i += W * 32) s_kt[i] = t.kt2[i];
+    if constexpr (PAIRS) {
+        for (int i = tid; i < (p.nnu_pad / 2) * t.n_t; i += W * 32) {
+            const int pp = i / t.n_t, j = i - pp * t.n_t;
+            const float2 a = t.kt2[2 * pp * t.n_t + j], b = t.kt2[(2 * pp + 1) * t.n_t + j];
+            s_kt4[i] = make_float4(a.x, b.x, a.y, b.y);
+        }
+    } else {
+        for (int i = tid; i < p.nnu_pad * t.n_t; i += W * 32) s_kt[i] = t.kt2[i];
+    }
     for (int i = tid; i < t.n_t; i += W * 32) {
         s_tg[i] = t.tg[i];
         s_idt[i] = i + 1 < t.n_t ? 1.0f / (t.tg[i + 1] - t.tg[i]) : 0.0f;
@@ -169,11 +262,24 @@ __global__ void __launch_bounds__(W * 32, MINB) k_ray_tdep(const TraceArgs p, co
         const int na = p.n_active;
         const BinClasses bc = classify_bins(s_nu, na, lane, dmax, 0.0f);
         float esc = 0.0f;
-        tdep_range<1, C>(0, bc.b1, s_lf, s_kt, nt, jt, wt, wb, d.v, acc.v, acc0.v, any_zero, lane, esc);
-        tdep_range<2, C>(bc.b1, bc.b2, s_lf, s_kt, nt, jt, wt, wb, d.v, acc.v, acc0.v, any_zero, lane, esc);
-        tdep_range<3, C>(bc.b2, bc.b3, s_lf, s_kt, nt, jt, wt, wb, d.v, acc.v, acc0.v, any_zero, lane, esc);
-        tdep_range<5, C>(bc.b3, bc.b5, s_lf, s_kt, nt, jt, wt, wb, d.v, acc.v, acc0.v, any_zero, lane, esc);
-        tdep_range<6, C>(bc.b5, na, s_lf, s_kt, nt, jt, wt, wb, d.v, acc.v, acc0.v, any_zero, lane, esc);
+        if constexpr (PAIRS) {
+            // pair p (bins 2p, 2p + 1) belongs to the class of its upper bin: the pairs
+            // below a class boundary b are those with 2p + 1 < b; a last odd bin pairs with
+            // a padding bin (kappa 0, no flux: it adds nothing)
+            const int q1 = bc.b1 / 2, q2 = max(bc.b2 / 2, q1), q3 = max(bc.b3 / 2, q2), q5 = max(bc.b5 / 2, q3);
+            const int qn = (na + 1) / 2;
+            tdep_pairs<1, C>(0, q1, s_lf, s_kt4, nt, jt, wt, wb, d, acc, acc0, any_zero, lane, esc);
+            tdep_pairs<2, C>(q1, q2, s_lf, s_kt4, nt, jt, wt, wb, d, acc, acc0, any_zero, lane, esc);
+            tdep_pairs<3, C>(q2, q3, s_lf, s_kt4, nt, jt, wt, wb, d, acc, acc0, any_zero, lane, esc);
+            tdep_pairs<5, C>(q3, q5, s_lf, s_kt4, nt, jt, wt, wb, d, acc, acc0, any_zero, lane, esc);
+            tdep_pairs<6, C>(q5, qn, s_lf, s_kt4, nt, jt, wt, wb, d, acc, acc0, any_zero, lane, esc);
+        } else {
+            tdep_range<1, C>(0, bc.b1, s_lf, s_kt, nt, jt, wt, wb, d.v, acc.v, acc0.v, any_zero, lane, esc);
+            tdep_range<2, C>(bc.b1, bc.b2, s_lf, s_kt, nt, jt, wt, wb, d.v, acc.v, acc0.v, any_zero, lane, esc);
+            tdep_range<3, C>(bc.b2, bc.b3, s_lf, s_kt, nt, jt, wt, wb, d.v, acc.v, acc0.v, any_zero, lane, esc);
+            tdep_range<5, C>(bc.b3, bc.b5, s_lf, s_kt, nt, jt, wt, wb, d.v, acc.v, acc0.v, any_zero, lane, esc);
+            tdep_range<6, C>(bc.b5, na, s_lf, s_kt, nt, jt, wt, wb, d.v, acc.v, acc0.v, any_zero, lane, esc);
+        }
 
         const float w = __ldg(p.domega32 + ray);
         if (lane == 31) eesc.add(esc * w);
@@ -228,11 +334,11 @@ __global__ void k_build_tdep(int n_active, int nnu_pad, int n_t, const double *k
     kt2[idx] = make_float2((float)row[j], (float)row[j + 1 < n_t ? j + 1 : j]);
 }
 
-template <int C, int W, int MINB>
+template <int C, int W, int MINB, bool PAIRS>
 cudaError_t launch_tdep_shape(const TraceArgs &a, const TdepTab &t, cudaStream_t stream, unsigned *grid_out)
 {
-    const size_t smem = (size_t)a.nnu_pad * (16 + 4) + 8 + 16 + (size_t)a.nnu_pad * t.n_t * sizeof(float2);
-    auto kern = k_ray_tdep<C, W, MINB>;
+    const size_t smem = (size_t)a.nnu_pad * (16 + 4) + 16 + (size_t)(a.nnu_pad / 2) * t.n_t * sizeof(float4);
+    auto kern = k_ray_tdep<C, W, MINB, PAIRS>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -256,9 +362,11 @@ struct TdepEntry {
     int c, w, minb;
     cudaError_t (*fn)(const TraceArgs &, const TdepTab &, cudaStream_t, unsigned *);
 };
-#define RT_TD(C, W, MB) {C, W, MB, &launch_tdep_shape<C, W, MB>}
-const TdepEntry kTdepShapes[] = {RT_TD(2, 4, 8), RT_TD(4, 4, 8), RT_TD(8, 4, 6), RT_TD(8, 4, 4), RT_TD(16, 4, 3),
-                                 RT_TD(32, 4, 2)};
+// the bin-pair form where its registers fit the cap without more than a few bytes of spill
+#define RT_TD(C, W, MB, PR) {C, W, MB, &launch_tdep_shape<C, W, MB, PR>}
+const TdepEntry kTdepShapes[] = {RT_TD(2, 4, 8, true),  RT_TD(4, 4, 8, false),  RT_TD(4, 4, 6, true),
+                                 RT_TD(8, 4, 6, false), RT_TD(8, 4, 4, true),   RT_TD(16, 4, 3, false),
+                                 RT_TD(32, 4, 2, false)};
 #undef RT_TD
 
 }  // namespace
